@@ -1,0 +1,331 @@
+"""Pins of the CPU oracle against things other than itself (runs without a GPU).
+
+Each test ties one oracle routine to an independent fact: a library routine
+used as a special case, a closed form, an invariant the paper states, or brute
+force on tiny inputs.  The comment on each names the mistake it would catch.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+import workloads as W
+from oracle import dense as D
+from oracle import krylov as K
+from oracle import philox as PH
+from oracle import sketch as OS
+from oracle import truth as TR
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- Philox ----
+def _triton_randint4x(seed, offsets):
+    os.environ["TRITON_INTERPRET"] = "1"
+    triton = pytest.importorskip("triton")
+    import torch
+    import triton.language as tl
+
+    @triton.jit
+    def kern(out_ptr, off_ptr, seed, N: tl.constexpr):
+        i = tl.arange(0, N)
+        off = tl.load(off_ptr + i)
+        a, b, c, d = tl.randint4x(seed, off, 10)
+        tl.store(out_ptr + i * 4 + 0, a)
+        tl.store(out_ptr + i * 4 + 1, b)
+        tl.store(out_ptr + i * 4 + 2, c)
+        tl.store(out_ptr + i * 4 + 3, d)
+
+    N = len(offsets)
+    out = torch.zeros(4 * N, dtype=torch.int32)
+    off = torch.tensor(offsets, dtype=torch.int64)
+    kern[(1,)](out, off, seed, N)
+    return (out.numpy().astype(np.int64) & 0xFFFFFFFF).reshape(N, 4)
+
+
+def test_philox_matches_independent_implementation():
+    """Triton's Philox4x32-10 (counter (lo, hi, 0, 0) of a 64-bit offset, key
+    from the 64-bit seed) must agree word for word: catches a wrong multiplier,
+    Weyl constant, word order or key schedule."""
+    for seed in (0, 1, 0xDEADBEEF, 0x1234_5678_9ABC_DEF0):
+        offs = [0, 1, 2, 3, 12345, (1 << 32) + 5, (7 << 32) + 99, (63 << 32) + 4_000_000]
+        ref = _triton_randint4x(seed, offs)
+        c0 = np.array([o & 0xFFFFFFFF for o in offs], dtype=np.uint64)
+        c1 = np.array([o >> 32 for o in offs], dtype=np.uint64)
+        got = np.stack(PH.philox4x32_10(c0, c1, 0, 0, seed & 0xFFFFFFFF, seed >> 32), axis=1).astype(np.int64)
+        assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- sketch ----
+def test_sketch_columns_invariants():
+    """Eq. (3): zeta distinct rows per column, +-1/sqrt(zeta) entries, so every
+    column of S has norm exactly 1."""
+    for n, s, zeta in [(3000, 160, 8), (2000, 17, 4), (500, 40, 32), (400, 8, 8), (1000, 60, 1)]:
+        rows, signs = OS.sketch_columns(n, s, zeta, 99)
+        assert rows.shape == (n, zeta)
+        assert rows.min() >= 0 and rows.max() < s
+        assert all(len(set(r)) == zeta for r in rows)
+        assert set(np.unique(signs)) <= {-1.0, 1.0}
+        S = OS.SparseSign(n, s, zeta, 99).dense()
+        assert np.allclose(np.linalg.norm(S, axis=0), 1.0, atol=1e-15)
+    # subsets of columns reproduce the full generation (counter-based)
+    rows, signs = OS.sketch_columns(5000, 60, 8, 7)
+    r2, s2 = OS.sketch_columns(5000, 60, 8, 7, cols=np.arange(1000, 1200))
+    assert np.array_equal(rows[1000:1200], r2) and np.array_equal(signs[1000:1200], s2)
+
+
+def test_sketch_uniform_rows_and_balanced_signs():
+    """Rows uniform over [0, s) and Rademacher signs: chi-square and binomial
+    checks on 2e5 columns (catches a biased row map such as v % s without
+    rejection at large s, or a sign bit tied to the row)."""
+    n, s, zeta = 200_000, 1000, 1
+    rows, signs = OS.sketch_columns(n, s, zeta, 2024)
+    counts = np.bincount(rows.ravel(), minlength=s)
+    expected = n * zeta / s
+    chi2 = ((counts - expected) ** 2 / expected).sum()
+    # chi-square with s-1 dof: mean s-1, sd sqrt(2(s-1)); allow 5 sd
+    assert abs(chi2 - (s - 1)) < 5 * math.sqrt(2 * (s - 1))
+    frac_neg = np.mean(signs < 0)
+    assert abs(frac_neg - 0.5) < 5 * math.sqrt(0.25 / signs.size)
+    # sign independent of row parity
+    odd = rows.ravel() % 2 == 1
+    assert abs(np.mean(signs.ravel()[odd] < 0) - 0.5) < 5 * math.sqrt(0.25 / odd.sum())
+
+
+def test_sketch_is_an_embedding_in_expectation():
+    """Eq. (1): E ||S x||^2 = ||x||^2 over the random S; mean over 400 seeds
+    within 4 standard errors."""
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(300)
+    vals = [np.linalg.norm(OS.SparseSign(300, 40, 4, sd).apply(x)) ** 2 / np.dot(x, x) for sd in range(400)]
+    vals = np.array(vals)
+    assert abs(vals.mean() - 1.0) < 4 * vals.std() / math.sqrt(len(vals))
+
+
+def test_sketch_apply_matches_dense_product():
+    """S applied column-wise equals the dense S matrix product (catches a
+    missing 1/sqrt(zeta) or a sign flip in apply)."""
+    Sk = OS.SparseSign(700, 50, 8, 3)
+    V = np.random.default_rng(1).standard_normal((700, 3))
+    dense = np.zeros((50, 700))
+    for j in range(700):
+        for q in range(8):
+            dense[Sk.rows[j, q], j] += Sk.signs[j, q] / math.sqrt(8)
+    assert np.allclose(Sk.apply(V), dense @ V, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- dense -----
+def test_qr_positive_is_cholesky_factor():
+    """T with positive diagonal is unique: it equals the Cholesky factor of
+    U^T U, and Q T = U with orthonormal Q."""
+    rng = np.random.default_rng(2)
+    for s, c in [(60, 31), (160, 41), (20, 20), (5, 1)]:
+        U = rng.standard_normal((s, c)) * rng.uniform(0.1, 10, size=c)
+        Q, T = D.qr_positive(U)
+        assert np.allclose(Q @ T, U, atol=1e-12 * np.abs(U).max())
+        assert np.allclose(Q.T @ Q, np.eye(c), atol=1e-13)
+        assert np.all(np.diag(T) > 0) and np.allclose(np.tril(T, -1), 0)
+        L = np.linalg.cholesky(U.T @ U)
+        assert rel(T, L.T) < 1e-10
+
+
+@pytest.mark.parametrize("scale", [1e-3, 0.3, 4.0, 40.0, 400.0])
+def test_expm_matches_scipy(scale):
+    """Degree-13 Pade scaling and squaring against scipy's expm."""
+    rng = np.random.default_rng(int(scale * 1000) % 97)
+    A = rng.standard_normal((25, 25)) / 5.0 * scale
+    A = A - np.diag(np.full(25, 1.2 * scale))  # keep exp(A) of moderate size
+    assert rel(D.expm(A), sl.expm(A)) < 1e-12
+
+
+def test_expm_closed_forms():
+    """Rotation generator, a Jordan block, and exp(A) exp(-A) = I."""
+    th = 2.7
+    R = D.expm(np.array([[0.0, th], [-th, 0.0]]))
+    assert np.allclose(R, [[math.cos(th), math.sin(th)], [-math.sin(th), math.cos(th)]], atol=1e-15)
+    lam = -3.0
+    J = lam * np.eye(4) + np.diag(np.ones(3), 1)
+    E = D.expm(J)
+    ref = math.exp(lam) * np.array([[1, 1, 1 / 2, 1 / 6], [0, 1, 1, 1 / 2], [0, 0, 1, 1], [0, 0, 0, 1]])
+    assert np.allclose(E, ref, rtol=1e-14, atol=1e-16)
+    A = np.random.default_rng(5).standard_normal((12, 12))
+    assert np.allclose(D.expm(A) @ D.expm(-A), np.eye(12), atol=1e-12)
+
+
+def test_invsqrtm():
+    """Z^2 A = I, and agreement with the eigendecomposition for SPD A and with
+    scipy's sqrtm for a non-symmetric matrix with positive spectrum."""
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((30, 30))
+    S = B @ B.T + 1e-3 * np.eye(30)
+    lam, Q = np.linalg.eigh(S)
+    Z = D.invsqrtm(S)
+    assert rel(Z, Q @ np.diag(lam ** -0.5) @ Q.T) < 1e-10
+    N = np.eye(20) * 5 + rng.standard_normal((20, 20)) * 0.5
+    Z = D.invsqrtm(N)
+    assert rel(Z @ Z @ N, np.eye(20)) < 1e-12
+    assert rel(Z, np.linalg.inv(sl.sqrtm(N))) < 1e-11
+
+
+# ---------------------------------------------------------------- truth -----
+def test_kronecker_truth_matches_dense_exponential():
+    """exp(-tA) of the Kronecker-sum grid operator applied by mode products
+    equals the dense exponential of the assembled CSR matrix."""
+    for N, dim, beta, t in [(6, 3, (50.0, 50.0, 50.0), 1e-2), (9, 2, (0.0, 0.0), 1e-3), (5, 3, (20.0, 0.0, 0.0), 5e-3)]:
+        A = W.convdiff(N, dim, beta)
+        b = np.random.default_rng(N).standard_normal(A.n)
+        ref = sl.expm(-t * A.to_dense()) @ b
+        assert rel(TR.kron_expm_apply(N, dim, beta, t, b), ref) < 1e-12
+        refT = sl.expm(-t * A.to_dense()).T @ b
+        assert rel(TR.kron_expm_apply(N, dim, beta, t, b, transpose=True), refT) < 1e-12
+
+
+def test_sine_modes_are_eigenvectors():
+    N = 16
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 5, 1)
+    assert rel(TR.sine_mode_exp(N, c, p, q, 3e-3), sl.expm(-3e-3 * A.to_dense()) @ b) < 1e-12
+
+
+def test_csr_matvec_matches_dense():
+    A = W.convdiff3d(7, (50.0, 10.0, 0.0))
+    x = np.random.default_rng(4).standard_normal(A.n)
+    assert rel(K.csr_matvec(A, x), A.to_dense() @ x) < 1e-15
+
+
+def test_workload_sizes_match_configurations():
+    """Matrix sizes quoted for the workloads (n, nnz)."""
+    A = W.poisson2d(64)
+    assert (A.n, A.nnz) == (4096, 20224)
+    B = W.convdiff3d(12)
+    assert B.nnz == 7 * 12**3 - 6 * 12**2
+    assert set(np.unique(W.convdiff3d(4).val)) == {-275.0, -25.0, 900.0}  # h=1/5, beta/h=250
+    F = W.fem_p1_kuhn(6, 1.0, 1)
+    Fd = F.to_dense()
+    assert np.allclose(Fd, Fd.T) and np.linalg.eigvalsh(Fd).min() > 0
+    assert np.diff(F.row_ptr).max() == 15
+    N = 5  # interior nodes per axis: diagonal + 6 axis + 6 face-diagonal + 2 body-diagonal couplings
+    assert F.nnz == N**3 + 6 * N * N * (N - 1) + 6 * N * (N - 1) ** 2 + 2 * (N - 1) ** 3
+
+
+# ---------------------------------------------------------------- Krylov ----
+MODES = [K.TRUNC, K.RGS, K.CLASSICAL]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_restarted_converges_to_kronecker_truth(mode):
+    """Algorithm 2 in every orthogonalization mode reaches exp(-tA)b of the
+    closed form (non-symmetric 3D convection-diffusion)."""
+    N, beta, t = 10, (50.0, 50.0, 50.0), 3e-3
+    A = W.convdiff3d(N, beta)
+    b = W.rhs_uniform(A.n, 1)
+    k = 2 if mode == K.TRUNC else 20
+    r = K.restarted(A, b, D.EXP_NEG, t, 20, k, 80, 8, 5, mode=mode, tol=1e-13, max_cycles=40)
+    assert rel(r.x, TR.kron_expm_apply(N, 3, beta, t, b)) < 1e-11
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_sine_mixture_closed_form(mode):
+    N, t = 32, 1e-3
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 20, 4)
+    k = 2 if mode == K.TRUNC else 30
+    r = K.restarted(A, b, D.EXP_NEG, t, 30, k, 60, 8, 6, mode=mode, tol=1e-13, max_cycles=30)
+    assert rel(r.x, TR.sine_mode_exp(N, c, p, q, t)) < 1e-11
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_single_mode_breaks_down_exactly(mode):
+    N = 20
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 1, 2)
+    r = K.restarted(A, b, D.EXP_NEG, 2e-3, 10, 2 if mode == K.TRUNC else 10, 30, 4, 1, mode=mode, max_cycles=5)
+    assert r.breakdown and r.cycles == 1 and r.info[0].m_eff == 1
+    assert rel(r.x, TR.sine_mode_exp(N, c, p, q, 2e-3)) < 1e-13
+
+
+@pytest.mark.parametrize("fkind", [D.EXP_NEG, D.INV, D.INVSQRT])
+def test_exact_when_m_reaches_n(fkind):
+    """With m = n the Krylov space is the whole space: one cycle is exact."""
+    A = W.fem_p1_kuhn(4, 1.0, 2)  # 27 unknowns, SPD
+    b = np.random.default_rng(7).standard_normal(A.n)
+    r = K.restarted(A, b, fkind, 0.05, A.n, A.n, A.n + 10, 4, 9, mode=K.TRUNC, max_cycles=1)
+    ref = TR.dense_fAb(A.to_dense(), b, fkind, 0.05, symmetric=True)
+    assert rel(r.x, ref) < 1e-10
+
+
+def test_inverse_residual():
+    """f = 1/z: the restarted result solves A x = b (true residual)."""
+    A = W.convdiff(20, 2, (10.0, 5.0))
+    b = W.rhs_normal(A.n, 2)
+    r = K.restarted(A, b, D.INV, 1.0, 30, 2, 90, 8, 3, mode=K.TRUNC, tol=1e-12, max_cycles=200)
+    assert np.linalg.norm(b - K.csr_matvec(A, r.x)) / np.linalg.norm(b) < 1e-9
+
+
+def test_arnoldi_like_relations():
+    """Eq. (5) A W_m = W_{m+1} R_m for every mode; RGS sketches orthonormal
+    (Algorithm 1); whitened TRUNC: the restart decomposition
+    A (W_m T_m^-1) = (W_m T_m^-1) X + v rho e_m^T holds (Eq. A.1 reading)."""
+    A = W.convdiff3d(8, (50.0, 50.0, 50.0))
+    b = W.rhs_uniform(A.n, 3)
+    m = 12
+    Ad = A.to_dense()
+    for mode, k in [(K.TRUNC, 2), (K.RGS, m), (K.RGS, 3), (K.CLASSICAL, m)]:
+        r = K.restarted(A, b, D.EXP_NEG, 1e-3, m, k, 4 * m, 8, 3, mode=mode, max_cycles=2, keep=True)
+        for ci in r.info:
+            Wm, Rb = ci.W, ci.R
+            res = np.linalg.norm(Ad @ Wm[:, :m] - Wm @ Rb) / (np.linalg.norm(Ad) * np.linalg.norm(Wm))
+            assert res < 1e-14
+            if mode == K.RGS and k >= m:  # full sketch orthogonalization
+                assert ci.sketch_orth_err < 1e-12
+        if mode == K.TRUNC:
+            ci = r.info[0]
+            T = ci.T
+            Tm = T[:m, :m]
+            What = ci.W[:, :m] @ np.linalg.inv(Tm)
+            v = (ci.W[:, m] - ci.W[:, :m] @ np.linalg.solve(Tm, T[:m, m])) / T[m, m]
+            rho = ci.R[m, m - 1] * T[m, m] / Tm[-1, -1]
+            lhs = Ad @ What
+            rhs = What @ ci.X + np.outer(v, np.eye(m)[-1]) * rho
+            assert rel(lhs, rhs) < 1e-12
+            Sk = OS.SparseSign(A.n, 4 * m, 8, 3)
+            SW = Sk.apply(What)
+            assert np.allclose(SW.T @ SW, np.eye(m), atol=1e-12)
+            assert abs(np.linalg.norm(Sk.apply(v)) - 1.0) < 1e-12
+
+
+def test_interpolation_property():
+    """Proposition (Eqs. 7-8): the restarted result equals q(A) b where q
+    interpolates f at the eigenvalues of H_{km} (Newton divided differences,
+    Horner form), independently of the basis."""
+    A = W.convdiff(12, 1, (30.0,))
+    b = W.rhs_normal(A.n, 5)
+    t = 2e-4
+    for mode, k in [(K.TRUNC, 2), (K.RGS, 3), (K.CLASSICAL, 3)]:
+        r = K.restarted(A, b, D.EXP_NEG, t, 3, k, 12, 2, 8, mode=mode, max_cycles=2)
+        lam = np.linalg.eigvals(r.H).astype(complex)
+        # divided differences of f(z) = exp(-t z) at the nodes
+        dd = np.exp(-t * lam)
+        for lev in range(1, len(lam)):
+            dd[lev:] = (dd[lev:] - dd[lev - 1:-1]) / (lam[lev:] - lam[:-lev])
+        Ad = A.to_dense().astype(complex)
+        acc = dd[-1] * b.astype(complex)
+        for i in range(len(lam) - 2, -1, -1):
+            acc = dd[i] * b + (Ad @ acc - lam[i] * acc)
+        assert np.abs(acc.imag).max() < 1e-9 * np.abs(acc).max()
+        assert rel(acc.real, r.x) < 1e-9
+
+
+def test_stopping_estimate_decreases():
+    """Sec. 4: ||y|| of successive cycles decreases for the convergent case and
+    the final update is below tol ||x||."""
+    A = W.poisson2d(48)
+    b = W.rhs_normal(A.n, 8, normalize=True)
+    r = K.restarted(A, b, D.EXP_NEG, 1e-3, 20, 2, 60, 8, 3, mode=K.TRUNC, tol=1e-10, max_cycles=30)
+    ys = [ci.update_norm for ci in r.info]
+    assert ys[-1] <= 1e-10 * r.info[-1].x_norm
+    assert all(ys[i + 1] < ys[i] for i in range(1, len(ys) - 1))
