@@ -1,0 +1,180 @@
+/*
+ * krylov.h -- C ABI of the GB300 randomized restarted Krylov library for f(A) b.
+ *
+ * Method: Guidotti, Martinsson, Acebron, Monteiro, "Accelerating a restarted
+ * Krylov method for matrix functions with randomization" (arXiv 2503.22631).
+ * The library approximates f(A) b for a square sparse A (CSR), a vector b and
+ * f analytic on the spectrum of A (Sec. 1), by restart cycles of m Arnoldi-like
+ * steps (Sec. 4, Algorithm 2).  Each step is one sparse matrix-vector product,
+ * an orthogonalization of the new vector against the last k basis vectors, and
+ * one sparse-sign sketch of the stored vector (Sec. 2.1, Eq. 3).  Each cycle
+ * ends with the sketched small problem in FP64: a thin QR of the sketched
+ * basis (basis whitening, App. A, Eq. A.1), f of the block lower-bidiagonal
+ * projected matrix (Algorithm 2), and one streaming solution update.
+ *
+ * Conventions for every call:
+ *  - Pointers named "device" are CUDA device pointers on the current device;
+ *    pointers named "host" are ordinary host memory.  All vectors are dense,
+ *    contiguous float64 of length n unless stated.
+ *  - Work is issued on the handle's stream (krylov_options.stream, NULL =
+ *    legacy default stream).  Calls return after the result is complete
+ *    (the library synchronizes the stream at cycle boundaries).
+ *  - No call throws; errors are returned as krylov_status.  Negative codes are
+ *    errors (outputs unspecified), positive codes are informational (outputs
+ *    hold the last iterate).
+ *  - A handle is not thread-safe: one call at a time per handle.
+ *  - Every entry point fails with KRYLOV_ECUDA when the CUDA runtime reports an
+ *    error, and never falls back to host computation.
+ */
+#ifndef KRYLOV_H
+#define KRYLOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct krylov_handle krylov_handle; /* opaque, owned by the library */
+
+typedef enum {
+  KRYLOV_OK = 0,
+  KRYLOV_NOT_CONVERGED = 1,   /* max_cycles reached before ||y|| <= tol ||x||   */
+  KRYLOV_BREAKDOWN_EXACT = 2, /* happy breakdown: invariant subspace, x exact   */
+  KRYLOV_EINVAL = -1,         /* invalid argument (sizes, CSR structure, ...)   */
+  KRYLOV_ENOMEM = -2,         /* device allocation failed                       */
+  KRYLOV_ECUDA = -3,          /* CUDA runtime / launch error                    */
+  KRYLOV_ENONFINITE = -4,     /* NaN/Inf in b or in the projected problem       */
+  KRYLOV_ETIMEOUT = -5,       /* reserved: a bounded device wait gave up        */
+  KRYLOV_EUNSUPPORTED = -6    /* option combination not implemented             */
+} krylov_status;
+
+/* f(z); exp(-t z) is Eq. (19)'s heat kernel and the exponential of Sec. 5.1 with
+ * the time folded in; z^{-1/2} and 1/z are extensions (Stieltjes functions). */
+typedef enum {
+  KRYLOV_F_EXP_NEG = 0, /* f(z) = exp(-t z) */
+  KRYLOV_F_INVSQRT = 1, /* f(z) = z^{-1/2}  */
+  KRYLOV_F_INV = 2      /* f(z) = 1/z       */
+} krylov_fkind;
+
+typedef struct {
+  int kind;  /* krylov_fkind */
+  double t;  /* time parameter of exp(-t z); ignored otherwise */
+} krylov_func;
+
+/* CSR matrix, borrowed for the duration of krylov_create (the library copies
+ * it).  row_ptr: n+1 int32, monotone, row_ptr[0] = 0, row_ptr[n] = nnz;
+ * col_idx: nnz int32 in [0, n); val: nnz float64.  on_device != 0 means the
+ * three arrays are device pointers, else host pointers.  (App. A: CSR.) */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  int on_device;
+} krylov_csr;
+
+typedef enum { KRYLOV_BASIS_F64 = 0, KRYLOV_BASIS_F32 = 1, KRYLOV_BASIS_BF16 = 2 } krylov_basis;
+typedef enum { KRYLOV_ORTHO_TRUNC = 0 } krylov_ortho;
+
+typedef struct {
+  int zeta;        /* nonzeros per sketch column (Eq. 3); 1 <= zeta <= min(s, 32). Default 8 */
+  int basis_dtype; /* krylov_basis: storage of the Krylov basis and step vectors. Default F64 */
+  int ortho;       /* krylov_ortho: truncated classical Gram-Schmidt + whitening (App. A) */
+  int narrow_values_if_exact; /* F64 basis: stream A's values as float32 when every value
+                                 round-trips exactly (lossless). Default 1 */
+  int use_graph;   /* capture the m steps of a cycle in a CUDA graph. Default 1 */
+  int abs_tol;     /* 1: stop when ||y|| <= tol (Algorithm 2 as printed);
+                      0: stop when ||y|| <= tol * ||x|| (default) */
+  void* stream;    /* cudaStream_t for all work; NULL = legacy default stream */
+} krylov_options;
+
+typedef struct {
+  int cycles;              /* restart cycles run */
+  int breakdown;           /* 1 if the last cycle ended in a happy breakdown */
+  int steps;               /* Arnoldi steps (sparse products) run */
+  double last_update_norm; /* ||y|| of the last cycle (Sec. 4 error estimate) */
+  double x_norm;           /* ||x|| after the last cycle */
+  double kappa_T_max;      /* max over cycles of cond_1 estimate of T (whitening) */
+  double ms_total;         /* wall time of the call measured with CUDA events */
+  double bytes_moved;      /* algorithmic HBM bytes of the call (roofline model) */
+} krylov_stats;
+
+/* Fill *opt with the defaults listed above. */
+void krylov_options_default(krylov_options* opt);
+
+/* Create a handle: copy A to the device, validate it (EINVAL on a non-monotone
+ * row_ptr or a column index out of range), fix the sketch S from (s, zeta,
+ * seed) and allocate the cycle workspaces (m+1 basis vectors, two product
+ * vectors, the s x (m+1) sketch, the projected-problem history).
+ *   f      : the function and its parameter;
+ *   m      : restart length (Algorithm 2), 1 <= m <= 256;
+ *   k      : orthogonalization window, 1 <= k <= 4 (Sec. 5: incomplete
+ *            orthogonalization against the last k vectors);
+ *   s      : sketch rows d of Eq. (3), m+1 <= s <= 1024;
+ *   seed   : keys the counter-based generator of S;
+ *   opt    : may be NULL (defaults);
+ *   out    : receives the handle (owned by the caller, free with krylov_destroy). */
+krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, int s,
+                            uint64_t seed, const krylov_options* opt, krylov_handle** out);
+
+/* x <- approximation of f(A) b by Algorithm 2 (with the whitened restart of
+ * App. A).  b: device, n float64, read only; x: device, n float64, overwritten.
+ * tol: stopping tolerance (relative unless opt.abs_tol); tol = 0 runs exactly
+ * max_cycles cycles.  st may be NULL.  Returns OK, NOT_CONVERGED or
+ * BREAKDOWN_EXACT on success. */
+krylov_status krylov_apply(krylov_handle* h, const double* b, double* x, double tol,
+                           int max_cycles, krylov_stats* st);
+
+/* Same as krylov_apply with b and x in HOST memory; the copies to and from the
+ * device are part of the call (and of st->ms_total). */
+krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* x_host,
+                                double tol, int max_cycles, krylov_stats* st);
+
+/* x <- f(A)^T b = f(A^T) b for real A and real-coefficient f: the same method on
+ * the transposed CSR, which is built on the device on first use and cached.
+ * Arguments as for krylov_apply. */
+krylov_status krylov_apply_adjoint(krylov_handle* h, const double* b, double* x, double tol,
+                                   int max_cycles, krylov_stats* st);
+
+/* Change the parameter t of f for subsequent calls (e.g. exp(-t z) at a new t). */
+krylov_status krylov_set_param(krylov_handle* h, double t);
+
+/* y <- A x (transpose = 0) or A^T x (transpose = 1).  x, y: device float64, n.
+ * If dot_with is not NULL, also *dot_out (host) <- <dot_with, y>.  Used for the
+ * derivative in t of exp(-tA) b (d/dt = -A exp(-tA) b). */
+krylov_status krylov_spmv(krylov_handle* h, const double* x, double* y, int transpose,
+                          const double* dot_with, double* dot_out);
+
+/* Problem size of a handle. */
+int64_t krylov_size(const krylov_handle* h);
+
+/* Release the handle and all device memory it owns.  NULL is ignored. */
+void krylov_destroy(krylov_handle* h);
+
+/* Static description of a status code. */
+const char* krylov_status_string(krylov_status s);
+
+/* ---- inspection entry points used by the parity tests ------------------ */
+
+/* Sparse sign columns [col0, col0 + count) of S as generated on the device
+ * (Sec. 2.1, Eq. 3): rows_out (host, count*zeta int32) and signs_out (host,
+ * count*zeta int8, +1/-1), entries of a column in acceptance order.  The same
+ * generator feeds every sketch the library computes. */
+krylov_status krylov_sketch_columns(int64_t n, int s, int zeta, uint64_t seed, int64_t col0,
+                                    int64_t count, int32_t* rows_out, int8_t* signs_out);
+
+/* Matrices of the last cycle run by h (host copies, column-major):
+ * T (s_cols x s_cols, s_cols = m_eff + 1 or m_eff after a breakdown),
+ * X (m_eff x m_eff, Eq. A.1), z (m_eff coefficients of the update
+ * x += W_m z) and m_eff itself.  Any output pointer may be NULL; sizes given
+ * in elements must be large enough (EINVAL otherwise). */
+krylov_status krylov_last_cycle(const krylov_handle* h, double* T, int64_t T_cap, double* X,
+                                int64_t X_cap, double* z, int64_t z_cap, int* m_eff);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRYLOV_H */

@@ -1,0 +1,604 @@
+// api.cu -- the C ABI (include/krylov.h): handle management and the host
+// driver of Algorithm 2 (restart cycles) on top of the kernels.
+//
+// Per cycle the host launches m+1 step kernels, the sketch reduction, the
+// whitening kernel and the projected-function kernels, then the streaming
+// update.  It synchronizes twice per cycle: once to read m_eff, the breakdown
+// flag and the norm of the new projected block (to fix the number of
+// squarings), once to read ||y|| and ||x|| for the stopping test of Sec. 4.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/krylov.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+using namespace krylov;
+
+namespace {
+
+constexpr double EXP_THETA = 2.0;  // ||B||_1 bound after scaling
+constexpr int EXP_TAYLOR_DEG = 24; // theta^25/25! e^theta < 2^-53
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct krylov_handle {
+  int n = 0;
+  int64_t nnz = 0;
+  int m = 0, k = 0, s = 0;
+  uint64_t seed = 0;
+  krylov_func f{};
+  krylov_options opt{};
+  cudaStream_t st = nullptr;
+  int num_sms = 0;
+  int grid = 0;
+
+  // matrix (and its transpose, built on first adjoint use)
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  int vals_exact_f32 = 0;
+  int* rpt = nullptr;
+  int* cit = nullptr;
+  double* valt = nullptr;
+  float* valt32 = nullptr;
+  int have_t = 0;
+
+  // cycle workspaces
+  void* W = nullptr;
+  int64_t ldw = 0;
+  void* p[2] = {nullptr, nullptr};
+  void* sk_part = nullptr;
+  int64_t sk_col_stride = 0;
+  double* part = nullptr;
+  CycleDev cd{};
+  SmallDev sd{};
+  int cap_rows = 0;     // block rows of the projected-function storage
+  int cap_levels = 0;   // scale levels allocated in sd.G
+  int64_t level_stride = 0;
+  int* d_flag = nullptr;
+  double* d_dot = nullptr;
+
+  // host mirrors
+  int* h_flags = nullptr;     // pinned: flags[4]
+  double* h_scal = nullptr;   // pinned: 16 doubles
+  int last_me = 0, last_nc = 0, last_cycle = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int basis_bytes(int basis) { return basis == 0 ? 8 : (basis == 1 ? 4 : 2); }
+
+krylov_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return KRYLOV_OK;
+  if (e == cudaErrorMemoryAllocation) return KRYLOV_ENOMEM;
+  return KRYLOV_ECUDA;
+}
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_status(e_);        \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(krylov_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+void dfree(krylov_handle* h, void* p) {
+  if (!p) return;
+  for (auto& q : h->allocs)
+    if (q == p) {
+      cudaFree(q);
+      q = nullptr;
+    }
+}
+
+// Projected-function storage for `rows` block rows and `levels` scale levels.
+krylov_status ensure_small_capacity(krylov_handle* h, int rows, int levels) {
+  const size_t MM = (size_t)h->m * h->m;
+  if (rows > h->cap_rows) {
+    int nr = std::max(rows, std::max(8, 2 * h->cap_rows));
+    dfree(h, h->sd.Xblk);
+    dfree(h, h->sd.gam);
+    dfree(h, h->sd.S0);
+    dfree(h, h->sd.G);
+    h->sd.G = nullptr;
+    CK(dalloc(h, &h->sd.Xblk, (size_t)nr * MM));
+    CK(dalloc(h, &h->sd.gam, (size_t)nr));
+    CK(dalloc(h, &h->sd.S0, std::max<size_t>(2 * (size_t)nr * MM, (size_t)h->m * h->m)));
+    h->cap_rows = nr;
+    h->cap_levels = 0;
+  }
+  if (levels > h->cap_levels || h->sd.G == nullptr) {
+    int nl = std::max(levels, h->cap_levels + 4);
+    dfree(h, h->sd.G);
+    h->level_stride = (int64_t)h->cap_rows * (h->cap_rows + 1) / 2 * (int64_t)MM;
+    CK(dalloc(h, &h->sd.G, (size_t)nl * h->level_stride));
+    h->cap_levels = nl;
+  }
+  return KRYLOV_OK;
+}
+
+int scale_levels_for(double normH) {
+  if (!(normH > EXP_THETA)) return 0;
+  return (int)std::ceil(std::log2(normH / EXP_THETA));
+}
+
+// Block row a of exp(-t H) at all scale levels 0..sl (scale 2^-sl).
+void exp_row(krylov_handle* h, int a, int sl) {
+  const int M = h->m;
+  const size_t MM = (size_t)M * M;
+  const double scale = -h->f.t / std::ldexp(1.0, sl);
+  double* g0row = h->sd.G + (size_t)a * (a + 1) / 2 * MM;
+  int src = 0;
+  for (int kdeg = EXP_TAYLOR_DEG; kdeg >= 1; --kdeg) {
+    const int first = (kdeg == EXP_TAYLOR_DEG);
+    double* dst = (kdeg == 1) ? g0row : h->sd.S0 + (size_t)(1 - src) * (size_t)(a + 1) * MM;
+    launch_exp_taylor_step(h->sd, M, a, kdeg, scale, first, kdeg == 1, src, dst, h->st);
+    src = 1 - src;
+  }
+  for (int lv = 0; lv < sl; ++lv) launch_exp_square(h->sd, M, a, lv, h->level_stride, h->st);
+}
+
+struct Operator {
+  const int* rp;
+  const int* ci;
+  const double* val;
+  const float* val32;
+};
+
+krylov_status build_transpose(krylov_handle* h) {
+  if (h->have_t) return KRYLOV_OK;
+  int* work = nullptr;
+  CK(dalloc(h, &h->rpt, (size_t)h->n + 1));
+  CK(dalloc(h, &h->cit, (size_t)h->nnz));
+  CK(dalloc(h, &h->valt, (size_t)h->nnz));
+  CK(dalloc(h, &work, 2 * (size_t)h->n));
+  CK(transpose_csr(h->n, h->nnz, h->rp, h->ci, h->val, h->rpt, h->cit, h->valt, work, h->st));
+  if (h->val32) {
+    CK(dalloc(h, &h->valt32, (size_t)h->nnz));
+    CK(narrow_values(h->nnz, h->valt, h->valt32, h->d_flag, h->h_flags, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  dfree(h, work);
+  h->have_t = 1;
+  return KRYLOV_OK;
+}
+
+double model_bytes_step(const krylov_handle* h, int use32) {
+  const double bv = basis_bytes(h->opt.basis_dtype);
+  const double ba = use32 ? 4.0 : 8.0;
+  return (double)h->nnz * (ba + 4.0) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
+}
+
+krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, double* x, double tol,
+                         int max_cycles, krylov_stats* stout) {
+  if (!h || !b || !x || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
+  if (transpose) {
+    krylov_status s = build_transpose(h);
+    if (s != KRYLOV_OK) return s;
+  }
+  const int basis = h->opt.basis_dtype;
+  const int use32 = (basis != 0) || (h->opt.narrow_values_if_exact && h->vals_exact_f32);
+  Operator op{transpose ? h->rpt : h->rp, transpose ? h->cit : h->ci, transpose ? h->valt : h->val,
+              transpose ? h->valt32 : h->val32};
+  const int n = h->n, M = h->m;
+  cudaStream_t st = h->st;
+  krylov_stats stats{};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+
+  int levels_needed = 1;
+  if (h->f.kind == KRYLOV_F_EXP_NEG) levels_needed = std::max(1, h->cap_levels);
+  krylov_status cs = ensure_small_capacity(h, max_cycles, levels_needed);
+  if (cs != KRYLOV_OK) return cs;
+
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st));
+  CK(cudaMemsetAsync(h->cd.flags, 0, 4 * sizeof(int), st));
+  CK(cudaMemsetAsync(h->sd.misc, 0, 8 * sizeof(double), st));
+  launch_norm_b(b, n, h->part, h->grid, h->cd, st);
+  CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
+  if (h->h_scal[0] == 0.0) {  // b = 0: f(A) 0 = 0
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    if (stout) *stout = stats;
+    return KRYLOV_OK;
+  }
+  launch_start(basis, b, h->W, n, h->cd, h->grid, st);
+
+  const double thr = (basis == 0) ? 1e-14 : 1e-6;
+  int s_lv = -1;        // scale levels in use (exp)
+  double maxX = 0.0, maxG = 0.0;
+  krylov_status result = KRYLOV_NOT_CONVERGED;
+  for (int c = 1; c <= max_cycles; ++c) {
+    launch_cycle_reset(h->cd, M, st);
+    for (int j = 0; j <= M; ++j) {
+      StepLaunch L{};
+      L.n = n;
+      L.row_ptr = op.rp;
+      L.col = op.ci;
+      L.val = use32 ? (const void*)op.val32 : (const void*)op.val;
+      L.val_f32 = use32;
+      L.W = h->W;
+      L.ldw = h->ldw;
+      L.j = j;
+      L.k = h->k;
+      L.mat = (j > 0);
+      L.spmv = (j < M);
+      L.p_prev = h->p[(j + 1) & 1];
+      L.p_out = h->p[j & 1];
+      L.sk_part = (char*)h->sk_part + (size_t)j * h->sk_col_stride * (basis == 0 ? 8 : 4);
+      L.part = h->part;
+      L.thr = thr;
+      L.s = h->s;
+      L.zeta = h->opt.zeta;
+      L.seed = h->seed;
+      L.grid = h->grid;
+      L.rows_per_cta = (n + h->grid - 1) / h->grid;
+      launch_step(basis, L, h->cd, M, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
+    if (h->h_flags[2] & ERR_SKETCH) return KRYLOV_ECUDA;
+    const int me = std::min(h->h_flags[0], M);
+    const int brk = h->h_flags[1];
+    if (me < 1) return KRYLOV_ENONFINITE;
+    const int has_next = brk ? 0 : 1;
+    const int nc = me + has_next;
+    stats.steps += me;
+    launch_sketch_reduce(basis, h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
+    launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->f.t, st);
+    const int a = c - 1;
+    if (h->f.kind == KRYLOV_F_EXP_NEG) {
+      CK(cudaMemcpyAsync(h->h_scal, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      maxX = std::max(maxX, h->h_scal[2]);
+      maxG = std::max(maxG, h->h_scal[3]);
+      stats.kappa_T_max = std::max(stats.kappa_T_max, h->h_scal[4]);
+      if (!std::isfinite(maxX) || !std::isfinite(maxG)) return KRYLOV_ENONFINITE;
+      const int need = scale_levels_for(maxX + maxG);
+      if (need > s_lv) {
+        s_lv = need;
+        cs = ensure_small_capacity(h, max_cycles, s_lv + 1);
+        if (cs != KRYLOV_OK) return cs;
+        for (int ap = 0; ap < a; ++ap) exp_row(h, ap, s_lv);
+      }
+      exp_row(h, a, s_lv);
+      const size_t MM = (size_t)M * M;
+      const double* fsrc = h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
+      launch_z(h->sd, M, me, fsrc, st);
+    } else if (h->f.kind == KRYLOV_F_INV) {
+      launch_inv_block(h->sd, M, a, st);
+      launch_z(h->sd, M, me, h->sd.fcol, st);
+    } else {
+      return KRYLOV_EUNSUPPORTED;
+    }
+    launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid, h->cd, M, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
+    const double ynorm = std::sqrt(h->h_scal[2]);
+    const double xnorm = std::sqrt(h->h_scal[3]);
+    stats.cycles = c;
+    stats.last_update_norm = ynorm;
+    stats.x_norm = xnorm;
+    h->last_me = me;
+    h->last_nc = nc;
+    h->last_cycle = c;
+    if (!std::isfinite(ynorm) || !std::isfinite(xnorm)) return KRYLOV_ENONFINITE;
+    if (brk) {
+      stats.breakdown = 1;
+      result = KRYLOV_BREAKDOWN_EXACT;
+      break;
+    }
+    const double lim = h->opt.abs_tol ? tol : tol * xnorm;
+    if (ynorm <= lim) {
+      result = KRYLOV_OK;
+      break;
+    }
+  }
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  stats.ms_total = ms;
+  const double bv = basis_bytes(basis);
+  stats.bytes_moved = stats.steps * model_bytes_step(h, use32) +
+                      stats.cycles * ((M + 1) * (double)n * bv + 16.0 * n + n * bv);
+  if (stout) *stout = stats;
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+void krylov_options_default(krylov_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->zeta = 8;
+  opt->basis_dtype = KRYLOV_BASIS_F64;
+  opt->ortho = KRYLOV_ORTHO_TRUNC;
+  opt->narrow_values_if_exact = 1;
+  opt->use_graph = 0;
+  opt->abs_tol = 0;
+  opt->stream = nullptr;
+}
+
+const char* krylov_status_string(krylov_status s) {
+  switch (s) {
+    case KRYLOV_OK: return "ok";
+    case KRYLOV_NOT_CONVERGED: return "not converged within max_cycles";
+    case KRYLOV_BREAKDOWN_EXACT: return "happy breakdown: exact result";
+    case KRYLOV_EINVAL: return "invalid argument";
+    case KRYLOV_ENOMEM: return "device out of memory";
+    case KRYLOV_ECUDA: return "CUDA error";
+    case KRYLOV_ENONFINITE: return "non-finite value";
+    case KRYLOV_ETIMEOUT: return "device wait timed out";
+    case KRYLOV_EUNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+void krylov_destroy(krylov_handle* h) {
+  if (!h) return;
+  for (void* p : h->allocs)
+    if (p) cudaFree(p);
+  if (h->h_flags) cudaFreeHost(h->h_flags);
+  if (h->h_scal) cudaFreeHost(h->h_scal);
+  delete h;
+}
+
+krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, int s, uint64_t seed,
+                            const krylov_options* opt_in, krylov_handle** out) {
+  if (!A || !out) return KRYLOV_EINVAL;
+  *out = nullptr;
+  krylov_options opt;
+  krylov_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  if (A->n < 1 || A->n > 0x7FFFFFF0LL || A->nnz < 0 || A->nnz > 0x7FFFFFF0LL) return KRYLOV_EINVAL;
+  if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return KRYLOV_EINVAL;
+  if (m < 1 || m > 256 || k < 1 || k > MAX_WINDOW || s < m + 1 || s > 1024) return KRYLOV_EINVAL;
+  if (opt.zeta < 1 || opt.zeta > std::min(s, MAX_ZETA)) return KRYLOV_EINVAL;
+  if (opt.basis_dtype < 0 || opt.basis_dtype > 2 || opt.ortho != KRYLOV_ORTHO_TRUNC) return KRYLOV_EINVAL;
+  if (f.kind != KRYLOV_F_EXP_NEG && f.kind != KRYLOV_F_INV && f.kind != KRYLOV_F_INVSQRT) return KRYLOV_EINVAL;
+  if (!std::isfinite(f.t)) return KRYLOV_EINVAL;
+
+  krylov_handle* h = new (std::nothrow) krylov_handle();
+  if (!h) return KRYLOV_ENOMEM;
+  h->n = (int)A->n;
+  h->nnz = A->nnz;
+  h->m = m;
+  h->k = k;
+  h->s = s;
+  h->seed = seed;
+  h->f = f;
+  h->opt = opt;
+  h->st = static_cast<cudaStream_t>(opt.stream);
+  auto fail = [&](krylov_status st) {
+    krylov_destroy(h);
+    return st;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(KRYLOV_ECUDA);
+  if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(KRYLOV_ECUDA);
+  if (cudaMallocHost(&h->h_flags, 16 * sizeof(int)) != cudaSuccess) return fail(KRYLOV_ENOMEM);
+  if (cudaMallocHost(&h->h_scal, 16 * sizeof(double)) != cudaSuccess) return fail(KRYLOV_ENOMEM);
+
+  const int n = h->n;
+  const int64_t nnz = h->nnz;
+  const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+#define CKF(call)                                     \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return fail(cuda_status(e_)); \
+  } while (0)
+  CKF(dalloc(h, &h->rp, (size_t)n + 1));
+  CKF(dalloc(h, &h->ci, (size_t)nnz));
+  CKF(dalloc(h, &h->val, (size_t)nnz));
+  CKF(dalloc(h, &h->d_flag, 4));
+  CKF(cudaMemcpyAsync(h->rp, A->row_ptr, sizeof(int) * ((size_t)n + 1), kind, h->st));
+  if (nnz > 0) {
+    CKF(cudaMemcpyAsync(h->ci, A->col_idx, sizeof(int) * (size_t)nnz, kind, h->st));
+    CKF(cudaMemcpyAsync(h->val, A->val, sizeof(double) * (size_t)nnz, kind, h->st));
+  }
+  CKF(validate_csr(n, nnz, h->rp, h->ci, h->d_flag, h->h_flags, h->st));
+  if (h->h_flags[0] != 0) return fail(KRYLOV_EINVAL);
+  // float32 copy of the values: exact-narrowing test, and the operand of the
+  // float32/bfloat16 basis modes
+  CKF(dalloc(h, &h->val32, (size_t)nnz));
+  CKF(narrow_values(nnz, h->val, h->val32, h->d_flag, h->h_flags, h->st));
+  h->vals_exact_f32 = (h->h_flags[0] == 0);
+
+  // workspaces
+  h->grid = std::max(1, std::min(h->num_sms * 4, (n + STEP_THREADS - 1) / STEP_THREADS));
+  const int bb = basis_bytes(opt.basis_dtype);
+  h->ldw = ((int64_t)n + 63) / 64 * 64;
+  CKF(cudaMalloc(&h->W, (size_t)(m + 1) * h->ldw * bb));
+  h->allocs.push_back(h->W);
+  const int pb = (opt.basis_dtype == 0) ? 8 : 4;
+  for (int i = 0; i < 2; ++i) {
+    CKF(cudaMalloc(&h->p[i], (size_t)n * pb));
+    h->allocs.push_back(h->p[i]);
+  }
+  h->sk_col_stride = (int64_t)h->grid * s;
+  CKF(cudaMalloc(&h->sk_part, (size_t)(m + 1) * h->sk_col_stride * pb));
+  h->allocs.push_back(h->sk_part);
+  CKF(dalloc(h, &h->part, (size_t)h->grid * 8));
+  CKF(dalloc(h, &h->cd.flags, 4));
+  CKF(dalloc(h, &h->cd.sig2, (size_t)m + 1));
+  CKF(dalloc(h, &h->cd.pi, (size_t)m + 1));
+  CKF(dalloc(h, &h->cd.coef, (size_t)(m + 1) * (MAX_WINDOW + 1)));
+  CKF(dalloc(h, &h->cd.R, (size_t)(m + 1) * m));
+  CKF(dalloc(h, &h->cd.scal, 8));
+  CKF(dalloc(h, &h->cd.counter, 4));
+  CKF(cudaMemsetAsync(h->cd.counter, 0, 4 * sizeof(unsigned), h->st));
+  CKF(cudaMemsetAsync(h->cd.R, 0, sizeof(double) * (size_t)(m + 1) * m, h->st));
+  CKF(dalloc(h, &h->sd.U, (size_t)s * (m + 1)));
+  CKF(dalloc(h, &h->sd.Tw, (size_t)s * (m + 1)));
+  CKF(dalloc(h, &h->sd.Tinv, (size_t)m * m));
+  CKF(dalloc(h, &h->sd.zg, (size_t)2 * m + 1));
+  CKF(dalloc(h, &h->sd.misc, 8));
+  CKF(dalloc(h, &h->sd.fcol, (size_t)m));
+  CKF(dalloc(h, &h->d_dot, 1));
+  CKF(cudaStreamSynchronize(h->st));
+#undef CKF
+  *out = h;
+  return KRYLOV_OK;
+}
+
+krylov_status krylov_apply(krylov_handle* h, const double* b, double* x, double tol, int max_cycles,
+                           krylov_stats* st) {
+  return apply_impl(h, 0, b, x, tol, max_cycles, st);
+}
+
+krylov_status krylov_apply_adjoint(krylov_handle* h, const double* b, double* x, double tol, int max_cycles,
+                                   krylov_stats* st) {
+  return apply_impl(h, 1, b, x, tol, max_cycles, st);
+}
+
+krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* x_host, double tol,
+                                int max_cycles, krylov_stats* st) {
+  if (!h || !b_host || !x_host) return KRYLOV_EINVAL;
+  double *db = nullptr, *dx = nullptr;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->st));
+  CK(cudaMalloc(&db, sizeof(double) * (size_t)h->n));
+  if (cudaMalloc(&dx, sizeof(double) * (size_t)h->n) != cudaSuccess) {
+    cudaFree(db);
+    return KRYLOV_ENOMEM;
+  }
+  krylov_status r = KRYLOV_ECUDA;
+  if (cudaMemcpyAsync(db, b_host, sizeof(double) * (size_t)h->n, cudaMemcpyHostToDevice, h->st) == cudaSuccess) {
+    r = apply_impl(h, 0, db, dx, tol, max_cycles, st);
+    if (r >= 0 &&
+        cudaMemcpyAsync(x_host, dx, sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+      r = KRYLOV_ECUDA;
+  }
+  cudaEventRecord(e1, h->st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (st) st->ms_total = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(db);
+  cudaFree(dx);
+  return r;
+}
+
+krylov_status krylov_set_param(krylov_handle* h, double t) {
+  if (!h || !std::isfinite(t)) return KRYLOV_EINVAL;
+  h->f.t = t;
+  return KRYLOV_OK;
+}
+
+krylov_status krylov_spmv(krylov_handle* h, const double* x, double* y, int transpose, const double* dot_with,
+                          double* dot_out) {
+  if (!h || !x || !y) return KRYLOV_EINVAL;
+  if (transpose) {
+    krylov_status s = build_transpose(h);
+    if (s != KRYLOV_OK) return s;
+  }
+  launch_spmv_f64(h->n, transpose ? h->rpt : h->rp, transpose ? h->cit : h->ci, transpose ? h->valt : h->val, x, y,
+                  h->st);
+  CK(cudaGetLastError());
+  if (dot_with && dot_out) {
+    launch_dot_f64(dot_with, y, h->n, h->part, h->grid, h->d_dot, h->cd.counter, h->st);
+    CK(cudaMemcpyAsync(h->h_scal + 8, h->d_dot, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    *dot_out = h->h_scal[8];
+  } else {
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return KRYLOV_OK;
+}
+
+int64_t krylov_size(const krylov_handle* h) { return h ? h->n : 0; }
+
+krylov_status krylov_sketch_columns(int64_t n, int s, int zeta, uint64_t seed, int64_t col0, int64_t count,
+                                    int32_t* rows_out, int8_t* signs_out) {
+  if (n < 1 || s < 1 || s > 32768 || zeta < 1 || zeta > std::min(s, MAX_ZETA) || col0 < 0 || count < 0 ||
+      col0 + count > n || col0 + count > 0xFFFFFFFFLL || !rows_out || !signs_out)
+    return KRYLOV_EINVAL;
+  if (count == 0) return KRYLOV_OK;
+  int* drows = nullptr;
+  signed char* dsigns = nullptr;
+  int* derr = nullptr;
+  CK(cudaMalloc(&drows, sizeof(int) * (size_t)count * zeta));
+  CK(cudaMalloc(&dsigns, (size_t)count * zeta));
+  CK(cudaMalloc(&derr, sizeof(int)));
+  cudaMemset(derr, 0, sizeof(int));
+  launch_sketch_columns(col0, count, s, zeta, seed, drows, dsigns, derr, nullptr);
+  int herr = 0;
+  cudaError_t e = cudaMemcpy(rows_out, drows, sizeof(int) * (size_t)count * zeta, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(signs_out, dsigns, (size_t)count * zeta, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(drows);
+  cudaFree(dsigns);
+  cudaFree(derr);
+  if (e != cudaSuccess) return cuda_status(e);
+  return herr ? KRYLOV_ECUDA : KRYLOV_OK;
+}
+
+krylov_status krylov_last_cycle(const krylov_handle* h, double* T, int64_t T_cap, double* X, int64_t X_cap,
+                                double* z, int64_t z_cap, int* m_eff) {
+  if (!h) return KRYLOV_EINVAL;
+  if (h->last_cycle < 1) return KRYLOV_EINVAL;
+  const int me = h->last_me, nc = h->last_nc, M = h->m;
+  if (m_eff) *m_eff = me;
+  if (T) {
+    if (T_cap < (int64_t)nc * nc) return KRYLOV_EINVAL;
+    std::vector<double> tw((size_t)h->s * nc);
+    CK(cudaMemcpy(tw.data(), h->sd.Tw, sizeof(double) * tw.size(), cudaMemcpyDeviceToHost));
+    for (int b = 0; b < nc; ++b)
+      for (int a = 0; a < nc; ++a) T[(size_t)b * nc + a] = (a <= b) ? tw[(size_t)b * h->s + a] : 0.0;
+  }
+  if (X) {
+    if (X_cap < (int64_t)me * me) return KRYLOV_EINVAL;
+    std::vector<double> xb((size_t)M * M);
+    CK(cudaMemcpy(xb.data(), h->sd.Xblk + (size_t)(h->last_cycle - 1) * M * M, sizeof(double) * xb.size(),
+                  cudaMemcpyDeviceToHost));
+    for (int b = 0; b < me; ++b)
+      for (int a = 0; a < me; ++a) X[(size_t)b * me + a] = xb[(size_t)b * M + a];
+  }
+  if (z) {
+    if (z_cap < me) return KRYLOV_EINVAL;
+    CK(cudaMemcpy(z, h->sd.zg, sizeof(double) * me, cudaMemcpyDeviceToHost));
+  }
+  return KRYLOV_OK;
+}
+
+}  // extern "C"

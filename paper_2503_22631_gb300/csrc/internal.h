@@ -1,0 +1,96 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace krylov {
+
+// Per-cycle device state written by the step kernels' reducers and read by the
+// following kernels (all device memory, owned by the handle).
+struct CycleDev {
+  int* flags;      // [0] m_eff, [1] breakdown, [2] error bits, [3] spare
+  double* sig2;    // (m+1) squared norms of the stored basis vectors
+  double* pi;      // (m+1) squared norms of the raw products A w_j
+  double* coef;    // (m+1) x (MAX_WINDOW+1): window coefficients then rho
+  double* R;       // (m+1) x m column-major, leading dimension m+1
+  double* scal;    // [0] eta, [1] 1/eta, [2] ||y||^2, [3] ||x||^2, [4] ||b||^2
+  unsigned* counter;  // arrival counters of the last-block reducers (zeroed)
+};
+
+enum : int { ERR_SKETCH = 1, ERR_NONFINITE = 2 };
+
+struct StepLaunch {
+  int n;
+  const int* row_ptr;
+  const int* col;
+  const void* val;   // double or float (narrowed)
+  int val_f32;       // 1 if val is float
+  void* W;           // basis slots, slot stride ldw elements
+  int64_t ldw;
+  int j;             // column handled by this launch
+  int k;             // window
+  int mat;           // 1: materialize column j from p_prev; 0: column j already stored
+  int spmv;          // 1: form p_j = A w_j and the window dots
+  const void* p_prev;
+  void* p_out;
+  void* sk_part;     // sketch partials of column j: [grid][s] (double or float)
+  double* part;      // scalar partials [grid][2 + MAX_WINDOW]
+  double thr;        // breakdown threshold (relative)
+  int s, zeta;
+  uint64_t seed;
+  int grid;          // number of CTAs (persistent)
+  int rows_per_cta;
+};
+
+// basis dtype codes (krylov_basis)
+void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
+void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st);
+void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& cd, int grid,
+                  cudaStream_t st);
+void launch_update(int basis, void* W, int64_t ldw, int n, int m_eff, int has_next,
+                   const double* zg, double* x, double* part, int grid, const CycleDev& cd, int m,
+                   cudaStream_t st);
+void launch_sketch_reduce(int basis, const void* sk_part, int ncols, int grid, int s, int zeta,
+                          int64_t col_stride, double* U, cudaStream_t st);
+void launch_spmv_f64(int n, const int* row_ptr, const int* col, const double* val, const double* x,
+                     double* y, cudaStream_t st);
+void launch_dot_f64(const double* a, const double* b, int n, double* part, int grid, double* out,
+                    unsigned* counter, cudaStream_t st);
+void launch_sketch_columns(int64_t col0, int64_t count, int s, int zeta, uint64_t seed, int* rows,
+                           signed char* signs, int* err, cudaStream_t st);
+
+// ---- handle creation ------------------------------------------------------
+cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* d_flag, int* h_flag,
+                         cudaStream_t st);
+cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag,
+                          cudaStream_t st);
+cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
+                          int* cit, double* vt, int* work, cudaStream_t st);
+void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st);
+
+// ---- small projected problem (FP64) ---------------------------------------
+struct SmallDev {
+  double* U;       // s x (m+1) sketched basis (column-major)
+  double* Tw;      // s x (m+1) Householder work / T on output (leading dim s)
+  double* Tinv;    // m x m
+  double* zg;      // [0,m) z, [m,2m) g, [2m] 1/tau
+  double* Xblk;    // cycles x (m x m): diagonal blocks X^{(c)}
+  double* gam;     // cycles: coupling gamma^{(c)} between block c and c+1
+  double* misc;    // [0] beta, [1] rho of the last cycle, [2] ||tX||_1 of the last cycle,
+                   // [3] |t gamma| of the last coupling, [4] kappa estimate of T,
+                   // [5] last entry of the previous inverse block solve (f = 1/z)
+  double* G;       // exp block rows, all scale levels
+  double* S0;      // Horner ping-pong buffers (2 x cycles x m x m)
+  double* fcol;    // m: first column of the last block row of f(H)
+};
+
+void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
+                   int has_next, int cycle, double t, cudaStream_t st);
+void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first,
+                            int last, int src, double* dst, cudaStream_t st);
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride,
+                       cudaStream_t st);
+void launch_inv_block(const SmallDev& sd, int m, int a, cudaStream_t st);
+void launch_z(const SmallDev& sd, int m, int m_eff, const double* fcol_src, cudaStream_t st);
+
+}  // namespace krylov

@@ -1,0 +1,152 @@
+// kernels.cuh -- device-side building blocks shared by the library's kernels.
+//
+// Contents
+//  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the sparse sign
+//    column generator of Sec. 2.1, Eq. (3): zeta distinct rows per column,
+//    uniform, Rademacher signs.  The exact word-to-entry mapping (fixed so the
+//    host-side reference implementation can reproduce S bit for bit) is:
+//      counter (j, block, 0, 0), key (seed lo, seed hi); each output word is
+//      split into two 16-bit chunks, low half first; a chunk c proposes row
+//      (c & 0x7FFF) mod s with sign bit c >> 15; the proposal is rejected when
+//      (c & 0x7FFF) >= 32768 - (32768 mod s) or when the row was already taken
+//      by this column; at most SKETCH_MAX_BLOCKS counter blocks per column.
+//  * storage-type conversions for the basis (float64 / float32 / bfloat16).
+//  * the deterministic "last block reduces" pattern used by the step kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace krylov {
+
+constexpr int SKETCH_MAX_BLOCKS = 64;
+constexpr int MAX_WINDOW = 4;       // k <= 4 (orthogonalization window)
+constexpr int STEP_THREADS = 256;   // threads per CTA of the streaming kernels
+constexpr int MAX_ZETA = 32;
+
+struct Philox4 {
+  uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+// Ten Philox rounds on counter c with key (k0, k1).
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(Philox4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t MA = 0xD2511F53u, MB = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = mulhi32(MA, c.x), lo0 = MA * c.x;
+    const uint32_t hi1 = mulhi32(MB, c.z), lo1 = MB * c.z;
+    Philox4 o;
+    o.x = hi1 ^ c.y ^ k0;
+    o.y = lo1;
+    o.z = hi0 ^ c.w ^ k1;
+    o.w = lo0;
+    c = o;
+  }
+  return c;
+}
+
+struct SketchSpec {
+  int s;          // rows of S
+  int zeta;       // nonzeros per column
+  uint32_t lim;   // 32768 - 32768 % s
+  uint32_t k0, k1;
+  float scale;    // 1/sqrt(zeta)
+};
+
+// Generate column j of S.  Calls emit(row, negative) once per accepted entry,
+// in acceptance order.  Returns the number of entries produced (== zeta unless
+// the block budget ran out, which the caller reports as an error).
+template <int ZMAX, typename Emit>
+__host__ __device__ __forceinline__ int sketch_column(uint32_t j, const SketchSpec& sp, Emit&& emit) {
+  int rows[ZMAX];
+  int cnt = 0;
+  for (uint32_t blk = 0; blk < (uint32_t)SKETCH_MAX_BLOCKS && cnt < sp.zeta; ++blk) {
+    const Philox4 w = philox4x32_10(Philox4{j, blk, 0u, 0u}, sp.k0, sp.k1);
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t ch = (words[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+      const uint32_t v = ch & 0x7FFFu;
+      if (cnt < sp.zeta && v < sp.lim) {
+        const int row = (int)(v % (uint32_t)sp.s);
+        bool dup = false;
+#pragma unroll
+        for (int e = 0; e < ZMAX; ++e) dup |= (e < cnt) && (rows[e] == row);
+        if (!dup) {
+#pragma unroll
+          for (int e = 0; e < ZMAX; ++e)
+            if (e == cnt) rows[e] = row;
+          emit(row, (ch >> 15) != 0u);
+          ++cnt;
+        }
+      }
+    }
+  }
+  return cnt;
+}
+
+// ---- storage conversions --------------------------------------------------
+template <typename T> struct Store;
+template <> struct Store<double> {
+  __device__ __forceinline__ static double load(const double* p) { return *p; }
+  __device__ __forceinline__ static double round_f64(double v) { return v; }
+  __device__ __forceinline__ static float round_f32(float v) { return v; }
+  __device__ __forceinline__ static void put(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+  __device__ __forceinline__ static float load(const float* p) { return *p; }
+  __device__ __forceinline__ static void put(float* p, float v) { *p = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+  __device__ __forceinline__ static float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ __forceinline__ static void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Value of a number after a round trip through storage type T.
+template <typename T, typename A> __device__ __forceinline__ A stored(A v);
+template <> __device__ __forceinline__ double stored<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float stored<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ float stored<__nv_bfloat16, float>(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+template <typename A> __device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum in a fixed order (warp shuffles, then warp 0 over the warp
+// partials).  Result valid in thread 0.  `sh` holds >= 32 entries.
+template <typename A> __device__ __forceinline__ A block_sum(A v, A* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  A r = 0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : A(0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+}  // namespace krylov

@@ -1,0 +1,135 @@
+// setup_kernels.cu -- one-time work at handle creation: CSR validation, the
+// lossless float32 narrowing test of the matrix values, and the device-side
+// transpose used by the adjoint (counting sort by column, then each row of
+// A^T sorted by the original row index, so the result is deterministic).
+#include <algorithm>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace krylov {
+namespace {
+
+__global__ void validate_kernel(int n, int64_t nnz, const int* rp, const int* ci, int* bad) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = tid; i < n; i += stride) {
+    const int a = rp[i], b = rp[i + 1];
+    if (b < a || a < 0 || (int64_t)b > nnz) atomicOr(bad, 1);
+  }
+  if (tid == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicOr(bad, 2);
+  for (int64_t e = tid; e < nnz; e += stride) {
+    const int c = ci[e];
+    if (c < 0 || c >= n) atomicOr(bad, 4);
+  }
+}
+
+__global__ void narrow_kernel(int64_t nnz, const double* v, float* v32, int* inexact) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const float f = __double2float_rn(v[e]);
+    v32[e] = f;
+    if ((double)f != v[e]) atomicOr(inexact, 1);
+  }
+}
+
+__global__ void count_cols_kernel(int64_t nnz, const int* ci, int* cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) atomicAdd(&cnt[ci[e]], 1);
+}
+
+// Exclusive scan of n counts into rp (n+1) by one CTA: chunked serial sums.
+__global__ void scan_kernel(int n, const int* cnt, int* rp) {
+  __shared__ long long part[1024];
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int chunk = (n + T - 1) / T;
+  const int a = tid * chunk, b = min(n, a + chunk);
+  long long s = 0;
+  for (int i = a; i < b; ++i) s += cnt[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    long long acc = 0;
+    for (int t = 0; t < T; ++t) {
+      const long long v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+  }
+  __syncthreads();
+  long long acc = part[tid];
+  for (int i = a; i < b; ++i) {
+    rp[i] = (int)acc;
+    acc += cnt[i];
+  }
+  if (tid == T - 1) rp[n] = (int)acc;
+}
+
+__global__ void scatter_kernel(int n, const int* rp, const int* ci, const double* v, const int* rpt, int* cursor,
+                               int* cit, double* vt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int c = ci[e];
+      const int pos = rpt[c] + atomicAdd(&cursor[c], 1);
+      cit[pos] = i;
+      vt[pos] = v[e];
+    }
+  }
+}
+
+__global__ void sort_rows_kernel(int n, const int* rpt, int* cit, double* vt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int a = rpt[i], b = rpt[i + 1];
+    for (int e = a + 1; e < b; ++e) {
+      const int kc = cit[e];
+      const double kv = vt[e];
+      int f = e - 1;
+      while (f >= a && cit[f] > kc) {
+        cit[f + 1] = cit[f];
+        vt[f + 1] = vt[f];
+        --f;
+      }
+      cit[f + 1] = kc;
+      vt[f + 1] = kv;
+    }
+  }
+}
+
+int grid_for(int64_t work) {
+  int64_t g = (work + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 8192) g = 8192;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* d_flag, int* h_flag,
+                         cudaStream_t st) {
+  cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+  validate_kernel<<<grid_for(std::max<int64_t>(n, nnz)), 256, 0, st>>>(n, nnz, rp, ci, d_flag);
+  cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag, cudaStream_t st) {
+  cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+  if (nnz > 0) narrow_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, v, v32, d_flag);
+  cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt, int* cit,
+                          double* vt, int* work, cudaStream_t st) {
+  // work: 2n ints (counts, cursors)
+  cudaMemsetAsync(work, 0, sizeof(int) * 2 * (size_t)n, st);
+  if (nnz > 0) count_cols_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, ci, work);
+  scan_kernel<<<1, 1024, 0, st>>>(n, work, rpt);
+  scatter_kernel<<<grid_for(n), 256, 0, st>>>(n, rp, ci, v, rpt, work + n, cit, vt);
+  sort_rows_kernel<<<grid_for(n), 256, 0, st>>>(n, rpt, cit, vt);
+  return cudaGetLastError();
+}
+
+}  // namespace krylov

@@ -1,0 +1,328 @@
+// small_kernels.cu -- the FP64 projected problem of one restart cycle.
+//
+// whiten_kernel   thin Householder QR of the sketched basis U = S W_{m+1}
+//                 (only T is formed; diag(T) > 0), T_m^{-1}, the projected
+//                 matrix X = T_m R_m T_m^{-1} + (r_{m+1,m} / T_m[m,m]) t e_m^T
+//                 (App. A, Eq. A.1), g = T_m^{-1} t, tau = T[m+1,m+1], and the
+//                 restart coupling of Algorithm 2 for the whitened basis:
+//                 gamma = rho_prev T[1,1] with rho = r_{m+1,m} tau / T_m[m,m].
+// exp kernels     the last block row of exp(-t H_{cm}) for the block lower
+//                 bidiagonal H_{cm} of Algorithm 2, by scaling and squaring:
+//                 B = -t H / 2^s, Taylor polynomial of degree q in Horner form
+//                 for block row c, then s squarings that reuse the stored block
+//                 rows of earlier cycles at every scale level.  Block row c of a
+//                 square of a block lower triangular matrix needs only block
+//                 rows <= c, so each cycle adds one block row per level instead
+//                 of recomputing f(H_{cm}) from scratch; the result equals the
+//                 last block row of the full scaling-and-squaring evaluation up
+//                 to the order of the floating-point sums.
+// inv_block       f(z) = 1/z: block forward substitution for H_{cm}^{-1} e_1,
+//                 which needs only the last entry of the previous block.
+// z_kernel        z = beta T_m^{-1} F[(c-1)m+1 : cm, 1] (Algorithm 2, update y).
+#include <cmath>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace krylov {
+namespace {
+
+constexpr int SMALL_THREADS = 256;
+
+__device__ __forceinline__ double& Tat(double* Tw, int s, int a, int b) { return Tw[(size_t)b * s + a]; }
+
+__global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, CycleDev cd, int s, int M,
+                                                               int nc, int me, int has_next, int cycle,
+                                                               double t, double* scratch) {
+  __shared__ double red[32];
+  __shared__ double sh_beta_h, sh_alpha;
+  __shared__ double diag[1024];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+  double* A = sd.Tw;  // s x nc, leading dimension s
+
+  for (size_t e = tid; e < (size_t)s * nc; e += blockDim.x) A[e] = sd.U[e];
+  __syncthreads();
+
+  // ---- Householder QR, T only ----
+  for (int jj = 0; jj < nc; ++jj) {
+    double acc = 0.0;
+    for (int r = jj + tid; r < s; r += blockDim.x) acc = fma(A[(size_t)jj * s + r], A[(size_t)jj * s + r], acc);
+    const double nrm2 = block_sum(acc, red);
+    if (tid == 0) {
+      const double x0 = A[(size_t)jj * s + jj];
+      const double nx = sqrt(nrm2);
+      const double alpha = (x0 >= 0.0) ? -nx : nx;
+      const double v0 = x0 - alpha;
+      const double vn2 = nrm2 - x0 * x0 + v0 * v0;
+      A[(size_t)jj * s + jj] = v0;
+      sh_beta_h = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+      sh_alpha = alpha;
+    }
+    __syncthreads();
+    const double bh = sh_beta_h;
+    for (int l = jj + 1 + wid; l < nc; l += nwarp) {
+      double d = 0.0;
+      for (int r = jj + lane; r < s; r += 32) d = fma(A[(size_t)jj * s + r], A[(size_t)l * s + r], d);
+      d = warp_sum(d) * bh;
+      for (int r = jj + lane; r < s; r += 32) A[(size_t)l * s + r] = fma(-d, A[(size_t)jj * s + r], A[(size_t)l * s + r]);
+    }
+    __syncthreads();
+    if (tid == 0) diag[jj] = sh_alpha;
+    __syncthreads();
+  }
+  // sign fix: row a of T times sign(diag[a]); write diagonal
+  for (int e = tid; e < nc * nc; e += blockDim.x) {
+    const int a = e % nc, b = e / nc;
+    if (a < b) {
+      const double sg = (diag[a] < 0.0) ? -1.0 : 1.0;
+      Tat(A, s, a, b) *= sg;
+    }
+  }
+  __syncthreads();
+  for (int a = tid; a < nc; a += blockDim.x) Tat(A, s, a, a) = fabs(diag[a]);
+  __syncthreads();
+
+  // ---- T_m^{-1} (upper triangular), one column per thread ----
+  double* Ti = sd.Tinv;  // me x me, leading dimension M
+  for (int b = tid; b < me; b += blockDim.x) {
+    for (int a = me - 1; a > b; --a) Ti[(size_t)b * M + a] = 0.0;
+    Ti[(size_t)b * M + b] = 1.0 / Tat(A, s, b, b);
+    for (int a = b - 1; a >= 0; --a) {
+      double acc = 0.0;
+      for (int l = a + 1; l <= b; ++l) acc = fma(Tat(A, s, a, l), Ti[(size_t)b * M + l], acc);
+      Ti[(size_t)b * M + a] = -acc / Tat(A, s, a, a);
+    }
+  }
+  __syncthreads();
+
+  // ---- TR = T_m R_m (R banded upper Hessenberg) into scratch ----
+  const int ldr = M + 1;
+  for (int e = tid; e < me * me; e += blockDim.x) {
+    const int a = e % me, b = e / me;
+    double acc = 0.0;
+    const int l1 = min(b + 1, me - 1);
+    for (int l = a; l <= l1; ++l) acc = fma(Tat(A, s, a, l), cd.R[(size_t)b * ldr + l], acc);
+    scratch[(size_t)b * M + a] = acc;
+  }
+  __syncthreads();
+  // ---- X = TR T_m^{-1} + (r / T_mm) t e_m^T, zero padded to M x M ----
+  double* X = sd.Xblk + (size_t)(cycle - 1) * M * M;
+  const double r = has_next ? cd.R[(size_t)(me - 1) * ldr + me] : 0.0;
+  const double rt = has_next ? r / Tat(A, s, me - 1, me - 1) : 0.0;
+  for (int e = tid; e < M * M; e += blockDim.x) {
+    const int a = e % M, b = e / M;
+    double acc = 0.0;
+    if (a < me && b < me) {
+      for (int l = 0; l <= b; ++l) acc = fma(scratch[(size_t)l * M + a], Ti[(size_t)b * M + l], acc);
+      if (b == me - 1 && has_next) acc = fma(rt, Tat(A, s, a, me), acc);
+    }
+    X[e] = acc;
+  }
+  __syncthreads();
+  // ---- g = T_m^{-1} t, tau, norms ----
+  for (int a = tid; a < me; a += blockDim.x) {
+    double acc = 0.0;
+    if (has_next)
+      for (int l = a; l < me; ++l) acc = fma(Ti[(size_t)l * M + a], Tat(A, s, l, me), acc);
+    sd.zg[M + a] = acc;
+  }
+  // column sums of |X| for ||tX||_1, and ||T||_1 ||T^{-1}||_1 for the condition estimate
+  double cmax = 0.0, tmax = 0.0, timax = 0.0;
+  for (int b = tid; b < me; b += blockDim.x) {
+    double cs = 0.0, ts = 0.0, tis = 0.0;
+    for (int a = 0; a < me; ++a) {
+      cs += fabs(X[(size_t)b * M + a]);
+      if (a <= b) {
+        ts += fabs(Tat(A, s, a, b));
+        tis += fabs(Ti[(size_t)b * M + a]);
+      }
+    }
+    cmax = fmax(cmax, cs);
+    tmax = fmax(tmax, ts);
+    timax = fmax(timax, tis);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    timax = fmax(timax, __shfl_xor_sync(0xffffffffu, timax, o));
+  }
+  __shared__ double wmax[3][32];
+  if (lane == 0) {
+    wmax[0][wid] = cmax;
+    wmax[1][wid] = tmax;
+    wmax[2][wid] = timax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double c0 = 0, c1 = 0, c2 = 0;
+    for (int w = 0; w < nwarp; ++w) {
+      c0 = fmax(c0, wmax[0][w]);
+      c1 = fmax(c1, wmax[1][w]);
+      c2 = fmax(c2, wmax[2][w]);
+    }
+    const double T11 = Tat(A, s, 0, 0);
+    double* misc = sd.misc;
+    if (cycle == 1) {
+      misc[0] = cd.scal[0] * T11;  // beta = ||b|| T[1,1]
+      misc[3] = 0.0;
+    } else {
+      const double gam = misc[1] * T11;  // gamma of the previous coupling
+      sd.gam[cycle - 2] = gam;
+      misc[3] = fabs(t * gam);
+    }
+    if (has_next) {
+      const double tau = Tat(A, s, me, me);
+      misc[1] = r * tau / Tat(A, s, me - 1, me - 1);
+      sd.zg[2 * M] = 1.0 / tau;
+    } else {
+      misc[1] = 0.0;
+      sd.zg[2 * M] = 0.0;
+    }
+    misc[2] = fabs(t) * c0;
+    misc[4] = c1 * c2;
+    bool ok = isfinite(c0) && isfinite(c1) && isfinite(c2) && isfinite(misc[0]) && isfinite(misc[1]);
+    if (!ok) cd.flags[2] |= ERR_NONFINITE;
+  }
+}
+
+// One Horner step for block row a of T_q(B), B = scale * H (scale = -t/2^s):
+//   S_new[j] = (S_old[j] X_j scale + S_old[j+1](:,1) scale gamma_j e_m^T) / kdeg + E[j]
+// with E the block row of the identity (E[a] = I).  first: S_old = E.
+__global__ void exp_taylor_kernel(const double* __restrict__ Xblk, const double* __restrict__ gam, int M,
+                                  int a, double kinv, double scale, int first, const double* __restrict__ Sold,
+                                  double* __restrict__ Snew) {
+  const int j = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > a || e >= M * M) return;
+  const int r = e % M, col = e / M;
+  const double* Xj = Xblk + (size_t)j * M * M;
+  double acc = 0.0;
+  if (first) {
+    if (j == a) acc = Xj[(size_t)col * M + r] * scale;
+    if (j + 1 == a && col == M - 1 && r == 0) acc += scale * gam[j];
+  } else {
+    const double* Sj = Sold + (size_t)j * M * M;
+    for (int l = 0; l < M; ++l) acc = fma(Sj[(size_t)l * M + r], Xj[(size_t)col * M + l], acc);
+    acc *= scale;
+    if (col == M - 1 && j < a) acc = fma(Sold[(size_t)(j + 1) * M * M + r], scale * gam[j], acc);
+  }
+  acc *= kinv;
+  if (j == a && r == col) acc += 1.0;
+  Snew[(size_t)j * M * M + e] = acc;
+}
+
+// Squaring for block row a: N[j] = sum_{l=j}^{a} G[a][l] G[l][j], blocks of
+// the lower triangle stored row-major by (row, col) pairs.
+__global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restrict__ Go, int M, int a) {
+  const int j = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > a || e >= M * M) return;
+  const int r = e % M, col = e / M;
+  const size_t MM = (size_t)M * M;
+  const size_t rowa = (size_t)a * (a + 1) / 2;
+  double acc = 0.0;
+  for (int l = j; l <= a; ++l) {
+    const double* L = Gi + (rowa + l) * MM;                      // G[a][l]
+    const double* Rb = Gi + ((size_t)l * (l + 1) / 2 + j) * MM;  // G[l][j]
+    for (int p = 0; p < M; ++p) acc = fma(L[(size_t)p * M + r], Rb[(size_t)col * M + p], acc);
+  }
+  Go[(rowa + j) * MM + e] = acc;
+}
+
+// f(z) = 1/z: y_a = X_a^{-1} rhs, rhs = e_1 (a = 0) or -gamma_{a-1} y_{a-1}[M-1] e_1.
+// LU with partial pivoting in one CTA on a scratch copy of X_a.
+__global__ void __launch_bounds__(SMALL_THREADS) inv_block_kernel(SmallDev sd, int M, int a, double* work) {
+  __shared__ double y[1024];
+  __shared__ int piv;
+  const int tid = threadIdx.x;
+  const double* X = sd.Xblk + (size_t)a * M * M;
+  for (int e = tid; e < M * M; e += blockDim.x) work[e] = X[e];
+  const double rhs0 = (a == 0) ? 1.0 : -sd.gam[a - 1] * sd.misc[5];
+  for (int r = tid; r < M; r += blockDim.x) y[r] = (r == 0) ? rhs0 : 0.0;
+  __syncthreads();
+  for (int c = 0; c < M; ++c) {
+    if (tid == 0) {
+      int p = c;
+      double best = fabs(work[(size_t)c * M + c]);
+      for (int r = c + 1; r < M; ++r) {
+        const double v = fabs(work[(size_t)c * M + r]);
+        if (v > best) {
+          best = v;
+          p = r;
+        }
+      }
+      piv = p;
+      if (p != c) {
+        for (int l = 0; l < M; ++l) {
+          const double tmp = work[(size_t)l * M + c];
+          work[(size_t)l * M + c] = work[(size_t)l * M + p];
+          work[(size_t)l * M + p] = tmp;
+        }
+        const double ty = y[c];
+        y[c] = y[p];
+        y[p] = ty;
+      }
+    }
+    __syncthreads();
+    const double d = work[(size_t)c * M + c];
+    for (int r = c + 1 + tid; r < M; r += blockDim.x) {
+      const double f = work[(size_t)c * M + r] / d;
+      for (int l = c + 1; l < M; ++l) work[(size_t)l * M + r] = fma(-f, work[(size_t)l * M + c], work[(size_t)l * M + r]);
+      y[r] = fma(-f, y[c], y[r]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int r = M - 1; r >= 0; --r) {
+      double acc = y[r];
+      for (int l = r + 1; l < M; ++l) acc = fma(-work[(size_t)l * M + r], y[l], acc);
+      y[r] = acc / work[(size_t)r * M + r];
+    }
+    sd.misc[5] = y[M - 1];
+  }
+  __syncthreads();
+  for (int r = tid; r < M; r += blockDim.x) sd.fcol[r] = y[r];
+}
+
+__global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc) {
+  const double beta = sd.misc[0];
+  for (int a = threadIdx.x; a < me; a += blockDim.x) {
+    double acc = 0.0;
+    for (int l = a; l < me; ++l) acc = fma(sd.Tinv[(size_t)l * M + a], fsrc[l], acc);
+    sd.zg[a] = beta * acc;
+  }
+}
+
+}  // namespace
+
+void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff, int has_next,
+                   int cycle, double t, cudaStream_t st) {
+  // scratch for T_m R_m: reuse the Horner buffer area (not in use at this point)
+  whiten_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0);
+}
+
+void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first, int last,
+                            int src, double* dst, cudaStream_t st) {
+  (void)last;
+  const int MM = m * m;
+  dim3 g((MM + 127) / 128, a + 1);
+  const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
+  exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst);
+}
+
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st) {
+  const int MM = m * m;
+  dim3 g((MM + 127) / 128, a + 1);
+  exp_square_kernel<<<g, 128, 0, st>>>(sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride,
+                                      m, a);
+}
+
+void launch_inv_block(const SmallDev& sd, int m, int a, cudaStream_t st) {
+  inv_block_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, m, a, sd.S0);
+}
+
+void launch_z(const SmallDev& sd, int m, int m_eff, const double* fcol_src, cudaStream_t st) {
+  z_kernel<<<1, 256, 0, st>>>(sd, m, m_eff, fcol_src);
+}
+
+}  // namespace krylov

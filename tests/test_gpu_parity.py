@@ -1,0 +1,135 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (relative 2-norm of the result): 1e-10 with a float64 basis,
+1e-5 with a float32 basis, 1e-3 with a bfloat16 basis; sketch rows and signs
+bit-exact.  Parity runs use a fixed number of cycles (tol = 0) on both sides so
+that no early-exit decision can differ.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dense as D
+from oracle import krylov as K
+from oracle import sketch as OS
+from oracle import truth as TR
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-5, 2: 1e-3}
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _gpu(A, b, fkind, t, m, k, s, zeta, seed, cycles, basis=0, adjoint=False, tol=0.0):
+    import torch
+
+    from paper_2503_22631_gb300 import Krylov
+
+    kr = Krylov(A.row_ptr, A.col_idx, A.val, f=fkind, t=t, m=m, k=k, s=s, seed=seed, zeta=zeta, basis=basis)
+    x = kr.apply(torch.from_numpy(b).cuda(), tol=tol, max_cycles=cycles, adjoint=adjoint)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), kr
+
+
+@pytest.mark.parametrize("n,s,zeta,col0", [(5000, 60, 8, 0), (3000, 160, 8, 1 << 20), (2000, 17, 4, 7),
+                                           (1000, 40, 32, 0), (4097, 200, 1, 123456)])
+def test_sketch_columns_bit_exact(lib, cuda, n, s, zeta, col0):
+    from paper_2503_22631_gb300 import sketch_columns
+
+    seed = 0x1234_5678_9ABC_DEF0
+    rows, signs = sketch_columns(col0 + n, s, zeta, seed, col0=col0, count=n)
+    orows, osigns = OS.sketch_columns(col0 + n, s, zeta, seed, cols=np.arange(col0, col0 + n))
+    assert np.array_equal(rows, orows)
+    assert np.array_equal(signs.astype(np.float64), osigns)
+
+
+@pytest.mark.parametrize("cycles", [1, 2, 3])
+def test_poisson2d_fp64_parity(lib, cuda, cycles):
+    A = W.poisson2d(64)
+    b = W.rhs_normal(A.n, W.SEED, normalize=True)
+    args = (D.EXP_NEG, 1e-3, 30, 2, 60, 8, 99)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=cycles)
+    x, _ = _gpu(A, b, *args, cycles)
+    assert _rel(x, ref.x) <= TOL[0]
+
+
+def test_poisson2d_converges_to_closed_form(lib, cuda):
+    N = 64
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 24, 3)
+    x, kr = _gpu(A, b, D.EXP_NEG, 1e-3, 30, 2, 60, 8, 5, cycles=20, tol=1e-12)
+    exact = TR.sine_mode_exp(N, c, p, q, 1e-3)
+    assert _rel(x, exact) <= 1e-10
+
+
+@pytest.mark.parametrize("basis", [1, 2])
+def test_reduced_precision_basis(lib, cuda, basis):
+    A = W.convdiff3d(24, (50.0, 50.0, 50.0))
+    b = W.rhs_uniform(A.n, 4)
+    args = (D.EXP_NEG, 2e-4, 24, 2, 96, 8, 17)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=3)
+    x, _ = _gpu(A, b, *args, 3, basis=basis)
+    assert _rel(x, ref.x) <= TOL[basis]
+
+
+def test_convdiff_fp64_parity_cycles(lib, cuda):
+    A = W.convdiff3d(20, (50.0, 50.0, 50.0))
+    b = W.rhs_uniform(A.n, 8)
+    args = (D.EXP_NEG, 1e-3, 20, 2, 80, 8, 23)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=4)
+    x, _ = _gpu(A, b, *args, 4)
+    assert _rel(x, ref.x) <= TOL[0]
+
+
+def test_inverse_function(lib, cuda):
+    A = W.convdiff(24, 2, (10.0, 5.0))
+    b = W.rhs_normal(A.n, 2)
+    args = (D.INV, 1.0, 30, 2, 90, 8, 3)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=3)
+    x, _ = _gpu(A, b, *args, 3)
+    assert _rel(x, ref.x) <= TOL[0]
+
+
+def test_breakdown_single_mode(lib, cuda):
+    N = 32
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 1, 9)
+    x, kr = _gpu(A, b, D.EXP_NEG, 1e-3, 10, 2, 30, 8, 1, cycles=5)
+    assert kr.stats["breakdown"] == 1
+    assert _rel(x, TR.sine_mode_exp(N, c, p, q, 1e-3)) <= 1e-12
+
+
+def test_adjoint_matches_oracle_on_transpose(lib, cuda):
+    A = W.convdiff3d(16, (20.0, 0.0, 0.0))
+    b = W.rhs_normal(A.n, 5)
+    args = (D.EXP_NEG, 2e-3, 20, 2, 80, 8, 41)
+    ref = K.restarted(A.transpose(), b, *args, mode=K.TRUNC, tol=0.0, max_cycles=3)
+    x, _ = _gpu(A, b, *args, 3, adjoint=True)
+    assert _rel(x, ref.x) <= TOL[0]
+
+
+def test_small_problem_matches_oracle(lib, cuda):
+    A = W.poisson2d(40)
+    b = W.rhs_normal(A.n, 6, normalize=True)
+    args = (D.EXP_NEG, 1e-3, 16, 2, 40, 8, 77)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=1, keep=True)
+    x, kr = _gpu(A, b, *args, 1)
+    T, X, z, me = kr.last_cycle()
+    ci = ref.info[0]
+    assert me == ci.m_eff
+    assert np.allclose(T, ci.T, rtol=1e-11, atol=1e-11 * np.abs(ci.T).max())
+    assert _rel(X, ci.X) <= 1e-10
+    assert _rel(z, ci.z) <= 1e-10
+
+
+@pytest.mark.parametrize("N", [1, 2, 5])
+def test_tiny_exact_when_m_exceeds_n(lib, cuda, N):
+    A = W.poisson2d(N)
+    b = W.rhs_normal(A.n, 1)
+    m = A.n + 2
+    x, kr = _gpu(A, b, D.EXP_NEG, 1e-2, m, 2, m + 8, 4, 2, cycles=3)
+    exact = TR.dense_fAb(A.to_dense(), b, D.EXP_NEG, 1e-2, symmetric=True)
+    assert _rel(x, exact) <= 1e-10
