@@ -100,6 +100,10 @@ typedef struct {
   double kappa_T_max;      /* max over cycles of cond_1 estimate of T (whitening) */
   double ms_total;         /* wall time of the call measured with CUDA events */
   double bytes_moved;      /* algorithmic HBM bytes of the call (roofline model) */
+  int launches;            /* kernels launched by the call */
+  int step_launches;       /* launches of the fused step kernel */
+  double ms_steps;         /* device time of the step-kernel phases (CUDA events) */
+  double step_bytes;       /* algorithmic HBM bytes of those phases */
 } krylov_stats;
 
 /* Fill *opt with the defaults listed above. */

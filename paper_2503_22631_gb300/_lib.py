@@ -67,7 +67,8 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("breakdown", C.c_int), ("steps", C.c_int),
                 ("last_update_norm", C.c_double), ("x_norm", C.c_double), ("kappa_T_max", C.c_double),
-                ("ms_total", C.c_double), ("bytes_moved", C.c_double)]
+                ("ms_total", C.c_double), ("bytes_moved", C.c_double), ("launches", C.c_int),
+                ("step_launches", C.c_int), ("ms_steps", C.c_double), ("step_bytes", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -68,6 +68,9 @@ struct krylov_handle {
   int64_t level_stride = 0;
   int* d_flag = nullptr;
   double* d_dot = nullptr;
+  double* stage_b = nullptr;  // device staging of krylov_apply_host
+  double* stage_x = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
 
   // host mirrors
   int* h_flags = nullptr;     // pinned: flags[4]
@@ -143,7 +146,8 @@ int scale_levels_for(double normH) {
 }
 
 // Block row a of exp(-t H) at all scale levels 0..sl (scale 2^-sl).
-void exp_row(krylov_handle* h, int a, int sl) {
+// Returns the number of kernels launched.
+int exp_row(krylov_handle* h, int a, int sl) {
   const int M = h->m;
   const size_t MM = (size_t)M * M;
   const double scale = -h->f.t / std::ldexp(1.0, sl);
@@ -156,6 +160,7 @@ void exp_row(krylov_handle* h, int a, int sl) {
     src = 1 - src;
   }
   for (int lv = 0; lv < sl; ++lv) launch_exp_square(h->sd, M, a, lv, h->level_stride, h->st);
+  return EXP_TAYLOR_DEG + sl;
 }
 
 struct Operator {
@@ -217,6 +222,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
   CK(cudaMemsetAsync(h->cd.flags, 0, 4 * sizeof(int), st));
   CK(cudaMemsetAsync(h->sd.misc, 0, 8 * sizeof(double), st));
   launch_norm_b(b, n, h->part, h->grid, h->cd, st);
+  stats.launches += 1;
   CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -228,6 +234,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
     return KRYLOV_OK;
   }
   launch_start(basis, b, h->W, n, h->cd, h->grid, st);
+  stats.launches += 1;
 
   const double thr = (basis == 0) ? 1e-14 : 1e-6;
   int s_lv = -1;        // scale levels in use (exp)
@@ -235,6 +242,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
   krylov_status result = KRYLOV_NOT_CONVERGED;
   for (int c = 1; c <= max_cycles; ++c) {
     launch_cycle_reset(h->cd, M, st);
+    CK(cudaEventRecord(h->ev[0], st));
     for (int j = 0; j <= M; ++j) {
       StepLaunch L{};
       L.n = n;
@@ -258,8 +266,12 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       L.seed = h->seed;
       L.grid = h->grid;
       L.rows_per_cta = (n + h->grid - 1) / h->grid;
+      L.m = M;
       launch_step(basis, L, h->cd, M, st);
     }
+    CK(cudaEventRecord(h->ev[1], st));
+    stats.launches += M + 2;
+    stats.step_launches += M + 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -271,8 +283,15 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
     const int has_next = brk ? 0 : 1;
     const int nc = me + has_next;
     stats.steps += me;
+    {
+      float ms_s = 0.f;
+      CK(cudaEventElapsedTime(&ms_s, h->ev[0], h->ev[1]));
+      stats.ms_steps += ms_s;
+      stats.step_bytes += me * model_bytes_step(h, use32);
+    }
     launch_sketch_reduce(basis, h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
     launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->f.t, st);
+    stats.launches += 2;
     const int a = c - 1;
     if (h->f.kind == KRYLOV_F_EXP_NEG) {
       CK(cudaMemcpyAsync(h->h_scal, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -286,19 +305,22 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
         s_lv = need;
         cs = ensure_small_capacity(h, max_cycles, s_lv + 1);
         if (cs != KRYLOV_OK) return cs;
-        for (int ap = 0; ap < a; ++ap) exp_row(h, ap, s_lv);
+        for (int ap = 0; ap < a; ++ap) stats.launches += exp_row(h, ap, s_lv);
       }
-      exp_row(h, a, s_lv);
+      stats.launches += exp_row(h, a, s_lv);
       const size_t MM = (size_t)M * M;
       const double* fsrc = h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
       launch_z(h->sd, M, me, fsrc, st);
+      stats.launches += 1;
     } else if (h->f.kind == KRYLOV_F_INV) {
       launch_inv_block(h->sd, M, a, st);
       launch_z(h->sd, M, me, h->sd.fcol, st);
+      stats.launches += 2;
     } else {
       return KRYLOV_EUNSUPPORTED;
     }
     launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid, h->cd, M, st);
+    stats.launches += 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -373,6 +395,8 @@ void krylov_destroy(krylov_handle* h) {
   if (!h) return;
   for (void* p : h->allocs)
     if (p) cudaFree(p);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   delete h;
@@ -440,8 +464,12 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(narrow_values(nnz, h->val, h->val32, h->d_flag, h->h_flags, h->st));
   h->vals_exact_f32 = (h->h_flags[0] == 0);
 
-  // workspaces
-  h->grid = std::max(1, std::min(h->num_sms * 4, (n + STEP_THREADS - 1) / STEP_THREADS));
+  if (cudaEventCreate(&h->ev[0]) != cudaSuccess || cudaEventCreate(&h->ev[1]) != cudaSuccess)
+    return fail(KRYLOV_ECUDA);
+  // workspaces: one persistent wave of the step kernel
+  h->grid = std::max(1, std::min(h->num_sms * step_ctas_per_sm(opt.basis_dtype, opt.zeta, s, h->vals_exact_f32 &&
+                                                                                              opt.narrow_values_if_exact),
+                                 (n + STEP_THREADS - 1) / STEP_THREADS));
   const int bb = basis_bytes(opt.basis_dtype);
   h->ldw = ((int64_t)n + 63) / 64 * 64;
   CKF(cudaMalloc(&h->W, (size_t)(m + 1) * h->ldw * bb));
@@ -490,21 +518,20 @@ krylov_status krylov_apply_adjoint(krylov_handle* h, const double* b, double* x,
 krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* x_host, double tol,
                                 int max_cycles, krylov_stats* st) {
   if (!h || !b_host || !x_host) return KRYLOV_EINVAL;
-  double *db = nullptr, *dx = nullptr;
+  if (!h->stage_b) {
+    CK(dalloc(h, &h->stage_b, (size_t)h->n));
+    CK(dalloc(h, &h->stage_x, (size_t)h->n));
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, h->st));
-  CK(cudaMalloc(&db, sizeof(double) * (size_t)h->n));
-  if (cudaMalloc(&dx, sizeof(double) * (size_t)h->n) != cudaSuccess) {
-    cudaFree(db);
-    return KRYLOV_ENOMEM;
-  }
   krylov_status r = KRYLOV_ECUDA;
-  if (cudaMemcpyAsync(db, b_host, sizeof(double) * (size_t)h->n, cudaMemcpyHostToDevice, h->st) == cudaSuccess) {
-    r = apply_impl(h, 0, db, dx, tol, max_cycles, st);
-    if (r >= 0 &&
-        cudaMemcpyAsync(x_host, dx, sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+  if (cudaMemcpyAsync(h->stage_b, b_host, sizeof(double) * (size_t)h->n, cudaMemcpyHostToDevice, h->st) ==
+      cudaSuccess) {
+    r = apply_impl(h, 0, h->stage_b, h->stage_x, tol, max_cycles, st);
+    if (r >= 0 && cudaMemcpyAsync(x_host, h->stage_x, sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToHost,
+                                  h->st) != cudaSuccess)
       r = KRYLOV_ECUDA;
   }
   cudaEventRecord(e1, h->st);
@@ -514,8 +541,6 @@ krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* 
   if (st) st->ms_total = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(db);
-  cudaFree(dx);
   return r;
 }
 

@@ -40,9 +40,11 @@ struct StepLaunch {
   uint64_t seed;
   int grid;          // number of CTAs (persistent)
   int rows_per_cta;
+  int m;             // restart length (leading dimension of R is m+1)
 };
 
 // basis dtype codes (krylov_basis)
+int step_ctas_per_sm(int basis, int zeta, int s, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
 void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st);
 void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& cd, int grid,

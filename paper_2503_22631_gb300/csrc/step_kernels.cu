@@ -52,8 +52,10 @@ __device__ __forceinline__ void reducer_step(const StepLaunch& L, const CycleDev
   const double sig2 = tot[0];
   cd.sig2[j] = sig2;
   if (!isfinite(sig2)) cd.flags[2] |= ERR_NONFINITE;
+  const int ldr = L.m + 1;  // R is (m+1) x m, column-major
   if (mat) {
     const double rho = cd.coef[(size_t)(j - 1) * (MAX_WINDOW + 1) + MAX_WINDOW];
+    cd.R[(size_t)(j - 1) * ldr + j] = 1.0 / rho;
     const double rnorm = sqrt(sig2) / rho;
     const double pprev = cd.pi[j - 1];
     if (!(rnorm > L.thr * sqrt(pprev))) {
@@ -77,6 +79,7 @@ __device__ __forceinline__ void reducer_step(const StepLaunch& L, const CycleDev
         const double s2 = cd.sig2[slot];
         h = (s2 > 0.0) ? tot[2 + q] / s2 : 0.0;
         est -= h * h * s2;
+        cd.R[(size_t)j * ldr + slot] = h;
       }
       c[q] = h;
     }
@@ -245,19 +248,6 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepLaunch L, 
   }
 }
 
-// Records R entries after the reducer (kept out of the hot kernel's tail):
-// R[j, j-1] = 1/rho_j and R[q, j] = h_q for the window of column j.
-__global__ void record_r_kernel(CycleDev cd, int j, int k, int m, int mat, int spmv) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int ldr = m + 1;
-  if (mat) cd.R[(size_t)(j - 1) * ldr + j] = 1.0 / cd.coef[(size_t)(j - 1) * (MAX_WINDOW + 1) + MAX_WINDOW];
-  if (spmv && cd.flags[1] == 0) {
-    const int dlo = max(0, j - k + 1);
-    for (int q = 0; dlo + q <= j && q < MAX_WINDOW; ++q)
-      cd.R[(size_t)j * ldr + dlo + q] = cd.coef[(size_t)j * (MAX_WINDOW + 1) + q];
-  }
-}
-
 template <typename VT, typename AT, bool MAT, bool SPMV>
 void launch_step_t(const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st) {
   using Sk = typename Types<VT>::Sk;
@@ -271,7 +261,6 @@ void launch_step_t(const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t 
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
   }
-  record_r_kernel<<<1, 32, 0, st>>>(cd, L.j, L.k, m, L.mat, L.spmv);
 }
 
 template <typename VT, typename AT>
@@ -428,6 +417,32 @@ __global__ void sketch_columns_kernel(int64_t col0, int64_t count, SketchSpec sp
 }
 
 }  // namespace
+
+namespace {
+template <typename VT, typename AT>
+int occupancy_t(int zeta, int s) {
+  using Sk = typename Types<VT>::Sk;
+  const size_t smem = (size_t)(STEP_THREADS / 32) * s * sizeof(Sk);
+  int blocks = 0;
+  if (zeta <= 8) {
+    auto k = step_kernel<VT, AT, true, true, 8>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, STEP_THREADS, smem);
+  } else {
+    auto k = step_kernel<VT, AT, true, true, MAX_ZETA>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, STEP_THREADS, smem);
+  }
+  return blocks < 1 ? 1 : blocks;
+}
+}  // namespace
+
+// Resident CTAs per SM of the main step kernel (one persistent wave).
+int step_ctas_per_sm(int basis, int zeta, int s, int vals_f32) {
+  if (basis == 0) return vals_f32 ? occupancy_t<double, float>(zeta, s) : occupancy_t<double, double>(zeta, s);
+  if (basis == 1) return occupancy_t<float, float>(zeta, s);
+  return occupancy_t<__nv_bfloat16, float>(zeta, s);
+}
 
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st) {
   if (basis == 0) {
