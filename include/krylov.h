@@ -76,7 +76,20 @@ typedef struct {
   int on_device;
 } krylov_csr;
 
-typedef enum { KRYLOV_BASIS_F64 = 0, KRYLOV_BASIS_F32 = 1, KRYLOV_BASIS_BF16 = 2 } krylov_basis;
+/* Storage and arithmetic of the Krylov basis and the step vectors:
+ *   F64   float64 storage, float64 arithmetic (reference precision);
+ *   F32   float32 storage and arithmetic (float64 across-CTA sums);
+ *   BF16  bfloat16 storage, float32 arithmetic;
+ *   DF64  float-float storage (hi + lo float pairs, ~48-bit significand, 8 bytes)
+ *         with float-float products, orthogonalization and sketches on the
+ *         float32 pipes: FP64-class accuracy without float64 arithmetic in the
+ *         streaming kernels. */
+typedef enum {
+  KRYLOV_BASIS_F64 = 0,
+  KRYLOV_BASIS_F32 = 1,
+  KRYLOV_BASIS_BF16 = 2,
+  KRYLOV_BASIS_DF64 = 3
+} krylov_basis;
 typedef enum { KRYLOV_ORTHO_TRUNC = 0 } krylov_ortho;
 
 typedef struct {
@@ -88,6 +101,11 @@ typedef struct {
   int use_graph;   /* capture the m steps of a cycle in a CUDA graph. Default 1 */
   int abs_tol;     /* 1: stop when ||y|| <= tol (Algorithm 2 as printed);
                       0: stop when ||y|| <= tol * ||x|| (default) */
+  int sketch_regenerate; /* 0 (default): S is generated once at create into a device table
+                            (9 bytes per column when s <= 255 and zeta <= 8) that the step
+                            kernels read; 1: the step kernels regenerate every column of S
+                            with the counter-based generator instead (no table, more
+                            arithmetic per step).  Both give bit-identical S. */
   void* stream;    /* cudaStream_t for all work; NULL = legacy default stream */
 } krylov_options;
 

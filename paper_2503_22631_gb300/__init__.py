@@ -15,11 +15,11 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (BASIS_BF16, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_EXP_NEG, F_INV, F_INVSQRT,
+from ._lib import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_EXP_NEG, F_INV, F_INVSQRT,
                    NOT_CONVERGED, OK, KrylovError, status_string)
 
 __all__ = ["Krylov", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT",
-           "BASIS_F64", "BASIS_F32", "BASIS_BF16", "OK", "NOT_CONVERGED", "BREAKDOWN_EXACT"]
+           "BASIS_F64", "BASIS_F32", "BASIS_BF16", "BASIS_DF64", "OK", "NOT_CONVERGED", "BREAKDOWN_EXACT"]
 
 _SUCCESS = (OK, NOT_CONVERGED, BREAKDOWN_EXACT)
 
@@ -39,7 +39,8 @@ class Krylov:
     """A handle: matrix A (CSR), f, restart length m, window k, sketch (s, zeta, seed)."""
 
     def __init__(self, row_ptr, col_idx, val, *, f=F_EXP_NEG, t=1.0, m=30, k=2, s=None, seed=0, zeta=8,
-                 basis=BASIS_F64, narrow_values_if_exact=True, abs_tol=False, stream=None):
+                 basis=BASIS_F64, narrow_values_if_exact=True, abs_tol=False, sketch_regenerate=False,
+                 stream=None):
         lib = _lib.load()
         torch = _torch()
         self._keep = []
@@ -68,6 +69,7 @@ class Krylov:
         opt.basis_dtype = int(basis)
         opt.narrow_values_if_exact = 1 if narrow_values_if_exact else 0
         opt.abs_tol = 1 if abs_tol else 0
+        opt.sketch_regenerate = 1 if sketch_regenerate else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

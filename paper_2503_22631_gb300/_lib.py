@@ -32,6 +32,7 @@ F_INV = 2
 BASIS_F64 = 0
 BASIS_F32 = 1
 BASIS_BF16 = 2
+BASIS_DF64 = 3
 
 EXPORTED = [
     "krylov_options_default",
@@ -61,7 +62,7 @@ class Func(C.Structure):
 class Options(C.Structure):
     _fields_ = [("zeta", C.c_int), ("basis_dtype", C.c_int), ("ortho", C.c_int),
                 ("narrow_values_if_exact", C.c_int), ("use_graph", C.c_int), ("abs_tol", C.c_int),
-                ("stream", C.c_void_p)]
+                ("sketch_regenerate", C.c_int), ("stream", C.c_void_p)]
 
 
 class Stats(C.Structure):

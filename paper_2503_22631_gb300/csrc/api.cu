@@ -47,11 +47,13 @@ struct krylov_handle {
   int* ci = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;
+  float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
   int* rpt = nullptr;
   int* cit = nullptr;
   double* valt = nullptr;
   float* valt32 = nullptr;
+  float2* valtff = nullptr;
   int have_t = 0;
 
   // cycle workspaces
@@ -71,6 +73,9 @@ struct krylov_handle {
   double* stage_b = nullptr;  // device staging of krylov_apply_host
   double* stage_x = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  SketchTable sk_tab{};
+  int sk_mode = SK_TAB8;
+  int sk_copies = 32;
 
   // host mirrors
   int* h_flags = nullptr;     // pinned: flags[4]
@@ -81,7 +86,8 @@ struct krylov_handle {
 
 namespace {
 
-int basis_bytes(int basis) { return basis == 0 ? 8 : (basis == 1 ? 4 : 2); }
+int basis_bytes(int basis) { return (basis == 0 || basis == 3) ? 8 : (basis == 1 ? 4 : 2); }
+int wide(int basis) { return basis == 0 || basis == 3; }
 
 krylov_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return KRYLOV_OK;
@@ -168,6 +174,7 @@ struct Operator {
   const int* ci;
   const double* val;
   const float* val32;
+  const float2* valff;
 };
 
 krylov_status build_transpose(krylov_handle* h) {
@@ -181,6 +188,10 @@ krylov_status build_transpose(krylov_handle* h) {
   if (h->val32) {
     CK(dalloc(h, &h->valt32, (size_t)h->nnz));
     CK(narrow_values(h->nnz, h->valt, h->valt32, h->d_flag, h->h_flags, h->st));
+  }
+  if (h->valff) {
+    CK(dalloc(h, &h->valtff, (size_t)h->nnz));
+    CK(split_values(h->nnz, h->valt, h->valtff, h->st));
   }
   CK(cudaStreamSynchronize(h->st));
   dfree(h, work);
@@ -202,9 +213,11 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
     if (s != KRYLOV_OK) return s;
   }
   const int basis = h->opt.basis_dtype;
-  const int use32 = (basis != 0) || (h->opt.narrow_values_if_exact && h->vals_exact_f32);
+  // float32 matrix values: always for the float32/bfloat16 bases, and for the
+  // wide bases only when the narrowing is lossless
+  const int use32 = (basis == 1 || basis == 2) || (h->opt.narrow_values_if_exact && h->vals_exact_f32);
   Operator op{transpose ? h->rpt : h->rp, transpose ? h->cit : h->ci, transpose ? h->valt : h->val,
-              transpose ? h->valt32 : h->val32};
+              transpose ? h->valt32 : h->val32, transpose ? h->valtff : h->valff};
   const int n = h->n, M = h->m;
   cudaStream_t st = h->st;
   krylov_stats stats{};
@@ -236,7 +249,8 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
   launch_start(basis, b, h->W, n, h->cd, h->grid, st);
   stats.launches += 1;
 
-  const double thr = (basis == 0) ? 1e-14 : 1e-6;
+  // breakdown threshold: a few hundred units of the basis arithmetic's roundoff
+  const double thr = (basis == 0) ? 1e-14 : (basis == 3 ? 1e-12 : 1e-6);
   int s_lv = -1;        // scale levels in use (exp)
   double maxX = 0.0, maxG = 0.0;
   krylov_status result = KRYLOV_NOT_CONVERGED;
@@ -248,7 +262,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       L.n = n;
       L.row_ptr = op.rp;
       L.col = op.ci;
-      L.val = use32 ? (const void*)op.val32 : (const void*)op.val;
+      L.val = use32 ? (const void*)op.val32 : (basis == 3 ? (const void*)op.valff : (const void*)op.val);
       L.val_f32 = use32;
       L.W = h->W;
       L.ldw = h->ldw;
@@ -258,7 +272,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       L.spmv = (j < M);
       L.p_prev = h->p[(j + 1) & 1];
       L.p_out = h->p[j & 1];
-      L.sk_part = (char*)h->sk_part + (size_t)j * h->sk_col_stride * (basis == 0 ? 8 : 4);
+      L.sk_part = (char*)h->sk_part + (size_t)j * h->sk_col_stride * sizeof(double);
       L.part = h->part;
       L.thr = thr;
       L.s = h->s;
@@ -267,11 +281,15 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       L.grid = h->grid;
       L.rows_per_cta = (n + h->grid - 1) / h->grid;
       L.m = M;
+      L.sk_tab = h->sk_tab;
+      L.sk_mode = h->sk_mode;
+      L.sk_copies = h->sk_copies;
+      L.fx_wb = sketch_word_bits(L.rows_per_cta, h->sk_copies);
       launch_step(basis, L, h->cd, M, st);
     }
     CK(cudaEventRecord(h->ev[1], st));
-    stats.launches += M + 2;
-    stats.step_launches += M + 1;
+    stats.launches += (basis == 3 ? 2 * M + 1 : M + 1) + 1;
+    stats.step_launches += (basis == 3 ? 2 * M + 1 : M + 1);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -289,7 +307,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       stats.ms_steps += ms_s;
       stats.step_bytes += me * model_bytes_step(h, use32);
     }
-    launch_sketch_reduce(basis, h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
+    launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
     launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->f.t, st);
     stats.launches += 2;
     const int a = c - 1;
@@ -413,7 +431,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return KRYLOV_EINVAL;
   if (m < 1 || m > 256 || k < 1 || k > MAX_WINDOW || s < m + 1 || s > 1024) return KRYLOV_EINVAL;
   if (opt.zeta < 1 || opt.zeta > std::min(s, MAX_ZETA)) return KRYLOV_EINVAL;
-  if (opt.basis_dtype < 0 || opt.basis_dtype > 2 || opt.ortho != KRYLOV_ORTHO_TRUNC) return KRYLOV_EINVAL;
+  if (opt.basis_dtype < 0 || opt.basis_dtype > 3 || opt.ortho != KRYLOV_ORTHO_TRUNC) return KRYLOV_EINVAL;
   if (f.kind != KRYLOV_F_EXP_NEG && f.kind != KRYLOV_F_INV && f.kind != KRYLOV_F_INVSQRT) return KRYLOV_EINVAL;
   if (!std::isfinite(f.t)) return KRYLOV_EINVAL;
 
@@ -463,24 +481,52 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(dalloc(h, &h->val32, (size_t)nnz));
   CKF(narrow_values(nnz, h->val, h->val32, h->d_flag, h->h_flags, h->st));
   h->vals_exact_f32 = (h->h_flags[0] == 0);
+  if (opt.basis_dtype == KRYLOV_BASIS_DF64 && !(h->vals_exact_f32 && opt.narrow_values_if_exact)) {
+    CKF(dalloc(h, &h->valff, (size_t)nnz));
+    CKF(split_values(nnz, h->val, h->valff, h->st));
+  }
 
   if (cudaEventCreate(&h->ev[0]) != cudaSuccess || cudaEventCreate(&h->ev[1]) != cudaSuccess)
     return fail(KRYLOV_ECUDA);
-  // workspaces: one persistent wave of the step kernel
-  h->grid = std::max(1, std::min(h->num_sms * step_ctas_per_sm(opt.basis_dtype, opt.zeta, s, h->vals_exact_f32 &&
-                                                                                              opt.narrow_values_if_exact),
+  // the sparse sign embedding S: a device table (default) or regenerated in
+  // every step kernel
+  const bool packed = (s <= 255 && opt.zeta <= 8);
+  h->sk_copies = sketch_bin_copies(opt.basis_dtype, s);
+  if (opt.sketch_regenerate) {
+    h->sk_mode = packed ? SK_GEN8 : SK_GEN;
+  } else {
+    h->sk_mode = packed ? SK_TAB8 : SK_TAB16;
+    h->sk_tab.packed = packed ? 1 : 0;
+    if (packed) {
+      CKF(dalloc(h, &h->sk_tab.rows8, (size_t)n));
+      CKF(dalloc(h, &h->sk_tab.neg8, (size_t)n));
+    } else {
+      CKF(dalloc(h, &h->sk_tab.rows16, (size_t)n * opt.zeta));
+      CKF(dalloc(h, &h->sk_tab.neg32, (size_t)n));
+    }
+    CKF(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
+    launch_sketch_table(n, s, opt.zeta, seed, h->sk_tab, h->d_flag, h->st);
+    CKF(cudaGetLastError());
+    CKF(cudaMemcpyAsync(h->h_flags, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CKF(cudaStreamSynchronize(h->st));
+    if (h->h_flags[0] != 0) return fail(KRYLOV_ECUDA);
+  }
+  // workspaces: one persistent wave of the step kernel(s)
+  const int vals32 = (opt.basis_dtype == 1 || opt.basis_dtype == 2) ||
+                     (h->vals_exact_f32 && opt.narrow_values_if_exact);
+  h->grid = std::max(1, std::min(h->num_sms * step_ctas_per_sm(opt.basis_dtype, h->sk_mode, s, h->sk_copies, vals32),
                                  (n + STEP_THREADS - 1) / STEP_THREADS));
   const int bb = basis_bytes(opt.basis_dtype);
   h->ldw = ((int64_t)n + 63) / 64 * 64;
   CKF(cudaMalloc(&h->W, (size_t)(m + 1) * h->ldw * bb));
   h->allocs.push_back(h->W);
-  const int pb = (opt.basis_dtype == 0) ? 8 : 4;
+  const int pb = wide(opt.basis_dtype) ? 8 : 4;
   for (int i = 0; i < 2; ++i) {
     CKF(cudaMalloc(&h->p[i], (size_t)n * pb));
     h->allocs.push_back(h->p[i]);
   }
   h->sk_col_stride = (int64_t)h->grid * s;
-  CKF(cudaMalloc(&h->sk_part, (size_t)(m + 1) * h->sk_col_stride * pb));
+  CKF(cudaMalloc(&h->sk_part, (size_t)(m + 1) * h->sk_col_stride * sizeof(double)));
   h->allocs.push_back(h->sk_part);
   CKF(dalloc(h, &h->part, (size_t)h->grid * 8));
   CKF(dalloc(h, &h->cd.flags, 4));

@@ -1,0 +1,378 @@
+// cycle_kernels.cu -- the streaming kernels around the Arnoldi steps of a
+// restart cycle, and the sparse-sign table.
+//
+//   norm_b_kernel         ||b|| (cycle 1 start, Algorithm 2 line 2 with the
+//                         truncated mode's w_1 = b / ||b||)
+//   start_kernel          w_1 = b / ||b|| in the basis storage type
+//   update_kernel         cycle end (Algorithm 2, solution update):
+//                         x += W_m z and the next start vector
+//                         v = (w_{m+1} - W_m g) / tau of the whitened restart
+//   sketch_reduce_kernel  U[:, j] = (1/sqrt(zeta)) * sum over CTAs of the
+//                         per-CTA sketch partials, in CTA order
+//   sketch_table_kernel   the sparse sign embedding S of Sec. 2.1, Eq. (3),
+//                         generated once per handle with the counter-based
+//                         generator (S is likewise generated once per run and
+//                         stored in App. A)
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace krylov {
+namespace {
+
+__device__ __forceinline__ bool last_block(unsigned* counter, int* s_last) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (*s_last) __threadfence();
+  return *s_last != 0;
+}
+
+__global__ void norm_b_kernel(const double* b, int n, double* part, CycleDev cd, int rows_per_cta) {
+  __shared__ double red[32];
+  __shared__ int s_last;
+  double acc = 0.0;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) acc = fma(b[i], b[i], acc);
+  const double v = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+  if (!last_block(cd.counter, &s_last)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + c);
+    cd.scal[4] = t;
+    const double eta = sqrt(t);
+    cd.scal[0] = eta;
+    cd.scal[1] = (eta > 0.0) ? 1.0 / eta : 0.0;
+    cd.scal[5] = 1.0;  // w_1 = b / ||b||
+    if (!isfinite(t)) cd.flags[2] |= ERR_NONFINITE;
+    *cd.counter = 0u;
+  }
+}
+
+template <typename VT>
+__global__ void start_kernel(const double* b, VT* W0, int n, CycleDev cd) {
+  const double inv = cd.scal[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = b[i] * inv;
+    if constexpr (sizeof(VT) == 8) W0[i] = v;
+    else Store<VT>::put(W0 + i, __double2float_rn(v));
+  }
+}
+
+__global__ void ff_start_kernel(const double* b, float2* W0, int n, CycleDev cd) {
+  const double inv = cd.scal[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const ff v = ff_from_double(b[i] * inv);
+    W0[i] = make_float2(v.hi, v.lo);
+  }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw, int n, int m_eff,
+                                                              int has_next, const double* zg, int m,
+                                                              double* x, double* part, CycleDev cd,
+                                                              int rows_per_cta) {
+  __shared__ double zs[256], gs[256];
+  __shared__ double red[32];
+  __shared__ int s_last;
+  for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
+    zs[q] = zg[q];
+    gs[q] = zg[m + q];
+  }
+  const double tau_inv = zg[2 * m];
+  __syncthreads();
+  double ay = 0.0, ax = 0.0, av = 0.0;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+    double y = 0.0;
+    double v = has_next ? double(Store<VT>::load(W + (int64_t)m_eff * ldw + i)) : 0.0;
+    for (int q = 0; q < m_eff; ++q) {
+      const double w = double(Store<VT>::load(W + (int64_t)q * ldw + i));
+      y = fma(w, zs[q], y);
+      v = fma(-w, gs[q], v);
+    }
+    const double xn = x[i] + y;
+    x[i] = xn;
+    if (has_next) {
+      const double vn = v * tau_inv;
+      double vs;
+      if constexpr (sizeof(VT) == 8) {
+        W[i] = vn;
+        vs = vn;
+      } else {
+        Store<VT>::put(W + i, __double2float_rn(vn));
+        vs = (double)Store<VT>::load(W + i);
+      }
+      av = fma(vs, vs, av);
+    }
+    ay = fma(y, y, ay);
+    ax = fma(xn, xn, ax);
+  }
+  double v = block_sum(ay, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x] = v;
+  v = block_sum(ax, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = v;
+  v = block_sum(av, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = v;
+  if (!last_block(cd.counter, &s_last)) return;
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + 3 * c + threadIdx.x);
+    cd.scal[threadIdx.x < 2 ? 2 + threadIdx.x : 5] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *cd.counter = 0u;
+}
+
+// Compensated accumulation of products (float-float): S + E tracks sum a * w.
+struct ffsum {
+  float S = 0.f, E = 0.f;
+  __device__ __forceinline__ void add_prod(ff a, ff w) {
+    const float p = __fmul_rn(a.hi, w.hi);
+    float e = __fmaf_rn(a.hi, w.hi, -p);
+    e = __fmaf_rn(a.hi, w.lo, e);
+    e = __fmaf_rn(a.lo, w.hi, e);
+    const ff t = two_sum(S, p);
+    S = t.hi;
+    E = __fadd_rn(E, __fadd_rn(t.lo, e));
+  }
+  __device__ __forceinline__ ff result() const { return fast_two_sum(S, E); }
+};
+
+// Cycle end for the float-float basis (x stays float64).
+__global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int64_t ldw, int n, int m_eff,
+                                                                 int has_next, const double* zg, int m, double* x,
+                                                                 double* part, CycleDev cd, int rows_per_cta) {
+  __shared__ ff zs[256], gs[256];
+  __shared__ float red[32];
+  __shared__ int s_last;
+  for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
+    zs[q] = ff_from_double(zg[q]);
+    gs[q] = ff_neg(ff_from_double(zg[m + q]));
+  }
+  const ff tau_inv = ff_from_double(zg[2 * m]);
+  __syncthreads();
+  float ay = 0.f, ax = 0.f, av = 0.f;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+    ffsum y, v;
+    if (has_next) {
+      const float2 wm = W[(int64_t)m_eff * ldw + i];
+      v.S = wm.x;
+      v.E = wm.y;
+    }
+#pragma unroll 4
+    for (int q = 0; q < m_eff; ++q) {
+      const float2 w2 = W[(int64_t)q * ldw + i];
+      const ff w{w2.x, w2.y};
+      y.add_prod(zs[q], w);
+      if (has_next) v.add_prod(gs[q], w);
+    }
+    const ff yy = y.result();
+    const double xn = x[i] + ((double)yy.hi + (double)yy.lo);
+    x[i] = xn;
+    if (has_next) {
+      const ff vn = ff_mul(v.result(), tau_inv);
+      W[i] = make_float2(vn.hi, vn.lo);
+      av = __fmaf_rn(vn.hi, vn.hi, av);
+    }
+    ay = __fmaf_rn(yy.hi, yy.hi, ay);
+    const float xf = __double2float_rn(xn);
+    ax = __fmaf_rn(xf, xf, ax);
+  }
+  float v = block_sum(ay, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x] = double(v);
+  v = block_sum(ax, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = double(v);
+  v = block_sum(av, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = double(v);
+  if (!last_block(cd.counter, &s_last)) return;
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + 3 * c + threadIdx.x);
+    cd.scal[threadIdx.x < 2 ? 2 + threadIdx.x : 5] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *cd.counter = 0u;
+}
+
+template <typename Sk>
+__global__ void sketch_reduce_kernel(const Sk* part, int ncols, int grid, int s, double scale,
+                                     int64_t col_stride, double* U) {
+  const int j = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols || r >= s) return;
+  const Sk* p = part + (size_t)j * col_stride;
+  double acc = 0.0;
+  for (int c = 0; c < grid; ++c) acc += double(p[(size_t)c * s + r]);
+  U[(size_t)j * s + r] = acc * scale;
+}
+
+__global__ void spmv_f64_kernel(int n, const int* rp, const int* ci, const double* val, const double* x,
+                                double* y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) acc = fma(val[e], x[ci[e]], acc);
+    y[i] = acc;
+  }
+}
+
+__global__ void dot_f64_kernel(const double* a, const double* b, int n, double* part, double* out,
+                               unsigned* counter, int rows_per_cta) {
+  __shared__ double red[32];
+  __shared__ int s_last;
+  double acc = 0.0;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) acc = fma(a[i], b[i], acc);
+  const double v = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+  if (!last_block(counter, &s_last)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + c);
+    *out = t;
+    *counter = 0u;
+  }
+}
+
+// Columns of S generated by the same routine the step kernels use when they
+// regenerate S (packed path for s <= 255, zeta <= 8; generic otherwise).
+__global__ void sketch_columns_kernel(int64_t col0, int64_t count, SketchSpec sp, int* rows,
+                                      signed char* signs, int* err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int* rr = rows + t * sp.zeta;
+  signed char* ss = signs + t * sp.zeta;
+  int got;
+  if (sp.s <= 255 && sp.zeta <= 8) {
+    uint32_t p0, p1, ng;
+    got = sketch_column_packed((uint32_t)(col0 + t), sp, sketch_inv_s(sp.s), &p0, &p1, &ng);
+    for (int e = 0; e < got; ++e) {
+      rr[e] = (int)(((e < 4 ? p0 : p1) >> (8 * (e & 3))) & 0xFFu);
+      ss[e] = ((ng >> e) & 1u) ? (signed char)-1 : (signed char)1;
+    }
+  } else {
+    int e = 0;
+    got = sketch_column<MAX_ZETA>((uint32_t)(col0 + t), sp, [&](int row, bool neg) {
+      rr[e] = row;
+      ss[e] = neg ? (signed char)-1 : (signed char)1;
+      ++e;
+    });
+  }
+  if (got < sp.zeta) atomicOr(err, ERR_SKETCH);
+}
+
+// The table of S: packed (s <= 255, zeta <= 8): 8 row bytes per column in a
+// uint2 (0xFF in unused bytes) and a sign byte; generic: zeta uint16 rows and
+// a 32-bit sign mask per column.
+__global__ void sketch_table_kernel(int n, SketchSpec sp, SketchTable tab, int* err) {
+  const int stride = gridDim.x * blockDim.x;
+  const uint32_t inv_s = sketch_inv_s(sp.s);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int got;
+    if (tab.packed) {
+      uint32_t p0, p1, ng;
+      got = sketch_column_packed((uint32_t)i, sp, inv_s, &p0, &p1, &ng);
+      tab.rows8[i] = make_uint2(p0, p1);
+      tab.neg8[i] = (uint8_t)ng;
+    } else {
+      int e = 0;
+      uint32_t ng = 0u;
+      uint16_t* rr = tab.rows16 + (size_t)i * sp.zeta;
+      got = sketch_column<MAX_ZETA>((uint32_t)i, sp, [&](int row, bool neg) {
+        rr[e] = (uint16_t)row;
+        ng |= (neg ? 1u : 0u) << e;
+        ++e;
+      });
+      tab.neg32[i] = ng;
+    }
+    if (got < sp.zeta) atomicOr(err, ERR_SKETCH);
+  }
+}
+
+__global__ void cycle_reset_kernel(CycleDev cd, int m) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    cd.flags[0] = m;
+    cd.flags[1] = 0;
+  }
+}
+
+}  // namespace
+
+SketchSpec make_sketch_spec(int s, int zeta, uint64_t seed) {
+  SketchSpec sp;
+  sp.s = s;
+  sp.zeta = zeta;
+  sp.lim = 32768u - 32768u % (uint32_t)s;
+  sp.k0 = (uint32_t)(seed & 0xFFFFFFFFull);
+  sp.k1 = (uint32_t)(seed >> 32);
+  sp.scale = 1.f;
+  return sp;
+}
+
+void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st) { cycle_reset_kernel<<<1, 32, 0, st>>>(cd, m); }
+
+void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st) {
+  const int rpc = (n + grid - 1) / grid;
+  norm_b_kernel<<<grid, STEP_THREADS, 0, st>>>(b, n, part, cd, rpc);
+}
+
+void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& cd, int grid, cudaStream_t st) {
+  if (basis == 3) ff_start_kernel<<<grid, STEP_THREADS, 0, st>>>(b, (float2*)W0, n, cd);
+  else if (basis == 0) start_kernel<double><<<grid, STEP_THREADS, 0, st>>>(b, (double*)W0, n, cd);
+  else if (basis == 1) start_kernel<float><<<grid, STEP_THREADS, 0, st>>>(b, (float*)W0, n, cd);
+  else start_kernel<__nv_bfloat16><<<grid, STEP_THREADS, 0, st>>>(b, (__nv_bfloat16*)W0, n, cd);
+}
+
+void launch_update(int basis, void* W, int64_t ldw, int n, int m_eff, int has_next, const double* zg, double* x,
+                   double* part, int grid, const CycleDev& cd, int m, cudaStream_t st) {
+  const int rpc = (n + grid - 1) / grid;
+  if (basis == 3)
+    ff_update_kernel<<<grid, STEP_THREADS, 0, st>>>((float2*)W, ldw, n, m_eff, has_next, zg, m, x, part, cd, rpc);
+  else if (basis == 0)
+    update_kernel<double><<<grid, STEP_THREADS, 0, st>>>((double*)W, ldw, n, m_eff, has_next, zg, m, x, part, cd,
+                                                          rpc);
+  else if (basis == 1)
+    update_kernel<float><<<grid, STEP_THREADS, 0, st>>>((float*)W, ldw, n, m_eff, has_next, zg, m, x, part, cd, rpc);
+  else
+    update_kernel<__nv_bfloat16><<<grid, STEP_THREADS, 0, st>>>((__nv_bfloat16*)W, ldw, n, m_eff, has_next, zg, m,
+                                                                 x, part, cd, rpc);
+}
+
+void launch_sketch_reduce(const void* sk_part, int ncols, int grid, int s, int zeta, int64_t col_stride, double* U,
+                          cudaStream_t st) {
+  dim3 g((s + 127) / 128, ncols);
+  const double scale = 1.0 / std::sqrt((double)zeta);
+  sketch_reduce_kernel<double><<<g, 128, 0, st>>>((const double*)sk_part, ncols, grid, s, scale, col_stride, U);
+}
+
+void launch_spmv_f64(int n, const int* row_ptr, const int* col, const double* val, const double* x, double* y,
+                     cudaStream_t st) {
+  const int grid = std::max(1, std::min(4096, (n + 255) / 256));
+  spmv_f64_kernel<<<grid, 256, 0, st>>>(n, row_ptr, col, val, x, y);
+}
+
+void launch_dot_f64(const double* a, const double* b, int n, double* part, int grid, double* out, unsigned* counter,
+                    cudaStream_t st) {
+  const int rpc = (n + grid - 1) / grid;
+  dot_f64_kernel<<<grid, STEP_THREADS, 0, st>>>(a, b, n, part, out, counter, rpc);
+}
+
+void launch_sketch_columns(int64_t col0, int64_t count, int s, int zeta, uint64_t seed, int* rows,
+                           signed char* signs, int* err, cudaStream_t st) {
+  const SketchSpec sp = make_sketch_spec(s, zeta, seed);
+  const int grid = (int)((count + 255) / 256);
+  if (grid > 0) sketch_columns_kernel<<<grid, 256, 0, st>>>(col0, count, sp, rows, signs, err);
+}
+
+void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTable& tab, int* err, cudaStream_t st) {
+  const SketchSpec sp = make_sketch_spec(s, zeta, seed);
+  const int grid = std::max(1, std::min(8192, (n + 255) / 256));
+  sketch_table_kernel<<<grid, 256, 0, st>>>(n, sp, tab, err);
+}
+
+}  // namespace krylov

@@ -13,11 +13,24 @@ struct CycleDev {
   double* pi;      // (m+1) squared norms of the raw products A w_j
   double* coef;    // (m+1) x (MAX_WINDOW+1): window coefficients then rho
   double* R;       // (m+1) x m column-major, leading dimension m+1
-  double* scal;    // [0] eta, [1] 1/eta, [2] ||y||^2, [3] ||x||^2, [4] ||b||^2
+  double* scal;    // [0] eta, [1] 1/eta, [2] ||y||^2, [3] ||x||^2, [4] ||b||^2,
+                   // [5] bound on ||w_1||^2 of the next cycle
   unsigned* counter;  // arrival counters of the last-block reducers (zeroed)
 };
 
 enum : int { ERR_SKETCH = 1, ERR_NONFINITE = 2 };
+
+// Stored sparse sign embedding (generated once per handle on the device).
+struct SketchTable {
+  int packed;          // 1: rows8/neg8 (s <= 255, zeta <= 8); 0: rows16/neg32
+  uint2* rows8;        // n: 8 row bytes per column (0xFF = unused)
+  uint8_t* neg8;       // n: sign bits (1 = -1)
+  uint16_t* rows16;    // n * zeta
+  uint32_t* neg32;     // n
+};
+
+// Where the step kernels take the entries of S from.
+enum : int { SK_TAB8 = 0, SK_TAB16 = 1, SK_GEN8 = 2, SK_GEN = 3 };
 
 struct StepLaunch {
   int n;
@@ -41,10 +54,14 @@ struct StepLaunch {
   int grid;          // number of CTAs (persistent)
   int rows_per_cta;
   int m;             // restart length (leading dimension of R is m+1)
+  SketchTable sk_tab;
+  int sk_mode;       // SK_* : stored table or regeneration in the kernel
+  int sk_copies;     // lane-private copies of each sketch bin in shared memory
+  int fx_wb;         // bits per fixed-point word of the sketch bins
 };
 
 // basis dtype codes (krylov_basis)
-int step_ctas_per_sm(int basis, int zeta, int s, int vals_f32);
+int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
 void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st);
 void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& cd, int grid,
@@ -52,20 +69,25 @@ void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& c
 void launch_update(int basis, void* W, int64_t ldw, int n, int m_eff, int has_next,
                    const double* zg, double* x, double* part, int grid, const CycleDev& cd, int m,
                    cudaStream_t st);
-void launch_sketch_reduce(int basis, const void* sk_part, int ncols, int grid, int s, int zeta,
-                          int64_t col_stride, double* U, cudaStream_t st);
+void launch_sketch_reduce(const void* sk_part, int ncols, int grid, int s, int zeta, int64_t col_stride,
+                          double* U, cudaStream_t st);
 void launch_spmv_f64(int n, const int* row_ptr, const int* col, const double* val, const double* x,
                      double* y, cudaStream_t st);
 void launch_dot_f64(const double* a, const double* b, int n, double* part, int grid, double* out,
                     unsigned* counter, cudaStream_t st);
 void launch_sketch_columns(int64_t col0, int64_t count, int s, int zeta, uint64_t seed, int* rows,
                            signed char* signs, int* err, cudaStream_t st);
+void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTable& tab, int* err,
+                         cudaStream_t st);
+int sketch_bin_copies(int basis, int s);
+int sketch_word_bits(int rows_per_cta, int copies);
 
 // ---- handle creation ------------------------------------------------------
 cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* d_flag, int* h_flag,
                          cudaStream_t st);
 cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag,
                           cudaStream_t st);
+cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st);
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
                           int* cit, double* vt, int* work, cudaStream_t st);
 void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st);

@@ -97,6 +97,104 @@ __host__ __device__ __forceinline__ int sketch_column(uint32_t j, const SketchSp
   return cnt;
 }
 
+// ceil(2^32 / s): floor(v / s) = umulhi(v, sketch_inv_s(s)) for v < 2^15, s < 2^15.
+__host__ __device__ __forceinline__ uint32_t sketch_inv_s(int s) {
+  return (uint32_t)((0x100000000ull + (uint64_t)s - 1) / (uint64_t)s);
+}
+
+// Fast path of sketch_column for s <= 255 and zeta <= 8: the accepted rows are
+// kept as bytes packed in two words (0xFF marks an empty slot, never a row),
+// duplicates are found with SIMD byte compares, and v mod s uses the exact
+// multiply-high identity floor(v / s) = umulhi(v, ceil(2^32 / s)) for
+// v < 2^15.  Produces the same entries, in the same order, as sketch_column.
+// Returns the count; rows in (*p0, *p1) byte e, sign bit e of *neg.
+__device__ __forceinline__ int sketch_column_packed(uint32_t j, const SketchSpec& sp, uint32_t inv_s,
+                                                     uint32_t* p0, uint32_t* p1, uint32_t* neg) {
+  uint32_t r0 = 0xFFFFFFFFu, r1 = 0xFFFFFFFFu, ng = 0u;
+  int cnt = 0;
+  for (uint32_t blk = 0; blk < (uint32_t)SKETCH_MAX_BLOCKS && cnt < sp.zeta; ++blk) {
+    const Philox4 w = philox4x32_10(Philox4{j, blk, 0u, 0u}, sp.k0, sp.k1);
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t ch = (words[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+      const uint32_t v = ch & 0x7FFFu;
+      const uint32_t row = v - (uint32_t)sp.s * __umulhi(v, inv_s);
+      const uint32_t rep = row * 0x01010101u;
+      const bool dup = (__vcmpeq4(r0, rep) | __vcmpeq4(r1, rep)) != 0u;
+      if (cnt < sp.zeta && v < sp.lim && !dup) {
+        const uint32_t sh = 8u * (uint32_t)(cnt & 3);
+        const uint32_t keep = ~(0xFFu << sh);
+        if (cnt < 4) r0 = (r0 & keep) | (row << sh);
+        else r1 = (r1 & keep) | (row << sh);
+        ng |= (ch >> 15) << cnt;
+        ++cnt;
+      }
+    }
+  }
+  *p0 = r0;
+  *p1 = r1;
+  *neg = ng;
+  return cnt;
+}
+
+// ---- float-float ("df64") arithmetic ---------------------------------------
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  Built from the error-free transformations
+// TwoSum (Knuth) and TwoProduct via fused multiply-add (e.g. Dekker 1971;
+// Muller et al., Handbook of Floating-Point Arithmetic, ch. 4).
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  const float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, e);
+}
+// a * b with a float and b float-float
+__device__ __forceinline__ ff ff_mul_f(ff b, float a) {
+  const float p = __fmul_rn(a, b.hi);
+  float e = __fmaf_rn(a, b.hi, -p);
+  e = __fmaf_rn(a, b.lo, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+// acc + a * b (a float, b float-float)
+__device__ __forceinline__ ff ff_fma_f(float a, ff b, ff acc) { return ff_add(acc, ff_mul_f(b, a)); }
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_from_double(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// Add v to the pair of shared-memory bins (hi[b], lo[b]): the rounding error
+// of the atomic float add on hi is recovered exactly from the returned old
+// value (TwoSum) and added to lo together with v.lo, so hi + lo carries the
+// float-float sum regardless of the order in which threads arrive.
+__device__ __forceinline__ void ff_atomic_add(float* hi, float* lo, ff v) {
+  const float old = atomicAdd(hi, v.hi);
+  const ff s = two_sum(old, v.hi);
+  atomicAdd(lo, __fadd_rn(s.lo, v.lo));
+}
+
 // ---- storage conversions --------------------------------------------------
 template <typename T> struct Store;
 template <> struct Store<double> {

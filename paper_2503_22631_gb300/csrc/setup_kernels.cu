@@ -33,6 +33,14 @@ __global__ void narrow_kernel(int64_t nnz, const double* v, float* v32, int* ine
   }
 }
 
+__global__ void split_kernel(int64_t nnz, const double* v, float2* vff) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const float h = __double2float_rn(v[e]);
+    vff[e] = make_float2(h, __double2float_rn(v[e] - (double)h));
+  }
+}
+
 __global__ void count_cols_kernel(int64_t nnz, const int* ci, int* cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride) atomicAdd(&cnt[ci[e]], 1);
@@ -119,6 +127,11 @@ cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag,
   if (nnz > 0) narrow_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, v, v32, d_flag);
   cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   return cudaStreamSynchronize(st);
+}
+
+cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st) {
+  if (nnz > 0) split_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, v, vff);
+  return cudaGetLastError();
 }
 
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt, int* cit,

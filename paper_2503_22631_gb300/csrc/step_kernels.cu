@@ -1,30 +1,43 @@
-// step_kernels.cu -- the streaming kernels of one restart cycle.
+// step_kernels.cu -- the Arnoldi-step kernels of one restart cycle.
 //
-// One launch of step_kernel handles basis column j of a cycle (Algorithm 1's
-// loop body, with the truncated orthogonalization of Sec. 5 "incomplete" and
-// the sketch of Sec. 2.1) in a single pass over the rows:
+// A step handles basis column j (Algorithm 1's loop body, with the truncated
+// orthogonalization of Sec. 5 "incomplete" and the sketch of Sec. 2.1):
 //
-//   materialize   w_j = rho_j (p_{j-1} - sum_{q in win(j-1)} h_q w_q)
-//                 (the orthogonalization of the previous product, rounded to
-//                 the basis storage type and stored in slot j)
+//   materialize   w_j = rho_j (p_{j-1} - sum_{q in win(j-1)} h_q w_q), the
+//                 orthogonalization of the previous product, rounded to the
+//                 basis storage type and stored in slot j
 //   sketch        u_j += S e_i w_j[i] for the zeta entries of column i of S,
-//                 generated in-kernel (Eq. 3), accumulated in shared memory
-//   product       p_j = A w_j, where w_j at a neighbour column c is
-//                 recomputed from p_{j-1}[c] and the window vectors at c with
-//                 the same rounded arithmetic, so w_j is never re-read
+//                 accumulated in warp-private bins in shared memory: lanes
+//                 that hit the same bin in a round are combined first (match
+//                 + shuffles, lane order), then one plain read-modify-write
+//                 per bin -- no atomics, deterministic
+//   product       p_j = A w_j by a warp-cooperative CSR stream: a warp loads
+//                 the nonzeros of its 32 consecutive rows with coalesced
+//                 loads (batches of U per lane, indices first, then gathers),
+//                 stages the products in shared memory and sums each row's
+//                 segment in storage order
 //   dots          <w_q, p_j> for the window of the next column, ||p_j||^2,
 //                 ||w_j||^2
 //
-// Basis vectors are stored unnormalized: rho_j only keeps ||w_j|| near 1
-// (estimated from ||p||^2 - sum h_q^2 ||w_q||^2), the exact norm is reduced
-// here and h_q = <w_q, p_j> / ||w_q||^2 are projection coefficients, so the
-// Arnoldi-like relation A w_{j-1} = sum h_q w_q + w_j / rho_j (Eq. 5) holds
-// for whatever rho_j was used.  Whitening absorbs the column scaling.
+// step_kernel (float64 / float32 / bfloat16 bases) fuses all four in one
+// pass: w_j at a neighbour column c is recomputed from p_{j-1}[c] and the
+// window vectors at c with the same rounded arithmetic, so w_j is written
+// once and never re-read.  The float-float basis splits a step into
+// ff_mat_kernel (materialize + sketch) and ff_spmv_kernel (product + dots):
+// recomputing a float-float orthogonalization at every neighbour would make
+// the step arithmetic-bound.
 //
-// Reductions are deterministic: per-CTA partials in a fixed slot, then the
+// Basis vectors are stored unnormalized: rho_j only keeps ||w_j|| near 1
+// (from ||p||^2 - sum h_q^2 ||w_q||^2); the exact norm is reduced here and
+// h_q = <w_q, p_j> / ||w_q||^2 are projection coefficients, so the
+// Arnoldi-like relation A w_{j-1} = sum h_q w_q + w_j / rho_j (Eq. 5) holds
+// for whatever rho_j was used.  The whitening absorbs the column scaling.
+//
+// Reductions are deterministic: per-CTA partials in fixed slots, then the
 // last CTA to arrive (atomic ticket) sums them in CTA order and writes the
-// next column's coefficients.  The sketch partials stay per CTA and are
-// summed once per cycle by sketch_reduce_kernel.
+// next column's coefficients.  Sketch partials stay per CTA and are summed
+// once per cycle by sketch_reduce_kernel.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -36,7 +49,7 @@ namespace {
 template <typename VT> struct Types {
   using A = float;   // arithmetic
   using P = float;   // raw product storage
-  using Sk = float;  // sketch partials
+  using Sk = float;  // sketch bins / partials
 };
 template <> struct Types<double> {
   using A = double;
@@ -45,14 +58,34 @@ template <> struct Types<double> {
 };
 
 constexpr int NQ = 2 + MAX_WINDOW;  // scalar partials per CTA: ||w||^2, ||p||^2, dots
+constexpr int STAGE = 512;          // staged nonzeros per warp in the CSR stream
+constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ void reducer_step(const StepLaunch& L, const CycleDev& cd,
-                                             const double* tot, int mat, int spmv) {
+__device__ __forceinline__ float shfl_T(unsigned m, float v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ double shfl_T(unsigned m, double v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ ff shfl_T(unsigned m, ff v, int src) {
+  return ff{__shfl_sync(m, v.hi, src), __shfl_sync(m, v.lo, src)};
+}
+
+// Arrival ticket of the deterministic "last CTA reduces" pattern: true in the
+// CTA that arrives last (it then sums the per-CTA partials in CTA order).
+__device__ __forceinline__ bool last_block_flag(unsigned* counter, int* s_last) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (*s_last) __threadfence();
+  return *s_last != 0;
+}
+
+// Reducer of a materialized column j: record ||w_j||^2 and R[j, j-1] = 1/rho_j,
+// and flag a happy breakdown when ||w_j|| / rho_j (the norm of the
+// orthogonalized product) is below thr * ||A w_{j-1}||.
+__device__ __forceinline__ void reduce_mat(const StepLaunch& L, const CycleDev& cd, double sig2, int mat) {
   const int j = L.j;
-  const double sig2 = tot[0];
+  const int ldr = L.m + 1;  // R is (m+1) x m, column-major
   cd.sig2[j] = sig2;
   if (!isfinite(sig2)) cd.flags[2] |= ERR_NONFINITE;
-  const int ldr = L.m + 1;  // R is (m+1) x m, column-major
   if (mat) {
     const double rho = cd.coef[(size_t)(j - 1) * (MAX_WINDOW + 1) + MAX_WINDOW];
     cd.R[(size_t)(j - 1) * ldr + j] = 1.0 / rho;
@@ -65,143 +98,367 @@ __device__ __forceinline__ void reducer_step(const StepLaunch& L, const CycleDev
       }
     }
   }
-  if (spmv && cd.flags[1] == 0) {
-    const double pi = tot[1];
-    cd.pi[j] = pi;
-    if (!isfinite(pi)) cd.flags[2] |= ERR_NONFINITE;
-    const int dlo = max(0, j - L.k + 1);
-    double est = pi;
-    double* c = cd.coef + (size_t)j * (MAX_WINDOW + 1);
-    for (int q = 0; q < MAX_WINDOW; ++q) {
-      const int slot = dlo + q;
-      double h = 0.0;
-      if (slot <= j) {
-        const double s2 = cd.sig2[slot];
-        h = (s2 > 0.0) ? tot[2 + q] / s2 : 0.0;
-        est -= h * h * s2;
-        cd.R[(size_t)j * ldr + slot] = h;
-      }
-      c[q] = h;
-    }
-    est = fmax(est, 1e-20 * pi);
-    c[MAX_WINDOW] = (pi > 0.0) ? 1.0 / sqrt(est) : 1.0;
-  }
 }
 
-template <typename VT, typename AT, bool MAT, bool SPMV, int ZM>
-__global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepLaunch L, const CycleDev cd) {
+// Reducer of a product p_j = A w_j: projection coefficients h_q = <w_q, p_j> /
+// ||w_q||^2 for the window, R[q, j] = h_q, and the scale rho_{j+1} of the next
+// column from ||p_j||^2 - sum h_q^2 ||w_q||^2 (the window is orthogonal).
+__device__ __forceinline__ void reduce_spmv(const StepLaunch& L, const CycleDev& cd, const double* tot) {
+  if (cd.flags[1] != 0) return;
+  const int j = L.j;
+  const int ldr = L.m + 1;
+  const double pi = tot[1];
+  cd.pi[j] = pi;
+  if (!isfinite(pi)) cd.flags[2] |= ERR_NONFINITE;
+  const int dlo = max(0, j - L.k + 1);
+  double est = pi;
+  double* c = cd.coef + (size_t)j * (MAX_WINDOW + 1);
+  for (int q = 0; q < MAX_WINDOW; ++q) {
+    const int slot = dlo + q;
+    double h = 0.0;
+    if (slot <= j) {
+      const double s2 = cd.sig2[slot];
+      h = (s2 > 0.0) ? tot[2 + q] / s2 : 0.0;
+      est -= h * h * s2;
+      cd.R[(size_t)j * ldr + slot] = h;
+    }
+    c[q] = h;
+  }
+  est = fmax(est, 1e-20 * pi);
+  c[MAX_WINDOW] = (pi > 0.0) ? 1.0 / sqrt(est) : 1.0;
+}
+
+// Column i of S held by one lane: the entries (row, negative) e = 0..zeta-1,
+// from the stored table or regenerated with the counter-based generator.
+template <int SKM> struct SkCol {
+  uint32_t p0 = 0xFFFFFFFFu, p1 = 0xFFFFFFFFu, ng = 0u;
+  int got = 0;
+  const uint16_t* r16 = nullptr;
+  __device__ __forceinline__ void load(const StepLaunch& L, const SketchSpec& sp, uint32_t inv_s, int i) {
+    if constexpr (SKM == SK_TAB8) {
+      const uint2 r = __ldg(L.sk_tab.rows8 + i);
+      p0 = r.x;
+      p1 = r.y;
+      ng = __ldg(L.sk_tab.neg8 + i);
+      got = sp.zeta;
+    } else if constexpr (SKM == SK_TAB16) {
+      r16 = L.sk_tab.rows16 + (size_t)i * sp.zeta;
+      ng = __ldg(L.sk_tab.neg32 + i);
+      got = sp.zeta;
+    } else if constexpr (SKM == SK_GEN8) {
+      got = sketch_column_packed((uint32_t)i, sp, inv_s, &p0, &p1, &ng);
+    }
+  }
+  __device__ __forceinline__ int row(int e) const {
+    if constexpr (SKM == SK_TAB16) return (int)__ldg(r16 + e);
+    return (int)(((e < 4 ? p0 : p1) >> (8 * (e & 3))) & 0xFFu);
+  }
+  __device__ __forceinline__ bool neg(int e) const { return (ng >> e) & 1u; }
+};
+
+// Generic regeneration (any s <= 32768, zeta <= 32): entries kept in a local array.
+struct SkColGen {
+  int rows[MAX_ZETA];
+  uint32_t ng = 0u;
+  int got = 0;
+  __device__ __forceinline__ void load(const StepLaunch& L, const SketchSpec& sp, uint32_t inv_s, int i) {
+    (void)L;
+    (void)inv_s;
+    got = 0;
+    ng = 0u;
+    sketch_column<MAX_ZETA>((uint32_t)i, sp, [&](int r, bool n) {
+      rows[got] = r;
+      ng |= (n ? 1u : 0u) << got;
+      ++got;
+    });
+  }
+  __device__ __forceinline__ int row(int e) const { return rows[e]; }
+  __device__ __forceinline__ bool neg(int e) const { return (ng >> e) & 1u; }
+};
+
+template <int SKM> struct SkColOf { using type = SkCol<SKM>; };
+template <> struct SkColOf<SK_GEN> { using type = SkColGen; };
+
+// ---- exact fixed-point sketch bins ---------------------------------------
+// A contribution v with |v| <= B is scaled by the power of two 2^(WB - E),
+// E = ceil(log2 B) + 1, so |x| <= 2^(WB-1), and split into NW integer words
+// x = q_0 + 2^-WB q_1 + 2^-2WB q_2 + ... (each |q_w| <= 2^(WB-1)), rounding
+// with the 1.5 * 2^23 addition trick on the FP32 pipes.  Word w of bin b
+// lives in a lane-private column (address (w s + b) C + copy), so the integer
+// atomic adds of a warp hit distinct banks; integer sums are exact and
+// independent of the order in which threads arrive.  WB is chosen on the host
+// so that no column can overflow (entries per column <= rows per CTA / C).
+struct FxScale {
+  float to_fixed;  // 2^(WB - E)
+  float word;      // 2^WB
+  int E;
+};
+
+template <int NW> struct FxWords {
+  int q[NW];
+};
+
+// Split the contribution (h + l) of one row into its fixed-point words (once
+// per row: every entry of the row adds the same value up to its sign).
+template <int NW>
+__device__ __forceinline__ FxWords<NW> fx_split(float h, float l, const FxScale& f) {
+  const float magic = 12582912.0f;  // 1.5 * 2^23
+  FxWords<NW> out;
+  h = __fmul_rn(h, f.to_fixed);
+  l = __fmul_rn(l, f.to_fixed);
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const float r = __fadd_rn(h, magic);
+    out.q[w] = __float_as_int(r) - 0x4B400000;
+    if (w + 1 < NW) {
+      const ff d = two_sum(__fsub_rn(h, __fsub_rn(r, magic)), l);
+      h = __fmul_rn(d.hi, f.word);
+      l = __fmul_rn(d.lo, f.word);
+    }
+  }
+  return out;
+}
+
+// Add +-words to bin `row` in this lane's column.
+template <int NW>
+__device__ __forceinline__ void fx_emit(int* bins, int sC, int row, int cp, const FxWords<NW>& x, bool neg,
+                                        int C) {
+  int* b = bins + row * C + cp;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) atomicAdd(b + w * sC, neg ? -x.q[w] : x.q[w]);
+}
+
+// Value of bin b of this CTA: sum of its words over the copies, as a double.
+template <int NW>
+__device__ __forceinline__ double fx_value(const int* bins, int s, int C, int b, const FxScale& f, int WB) {
+  double v = 0.0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    long long t = 0;
+    for (int c = 0; c < C; ++c) t += bins[(w * s + b) * C + c];
+    v += ldexp((double)t, f.E - (w + 1) * WB);
+  }
+  return v;
+}
+
+// Scale for the contributions of column j: |w_j[i]| <= ||w_j|| <= B where, for a
+// materialized column, B = rho (||p_{j-1}|| + sum_q |h_q| ||w_q||) (triangle
+// inequality on the orthogonalization), else the stored bound of slot 0.
+__device__ __forceinline__ FxScale fx_scale(const StepLaunch& L, const CycleDev& cd, int mat) {
+  double B;
+  const int j = L.j;
+  if (mat) {
+    const double* c = cd.coef + (size_t)(j - 1) * (MAX_WINDOW + 1);
+    const int lo = max(0, j - L.k);
+    B = sqrt(cd.pi[j - 1]);
+    for (int q = 0; q < j - lo; ++q) B += fabs(c[q]) * sqrt(cd.sig2[lo + q]);
+    B *= fabs(c[MAX_WINDOW]);
+  } else {
+    B = sqrt(cd.scal[5]);
+  }
+  B = B * 1.0001 + 1e-300;
+  FxScale f;
+  f.E = ilogb(B) + 2;  // 2^(E-1) > B
+  f.to_fixed = ldexpf(1.0f, L.fx_wb - f.E);
+  f.word = ldexpf(1.0f, L.fx_wb);
+  return f;
+}
+
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__device__ __forceinline__ SketchSpec spec_of(const StepLaunch& L) {
+  SketchSpec t;
+  t.s = L.s;
+  t.zeta = L.zeta;
+  t.lim = 32768u - 32768u % (uint32_t)L.s;
+  t.k0 = (uint32_t)(L.seed & 0xFFFFFFFFull);
+  t.k1 = (uint32_t)(L.seed >> 32);
+  t.scale = 1.f;
+  return t;
+}
+
+// Products of the CSR stream are formed in batches of U nonzeros per lane:
+// all column indices and values of a batch are loaded first, then all the
+// gathers, so each lane keeps many independent loads in flight.
+constexpr int U_FUSED = 4;
+constexpr int U_FF = 4;
+
+// ---------------------------------------------------------------------------
+template <typename VT, typename AT, bool MAT, bool SPMV, int SKM>
+__global__ void __launch_bounds__(STEP_THREADS, 3) step_kernel(const StepLaunch L, const CycleDev cd) {
   using A = typename Types<VT>::A;
   using P = typename Types<VT>::P;
   using Sk = typename Types<VT>::Sk;
+  constexpr int NW = (sizeof(A) == 8) ? 3 : 2;  // fixed-point words per contribution
   extern __shared__ __align__(16) unsigned char smem[];
-  Sk* bins = reinterpret_cast<Sk*>(smem);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int C = L.sk_copies;
+  int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
+  A* stage = reinterpret_cast<A*>(smem + align16((size_t)NW * L.s * C * sizeof(int)));
   __shared__ A red[32];
   __shared__ double tot[NQ];
   __shared__ int s_last;
 
+  __shared__ FxScale s_fx;
+  __shared__ A s_h[MAX_WINDOW + 1];
+
   const int j = L.j;
   if (cd.flags[0] < j) return;  // an earlier column broke down
-
-  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < nw * L.s; e += blockDim.x) bins[e] = Sk(0);
+  const int lo = MAT ? max(0, j - L.k) : j;
+  const int nl = j - lo;
+  for (int e = threadIdx.x; e < NW * L.s * C; e += blockDim.x) bins[e] = 0;
+  if (threadIdx.x == 0) {  // per-CTA prologue (float64 work done once)
+    s_fx = fx_scale(L, cd, MAT ? 1 : 0);
+    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? A(c[q]) : A(0);
+    s_h[MAX_WINDOW] = MAT ? A(c[MAX_WINDOW]) : A(1);
+  }
   __syncthreads();
+  const FxScale fxs = s_fx;
+  const int cp = lane & (C - 1);
+  const int sC = L.s * C;
 
   const VT* W = static_cast<const VT*>(L.W);
   VT* Wj = static_cast<VT*>(L.W) + (int64_t)j * L.ldw;
   const P* pprev = static_cast<const P*>(L.p_prev);
-  const int lo = MAT ? max(0, j - L.k) : j;
-  const int nl = j - lo;
+  const AT* val = static_cast<const AT*>(L.val);
   A h[MAX_WINDOW];
-  A rho = A(1);
+  const VT* Wq[MAX_WINDOW];
 #pragma unroll
-  for (int q = 0; q < MAX_WINDOW; ++q) h[q] = A(0);
-  if (MAT) {
-    const double* c = cd.coef + (size_t)(j - 1) * (MAX_WINDOW + 1);
-#pragma unroll
-    for (int q = 0; q < MAX_WINDOW; ++q) h[q] = (q < nl) ? A(c[q]) : A(0);
-    rho = A(c[MAX_WINDOW]);
+  for (int q = 0; q < MAX_WINDOW; ++q) {
+    h[q] = s_h[q];
+    Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * L.ldw;
   }
+  const A rho = s_h[MAX_WINDOW];
   const int dlo = max(0, j - L.k + 1);
   const int nd = j - dlo + 1;
   const int off = dlo - lo;
+  const SketchSpec sp = spec_of(L);
+  const uint32_t inv_s = sketch_inv_s(L.s);
 
-  SketchSpec sp;
-  sp.s = L.s;
-  sp.zeta = L.zeta;
-  sp.lim = 32768u - 32768u % (uint32_t)L.s;
-  sp.k0 = (uint32_t)(L.seed & 0xFFFFFFFFull);
-  sp.k1 = (uint32_t)(L.seed >> 32);
-  sp.scale = 1.f;
-
+  // value of w_j at row c, exactly as its owner thread rounds and stores it
+  auto wj_at = [&](int c) -> A {
+    if (MAT) {
+      A t = A(__ldg(pprev + c));
+#pragma unroll
+      for (int q = 0; q < MAX_WINDOW; ++q)
+        if (q < nl) t = fma_rn(-h[q], A(Store<VT>::load(Wq[q] + c)), t);
+      return stored<VT, A>(mul_rn(t, rho));
+    }
+    return A(Store<VT>::load(Wj + c));
+  };
   A acc_sig = A(0), acc_pi = A(0);
   A acc_dot[MAX_WINDOW];
 #pragma unroll
   for (int q = 0; q < MAX_WINDOW; ++q) acc_dot[q] = A(0);
   int bad = 0;
-  Sk* mybins = bins + wid * L.s;
+  A* mystage = stage + wid * STAGE;
 
   const int r0 = blockIdx.x * L.rows_per_cta;
   const int r1 = min(L.n, r0 + L.rows_per_cta);
-  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+  for (int t0 = r0; t0 < r1; t0 += STEP_THREADS) {
+    const int i0 = t0 + wid * 32;
+    if (i0 >= r1) continue;  // warp-uniform
+    const int i = i0 + lane;
+    const bool valid = i < r1;
+    const int nval = min(32, r1 - i0);
+    // ---- own row: loads first ----
+    int rb = 0, re = 0;
+    A pv0 = A(0);
     A wl[MAX_WINDOW];
-    A wj;
-    if (MAT) {
-      A acc = A(pprev[i]);
 #pragma unroll
-      for (int q = 0; q < MAX_WINDOW; ++q) {
-        wl[q] = A(0);
-        if (q < nl) {
-          wl[q] = Store<VT>::load(W + (int64_t)(lo + q) * L.ldw + i);
-          acc = fma_rn(-h[q], wl[q], acc);
-        }
+    for (int q = 0; q < MAX_WINDOW; ++q) wl[q] = A(0);
+    typename SkColOf<SKM>::type col;
+    if (valid) {
+      if (SPMV) {
+        rb = __ldg(L.row_ptr + i);
+        re = __ldg(L.row_ptr + i + 1);
       }
-      wj = stored<VT, A>(mul_rn(acc, rho));
-      Store<VT>::put(Wj + i, wj);
-    } else {
+      if (MAT) {
+        pv0 = A(__ldg(pprev + i));
 #pragma unroll
-      for (int q = 0; q < MAX_WINDOW; ++q) wl[q] = A(0);
-      wj = Store<VT>::load(Wj + i);
+        for (int q = 0; q < MAX_WINDOW; ++q)
+          if (q < nl) wl[q] = Store<VT>::load(Wq[q] + i);
+      }
+      col.load(L, sp, inv_s, i);
     }
-    acc_sig = fma_rn(wj, wj, acc_sig);
-
-    const Sk wv = Sk(wj);
-    const int got = sketch_column<ZM>((uint32_t)i, sp, [&](int row, bool neg) {
-      atomicAdd(&mybins[row], neg ? -wv : wv);
-    });
-    bad |= (got < L.zeta);
-
-    if (SPMV) {
-      const int e0 = L.row_ptr[i], e1 = L.row_ptr[i + 1];
-      A accp = A(0);
-      for (int e = e0; e < e1; ++e) {
-        const int c = L.col[e];
-        const A av = A(static_cast<const AT*>(L.val)[e]);
-        A wc;
-        if (MAT) {
-          A t = A(pprev[c]);
+    A wj = A(0);
+    if (valid) {
+      if (MAT) {
+        A acc = pv0;
 #pragma unroll
-          for (int q = 0; q < MAX_WINDOW; ++q)
-            if (q < nl) t = fma_rn(-h[q], A(Store<VT>::load(W + (int64_t)(lo + q) * L.ldw + c)), t);
-          wc = stored<VT, A>(mul_rn(t, rho));
-        } else {
-          wc = Store<VT>::load(Wj + c);
-        }
-        accp = fma_rn(av, wc, accp);
+        for (int q = 0; q < MAX_WINDOW; ++q)
+          if (q < nl) acc = fma_rn(-h[q], wl[q], acc);
+        wj = stored<VT, A>(mul_rn(acc, rho));
+        Store<VT>::put(Wj + i, wj);
+      } else {
+        wj = Store<VT>::load(Wj + i);
       }
-      const P pst = P(accp);
-      static_cast<P*>(L.p_out)[i] = pst;
-      const A pv = A(pst);
-      acc_pi = fma_rn(pv, pv, acc_pi);
+      acc_sig = fma_rn(wj, wj, acc_sig);
+      bad |= (col.got < L.zeta);
+    }
+    // ---- sketch: exact fixed-point contributions ----
+    if (valid) {
+      float vh, vl;
+      if constexpr (sizeof(A) == 8) {
+        vh = __double2float_rn((double)wj);
+        vl = __double2float_rn((double)wj - (double)vh);
+      } else {
+        vh = (float)wj;
+        vl = 0.f;
+      }
+      const FxWords<NW> xw = fx_split<NW>(vh, vl, fxs);
+      for (int e = 0; e < col.got; ++e) fx_emit<NW>(bins, sC, col.row(e), cp, xw, col.neg(e), C);
+    }
+    // ---- product: warp-cooperative CSR stream ----
+    if (SPMV) {
+      const int ebeg = __shfl_sync(FULL, rb, 0);
+      const int eend = __shfl_sync(FULL, re, nval - 1);
+      const int nent = eend - ebeg;
+      A accp = A(0);
+      if (nent <= STAGE) {
+        for (int kb = 0; kb < nent; kb += 32 * U_FUSED) {
+          int cc[U_FUSED];
+          A av[U_FUSED];
 #pragma unroll
-      for (int q = 0; q < MAX_WINDOW; ++q) {
-        if (q < nd) {
-          A wq = wj;
-          if (dlo + q != j) {
-#pragma unroll
-            for (int r = 0; r < MAX_WINDOW; ++r)
-              if (r == q + off) wq = wl[r];
+          for (int u = 0; u < U_FUSED; ++u) {
+            const int k = kb + u * 32 + lane;
+            cc[u] = 0;
+            av[u] = A(0);
+            if (k < nent) {
+              cc[u] = __ldg(L.col + ebeg + k);
+              av[u] = A(__ldg(val + ebeg + k));
+            }
           }
-          acc_dot[q] = fma_rn(wq, pv, acc_dot[q]);
+#pragma unroll
+          for (int u = 0; u < U_FUSED; ++u) {
+            const int k = kb + u * 32 + lane;
+            if (k < nent) mystage[k] = mul_rn(av[u], wj_at(cc[u]));
+          }
+        }
+        __syncwarp();
+        if (valid)
+          for (int k = rb - ebeg; k < re - ebeg; ++k) accp += mystage[k];
+        __syncwarp();
+      } else if (valid) {
+        for (int e = rb; e < re; ++e) accp = fma_rn(A(__ldg(val + e)), wj_at(__ldg(L.col + e)), accp);
+      }
+      if (valid) {
+        const P pst = P(accp);
+        static_cast<P*>(L.p_out)[i] = pst;
+        const A pv = A(pst);
+        acc_pi = fma_rn(pv, pv, acc_pi);
+#pragma unroll
+        for (int q = 0; q < MAX_WINDOW; ++q) {
+          if (q < nd) {
+            A wq = wj;
+            if (dlo + q != j) {
+#pragma unroll
+              for (int r = 0; r < MAX_WINDOW; ++r)
+                if (r == q + off) wq = wl[r];
+            }
+            acc_dot[q] = fma_rn(wq, pv, acc_dot[q]);
+          }
         }
       }
     }
@@ -221,21 +478,11 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepLaunch L, 
     }
   }
   __syncthreads();
-  Sk* out = static_cast<Sk*>(L.sk_part) + (size_t)blockIdx.x * L.s;
-  for (int b = threadIdx.x; b < L.s; b += blockDim.x) {
-    Sk acc = Sk(0);
-    for (int w = 0; w < nw; ++w) acc += bins[w * L.s + b];
-    out[b] = acc;
-  }
+  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
+  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value<NW>(bins, L.s, C, b, fxs, L.fx_wb);
   if (bad) atomicOr(&cd.flags[2], ERR_SKETCH);
 
-  // ---- last CTA reduces the scalars in CTA order ----
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(cd.counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
+  if (!last_block_flag(cd.counter, &s_last)) return;
   if (threadIdx.x < NQ) {
     double acc = 0.0;
     for (int c = 0; c < (int)gridDim.x; ++c) acc += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
@@ -243,291 +490,407 @@ __global__ void __launch_bounds__(STEP_THREADS) step_kernel(const StepLaunch L, 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    reducer_step(L, cd, tot, MAT ? 1 : 0, SPMV ? 1 : 0);
+    reduce_mat(L, cd, tot[0], MAT ? 1 : 0);
+    if (SPMV) reduce_spmv(L, cd, tot);
     *cd.counter = 0u;
   }
-}
-
-template <typename VT, typename AT, bool MAT, bool SPMV>
-void launch_step_t(const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st) {
-  using Sk = typename Types<VT>::Sk;
-  const size_t smem = (size_t)(STEP_THREADS / 32) * L.s * sizeof(Sk);
-  if (L.zeta <= 8) {
-    auto k = step_kernel<VT, AT, MAT, SPMV, 8>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
-  } else {
-    auto k = step_kernel<VT, AT, MAT, SPMV, MAX_ZETA>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
-  }
-}
-
-template <typename VT, typename AT>
-void dispatch_mat(const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st) {
-  if (L.mat && L.spmv) launch_step_t<VT, AT, true, true>(L, cd, m, st);
-  else if (L.mat) launch_step_t<VT, AT, true, false>(L, cd, m, st);
-  else if (L.spmv) launch_step_t<VT, AT, false, true>(L, cd, m, st);
-  else launch_step_t<VT, AT, false, false>(L, cd, m, st);
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool last_block(unsigned* counter, int* s_last) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) *s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (*s_last) __threadfence();
-  return *s_last != 0;
+// Float-float basis ("df64"): (hi, lo) float pairs, arithmetic on the FP32
+// pipes.  The sums that define the Arnoldi relation (products and
+// orthogonalization), the sketch and the dots are float-float accurate.
+
+__device__ __forceinline__ ff ld_ff(const float2* p) {
+  const float2 v = __ldg(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st_ff(float2* p, ff v) { *p = make_float2(v.hi, v.lo); }
+
+// Compensated accumulation: S + E tracks a sum of float-float products.
+struct ffacc {
+  float S = 0.f, E = 0.f;
+  __device__ __forceinline__ void add_prod(ff a, ff w) {
+    const float p = __fmul_rn(a.hi, w.hi);
+    float e = __fmaf_rn(a.hi, w.hi, -p);
+    e = __fmaf_rn(a.hi, w.lo, e);
+    e = __fmaf_rn(a.lo, w.hi, e);
+    add_pe(p, e);
+  }
+  __device__ __forceinline__ void add_pe(float p, float e) {
+    const ff t = two_sum(S, p);
+    S = t.hi;
+    E = __fadd_rn(E, __fadd_rn(t.lo, e));
+  }
+  __device__ __forceinline__ ff result() const { return fast_two_sum(S, E); }
+};
+
+// product of a matrix value and a float-float entry as (p, e), p + e accurate
+// to float-float precision
+__device__ __forceinline__ float2 prod_pe(float a, ff w) {
+  const float p = __fmul_rn(a, w.hi);
+  float e = __fmaf_rn(a, w.hi, -p);
+  e = __fmaf_rn(a, w.lo, e);
+  return make_float2(p, e);
+}
+__device__ __forceinline__ float2 prod_pe(float2 a, ff w) {
+  const float p = __fmul_rn(a.x, w.hi);
+  float e = __fmaf_rn(a.x, w.hi, -p);
+  e = __fmaf_rn(a.x, w.lo, e);
+  e = __fmaf_rn(a.y, w.hi, e);
+  return make_float2(p, e);
 }
 
-__global__ void norm_b_kernel(const double* b, int n, double* part, CycleDev cd, int rows_per_cta) {
-  __shared__ double red[32];
+// Block-wide float-float sum, result (as double) in thread 0.
+__device__ __forceinline__ double block_sum_ff(ff v, float* sh_hi, float* sh_lo) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const ff u{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+    v = ff_add(v, u);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh_hi[wid] = v.hi;
+    sh_lo[wid] = v.lo;
+  }
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+    ff a{0.f, 0.f};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = ff_add(a, ff{sh_hi[w], sh_lo[w]});
+    r = ff_to_double(a);
+  }
+  return r;
+}
+
+template <bool MAT, int SKM>
+__global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunch L, const CycleDev cd) {
+  constexpr int NW = 3;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int C = L.sk_copies;
+  int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
+  __shared__ float red[64];
   __shared__ int s_last;
-  double acc = 0.0;
-  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
-  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) acc = fma(b[i], b[i], acc);
-  const double v = block_sum(acc, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = v;
-  if (!last_block(cd.counter, &s_last)) return;
+  __shared__ FxScale s_fx;
+  __shared__ ff s_h[MAX_WINDOW + 1];
+  const int j = L.j;
+  if (cd.flags[0] < j) return;
+  const int lo = MAT ? max(0, j - L.k) : j;
+  const int nl = j - lo;
+  for (int e = threadIdx.x; e < NW * L.s * C; e += blockDim.x) bins[e] = 0;
+  if (threadIdx.x == 0) {  // per-CTA prologue (float64 work done once)
+    s_fx = fx_scale(L, cd, MAT ? 1 : 0);
+    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
+    s_h[MAX_WINDOW] = MAT ? ff_from_double(c[MAX_WINDOW]) : ff{1.f, 0.f};
+  }
+  __syncthreads();
+  const FxScale fxs = s_fx;
+  const int cp = lane & (C - 1);
+  const int sC = L.s * C;
+
+  const float2* W = static_cast<const float2*>(L.W);
+  float2* Wj = static_cast<float2*>(L.W) + (int64_t)j * L.ldw;
+  const float2* pprev = static_cast<const float2*>(L.p_prev);
+  ff h[MAX_WINDOW];
+  const float2* Wq[MAX_WINDOW];
+#pragma unroll
+  for (int q = 0; q < MAX_WINDOW; ++q) {
+    h[q] = s_h[q];
+    Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * L.ldw;
+  }
+  const ff rho = s_h[MAX_WINDOW];
+  const SketchSpec sp = spec_of(L);
+  const uint32_t inv_s = sketch_inv_s(L.s);
+  ffacc acc_sig;
+  int bad = 0;
+  const int r0 = blockIdx.x * L.rows_per_cta;
+  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  for (int t0 = r0; t0 < r1; t0 += STEP_THREADS) {
+    const int i0 = t0 + wid * 32;
+    if (i0 >= r1) continue;  // warp-uniform
+    const int i = i0 + lane;
+    const bool valid = i < r1;
+    ff wj{0.f, 0.f};
+    typename SkColOf<SKM>::type col;
+    if (valid) {
+      ff pv{0.f, 0.f};
+      ff wl[MAX_WINDOW];
+      if (MAT) {
+        pv = ld_ff(pprev + i);
+#pragma unroll
+        for (int q = 0; q < MAX_WINDOW; ++q)
+          if (q < nl) wl[q] = ld_ff(Wq[q] + i);
+      }
+      col.load(L, sp, inv_s, i);
+      if (MAT) {
+        ff acc = pv;
+#pragma unroll
+        for (int q = 0; q < MAX_WINDOW; ++q)
+          if (q < nl) acc = ff_add(acc, ff_mul(h[q], wl[q]));
+        wj = ff_mul(acc, rho);
+        st_ff(Wj + i, wj);
+      } else {
+        wj = ld_ff(Wj + i);
+      }
+      acc_sig.add_prod(wj, wj);
+      bad |= (col.got < L.zeta);
+      const FxWords<NW> xw = fx_split<NW>(wj.hi, wj.lo, fxs);
+      for (int e = 0; e < col.got; ++e) fx_emit<NW>(bins, sC, col.row(e), cp, xw, col.neg(e), C);
+    }
+    (void)wid;
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  const double v = block_sum_ff(acc_sig.result(), red, red + 32);
+  if (threadIdx.x == 0) part[0] = v;
+  __syncthreads();
+  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
+  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value<NW>(bins, L.s, C, b, fxs, L.fx_wb);
+  if (bad) atomicOr(&cd.flags[2], ERR_SKETCH);
+  if (!last_block_flag(cd.counter, &s_last)) return;
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + c);
-    cd.scal[4] = t;
-    const double eta = sqrt(t);
-    cd.scal[0] = eta;
-    cd.scal[1] = (eta > 0.0) ? 1.0 / eta : 0.0;
-    if (!isfinite(t)) cd.flags[2] |= ERR_NONFINITE;
+    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ);
+    reduce_mat(L, cd, t, MAT ? 1 : 0);
     *cd.counter = 0u;
   }
 }
 
-template <typename VT>
-__global__ void start_kernel(const double* b, VT* W0, int n, CycleDev cd) {
-  const double inv = cd.scal[1];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double v = b[i] * inv;
-    if constexpr (sizeof(VT) == 8) W0[i] = v;
-    else Store<VT>::put(W0 + i, __double2float_rn(v));
-  }
-}
-
-// Cycle end: x += W_m z and the next start vector v = (w_{m+1} - W_m g) / tau
-// (written into slot 0), with ||y||^2 and ||x||^2 reduced for the stop test.
-template <typename VT>
-__global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw, int n, int m_eff,
-                                                              int has_next, const double* zg, int m,
-                                                              double* x, double* part, CycleDev cd,
-                                                              int rows_per_cta) {
-  __shared__ double zs[256], gs[256];
-  __shared__ double red[32];
+template <typename AT>
+__global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaunch L, const CycleDev cd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* stage = reinterpret_cast<float2*>(smem);  // [warps][STAGE] (p, e)
+  __shared__ float rhi[32], rlo[32];
   __shared__ int s_last;
-  for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
-    zs[q] = zg[q];
-    gs[q] = zg[m + q];
-  }
-  const double tau_inv = zg[2 * m];
-  __syncthreads();
-  double ay = 0.0, ax = 0.0;
-  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
-  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
-    double y = 0.0;
-    double v = has_next ? double(Store<VT>::load(W + (int64_t)m_eff * ldw + i)) : 0.0;
-    for (int q = 0; q < m_eff; ++q) {
-      const double w = double(Store<VT>::load(W + (int64_t)q * ldw + i));
-      y = fma(w, zs[q], y);
-      v = fma(-w, gs[q], v);
+  __shared__ double tot[NQ];
+  const int j = L.j;
+  if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float2* W = static_cast<const float2*>(L.W);
+  const float2* Wj = W + (int64_t)j * L.ldw;
+  const AT* val = static_cast<const AT*>(L.val);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = j - dlo + 1;
+  ffacc acc_pi;
+  ffacc acc_dot[MAX_WINDOW];
+  float2* mystage = stage + wid * STAGE;
+  const int r0 = blockIdx.x * L.rows_per_cta;
+  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  for (int t0 = r0; t0 < r1; t0 += STEP_THREADS) {
+    const int i0 = t0 + wid * 32;
+    if (i0 >= r1) continue;  // warp-uniform
+    const int i = i0 + lane;
+    const bool valid = i < r1;
+    const int nval = min(32, r1 - i0);
+    int rb = 0, re = 0;
+    ff wq[MAX_WINDOW];
+    if (valid) {
+      rb = __ldg(L.row_ptr + i);
+      re = __ldg(L.row_ptr + i + 1);
+#pragma unroll
+      for (int q = 0; q < MAX_WINDOW; ++q)
+        if (q < nd) wq[q] = ld_ff(W + (int64_t)(dlo + q) * L.ldw + i);
     }
-    const double xn = x[i] + y;
-    x[i] = xn;
-    if (has_next) {
-      const double vn = v * tau_inv;
-      if constexpr (sizeof(VT) == 8) W[i] = vn;
-      else Store<VT>::put(W + i, __double2float_rn(vn));
+    const int ebeg = __shfl_sync(FULL, rb, 0);
+    const int eend = __shfl_sync(FULL, re, nval - 1);
+    const int nent = eend - ebeg;
+    ffacc acc;
+    if (nent <= STAGE) {
+      for (int kb = 0; kb < nent; kb += 32 * U_FF) {
+        int cc[U_FF];
+        AT av[U_FF];
+#pragma unroll
+        for (int u = 0; u < U_FF; ++u) {
+          const int k = kb + u * 32 + lane;
+          cc[u] = 0;
+          if (k < nent) {
+            cc[u] = __ldg(L.col + ebeg + k);
+            av[u] = __ldg(val + ebeg + k);
+          }
+        }
+        ff wv[U_FF];
+#pragma unroll
+        for (int u = 0; u < U_FF; ++u) {
+          const int k = kb + u * 32 + lane;
+          if (k < nent) wv[u] = ld_ff(Wj + cc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U_FF; ++u) {
+          const int k = kb + u * 32 + lane;
+          if (k < nent) mystage[k] = prod_pe(av[u], wv[u]);
+        }
+      }
+      __syncwarp();
+      if (valid)
+        for (int k = rb - ebeg; k < re - ebeg; ++k) {
+          const float2 pe = mystage[k];
+          acc.add_pe(pe.x, pe.y);
+        }
+      __syncwarp();
+    } else if (valid) {
+      for (int e = rb; e < re; ++e) {
+        const float2 pe = prod_pe(__ldg(val + e), ld_ff(Wj + __ldg(L.col + e)));
+        acc.add_pe(pe.x, pe.y);
+      }
     }
-    ay = fma(y, y, ay);
-    ax = fma(xn, xn, ax);
+    if (valid) {
+      const ff p = acc.result();
+      st_ff(static_cast<float2*>(L.p_out) + i, p);
+      acc_pi.add_prod(p, p);
+#pragma unroll
+      for (int q = 0; q < MAX_WINDOW; ++q)
+        if (q < nd) acc_dot[q].add_prod(wq[q], p);
+    }
   }
-  double v = block_sum(ay, red);
-  if (threadIdx.x == 0) part[2 * blockIdx.x] = v;
-  v = block_sum(ax, red);
-  if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = v;
-  if (!last_block(cd.counter, &s_last)) return;
-  if (threadIdx.x < 2) {
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
+  if (threadIdx.x == 0) part[1] = v;
+#pragma unroll
+  for (int q = 0; q < MAX_WINDOW; ++q) {
+    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
+    if (threadIdx.x == 0) part[2 + q] = v;
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  if (threadIdx.x < NQ) {
     double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + 2 * c + threadIdx.x);
-    cd.scal[2 + threadIdx.x] = t;
+    if (threadIdx.x >= 1)
+      for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
+    tot[threadIdx.x] = t;
   }
   __syncthreads();
-  if (threadIdx.x == 0) *cd.counter = 0u;
-}
-
-template <typename Sk>
-__global__ void sketch_reduce_kernel(const Sk* part, int ncols, int grid, int s, double scale,
-                                     int64_t col_stride, double* U) {
-  const int j = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ncols || r >= s) return;
-  const Sk* p = part + (size_t)j * col_stride;
-  double acc = 0.0;
-  for (int c = 0; c < grid; ++c) acc += double(p[(size_t)c * s + r]);
-  U[(size_t)j * s + r] = acc * scale;
-}
-
-__global__ void spmv_f64_kernel(int n, const int* rp, const int* ci, const double* val, const double* x,
-                                double* y) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) acc = fma(val[e], x[ci[e]], acc);
-    y[i] = acc;
-  }
-}
-
-__global__ void dot_f64_kernel(const double* a, const double* b, int n, double* part, double* out,
-                               unsigned* counter, int rows_per_cta) {
-  __shared__ double red[32];
-  __shared__ int s_last;
-  double acc = 0.0;
-  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
-  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) acc = fma(a[i], b[i], acc);
-  const double v = block_sum(acc, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = v;
-  if (!last_block(counter, &s_last)) return;
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + c);
-    *out = t;
-    *counter = 0u;
+    reduce_spmv(L, cd, tot);
+    *cd.counter = 0u;
   }
 }
 
-__global__ void sketch_columns_kernel(int64_t col0, int64_t count, SketchSpec sp, int* rows,
-                                      signed char* signs, int* err) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= count) return;
-  int e = 0;
-  int* rr = rows + t * sp.zeta;
-  signed char* ss = signs + t * sp.zeta;
-  const int got = sketch_column<MAX_ZETA>((uint32_t)(col0 + t), sp, [&](int row, bool neg) {
-    rr[e] = row;
-    ss[e] = neg ? (signed char)-1 : (signed char)1;
-    ++e;
-  });
-  if (got < sp.zeta) atomicOr(err, ERR_SKETCH);
+// ---------------------------------------------------------------------------
+// fixed-point sketch bins of a CTA: words x s x copies ints
+int fx_words(int basis) { return (basis == 0 || basis == 3) ? 3 : 2; }
+size_t bins_bytes(int basis, int s, int copies) { return (size_t)fx_words(basis) * s * copies * sizeof(int); }
+
+size_t fused_smem(int basis, int s, int copies) {
+  const size_t a = (basis == 0) ? 8 : 4;
+  return align16(bins_bytes(basis, s, copies)) + (size_t)(STEP_THREADS / 32) * STAGE * a;
 }
 
-}  // namespace
+template <typename VT, typename AT, bool MAT, bool SPMV, int SKM>
+void launch_fused(const StepLaunch& L, const CycleDev& cd, int basis, cudaStream_t st) {
+  const size_t smem = fused_smem(basis, L.s, L.sk_copies);
+  auto k = step_kernel<VT, AT, MAT, SPMV, SKM>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
+}
 
-namespace {
+template <typename VT, typename AT, bool MAT, bool SPMV>
+void fused_sk(const StepLaunch& L, const CycleDev& cd, int basis, cudaStream_t st) {
+  switch (L.sk_mode) {
+    case SK_TAB8: launch_fused<VT, AT, MAT, SPMV, SK_TAB8>(L, cd, basis, st); break;
+    case SK_TAB16: launch_fused<VT, AT, MAT, SPMV, SK_TAB16>(L, cd, basis, st); break;
+    case SK_GEN8: launch_fused<VT, AT, MAT, SPMV, SK_GEN8>(L, cd, basis, st); break;
+    default: launch_fused<VT, AT, MAT, SPMV, SK_GEN>(L, cd, basis, st); break;
+  }
+}
+
 template <typename VT, typename AT>
-int occupancy_t(int zeta, int s) {
-  using Sk = typename Types<VT>::Sk;
-  const size_t smem = (size_t)(STEP_THREADS / 32) * s * sizeof(Sk);
-  int blocks = 0;
-  if (zeta <= 8) {
-    auto k = step_kernel<VT, AT, true, true, 8>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, STEP_THREADS, smem);
-  } else {
-    auto k = step_kernel<VT, AT, true, true, MAX_ZETA>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, STEP_THREADS, smem);
-  }
-  return blocks < 1 ? 1 : blocks;
+void fused_dispatch(const StepLaunch& L, const CycleDev& cd, int basis, cudaStream_t st) {
+  if (L.mat && L.spmv) fused_sk<VT, AT, true, true>(L, cd, basis, st);
+  else if (L.mat) fused_sk<VT, AT, true, false>(L, cd, basis, st);
+  else if (L.spmv) fused_sk<VT, AT, false, true>(L, cd, basis, st);
+  else fused_sk<VT, AT, false, false>(L, cd, basis, st);
 }
+
+template <bool MAT, int SKM>
+void launch_ff_mat_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  const size_t smem = bins_bytes(3, L.s, L.sk_copies);
+  auto k = ff_mat_kernel<MAT, SKM>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
+}
+
+template <bool MAT>
+void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  switch (L.sk_mode) {
+    case SK_TAB8: launch_ff_mat_t<MAT, SK_TAB8>(L, cd, st); break;
+    case SK_TAB16: launch_ff_mat_t<MAT, SK_TAB16>(L, cd, st); break;
+    case SK_GEN8: launch_ff_mat_t<MAT, SK_GEN8>(L, cd, st); break;
+    default: launch_ff_mat_t<MAT, SK_GEN>(L, cd, st); break;
+  }
+}
+
+constexpr size_t FF_STAGE_SMEM = (size_t)(STEP_THREADS / 32) * STAGE * sizeof(float2);
+
+void launch_ff_step(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (L.mat) launch_ff_mat<true>(L, cd, st);
+  else launch_ff_mat<false>(L, cd, st);
+  if (L.spmv) {
+    if (L.val_f32) {
+      cudaFuncSetAttribute(ff_spmv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_STAGE_SMEM);
+      ff_spmv_kernel<float><<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
+    } else {
+      cudaFuncSetAttribute(ff_spmv_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_STAGE_SMEM);
+      ff_spmv_kernel<float2><<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
+    }
+  }
+}
+
+template <typename K>
+int occ(K kern, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, STEP_THREADS, smem);
+  return b < 1 ? 1 : b;
+}
+
 }  // namespace
 
-// Resident CTAs per SM of the main step kernel (one persistent wave).
-int step_ctas_per_sm(int basis, int zeta, int s, int vals_f32) {
-  if (basis == 0) return vals_f32 ? occupancy_t<double, float>(zeta, s) : occupancy_t<double, double>(zeta, s);
-  if (basis == 1) return occupancy_t<float, float>(zeta, s);
-  return occupancy_t<__nv_bfloat16, float>(zeta, s);
+int sketch_bin_copies(int basis, int s) {
+  // lane-private copies: the largest power of two <= 32 whose bins fit in 64 KB
+  int c = 32;
+  while (c > 1 && bins_bytes(basis, s, c) > 64 * 1024) c >>= 1;
+  return c;
+}
+
+// Bits per fixed-point word so that no bin column can overflow: a column
+// receives at most ceil(rows_per_cta / copies) contributions of magnitude
+// <= 2^(wb-1), and the rounding trick needs wb <= 22.
+int sketch_word_bits(int rows_per_cta, int copies) {
+  const long long per = (rows_per_cta + copies - 1) / copies + 1;
+  int lg = 0;
+  while ((1ll << lg) < per) ++lg;
+  return std::max(12, std::min(21, 30 - lg));
+}
+
+// Resident CTAs per SM of the main step kernel(s) (one persistent wave).
+int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
+  (void)sk_mode;
+  if (basis == 3) {
+    const int a = occ(ff_mat_kernel<true, SK_TAB8>, bins_bytes(3, s, copies));
+    const int b = occ(ff_spmv_kernel<float>, FF_STAGE_SMEM);
+    return std::min(a, b);
+  }
+  const size_t smem = fused_smem(basis, s, copies);
+  if (basis == 0)
+    return vals_f32 ? occ(step_kernel<double, float, true, true, SK_TAB8>, smem)
+                    : occ(step_kernel<double, double, true, true, SK_TAB8>, smem);
+  if (basis == 1) return occ(step_kernel<float, float, true, true, SK_TAB8>, smem);
+  return occ(step_kernel<__nv_bfloat16, float, true, true, SK_TAB8>, smem);
 }
 
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st) {
-  if (basis == 0) {
-    if (L.val_f32) dispatch_mat<double, float>(L, cd, m, st);
-    else dispatch_mat<double, double>(L, cd, m, st);
+  (void)m;
+  if (basis == 3) {
+    launch_ff_step(L, cd, st);
+  } else if (basis == 0) {
+    if (L.val_f32) fused_dispatch<double, float>(L, cd, basis, st);
+    else fused_dispatch<double, double>(L, cd, basis, st);
   } else if (basis == 1) {
-    dispatch_mat<float, float>(L, cd, m, st);
+    fused_dispatch<float, float>(L, cd, basis, st);
   } else {
-    dispatch_mat<__nv_bfloat16, float>(L, cd, m, st);
+    fused_dispatch<__nv_bfloat16, float>(L, cd, basis, st);
   }
 }
 
-void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st) {
-  const int rpc = (n + grid - 1) / grid;
-  norm_b_kernel<<<grid, STEP_THREADS, 0, st>>>(b, n, part, cd, rpc);
-}
-
-void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& cd, int grid,
-                  cudaStream_t st) {
-  if (basis == 0) start_kernel<double><<<grid, STEP_THREADS, 0, st>>>(b, (double*)W0, n, cd);
-  else if (basis == 1) start_kernel<float><<<grid, STEP_THREADS, 0, st>>>(b, (float*)W0, n, cd);
-  else start_kernel<__nv_bfloat16><<<grid, STEP_THREADS, 0, st>>>(b, (__nv_bfloat16*)W0, n, cd);
-}
-
-void launch_update(int basis, void* W, int64_t ldw, int n, int m_eff, int has_next, const double* zg,
-                   double* x, double* part, int grid, const CycleDev& cd, int m, cudaStream_t st) {
-  const int rpc = (n + grid - 1) / grid;
-  if (basis == 0)
-    update_kernel<double><<<grid, STEP_THREADS, 0, st>>>((double*)W, ldw, n, m_eff, has_next, zg, m, x,
-                                                          part, cd, rpc);
-  else if (basis == 1)
-    update_kernel<float><<<grid, STEP_THREADS, 0, st>>>((float*)W, ldw, n, m_eff, has_next, zg, m, x,
-                                                         part, cd, rpc);
-  else
-    update_kernel<__nv_bfloat16><<<grid, STEP_THREADS, 0, st>>>((__nv_bfloat16*)W, ldw, n, m_eff,
-                                                                 has_next, zg, m, x, part, cd, rpc);
-}
-
-void launch_sketch_reduce(int basis, const void* sk_part, int ncols, int grid, int s, int zeta,
-                          int64_t col_stride, double* U, cudaStream_t st) {
-  dim3 g((s + 127) / 128, ncols);
-  const double scale = 1.0 / std::sqrt((double)zeta);
-  if (basis == 0)
-    sketch_reduce_kernel<double><<<g, 128, 0, st>>>((const double*)sk_part, ncols, grid, s, scale,
-                                                    col_stride, U);
-  else
-    sketch_reduce_kernel<float><<<g, 128, 0, st>>>((const float*)sk_part, ncols, grid, s, scale,
-                                                   col_stride, U);
-}
-
-void launch_spmv_f64(int n, const int* row_ptr, const int* col, const double* val, const double* x,
-                     double* y, cudaStream_t st) {
-  const int grid = std::max(1, std::min(4096, (n + 255) / 256));
-  spmv_f64_kernel<<<grid, 256, 0, st>>>(n, row_ptr, col, val, x, y);
-}
-
-void launch_dot_f64(const double* a, const double* b, int n, double* part, int grid, double* out,
-                    unsigned* counter, cudaStream_t st) {
-  const int rpc = (n + grid - 1) / grid;
-  dot_f64_kernel<<<grid, STEP_THREADS, 0, st>>>(a, b, n, part, out, counter, rpc);
-}
-
-void launch_sketch_columns(int64_t col0, int64_t count, int s, int zeta, uint64_t seed, int* rows,
-                           signed char* signs, int* err, cudaStream_t st) {
-  SketchSpec sp;
-  sp.s = s;
-  sp.zeta = zeta;
-  sp.lim = 32768u - 32768u % (uint32_t)s;
-  sp.k0 = (uint32_t)(seed & 0xFFFFFFFFull);
-  sp.k1 = (uint32_t)(seed >> 32);
-  sp.scale = 1.f;
-  const int grid = (int)((count + 255) / 256);
-  if (grid > 0) sketch_columns_kernel<<<grid, 256, 0, st>>>(col0, count, sp, rows, signs, err);
-}
-
-}  // namespace krylov
-
-namespace krylov {
-namespace {
-__global__ void cycle_reset_kernel(CycleDev cd, int m) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    cd.flags[0] = m;
-    cd.flags[1] = 0;
-  }
-}
-}  // namespace
-void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st) { cycle_reset_kernel<<<1, 32, 0, st>>>(cd, m); }
 }  // namespace krylov
