@@ -156,6 +156,22 @@ def reference_main(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def step_traffic():
+    """DRAM bytes of one Arnoldi step from the committed ncu summary, or None
+    when the step kernels changed since those counters were taken."""
+    import hashlib
+
+    tf = ROOT / "profiles" / "step_kernel_traffic.txt"
+    src = ROOT / "paper_2503_22631_gb300" / "csrc" / "step_kernels.cu"
+    if not tf.exists() or not src.exists():
+        return None
+    kv = dict(line.split("=", 1) for line in tf.read_text().splitlines()
+              if "=" in line and not line.startswith("#"))
+    if kv.get("step_kernels_sha256_16") != hashlib.sha256(src.read_bytes()).hexdigest()[:16]:
+        return None
+    return float(kv["bytes_per_launch"])
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -282,10 +298,7 @@ def main():
             peaks = json.loads(pk.read_text())
         peak = peaks.get("hbm_gbs", 6800.0)
         achieved = step_bytes / (steps_ms / 1e3) / 1e9
-        traffic = None
-        tf = ROOT / "profiles" / "step_kernel_traffic.json"
-        if tf.exists():
-            traffic = json.loads(tf.read_text()).get("bytes_per_launch")
+        traffic = step_traffic()
 
         # end to end through the host entry point (pinned host buffers)
         e2e = None
@@ -329,7 +342,10 @@ def main():
                    "cycles": cycles, "basis": args.basis, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set > L2 (no flush)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "step_kernel (fused SpMV + truncated orthogonalization + sketch)",
+                     "traffic": traffic if args.basis == "df64" else None,
+                     "kernel": ("Arnoldi step: ff_mat_kernel + ff_spmv_kernel (materialize/sketch, SpMV/dots)"
+                                if args.basis == "df64" else
+                                "Arnoldi step: step_kernel (fused SpMV + truncated orthogonalization + sketch)"),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
         "cpu_baseline": cpu,
         "e2e": e2e,

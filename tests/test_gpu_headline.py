@@ -1,0 +1,76 @@
+"""Full-size checks at the launch configuration bench.py times.
+
+The 128^3 convection-diffusion workload (n = 2,097,152): the cycle count the
+benchmark uses reaches 1e-8 relative error against the Kronecker-sum closed
+form, one full-size cycle matches the oracle, and the float32 basis' error
+floor is what the design notes state.
+"""
+import numpy as np
+import pytest
+
+import bench
+import workloads as W
+from oracle import dense as D
+from oracle import krylov as K
+from oracle import truth as TR
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def headline():
+    A, b = bench.make_inputs()
+    wl = bench.WORKLOAD
+    ref = TR.kron_expm_apply(wl["grid"], 3, wl["beta"], wl["t"], b)
+    return A, b, ref
+
+
+def _solve(A, b, basis, cycles, tol=0.0):
+    import torch
+
+    from paper_2503_22631_gb300 import F_EXP_NEG, Krylov
+
+    wl = bench.WORKLOAD
+    kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=wl["t"], m=wl["m"], k=wl["k"], s=wl["s"],
+                seed=bench.SEED, zeta=wl["zeta"], basis=basis)
+    x = kr.apply(torch.from_numpy(b).cuda(), tol=tol, max_cycles=cycles)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), kr
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("basis", [3, 0])
+def test_benchmark_cycle_count_reaches_1e8(lib, cuda, headline, basis):
+    A, b, ref = headline
+    cycles = bench.CYCLES_TO_1E8["df64"]
+    x, kr = _solve(A, b, basis, cycles)
+    assert kr.stats["cycles"] == cycles
+    assert _rel(x, ref) <= 1e-8
+
+
+def test_relative_stop_rule_reaches_1e8(lib, cuda, headline):
+    A, b, ref = headline
+    x, kr = _solve(A, b, 3, 30, tol=1e-8)
+    assert _rel(x, ref) <= 1e-8
+    assert kr.stats["last_update_norm"] <= 1e-8 * kr.stats["x_norm"]
+
+
+def test_float32_basis_floor(lib, cuda, headline):
+    """The float32 basis stalls at its storage-rounding floor (~1e-5), far
+    above 1e-8 and far below O(1)."""
+    A, b, ref = headline
+    x, _ = _solve(A, b, 1, 12)
+    err = _rel(x, ref)
+    assert 1e-7 < err < 1e-4
+
+
+def test_full_size_first_cycle_matches_oracle(lib, cuda, headline):
+    A, b, _ = headline
+    wl = bench.WORKLOAD
+    r = K.restarted(A, b, D.EXP_NEG, wl["t"], wl["m"], wl["k"], wl["s"], wl["zeta"], bench.SEED,
+                    mode=K.TRUNC, tol=0.0, max_cycles=1)
+    x, _ = _solve(A, b, 3, 1)
+    assert _rel(x, r.x) <= 1e-10
