@@ -170,6 +170,25 @@ krylov_status krylov_set_param(krylov_handle* h, double t);
 krylov_status krylov_spmv(krylov_handle* h, const double* x, double* y, int transpose,
                           const double* dot_with, double* dot_out);
 
+/* y <- A x and, if dot_with is not NULL, *dot_out <- <dot_with, y>, without
+ * allocating anything.  The paper has no counterpart: this is for callers that
+ * cannot allocate device memory when they need the product (during CUDA graph
+ * capture, inside a custom allocator, in latency-critical loops).  Unlike
+ * krylov_spmv it needs no handle: row_ptr (n+1), col_idx, val (nnz, float64),
+ * x, y (n) and dot_with, dot_out (n and 1 element) are caller-owned DEVICE
+ * pointers (dot_with and dot_out both NULL or both set); stream is a
+ * cudaStream_t (NULL = legacy default stream).  The call is asynchronous on
+ * that stream; it does not validate the CSR structure (krylov_create does).
+ * Scratch: a fixed 16 KiB device array inside the library, shared by all
+ * calls on a device and kept until the process exits; the first call on a
+ * device looks its address up (make it before any stream capture), and calls
+ * that overlap on the GPU race on it.  Limits: 1 <= n <= 2^31 - 2,
+ * 0 <= nnz <= 2^31 - 1, else KRYLOV_EINVAL. */
+krylov_status krylov_spmv_dot_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr,
+                                      const int32_t* col_idx, const double* val, const double* x,
+                                      double* y, const double* dot_with, double* dot_out,
+                                      void* stream);
+
 /* Problem size of a handle. */
 int64_t krylov_size(const krylov_handle* h);
 

@@ -47,6 +47,7 @@ EXPORTED = [
     "krylov_status_string",
     "krylov_sketch_columns",
     "krylov_last_cycle",
+    "krylov_spmv_dot_noalloc",
 ]
 
 
@@ -116,6 +117,8 @@ def load() -> C.CDLL:
     lib.krylov_sketch_columns.restype = C.c_int
     lib.krylov_last_cycle.argtypes = [P, P, C.c_int64, P, C.c_int64, P, C.c_int64, C.POINTER(C.c_int)]
     lib.krylov_last_cycle.restype = C.c_int
+    lib.krylov_spmv_dot_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, P, P, P]
+    lib.krylov_spmv_dot_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
