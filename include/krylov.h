@@ -64,7 +64,8 @@ typedef struct {
 } krylov_func;
 
 /* CSR matrix, borrowed for the duration of krylov_create (the library copies
- * it).  row_ptr: n+1 int32, monotone, row_ptr[0] = 0, row_ptr[n] = nnz;
+ * it); 1 <= n <= 2^31 - 2^20 and 0 <= nnz <= 2^31 - 16, else KRYLOV_EINVAL.
+ * row_ptr: n+1 int32, monotone, row_ptr[0] = 0, row_ptr[n] = nnz;
  * col_idx: nnz int32 in [0, n); val: nnz float64.  on_device != 0 means the
  * three arrays are device pointers, else host pointers.  (App. A: CSR.) */
 typedef struct {

@@ -22,6 +22,13 @@ using namespace krylov;
 namespace {
 
 constexpr double EXP_THETA = 2.0;  // ||B||_1 bound after scaling
+// Column-index and value arrays get CSR_PAD zeroed elements past nnz so the
+// step kernels can read them in aligned 16-byte chunks.
+constexpr size_t CSR_PAD = 8;
+// row_ptr gets RP_PAD zeroed entries past n+1: staged row_ptr slices of a
+// 256-row tile are copied as 260 entries.
+constexpr size_t RP_PAD = 272;
+constexpr int TMA_MAX_CAP = 4096;  // largest staged tile span (nonzeros)
 constexpr int EXP_TAYLOR_DEG = 24; // theta^25/25! e^theta < 2^-53
 
 struct DevBuf {
@@ -49,6 +56,7 @@ struct krylov_handle {
   float* val32 = nullptr;
   float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
+  int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
   int* rpt = nullptr;
   int* cit = nullptr;
   double* valt = nullptr;
@@ -180,21 +188,28 @@ struct Operator {
 krylov_status build_transpose(krylov_handle* h) {
   if (h->have_t) return KRYLOV_OK;
   int* work = nullptr;
-  CK(dalloc(h, &h->rpt, (size_t)h->n + 1));
-  CK(dalloc(h, &h->cit, (size_t)h->nnz));
-  CK(dalloc(h, &h->valt, (size_t)h->nnz));
+  CK(dalloc(h, &h->rpt, (size_t)h->n + 1 + RP_PAD));
+  CK(cudaMemsetAsync(h->rpt + h->n + 1, 0, RP_PAD * sizeof(int), h->st));
+  CK(dalloc(h, &h->cit, (size_t)h->nnz + CSR_PAD));
+  CK(cudaMemsetAsync(h->cit + h->nnz, 0, CSR_PAD * sizeof(int), h->st));
+  CK(dalloc(h, &h->valt, (size_t)h->nnz + CSR_PAD));
+  CK(cudaMemsetAsync(h->valt + h->nnz, 0, CSR_PAD * sizeof(double), h->st));
   CK(dalloc(h, &work, 2 * (size_t)h->n));
   CK(transpose_csr(h->n, h->nnz, h->rp, h->ci, h->val, h->rpt, h->cit, h->valt, work, h->st));
   if (h->val32) {
-    CK(dalloc(h, &h->valt32, (size_t)h->nnz));
+    CK(dalloc(h, &h->valt32, (size_t)h->nnz + CSR_PAD));
+    CK(cudaMemsetAsync(h->valt32 + h->nnz, 0, CSR_PAD * sizeof(float), h->st));
     CK(narrow_values(h->nnz, h->valt, h->valt32, h->d_flag, h->h_flags, h->st));
   }
   if (h->valff) {
-    CK(dalloc(h, &h->valtff, (size_t)h->nnz));
+    CK(dalloc(h, &h->valtff, (size_t)h->nnz + CSR_PAD));
+    CK(cudaMemsetAsync(h->valtff + h->nnz, 0, CSR_PAD * sizeof(float2), h->st));
     CK(split_values(h->nnz, h->valt, h->valtff, h->st));
   }
   CK(cudaStreamSynchronize(h->st));
   dfree(h, work);
+  CK(tile_span_max(h->n, h->rpt, h->d_flag, h->h_flags, h->st));
+  h->tma_cap_t = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 4) : 0;
   h->have_t = 1;
   return KRYLOV_OK;
 }
@@ -279,8 +294,10 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       L.zeta = h->opt.zeta;
       L.seed = h->seed;
       L.grid = h->grid;
-      L.rows_per_cta = (n + h->grid - 1) / h->grid;
+      // whole 256-row tiles per CTA (tiles then start at multiples of 256)
+      L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
       L.m = M;
+      L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : 0;
       L.sk_tab = h->sk_tab;
       L.sk_mode = h->sk_mode;
       L.sk_copies = h->sk_copies;
@@ -293,6 +310,7 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (h->h_flags[2] & ERR_TIMEOUT) return KRYLOV_ETIMEOUT;
     if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
     if (h->h_flags[2] & ERR_SKETCH) return KRYLOV_ECUDA;
     const int me = std::min(h->h_flags[0], M);
@@ -427,7 +445,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   krylov_options opt;
   krylov_options_default(&opt);
   if (opt_in) opt = *opt_in;
-  if (A->n < 1 || A->n > 0x7FFFFFF0LL || A->nnz < 0 || A->nnz > 0x7FFFFFF0LL) return KRYLOV_EINVAL;
+  if (A->n < 1 || A->n > 0x7FF00000LL || A->nnz < 0 || A->nnz > 0x7FFFFFF0LL) return KRYLOV_EINVAL;
   if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return KRYLOV_EINVAL;
   if (m < 1 || m > 256 || k < 1 || k > MAX_WINDOW || s < m + 1 || s > 1024) return KRYLOV_EINVAL;
   if (opt.zeta < 1 || opt.zeta > std::min(s, MAX_ZETA)) return KRYLOV_EINVAL;
@@ -465,24 +483,31 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
     cudaError_t e_ = (call);                          \
     if (e_ != cudaSuccess) return fail(cuda_status(e_)); \
   } while (0)
-  CKF(dalloc(h, &h->rp, (size_t)n + 1));
-  CKF(dalloc(h, &h->ci, (size_t)nnz));
-  CKF(dalloc(h, &h->val, (size_t)nnz));
+  CKF(dalloc(h, &h->rp, (size_t)n + 1 + RP_PAD));
+  CKF(dalloc(h, &h->ci, (size_t)nnz + CSR_PAD));
+  CKF(dalloc(h, &h->val, (size_t)nnz + CSR_PAD));
   CKF(dalloc(h, &h->d_flag, 4));
   CKF(cudaMemcpyAsync(h->rp, A->row_ptr, sizeof(int) * ((size_t)n + 1), kind, h->st));
   if (nnz > 0) {
     CKF(cudaMemcpyAsync(h->ci, A->col_idx, sizeof(int) * (size_t)nnz, kind, h->st));
     CKF(cudaMemcpyAsync(h->val, A->val, sizeof(double) * (size_t)nnz, kind, h->st));
   }
+  CKF(cudaMemsetAsync(h->ci + nnz, 0, CSR_PAD * sizeof(int), h->st));
+  CKF(cudaMemsetAsync(h->rp + n + 1, 0, RP_PAD * sizeof(int), h->st));
+  CKF(cudaMemsetAsync(h->val + nnz, 0, CSR_PAD * sizeof(double), h->st));
   CKF(validate_csr(n, nnz, h->rp, h->ci, h->d_flag, h->h_flags, h->st));
   if (h->h_flags[0] != 0) return fail(KRYLOV_EINVAL);
   // float32 copy of the values: exact-narrowing test, and the operand of the
   // float32/bfloat16 basis modes
-  CKF(dalloc(h, &h->val32, (size_t)nnz));
+  CKF(dalloc(h, &h->val32, (size_t)nnz + CSR_PAD));
+  CKF(cudaMemsetAsync(h->val32 + nnz, 0, CSR_PAD * sizeof(float), h->st));
   CKF(narrow_values(nnz, h->val, h->val32, h->d_flag, h->h_flags, h->st));
   h->vals_exact_f32 = (h->h_flags[0] == 0);
+  CKF(tile_span_max(n, h->rp, h->d_flag, h->h_flags, h->st));
+  h->tma_cap = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 4) : 0;
   if (opt.basis_dtype == KRYLOV_BASIS_DF64 && !(h->vals_exact_f32 && opt.narrow_values_if_exact)) {
-    CKF(dalloc(h, &h->valff, (size_t)nnz));
+    CKF(dalloc(h, &h->valff, (size_t)nnz + CSR_PAD));
+    CKF(cudaMemsetAsync(h->valff + nnz, 0, CSR_PAD * sizeof(float2), h->st));
     CKF(split_values(nnz, h->val, h->valff, h->st));
   }
 

@@ -18,7 +18,7 @@ struct CycleDev {
   unsigned* counter;  // arrival counters of the last-block reducers (zeroed)
 };
 
-enum : int { ERR_SKETCH = 1, ERR_NONFINITE = 2 };
+enum : int { ERR_SKETCH = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
 // Stored sparse sign embedding (generated once per handle on the device).
 struct SketchTable {
@@ -58,6 +58,7 @@ struct StepLaunch {
   int sk_mode;       // SK_* : stored table or regeneration in the kernel
   int sk_copies;     // lane-private copies of each sketch bin in shared memory
   int fx_wb;         // bits per fixed-point word of the sketch bins
+  int tma_cap;       // staged nonzeros per 256-row tile (0: no bulk-copy staging)
 };
 
 // basis dtype codes (krylov_basis)
@@ -87,6 +88,7 @@ cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* 
                          cudaStream_t st);
 cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag,
                           cudaStream_t st);
+cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaStream_t st);
 cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st);
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
                           int* cit, double* vt, int* work, cudaStream_t st);

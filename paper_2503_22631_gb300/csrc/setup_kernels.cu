@@ -105,6 +105,18 @@ __global__ void sort_rows_kernel(int n, const int* rpt, int* cit, double* vt) {
   }
 }
 
+// Largest 16-byte-aligned nonzero span of a 256-row tile (tiles start at
+// multiples of 256): ((rp[end] + 3) & ~3) - (rp[start] & ~3).
+__global__ void tile_span_kernel(int n, const int* rp, int* out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; (int64_t)t * 256 < n; t += stride) {
+    const int ts = t * 256;
+    const int te = min(ts + 256, n);
+    const int span = ((rp[te] + 3) & ~3) - (rp[ts] & ~3);
+    atomicMax(out, span);
+  }
+}
+
 int grid_for(int64_t work) {
   int64_t g = (work + 255) / 256;
   if (g < 1) g = 1;
@@ -125,6 +137,13 @@ cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* 
 cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag, cudaStream_t st) {
   cudaMemsetAsync(d_flag, 0, sizeof(int), st);
   if (nnz > 0) narrow_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, v, v32, d_flag);
+  cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaStream_t st) {
+  cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+  tile_span_kernel<<<grid_for((n + 255) / 256), 256, 0, st>>>(n, rp, d_flag);
   cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   return cudaStreamSynchronize(st);
 }

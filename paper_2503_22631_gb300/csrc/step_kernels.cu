@@ -564,11 +564,18 @@ __device__ __forceinline__ double block_sum_ff(ff v, float* sh_hi, float* sh_lo)
   return r;
 }
 
-template <bool MAT, int SKM>
+// Inputs of one row of ff_mat_kernel, loaded before any use so that two rows
+// per thread have their loads in flight together.
+template <int KW, int SKM> struct FfRow {
+  ff pv, wl[KW];
+  typename SkColOf<SKM>::type col;
+};
+
+template <bool MAT, int SKM, int KW>
 __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunch L, const CycleDev cd) {
   constexpr int NW = 3;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int C = L.sk_copies;
   int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
   __shared__ float red[64];
@@ -579,7 +586,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   if (cd.flags[0] < j) return;
   const int lo = MAT ? max(0, j - L.k) : j;
   const int nl = j - lo;
-  for (int e = threadIdx.x; e < NW * L.s * C; e += blockDim.x) bins[e] = 0;
+  {
+    const int nb = NW * L.s * C;
+    int4* b4 = reinterpret_cast<int4*>(bins);
+    for (int e = threadIdx.x; e < nb / 4; e += blockDim.x) b4[e] = make_int4(0, 0, 0, 0);
+    for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
+  }
   if (threadIdx.x == 0) {  // per-CTA prologue (float64 work done once)
     s_fx = fx_scale(L, cd, MAT ? 1 : 0);
     const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
@@ -594,10 +606,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   const float2* W = static_cast<const float2*>(L.W);
   float2* Wj = static_cast<float2*>(L.W) + (int64_t)j * L.ldw;
   const float2* pprev = static_cast<const float2*>(L.p_prev);
-  ff h[MAX_WINDOW];
-  const float2* Wq[MAX_WINDOW];
+  ff h[KW];
+  const float2* Wq[KW];
 #pragma unroll
-  for (int q = 0; q < MAX_WINDOW; ++q) {
+  for (int q = 0; q < KW; ++q) {
     h[q] = s_h[q];
     Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * L.ldw;
   }
@@ -606,41 +618,52 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   const uint32_t inv_s = sketch_inv_s(L.s);
   ffacc acc_sig;
   int bad = 0;
+
+  auto load_row = [&](FfRow<KW, SKM>& r, int i) {
+    if (MAT) {
+      r.pv = ld_ff(pprev + i);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nl) r.wl[q] = ld_ff(Wq[q] + i);
+    } else {
+      r.pv = ld_ff(Wj + i);
+    }
+    r.col.load(L, sp, inv_s, i);
+  };
+  auto do_row = [&](const FfRow<KW, SKM>& r, int i) {
+    ff wj;
+    if (MAT) {
+      ff acc = r.pv;
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nl) acc = ff_add(acc, ff_mul(h[q], r.wl[q]));
+      wj = ff_mul(acc, rho);
+      st_ff(Wj + i, wj);
+    } else {
+      wj = r.pv;
+    }
+    acc_sig.add_prod(wj, wj);
+    bad |= (r.col.got < L.zeta);
+    const FxWords<NW> xw = fx_split<NW>(wj.hi, wj.lo, fxs);
+    if constexpr (SKM == SK_TAB8 || SKM == SK_GEN8) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (e < r.col.got) fx_emit<NW>(bins, sC, r.col.row(e), cp, xw, r.col.neg(e), C);
+    } else {
+      for (int e = 0; e < r.col.got; ++e) fx_emit<NW>(bins, sC, r.col.row(e), cp, xw, r.col.neg(e), C);
+    }
+  };
+
   const int r0 = blockIdx.x * L.rows_per_cta;
   const int r1 = min(L.n, r0 + L.rows_per_cta);
-  for (int t0 = r0; t0 < r1; t0 += STEP_THREADS) {
-    const int i0 = t0 + wid * 32;
-    if (i0 >= r1) continue;  // warp-uniform
-    const int i = i0 + lane;
-    const bool valid = i < r1;
-    ff wj{0.f, 0.f};
-    typename SkColOf<SKM>::type col;
-    if (valid) {
-      ff pv{0.f, 0.f};
-      ff wl[MAX_WINDOW];
-      if (MAT) {
-        pv = ld_ff(pprev + i);
-#pragma unroll
-        for (int q = 0; q < MAX_WINDOW; ++q)
-          if (q < nl) wl[q] = ld_ff(Wq[q] + i);
-      }
-      col.load(L, sp, inv_s, i);
-      if (MAT) {
-        ff acc = pv;
-#pragma unroll
-        for (int q = 0; q < MAX_WINDOW; ++q)
-          if (q < nl) acc = ff_add(acc, ff_mul(h[q], wl[q]));
-        wj = ff_mul(acc, rho);
-        st_ff(Wj + i, wj);
-      } else {
-        wj = ld_ff(Wj + i);
-      }
-      acc_sig.add_prod(wj, wj);
-      bad |= (col.got < L.zeta);
-      const FxWords<NW> xw = fx_split<NW>(wj.hi, wj.lo, fxs);
-      for (int e = 0; e < col.got; ++e) fx_emit<NW>(bins, sC, col.row(e), cp, xw, col.neg(e), C);
-    }
-    (void)wid;
+  const int T = blockDim.x;
+  for (int i = r0 + (int)threadIdx.x; i < r1; i += 2 * T) {
+    const int i2 = i + T;
+    FfRow<KW, SKM> a, b;
+    load_row(a, i);
+    if (i2 < r1) load_row(b, i2);
+    do_row(a, i);
+    if (i2 < r1) do_row(b, i2);
   }
   double* part = L.part + (size_t)blockIdx.x * NQ;
   const double v = block_sum_ff(acc_sig.result(), red, red + 32);
@@ -658,7 +681,31 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   }
 }
 
-template <typename AT>
+// Four consecutive matrix values, read as one aligned 16-byte (float) or two
+// 16-byte (float-float pair) loads.
+template <typename AT> struct Vals4;
+template <> struct Vals4<float> {
+  float4 v;
+  __device__ __forceinline__ void load(const float* p, int c4) { v = __ldg(reinterpret_cast<const float4*>(p) + c4); }
+  __device__ __forceinline__ float get(int q) const { return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w)); }
+};
+template <> struct Vals4<float2> {
+  float4 a, b;
+  __device__ __forceinline__ void load(const float2* p, int c4) {
+    const float4* q4 = reinterpret_cast<const float4*>(p) + 2 * c4;
+    a = __ldg(q4);
+    b = __ldg(q4 + 1);
+  }
+  __device__ __forceinline__ float2 get(int q) const {
+    return q == 0 ? make_float2(a.x, a.y)
+                  : (q == 1 ? make_float2(a.z, a.w) : (q == 2 ? make_float2(b.x, b.y) : make_float2(b.z, b.w)));
+  }
+};
+__device__ __forceinline__ int comp(const int4& v, int q) { return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w)); }
+
+constexpr int UC_FF = 1;  // 16-byte chunks (4 nonzeros) per lane per batch
+
+template <typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaunch L, const CycleDev cd) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* stage = reinterpret_cast<float2*>(smem);  // [warps][STAGE] (p, e)
@@ -671,10 +718,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
   const float2* W = static_cast<const float2*>(L.W);
   const float2* Wj = W + (int64_t)j * L.ldw;
   const AT* val = static_cast<const AT*>(L.val);
+  const int4* col4 = reinterpret_cast<const int4*>(L.col);
   const int dlo = max(0, j - L.k + 1);
   const int nd = j - dlo + 1;
+  const float2* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
   ffacc acc_pi;
-  ffacc acc_dot[MAX_WINDOW];
+  ffacc acc_dot[KW];
   float2* mystage = stage + wid * STAGE;
   const int r0 = blockIdx.x * L.rows_per_cta;
   const int r1 = min(L.n, r0 + L.rows_per_cta);
@@ -685,41 +736,49 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
     const bool valid = i < r1;
     const int nval = min(32, r1 - i0);
     int rb = 0, re = 0;
-    ff wq[MAX_WINDOW];
+    ff wq[KW];
     if (valid) {
       rb = __ldg(L.row_ptr + i);
       re = __ldg(L.row_ptr + i + 1);
 #pragma unroll
-      for (int q = 0; q < MAX_WINDOW; ++q)
-        if (q < nd) wq[q] = ld_ff(W + (int64_t)(dlo + q) * L.ldw + i);
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) wq[q] = ld_ff(Wd[q] + i);
     }
     const int ebeg = __shfl_sync(FULL, rb, 0);
     const int eend = __shfl_sync(FULL, re, nval - 1);
     const int nent = eend - ebeg;
     ffacc acc;
-    if (nent <= STAGE) {
-      for (int kb = 0; kb < nent; kb += 32 * U_FF) {
-        int cc[U_FF];
-        AT av[U_FF];
+    if (nent <= STAGE - 4) {
+      // 16-byte chunks of the warp's nonzero range, starting at the aligned
+      // chunk that contains ebeg (arrays are padded past nnz)
+      const int cbase = ebeg >> 2;
+      const int nch = ((eend + 3) >> 2) - cbase;
+      for (int cb = 0; cb < nch; cb += 32 * UC_FF) {
+        int4 cc[UC_FF];
+        Vals4<AT> av[UC_FF];
 #pragma unroll
-        for (int u = 0; u < U_FF; ++u) {
-          const int k = kb + u * 32 + lane;
-          cc[u] = 0;
-          if (k < nent) {
-            cc[u] = __ldg(L.col + ebeg + k);
-            av[u] = __ldg(val + ebeg + k);
+        for (int u = 0; u < UC_FF; ++u) {
+          const int ch = cb + u * 32 + lane;
+          cc[u] = make_int4(0, 0, 0, 0);
+          if (ch < nch) {
+            cc[u] = __ldg(col4 + cbase + ch);
+            av[u].load(val, cbase + ch);
           }
         }
-        ff wv[U_FF];
+        ff wv[UC_FF][4];
 #pragma unroll
-        for (int u = 0; u < U_FF; ++u) {
-          const int k = kb + u * 32 + lane;
-          if (k < nent) wv[u] = ld_ff(Wj + cc[u]);
+        for (int u = 0; u < UC_FF; ++u) {
+          const int e0 = (cbase + cb + u * 32 + lane) * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (e0 + q >= ebeg && e0 + q < eend) wv[u][q] = ld_ff(Wj + comp(cc[u], q));
         }
 #pragma unroll
-        for (int u = 0; u < U_FF; ++u) {
-          const int k = kb + u * 32 + lane;
-          if (k < nent) mystage[k] = prod_pe(av[u], wv[u]);
+        for (int u = 0; u < UC_FF; ++u) {
+          const int e0 = (cbase + cb + u * 32 + lane) * 4;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (e0 + q >= ebeg && e0 + q < eend) mystage[e0 + q - ebeg] = prod_pe(av[u].get(q), wv[u][q]);
         }
       }
       __syncwarp();
@@ -740,7 +799,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
       st_ff(static_cast<float2*>(L.p_out) + i, p);
       acc_pi.add_prod(p, p);
 #pragma unroll
-      for (int q = 0; q < MAX_WINDOW; ++q)
+      for (int q = 0; q < KW; ++q)
         if (q < nd) acc_dot[q].add_prod(wq[q], p);
     }
   }
@@ -748,14 +807,166 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
   double v = block_sum_ff(acc_pi.result(), rhi, rlo);
   if (threadIdx.x == 0) part[1] = v;
 #pragma unroll
-  for (int q = 0; q < MAX_WINDOW; ++q) {
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;  // nd is uniform across the block
     v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
     if (threadIdx.x == 0) part[2 + q] = v;
   }
   if (!last_block_flag(cd.counter, &s_last)) return;
   if (threadIdx.x < NQ) {
     double t = 0.0;
-    if (threadIdx.x >= 1)
+    if (threadIdx.x >= 1 && threadIdx.x < 2 + nd)
+      for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
+    tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    reduce_spmv(L, cd, tot);
+    *cd.counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Product kernel with bulk-copy staging of the CSR stream (float-float basis).
+// The CTA walks its rows in tiles of 256; for tile t the row_ptr slice and the
+// tile's column/value slices are brought into shared memory by one thread with
+// cp.async.bulk (completion tracked by an mbarrier), two tiles ahead in a
+// double buffer, so the CSR bytes stream while the previous tile computes.
+// Each thread then forms its row's product from shared memory; only the
+// gathers of w_j stay on the critical path.  Waits are bounded: on timeout the
+// kernel sets ERR_TIMEOUT and keeps going (the host reports it).
+constexpr int TMA_ROWS = STEP_THREADS;     // rows per staged tile
+constexpr int TMA_RP = TMA_ROWS + 4;       // staged row_ptr entries (16-byte multiple)
+constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
+
+template <typename AT>
+__host__ __device__ __forceinline__ size_t tma_stage_bytes(int cap) {
+  return (size_t)TMA_RP * 4 + (size_t)cap * 4 + (size_t)cap * sizeof(AT);
+}
+
+__device__ __forceinline__ void acc_val(ffacc& acc, float a, ff w) {
+  const float2 pe = prod_pe(a, w);
+  acc.add_pe(pe.x, pe.y);
+}
+__device__ __forceinline__ void acc_val(ffacc& acc, float2 a, ff w) {
+  const float2 pe = prod_pe(a, w);
+  acc.add_pe(pe.x, pe.y);
+}
+
+template <typename AT, int KW>
+__global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const StepLaunch L, const CycleDev cd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ float rhi[32], rlo[32];
+  __shared__ int s_last;
+  __shared__ double tot[NQ];
+  const int j = L.j;
+  if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
+  const int cap = L.tma_cap;
+  const size_t sb = tma_stage_bytes<AT>(cap);
+  // stage st: row_ptr slice (TMA_RP ints), columns (cap ints), values (cap AT)
+  auto rp_st = [&](int st) { return reinterpret_cast<int*>(smem + (size_t)st * sb); };
+  auto col_st = [&](int st) { return rp_st(st) + TMA_RP; };
+  auto val_st = [&](int st) { return reinterpret_cast<AT*>(col_st(st) + cap); };
+  const float2* W = static_cast<const float2*>(L.W);
+  const float2* Wj = W + (int64_t)j * L.ldw;
+  const AT* val = static_cast<const AT*>(L.val);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = j - dlo + 1;
+  const float2* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
+  const int r0 = blockIdx.x * L.rows_per_cta;
+  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // thread 0: stage tile t given its nonzero range [e0, e1)
+  auto issue = [&](int t, int e0, int e1) {
+    const int st = t & 1;
+    const int ts = r0 + t * TMA_ROWS;
+    const int ea = e0 & ~3, eb = (e1 + 3) & ~3;
+    const uint32_t brp = TMA_RP * 4u, bcol = (uint32_t)(eb - ea) * 4u, bval = (uint32_t)(eb - ea) * sizeof(AT);
+    mbar_arrive_expect_tx(&bars[st], brp + bcol + bval);
+    bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
+    if (eb > ea) {
+      bulk_g2s(col_st(st), L.col + ea, bcol, &bars[st]);
+      bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
+    }
+  };
+  auto tile_end = [&](int t) { return min(r0 + (t + 1) * TMA_ROWS, r1); };
+  if (threadIdx.x == 0) {
+    if (ntiles > 0) issue(0, __ldg(L.row_ptr + r0), __ldg(L.row_ptr + tile_end(0)));
+    if (ntiles > 1) issue(1, __ldg(L.row_ptr + r0 + TMA_ROWS), __ldg(L.row_ptr + tile_end(1)));
+  }
+  ffacc acc_pi;
+  ffacc acc_dot[KW];
+  bool timed_out = false;
+  int last_issued = min(ntiles, 2) - 1;  // thread 0: last tile whose copies were issued
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t & 1;
+    const uint32_t par = (uint32_t)(t >> 1) & 1u;
+    const int ts = r0 + t * TMA_ROWS;
+    const int i = ts + (int)threadIdx.x;
+    const bool valid = i < tile_end(t);
+    int nb0 = 0, nb1 = 0;
+    if (threadIdx.x == 0 && t + 2 < ntiles) {  // boundaries of tile t+2, loaded early
+      nb0 = __ldg(L.row_ptr + ts + 2 * TMA_ROWS);
+      nb1 = __ldg(L.row_ptr + tile_end(t + 2));
+    }
+    ff wq[KW];
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) wq[q] = ld_ff(Wd[q] + i);
+    }
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
+    if (valid && !timed_out) {
+      const int* rps = rp_st(st);
+      const int* cs = col_st(st);
+      const AT* vs = val_st(st);
+      const int ea = rps[0] & ~3;
+      const int rb = rps[threadIdx.x] - ea, re = rps[threadIdx.x + 1] - ea;
+      ffacc acc;
+#pragma unroll 4
+      for (int e = rb; e < re; ++e) acc_val(acc, vs[e], ld_ff(Wj + cs[e]));
+      const ff p = acc.result();
+      st_ff(static_cast<float2*>(L.p_out) + i, p);
+      acc_pi.add_prod(p, p);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) acc_dot[q].add_prod(wq[q], p);
+    }
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && t + 2 < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue(t + 2, nb0, nb1);
+      last_issued = t + 2;
+    }
+  }
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    // let copies still in flight land before the CTA exits (bounded again)
+    for (int t = max(0, last_issued - 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t & 1], (uint32_t)(t >> 1) & 1u, TMA_WAIT_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
+  if (threadIdx.x == 0) part[1] = v;
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;  // nd is uniform across the block
+    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
+    if (threadIdx.x == 0) part[2 + q] = v;
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  if (threadIdx.x < NQ) {
+    double t = 0.0;
+    if (threadIdx.x >= 1 && threadIdx.x < 2 + nd)
       for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
     tot[threadIdx.x] = t;
   }
@@ -805,7 +1016,7 @@ void fused_dispatch(const StepLaunch& L, const CycleDev& cd, int basis, cudaStre
 template <bool MAT, int SKM>
 void launch_ff_mat_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   const size_t smem = bins_bytes(3, L.s, L.sk_copies);
-  auto k = ff_mat_kernel<MAT, SKM>;
+  auto k = (L.k <= 2) ? ff_mat_kernel<MAT, SKM, 2> : ff_mat_kernel<MAT, SKM, MAX_WINDOW>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
 }
@@ -822,16 +1033,30 @@ void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
 
 constexpr size_t FF_STAGE_SMEM = (size_t)(STEP_THREADS / 32) * STAGE * sizeof(float2);
 
+template <typename AT, int KW>
+void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (L.tma_cap > 0) {
+    auto k = ff_spmv_tma_kernel<AT, KW>;
+    const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
+    return;
+  }
+  auto k = ff_spmv_kernel<AT, KW>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_STAGE_SMEM);
+  k<<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
+}
+
 void launch_ff_step(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   if (L.mat) launch_ff_mat<true>(L, cd, st);
   else launch_ff_mat<false>(L, cd, st);
   if (L.spmv) {
     if (L.val_f32) {
-      cudaFuncSetAttribute(ff_spmv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_STAGE_SMEM);
-      ff_spmv_kernel<float><<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
+      if (L.k <= 2) launch_ff_spmv_t<float, 2>(L, cd, st);
+      else launch_ff_spmv_t<float, MAX_WINDOW>(L, cd, st);
     } else {
-      cudaFuncSetAttribute(ff_spmv_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_STAGE_SMEM);
-      ff_spmv_kernel<float2><<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
+      if (L.k <= 2) launch_ff_spmv_t<float2, 2>(L, cd, st);
+      else launch_ff_spmv_t<float2, MAX_WINDOW>(L, cd, st);
     }
   }
 }
@@ -867,8 +1092,8 @@ int sketch_word_bits(int rows_per_cta, int copies) {
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
   (void)sk_mode;
   if (basis == 3) {
-    const int a = occ(ff_mat_kernel<true, SK_TAB8>, bins_bytes(3, s, copies));
-    const int b = occ(ff_spmv_kernel<float>, FF_STAGE_SMEM);
+    const int a = occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
+    const int b = occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM);
     return std::min(a, b);
   }
   const size_t smem = fused_smem(basis, s, copies);
