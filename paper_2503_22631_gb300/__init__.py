@@ -7,6 +7,7 @@ CUDA kernels for sm_103a.  PyTorch supplies device memory and streams.
     from paper_2503_22631_gb300 import Krylov, F_EXP_NEG
     K = Krylov(row_ptr, col_idx, val, f=F_EXP_NEG, t=1e-2, m=40, k=2, s=160, seed=1)
     x = K.apply(b)           # b: float64 CUDA tensor, x ~ exp(-t A) b
+    x = krylov_expm(b, t, K) # differentiable in b and t (autograd)
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ from . import _lib
 from ._lib import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_EXP_NEG, F_INV, F_INVSQRT,
                    NOT_CONVERGED, OK, KrylovError, status_string)
 
-__all__ = ["Krylov", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT",
+__all__ = ["Krylov", "KrylovExpm", "krylov_expm", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT",
            "BASIS_F64", "BASIS_F32", "BASIS_BF16", "BASIS_DF64", "OK", "NOT_CONVERGED", "BREAKDOWN_EXACT"]
 
 _SUCCESS = (OK, NOT_CONVERGED, BREAKDOWN_EXACT)
@@ -169,3 +170,6 @@ def sketch_columns(n, s, zeta, seed, col0=0, count=None):
                                            C.c_void_p(rows.ctypes.data), C.c_void_p(signs.ctypes.data))
     _lib.check(st, "krylov_sketch_columns")
     return rows, signs
+
+
+from .autograd import KrylovExpm, krylov_expm  # noqa: E402  (needs the names above)
