@@ -29,6 +29,11 @@ constexpr size_t CSR_PAD = 8;
 // 256-row tile are copied as 260 entries.
 constexpr size_t RP_PAD = 272;
 constexpr int TMA_MAX_CAP = 4096;  // largest staged tile span (nonzeros)
+// z^{-1/2}: trapezoidal nodes in u (s = e^u) with step INVSQRT_H on
+// [0.5 ln(alpha * 1e-18) - 38, 0.5 ln(alpha * 1e4) + 38], alpha = ||A||_inf >= |lambda|:
+// the two tails are below e^-38 relative for spectra inside [1e-18 alpha, 1e4 alpha], and
+// the step gives geometric accuracy exp(-2 pi d / h) with d = (pi - |arg z|) / 2.
+constexpr double INVSQRT_H = 0.2;
 constexpr int EXP_TAYLOR_DEG = 24; // theta^25/25! e^theta < 2^-53
 
 struct DevBuf {
@@ -56,6 +61,8 @@ struct krylov_handle {
   float* val32 = nullptr;
   float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
+  int q_nodes = 0;                 // z^{-1/2} quadrature nodes
+  double q_u0 = 0.0;               // first node
   int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
   int* rpt = nullptr;
   int* cit = nullptr;
@@ -348,8 +355,12 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       const double* fsrc = h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
       launch_z(h->sd, M, me, fsrc, st);
       stats.launches += 1;
+    } else if (h->f.kind == KRYLOV_F_INVSQRT) {
+      launch_invsqrt_block(h->sd, h->cd, M, me, a, h->q_u0, INVSQRT_H, h->q_nodes, st);
+      launch_z(h->sd, M, me, h->sd.fcol, st);
+      stats.launches += 3;
     } else if (h->f.kind == KRYLOV_F_INV) {
-      launch_inv_block(h->sd, M, a, st);
+      launch_inv_block(h->sd, M, me, a, st);
       launch_z(h->sd, M, me, h->sd.fcol, st);
       stats.launches += 2;
     } else {
@@ -359,9 +370,11 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
     stats.launches += 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_scal + 8, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
+    stats.kappa_T_max = std::max(stats.kappa_T_max, h->h_scal[8 + 4]);
     const double ynorm = std::sqrt(h->h_scal[2]);
     const double xnorm = std::sqrt(h->h_scal[3]);
     stats.cycles = c;
@@ -569,6 +582,20 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(dalloc(h, &h->sd.zg, (size_t)2 * m + 1));
   CKF(dalloc(h, &h->sd.misc, 8));
   CKF(dalloc(h, &h->sd.fcol, (size_t)m));
+  if (f.kind == KRYLOV_F_INVSQRT) {
+    double alpha = 0.0;
+    CKF(norm_inf(n, h->rp, h->val, h->d_flag, h->h_flags, &alpha, h->st));
+    if (!std::isfinite(alpha)) return fail(KRYLOV_EINVAL);
+    if (alpha == 0.0) alpha = 1.0;
+    const double u_lo = 0.5 * std::log(alpha * 1e-18) - 38.0;
+    const double u_hi = 0.5 * std::log(alpha * 1e4) + 38.0;
+    h->q_nodes = (int)std::ceil((u_hi - u_lo) / INVSQRT_H) + 1;
+    h->q_u0 = u_lo;
+    CKF(dalloc(h, &h->sd.qcarry, (size_t)h->q_nodes));
+    CKF(dalloc(h, &h->sd.qpart, (size_t)h->q_nodes * m));
+    if (invsqrt_smem(m) == (size_t)256 * sizeof(double))
+      CKF(dalloc(h, &h->sd.qwork, (size_t)h->q_nodes * m * m));
+  }
   CKF(dalloc(h, &h->d_dot, 1));
   CKF(cudaStreamSynchronize(h->st));
 #undef CKF

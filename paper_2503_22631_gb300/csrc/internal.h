@@ -88,6 +88,8 @@ cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* 
                          cudaStream_t st);
 cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag,
                           cudaStream_t st);
+cudaError_t norm_inf(int n, const int* rp, const double* val, int* d_flag, int* h_flag, double* out,
+                     cudaStream_t st);
 cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaStream_t st);
 cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st);
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
@@ -108,7 +110,14 @@ struct SmallDev {
   double* G;       // exp block rows, all scale levels
   double* S0;      // Horner ping-pong buffers (2 x cycles x m x m)
   double* fcol;    // m: first column of the last block row of f(H)
+  double* qcarry;  // z^{-1/2}: per quadrature node, last entry of the previous block solve
+  double* qpart;   // z^{-1/2}: nodes x m weighted block solutions
+  double* qwork;   // z^{-1/2}: nodes x m x m LU work when it does not fit in shared memory
 };
+
+// z^{-1/2} quadrature nodes keep their m x m LU work in shared memory up to this size.
+constexpr size_t INVSQRT_SMEM_MAX = 100 * 1024;
+size_t invsqrt_smem(int m);
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
                    int has_next, int cycle, double t, cudaStream_t st);
@@ -116,7 +125,9 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double s
                             int last, int src, double* dst, cudaStream_t st);
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride,
                        cudaStream_t st);
-void launch_inv_block(const SmallDev& sd, int m, int a, cudaStream_t st);
+void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st);
+void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double u0, double hq,
+                          int nodes, cudaStream_t st);
 void launch_z(const SmallDev& sd, int m, int m_eff, const double* fcol_src, cudaStream_t st);
 
 }  // namespace krylov

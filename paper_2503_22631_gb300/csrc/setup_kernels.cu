@@ -4,6 +4,8 @@
 // A^T sorted by the original row index, so the result is deterministic).
 #include <algorithm>
 
+#include <cstring>
+
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -117,6 +119,17 @@ __global__ void tile_span_kernel(int n, const int* rp, int* out) {
   }
 }
 
+// max_i sum_j |a_ij| (the infinity norm), as the bit pattern of a nonnegative
+// double (which orders like the double itself).
+__global__ void row_abs_sum_kernel(int n, const int* rp, const double* val, unsigned long long* out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double acc = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) acc += fabs(val[e]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(acc));
+  }
+}
+
 int grid_for(int64_t work) {
   int64_t g = (work + 255) / 256;
   if (g < 1) g = 1;
@@ -146,6 +159,17 @@ cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaSt
   tile_span_kernel<<<grid_for((n + 255) / 256), 256, 0, st>>>(n, rp, d_flag);
   cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   return cudaStreamSynchronize(st);
+}
+
+cudaError_t norm_inf(int n, const int* rp, const double* val, int* d_flag, int* h_flag, double* out,
+                     cudaStream_t st) {
+  unsigned long long* bits = reinterpret_cast<unsigned long long*>(d_flag);
+  cudaMemsetAsync(bits, 0, sizeof(unsigned long long), st);
+  row_abs_sum_kernel<<<grid_for(n), 256, 0, st>>>(n, rp, val, bits);
+  cudaMemcpyAsync(h_flag, bits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  std::memcpy(out, h_flag, sizeof(double));
+  return e;
 }
 
 cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st) {

@@ -229,59 +229,116 @@ __global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restr
   Go[(rowa + j) * MM + e] = acc;
 }
 
-// f(z) = 1/z: y_a = X_a^{-1} rhs, rhs = e_1 (a = 0) or -gamma_{a-1} y_{a-1}[M-1] e_1.
-// LU with partial pivoting in one CTA on a scratch copy of X_a.
-__global__ void __launch_bounds__(SMALL_THREADS) inv_block_kernel(SmallDev sd, int M, int a, double* work) {
-  __shared__ double y[1024];
-  __shared__ int piv;
+// f(z) = 1/z: y_a = X_a^{-1} rhs, rhs = e_1 (a = 0) or -gamma_{a-1} y_{a-1}[M-1] e_1
+// (block forward substitution on the block lower-bidiagonal H).  X_a is me x me
+// (me < M only in a cycle that ended in breakdown).  LU with partial pivoting in
+// one CTA on a scratch copy of X_a + sigma I (sigma = 0 here).
+__device__ void shifted_block_solve(const double* __restrict__ X, int M, int me, double sigma, double rhs0,
+                                    double* work, double* y, int* s_piv) {
   const int tid = threadIdx.x;
-  const double* X = sd.Xblk + (size_t)a * M * M;
-  for (int e = tid; e < M * M; e += blockDim.x) work[e] = X[e];
-  const double rhs0 = (a == 0) ? 1.0 : -sd.gam[a - 1] * sd.misc[5];
-  for (int r = tid; r < M; r += blockDim.x) y[r] = (r == 0) ? rhs0 : 0.0;
+  for (int e = tid; e < me * me; e += blockDim.x) {
+    const int r = e % me, c = e / me;
+    work[e] = X[(size_t)c * M + r] + (r == c ? sigma : 0.0);
+  }
+  for (int r = tid; r < me; r += blockDim.x) y[r] = (r == 0) ? rhs0 : 0.0;
   __syncthreads();
-  for (int c = 0; c < M; ++c) {
-    if (tid == 0) {
+  for (int c = 0; c < me; ++c) {
+    if (tid < 32) {  // pivot: largest |entry| of column c at or below the diagonal (ties: first row)
+      double best = -1.0;
       int p = c;
-      double best = fabs(work[(size_t)c * M + c]);
-      for (int r = c + 1; r < M; ++r) {
-        const double v = fabs(work[(size_t)c * M + r]);
+      for (int r = c + tid; r < me; r += 32) {
+        const double v = fabs(work[(size_t)c * me + r]);
         if (v > best) {
           best = v;
           p = r;
         }
       }
-      piv = p;
-      if (p != c) {
-        for (int l = 0; l < M; ++l) {
-          const double tmp = work[(size_t)l * M + c];
-          work[(size_t)l * M + c] = work[(size_t)l * M + p];
-          work[(size_t)l * M + p] = tmp;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) {
+          best = ob;
+          p = op;
         }
+      }
+      if (tid == 0) *s_piv = p;
+    }
+    __syncthreads();
+    const int p = *s_piv;
+    if (p != c) {
+      for (int l = tid; l < me; l += blockDim.x) {
+        const double tmp = work[(size_t)l * me + c];
+        work[(size_t)l * me + c] = work[(size_t)l * me + p];
+        work[(size_t)l * me + p] = tmp;
+      }
+      if (tid == 0) {
         const double ty = y[c];
         y[c] = y[p];
         y[p] = ty;
       }
     }
     __syncthreads();
-    const double d = work[(size_t)c * M + c];
-    for (int r = c + 1 + tid; r < M; r += blockDim.x) {
-      const double f = work[(size_t)c * M + r] / d;
-      for (int l = c + 1; l < M; ++l) work[(size_t)l * M + r] = fma(-f, work[(size_t)l * M + c], work[(size_t)l * M + r]);
+    const double d = work[(size_t)c * me + c];
+    for (int r = c + 1 + tid; r < me; r += blockDim.x) {
+      const double f = work[(size_t)c * me + r] / d;
+      for (int l = c + 1; l < me; ++l)
+        work[(size_t)l * me + r] = fma(-f, work[(size_t)l * me + c], work[(size_t)l * me + r]);
       y[r] = fma(-f, y[c], y[r]);
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    for (int r = M - 1; r >= 0; --r) {
-      double acc = y[r];
-      for (int l = r + 1; l < M; ++l) acc = fma(-work[(size_t)l * M + r], y[l], acc);
-      y[r] = acc / work[(size_t)r * M + r];
-    }
-    sd.misc[5] = y[M - 1];
+  for (int c = me - 1; c >= 0; --c) {  // back substitution, column by column
+    if (tid == 0) y[c] = y[c] / work[(size_t)c * me + c];
+    __syncthreads();
+    const double yc = y[c];
+    for (int r = tid; r < c; r += blockDim.x) y[r] = fma(-work[(size_t)c * me + r], yc, y[r]);
+    __syncthreads();
   }
-  __syncthreads();
-  for (int r = tid; r < M; r += blockDim.x) sd.fcol[r] = y[r];
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS) inv_block_kernel(SmallDev sd, int M, int me, int a, double* work) {
+  __shared__ double y[256];
+  __shared__ int piv;
+  const double rhs0 = (a == 0) ? 1.0 : -sd.gam[a - 1] * sd.misc[5];
+  shifted_block_solve(sd.Xblk + (size_t)a * M * M, M, me, 0.0, rhs0, work, y, &piv);
+  if (threadIdx.x == 0) sd.misc[5] = y[me - 1];
+  for (int r = threadIdx.x; r < me; r += blockDim.x) sd.fcol[r] = y[r];
+}
+
+// f(z) = z^{-1/2}.  Substituting s = e^u in the Stieltjes form
+//   z^{-1/2} = (2/pi) int_0^inf (z + s^2)^{-1} ds = (2/pi) int_R e^u (z + e^{2u})^{-1} du,
+// the trapezoidal rule with step hq at u_i = u0 + i hq converges geometrically for z
+// off the closed negative real axis (the integrand is analytic in the strip
+// |Im u| < (pi - |arg z|) / 2).  So the first column of H^{-1/2} is a weighted sum of
+// the first columns of (H + sigma_i I)^{-1}, sigma_i = e^{2 u_i}, each found block by
+// block exactly as for 1/z: block a solves (X_a + sigma_i I) y = rhs_i with
+// rhs_i = e_1 (a = 0) or -gamma_{a-1} carry_i e_1, carry_i = last entry of node i's
+// y in block a - 1.  One CTA per node; the work matrix is in shared memory when it
+// fits (glob = 0), else in the node's slice of sd.qwork.
+constexpr int QN_THREADS = 128;
+__global__ void __launch_bounds__(QN_THREADS) invsqrt_nodes_kernel(SmallDev sd, int M, int me, int a, double u0,
+                                                                      double hq, int glob) {
+  extern __shared__ double qs[];
+  __shared__ int piv;
+  const int i = blockIdx.x;
+  double* y = qs;
+  double* work = glob ? sd.qwork + (size_t)i * M * M : qs + 256;
+  const double u = u0 + hq * i;
+  const double rhs0 = (a == 0) ? 1.0 : -sd.gam[a - 1] * sd.qcarry[i];
+  shifted_block_solve(sd.Xblk + (size_t)a * M * M, M, me, exp(2.0 * u), rhs0, work, y, &piv);
+  const double w = (2.0 * hq / 3.14159265358979323846) * exp(u);
+  for (int r = threadIdx.x; r < me; r += blockDim.x) sd.qpart[(size_t)i * M + r] = w * y[r];
+  if (threadIdx.x == 0) sd.qcarry[i] = y[me - 1];
+}
+
+// fcol[r] = sum over nodes of qpart[i][r], in node order.
+__global__ void invsqrt_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, int nodes) {
+  for (int r = threadIdx.x; r < me; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < nodes; ++i) acc += sd.qpart[(size_t)i * M + r];
+    sd.fcol[r] = acc;
+    if (!isfinite(acc)) atomicOr(&cd.flags[2], ERR_NONFINITE);
+  }
 }
 
 __global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc) {
@@ -317,8 +374,22 @@ void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t leve
                                       m, a);
 }
 
-void launch_inv_block(const SmallDev& sd, int m, int a, cudaStream_t st) {
-  inv_block_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, m, a, sd.S0);
+void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
+  inv_block_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, m, m_eff, a, sd.S0);
+}
+
+size_t invsqrt_smem(int m) {
+  const size_t b = (size_t)(256 + (size_t)m * m) * sizeof(double);
+  return b <= INVSQRT_SMEM_MAX ? b : (size_t)256 * sizeof(double);
+}
+
+void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double u0, double hq,
+                          int nodes, cudaStream_t st) {
+  const size_t smem = invsqrt_smem(m);
+  const int glob = (smem == (size_t)256 * sizeof(double)) ? 1 : 0;
+  cudaFuncSetAttribute(invsqrt_nodes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  invsqrt_nodes_kernel<<<nodes, QN_THREADS, smem, st>>>(sd, m, m_eff, a, u0, hq, glob);
+  invsqrt_sum_kernel<<<1, 256, 0, st>>>(sd, cd, m, m_eff, nodes);
 }
 
 void launch_z(const SmallDev& sd, int m, int m_eff, const double* fcol_src, cudaStream_t st) {

@@ -837,6 +837,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
 // kernel sets ERR_TIMEOUT and keeps going (the host reports it).
 constexpr int TMA_ROWS = STEP_THREADS;     // rows per staged tile
 constexpr int TMA_RP = TMA_ROWS + 4;       // staged row_ptr entries (16-byte multiple)
+constexpr int TMA_ROW_FAST = 8;            // rows up to this length issue all gathers together
 constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
 
 template <typename AT>
@@ -932,8 +933,19 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
       const int ea = rps[0] & ~3;
       const int rb = rps[threadIdx.x] - ea, re = rps[threadIdx.x + 1] - ea;
       ffacc acc;
+      if (re - rb <= TMA_ROW_FAST) {
+        // short rows: every gather of the row in flight at once
+        float2 wv[TMA_ROW_FAST];
+#pragma unroll
+        for (int q = 0; q < TMA_ROW_FAST; ++q)
+          if (rb + q < re) wv[q] = __ldg(Wj + cs[rb + q]);
+#pragma unroll
+        for (int q = 0; q < TMA_ROW_FAST; ++q)
+          if (rb + q < re) acc_val(acc, vs[rb + q], ff{wv[q].x, wv[q].y});
+      } else {
 #pragma unroll 4
-      for (int e = rb; e < re; ++e) acc_val(acc, vs[e], ld_ff(Wj + cs[e]));
+        for (int e = rb; e < re; ++e) acc_val(acc, vs[e], ld_ff(Wj + cs[e]));
+      }
       const ff p = acc.result();
       st_ff(static_cast<float2*>(L.p_out) + i, p);
       acc_pi.add_prod(p, p);

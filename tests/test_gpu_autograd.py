@@ -43,7 +43,7 @@ def _loss_and_grads(kr, b_np, y_np, t, tol, cycles):
     loss = ((x - y) ** 2).sum()
     loss.backward()
     torch.cuda.synchronize()
-    return float(loss), x.detach().cpu().numpy(), b.grad.cpu().numpy(), float(tt.grad)
+    return float(loss.detach()), x.detach().cpu().numpy(), b.grad.cpu().numpy(), float(tt.grad)
 
 
 @pytest.mark.parametrize("basis", [0, 3])
