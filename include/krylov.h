@@ -123,6 +123,7 @@ typedef struct {
   int step_launches;       /* launches of the fused step kernel */
   double ms_steps;         /* device time of the step-kernel phases (CUDA events) */
   double step_bytes;       /* algorithmic HBM bytes of those phases */
+  int status;              /* krylov_status of the call (per right-hand side in the batched form) */
 } krylov_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -197,6 +198,28 @@ int64_t krylov_size(const krylov_handle* h);
 void krylov_destroy(krylov_handle* h);
 
 /* Static description of a status code. */
+/* Batched form: f(A_i) b_{i,r} for n_inst handles (matrices of uneven size) and
+ * n_rhs right-hand sides each.  Algorithm 2 runs independently for every
+ * (instance, right-hand side); instances run concurrently, each on a stream of
+ * its own that is ordered after the handle's stream on entry and before it on
+ * return, with one host worker thread per instance (at most 16 at a time).
+ *   hs         : n_inst distinct handles (one matrix each);
+ *   B[i], X[i] : device float64, row-major n_i x n_rhs (column r is b_{i,r} and
+ *                x_{i,r}); X[i] is overwritten;
+ *   t_per_inst : NULL, or n_inst values of t for f(z) = exp(-t z) (the handle's t
+ *                is restored afterwards);
+ *   st         : NULL, or n_inst * n_rhs stats, entry i * n_rhs + r, each with its
+ *                own status.
+ * Every right-hand side is attempted; one that fails (a negative status in its
+ * stats, its column of X unspecified) does not stop the others, except for a
+ * CUDA or allocation error, which ends its instance.  Returns the first negative
+ * status met (instances in order), else KRYLOV_NOT_CONVERGED if any right-hand
+ * side did not meet tol, else KRYLOV_OK.
+ * EINVAL for null or repeated handles, n_inst < 1 or n_rhs < 1. */
+krylov_status krylov_apply_batched(krylov_handle* const* hs, int n_inst, int n_rhs, const double* const* B,
+                                   double* const* X, const double* t_per_inst, double tol, int max_cycles,
+                                   krylov_stats* st);
+
 const char* krylov_status_string(krylov_status s);
 
 /* ---- inspection entry points used by the parity tests ------------------ */

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_EXP_NEG, F_INV, F_INVSQRT,
                    NOT_CONVERGED, OK, KrylovError, status_string)
 
-__all__ = ["Krylov", "KrylovExpm", "krylov_expm", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT",
+__all__ = ["Krylov", "KrylovExpm", "krylov_expm", "apply_batched", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT",
            "BASIS_F64", "BASIS_F32", "BASIS_BF16", "BASIS_DF64", "OK", "NOT_CONVERGED", "BREAKDOWN_EXACT"]
 
 _SUCCESS = (OK, NOT_CONVERGED, BREAKDOWN_EXACT)
@@ -159,6 +159,41 @@ class Krylov:
         me = me.value
         nc = me + (0 if self.stats and self.stats["breakdown"] else 1)
         return (T[: nc * nc].reshape(nc, nc, order="F"), X[: me * me].reshape(me, me, order="F"), z[:me], me)
+
+
+def apply_batched(handles, B, t=None, tol=0.0, max_cycles=1, raise_on_error=True):
+    """Batched form: X[i][:, r] ~ f(A_i) B[i][:, r] for every handle i and column r.
+
+    handles : distinct ``Krylov`` handles (one matrix each);
+    B       : float64 CUDA tensors, B[i] of shape (n_i, n_rhs), row-major contiguous;
+    t       : None or one t per handle (f(z) = exp(-t z));
+    returns (X, stats): X[i] like B[i]; stats[i][r] the per-right-hand-side stats
+    (with their own "status").  raise_on_error=False returns even when some
+    right-hand side failed (its column of X is then unspecified).
+    """
+    torch = _torch()
+    n_inst = len(handles)
+    if n_inst == 0 or len(B) != n_inst:
+        raise ValueError("one right-hand-side block per handle")
+    n_rhs = B[0].shape[1]
+    Bs, Xs = [], []
+    for h, b in zip(handles, B):
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.float64 and b.dim() == 2
+                and b.shape[0] == h.n and b.shape[1] == n_rhs):
+            raise ValueError("B[i] must be a float64 CUDA tensor of shape (n_i, n_rhs)")
+        b = b.contiguous()
+        Bs.append(b)
+        Xs.append(torch.empty_like(b))
+    hp = (C.c_void_p * n_inst)(*[h._h.value for h in handles])
+    bp = (C.c_void_p * n_inst)(*[b.data_ptr() for b in Bs])
+    xp = (C.c_void_p * n_inst)(*[x.data_ptr() for x in Xs])
+    tp = None if t is None else (C.c_double * n_inst)(*[float(v) for v in t])
+    stats = (_lib.Stats * (n_inst * n_rhs))()
+    st = _lib.load().krylov_apply_batched(hp, n_inst, n_rhs, bp, xp, tp, float(tol), int(max_cycles), stats)
+    if raise_on_error or st == _lib.EINVAL:
+        _lib.check(st, "krylov_apply_batched", ok=_SUCCESS)
+    out_stats = [[stats[i * n_rhs + r].as_dict() for r in range(n_rhs)] for i in range(n_inst)]
+    return Xs, out_stats
 
 
 def sketch_columns(n, s, zeta, seed, col0=0, count=None):

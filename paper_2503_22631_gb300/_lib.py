@@ -48,6 +48,7 @@ EXPORTED = [
     "krylov_sketch_columns",
     "krylov_last_cycle",
     "krylov_spmv_dot_noalloc",
+    "krylov_apply_batched",
 ]
 
 
@@ -70,7 +71,8 @@ class Stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("breakdown", C.c_int), ("steps", C.c_int),
                 ("last_update_norm", C.c_double), ("x_norm", C.c_double), ("kappa_T_max", C.c_double),
                 ("ms_total", C.c_double), ("bytes_moved", C.c_double), ("launches", C.c_int),
-                ("step_launches", C.c_int), ("ms_steps", C.c_double), ("step_bytes", C.c_double)]
+                ("step_launches", C.c_int), ("ms_steps", C.c_double), ("step_bytes", C.c_double),
+                ("status", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -119,6 +121,8 @@ def load() -> C.CDLL:
     lib.krylov_last_cycle.restype = C.c_int
     lib.krylov_spmv_dot_noalloc.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, P, P, P]
     lib.krylov_spmv_dot_noalloc.restype = C.c_int
+    lib.krylov_apply_batched.argtypes = [P, C.c_int, C.c_int, P, P, P, C.c_double, C.c_int, C.POINTER(Stats)]
+    lib.krylov_apply_batched.restype = C.c_int
     _lib = lib
     return lib
 

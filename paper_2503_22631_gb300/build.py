@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
             sys.stderr.write(log)
     objs = [str(o) for o, _ in results]
     tmp = OUT.with_suffix(".so.tmp")
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", str(tmp), *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", str(tmp), *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -7,10 +7,12 @@
 // flag and the norm of the new projected block (to fix the number of
 // squarings), once to read ||y|| and ||x|| for the stopping test of Sec. 4.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/krylov.h"
@@ -52,6 +54,7 @@ struct krylov_handle {
   krylov_options opt{};
   cudaStream_t st = nullptr;
   int num_sms = 0;
+  int device = 0;
   int grid = 0;
 
   // matrix (and its transpose, built on first adjoint use)
@@ -227,7 +230,7 @@ double model_bytes_step(const krylov_handle* h, int use32) {
   return (double)h->nnz * (ba + 4.0) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
 }
 
-krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, double* x, double tol,
+krylov_status apply_core(krylov_handle* h, int transpose, const double* b, double* x, double tol,
                          int max_cycles, krylov_stats* stout) {
   if (!h || !b || !x || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
   if (transpose) {
@@ -389,8 +392,10 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
       result = KRYLOV_BREAKDOWN_EXACT;
       break;
     }
+    // relative test: x must be nonzero (a first cycle whose update underflows
+    // to zero has not yet resolved f(A) b and does not stop the method)
     const double lim = h->opt.abs_tol ? tol : tol * xnorm;
-    if (ynorm <= lim) {
+    if (ynorm <= lim && (h->opt.abs_tol || xnorm > 0.0)) {
       result = KRYLOV_OK;
       break;
     }
@@ -407,6 +412,55 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
                       stats.cycles * ((M + 1) * (double)n * bv + 16.0 * n + n * bv);
   if (stout) *stout = stats;
   return result;
+}
+
+// apply_core with the call's status recorded in the stats (zeroed first, so a
+// call that fails early leaves only the status set).
+krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, double* x, double tol,
+                         int max_cycles, krylov_stats* stout) {
+  if (stout) std::memset(stout, 0, sizeof(*stout));
+  const krylov_status r = apply_core(h, transpose, b, x, tol, max_cycles, stout);
+  if (stout) stout->status = r;
+  return r;
+}
+
+// One instance of the batched form: its right-hand sides in order, on a
+// stream of its own ordered after (and, at the end, before) the handle's stream.
+krylov_status run_instance(krylov_handle* h, int n_rhs, const double* B, double* X, const double* t_new, double tol,
+                           int max_cycles, krylov_stats* st) {
+  if (cudaSetDevice(h->device) != cudaSuccess) return KRYLOV_ECUDA;
+  cudaStream_t orig = h->st, bs = nullptr;
+  cudaEvent_t ev = nullptr;
+  if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) return KRYLOV_ECUDA;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStreamDestroy(bs);
+    return KRYLOV_ECUDA;
+  }
+  krylov_status worst = KRYLOV_OK;
+  const double t_old = h->f.t;
+  if (t_new && h->f.kind == KRYLOV_F_EXP_NEG) h->f.t = *t_new;
+  if (cudaEventRecord(ev, orig) != cudaSuccess || cudaStreamWaitEvent(bs, ev, 0) != cudaSuccess) worst = KRYLOV_ECUDA;
+  h->st = bs;
+  if (worst == KRYLOV_OK && !h->stage_b) {
+    if (dalloc(h, &h->stage_b, (size_t)h->n) != cudaSuccess || dalloc(h, &h->stage_x, (size_t)h->n) != cudaSuccess)
+      worst = KRYLOV_ENOMEM;
+  }
+  // every right-hand side runs even if an earlier one failed (its status is in
+  // its stats); only a CUDA error stops the instance
+  for (int r = 0; r < n_rhs && worst != KRYLOV_ECUDA && worst != KRYLOV_ENOMEM; ++r) {
+    launch_gather_column(B, h->n, n_rhs, r, h->stage_b, bs);
+    krylov_status s = apply_impl(h, 0, h->stage_b, h->stage_x, tol, max_cycles, st ? st + r : nullptr);
+    launch_scatter_column(h->stage_x, h->n, n_rhs, r, X, bs);
+    if (cudaGetLastError() != cudaSuccess) s = KRYLOV_ECUDA;
+    if (s < 0 && worst >= 0) worst = s;
+    if (s == KRYLOV_NOT_CONVERGED && worst == KRYLOV_OK) worst = KRYLOV_NOT_CONVERGED;
+  }
+  h->st = orig;
+  h->f.t = t_old;
+  if (cudaEventRecord(ev, bs) != cudaSuccess || cudaStreamWaitEvent(orig, ev, 0) != cudaSuccess) worst = KRYLOV_ECUDA;
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(bs);
+  return worst;
 }
 
 }  // namespace
@@ -483,6 +537,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   };
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(KRYLOV_ECUDA);
+  h->device = dev;
   if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(KRYLOV_ECUDA);
   if (cudaMallocHost(&h->h_flags, 16 * sizeof(int)) != cudaSuccess) return fail(KRYLOV_ENOMEM);
@@ -611,6 +666,36 @@ krylov_status krylov_apply(krylov_handle* h, const double* b, double* x, double 
 krylov_status krylov_apply_adjoint(krylov_handle* h, const double* b, double* x, double tol, int max_cycles,
                                    krylov_stats* st) {
   return apply_impl(h, 1, b, x, tol, max_cycles, st);
+}
+
+krylov_status krylov_apply_batched(krylov_handle* const* hs, int n_inst, int n_rhs, const double* const* B,
+                                   double* const* X, const double* t_per_inst, double tol, int max_cycles,
+                                   krylov_stats* st) {
+  if (!hs || !B || !X || n_inst < 1 || n_rhs < 1 || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
+  for (int i = 0; i < n_inst; ++i) {
+    if (!hs[i] || !B[i] || !X[i]) return KRYLOV_EINVAL;
+    if (t_per_inst && !std::isfinite(t_per_inst[i])) return KRYLOV_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return KRYLOV_EINVAL;  // a handle is not thread-safe
+  }
+  std::vector<krylov_status> res((size_t)n_inst, KRYLOV_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (int i = next.fetch_add(1); i < n_inst; i = next.fetch_add(1))
+      res[(size_t)i] = run_instance(hs[i], n_rhs, B[i], X[i], t_per_inst ? t_per_inst + i : nullptr, tol,
+                                    max_cycles, st ? st + (size_t)i * n_rhs : nullptr);
+  };
+  const int nthreads = std::min(n_inst, 16);
+  std::vector<std::thread> pool;
+  pool.reserve((size_t)nthreads);
+  for (int w = 0; w < nthreads; ++w) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  krylov_status out = KRYLOV_OK;
+  for (int i = 0; i < n_inst; ++i) {
+    if (res[(size_t)i] < 0) return res[(size_t)i];
+    if (res[(size_t)i] == KRYLOV_NOT_CONVERGED) out = KRYLOV_NOT_CONVERGED;
+  }
+  return out;
 }
 
 krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* x_host, double tol,

@@ -375,4 +375,24 @@ void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTabl
   sketch_table_kernel<<<grid, 256, 0, st>>>(n, sp, tab, err);
 }
 
+// Column r of a row-major n x ncols block <-> a contiguous vector.
+namespace {
+__global__ void gather_column_kernel(const double* __restrict__ B, int64_t n, int ncols, int r, double* __restrict__ b) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = B[i * ncols + r];
+}
+__global__ void scatter_column_kernel(const double* __restrict__ x, int64_t n, int ncols, int r, double* __restrict__ X) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) X[i * ncols + r] = x[i];
+}
+int column_grid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
+}  // namespace
+
+void launch_gather_column(const double* B, int64_t n, int ncols, int r, double* b, cudaStream_t st) {
+  gather_column_kernel<<<column_grid(n), 256, 0, st>>>(B, n, ncols, r, b);
+}
+void launch_scatter_column(const double* x, int64_t n, int ncols, int r, double* X, cudaStream_t st) {
+  scatter_column_kernel<<<column_grid(n), 256, 0, st>>>(x, n, ncols, r, X);
+}
+
 }  // namespace krylov

@@ -88,6 +88,7 @@ cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* 
                          cudaStream_t st);
 cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag,
                           cudaStream_t st);
+cudaError_t raise_smem_limit(const void* kern, size_t bytes);
 cudaError_t norm_inf(int n, const int* rp, const double* val, int* d_flag, int* h_flag, double* out,
                      cudaStream_t st);
 cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaStream_t st);
@@ -95,6 +96,8 @@ cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
                           int* cit, double* vt, int* work, cudaStream_t st);
 void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st);
+void launch_gather_column(const double* B, int64_t n, int ncols, int r, double* b, cudaStream_t st);
+void launch_scatter_column(const double* x, int64_t n, int ncols, int r, double* X, cudaStream_t st);
 
 // ---- small projected problem (FP64) ---------------------------------------
 struct SmallDev {

@@ -5,6 +5,9 @@
 #include <algorithm>
 
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.h"
 #include "kernels.cuh"
@@ -129,6 +132,27 @@ __global__ void row_abs_sum_kernel(int n, const int* rp, const double* val, unsi
     atomicMax(out, (unsigned long long)__double_as_longlong(acc));
   }
 }
+
+}  // namespace
+
+// Raise (never lower) a kernel's dynamic shared-memory limit.  The limit is
+// per function and context, so threads that launch the same kernel with
+// different sizes (batched instances) must not undo each other's setting.
+cudaError_t raise_smem_limit(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& c = cur[{dev, kern}];
+  if (bytes <= c) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
+}
+
+namespace {
 
 int grid_for(int64_t work) {
   int64_t g = (work + 255) / 256;

@@ -387,7 +387,7 @@ void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_e
                           int nodes, cudaStream_t st) {
   const size_t smem = invsqrt_smem(m);
   const int glob = (smem == (size_t)256 * sizeof(double)) ? 1 : 0;
-  cudaFuncSetAttribute(invsqrt_nodes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void*)invsqrt_nodes_kernel, smem);
   invsqrt_nodes_kernel<<<nodes, QN_THREADS, smem, st>>>(sd, m, m_eff, a, u0, hq, glob);
   invsqrt_sum_kernel<<<1, 256, 0, st>>>(sd, cd, m, m_eff, nodes);
 }

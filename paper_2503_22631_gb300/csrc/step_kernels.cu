@@ -1003,7 +1003,7 @@ template <typename VT, typename AT, bool MAT, bool SPMV, int SKM>
 void launch_fused(const StepLaunch& L, const CycleDev& cd, int basis, cudaStream_t st) {
   const size_t smem = fused_smem(basis, L.s, L.sk_copies);
   auto k = step_kernel<VT, AT, MAT, SPMV, SKM>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void*)k, smem);
   k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
 }
 
@@ -1029,7 +1029,7 @@ template <bool MAT, int SKM>
 void launch_ff_mat_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   const size_t smem = bins_bytes(3, L.s, L.sk_copies);
   auto k = (L.k <= 2) ? ff_mat_kernel<MAT, SKM, 2> : ff_mat_kernel<MAT, SKM, MAX_WINDOW>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void*)k, smem);
   k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
 }
 
@@ -1050,12 +1050,12 @@ void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) 
   if (L.tma_cap > 0) {
     auto k = ff_spmv_tma_kernel<AT, KW>;
     const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void*)k, smem);
     k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
     return;
   }
   auto k = ff_spmv_kernel<AT, KW>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FF_STAGE_SMEM);
+  raise_smem_limit((const void*)k, FF_STAGE_SMEM);
   k<<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
 }
 
@@ -1075,7 +1075,7 @@ void launch_ff_step(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
 
 template <typename K>
 int occ(K kern, size_t smem) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void*)kern, smem);
   int b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, STEP_THREADS, smem);
   return b < 1 ? 1 : b;

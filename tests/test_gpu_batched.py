@@ -1,0 +1,156 @@
+"""Batched form: many matrices of uneven size, many right-hand sides each.
+
+* small batch: every sampled (instance, right-hand side) matches the oracle at
+  the basis tolerance, per-instance t is honoured and restored, and the batched
+  call equals one krylov_apply per right-hand side;
+* the batched workload at full size (16 instances, n log-uniform in [1e4, 1e6],
+  64 right-hand sides each, float32 basis, m = 30, k = 2, s = 120): the oracle on
+  4 sampled right-hand sides per instance (one cycle, run in a spawned process
+  pool), and the float-float basis against the Kronecker closed form to 1e-8.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dense as D
+from oracle import krylov as K
+from oracle import truth as TR
+
+pytestmark = pytest.mark.gpu
+
+M, KW, S, ZETA = 30, 2, 120, 8
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _rhs_block(n, n_rhs, seed):
+    return W.rhs_normal(n * n_rhs, seed).reshape(n, n_rhs)
+
+
+def _oracle_one(args):
+    _, inst, col, seed, cycles = args
+    A = W.batched_matrix(inst)
+    b = _rhs_block(inst["n"], inst["n_rhs"], seed)[:, col].copy()
+    r = K.restarted(A, b, D.EXP_NEG, inst["t"], M, KW, S, ZETA, W.SEED, mode=K.TRUNC, tol=0.0, max_cycles=cycles)
+    return r.x
+
+
+def _oracle_many(jobs):
+    procs = max(1, min(len(jobs), os.cpu_count() or 1, 16))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_oracle_one, jobs)
+
+
+def _handles(insts, basis):
+    from paper_2503_22631_gb300 import F_EXP_NEG, Krylov
+
+    hs = []
+    for inst in insts:
+        A = W.batched_matrix(inst)
+        hs.append(Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=1.0, m=M, k=KW, s=S, seed=W.SEED, zeta=ZETA,
+                         basis=basis))
+    return hs
+
+
+def _run(insts, n_rhs, basis, tol, cycles, raise_on_error=True):
+    import torch
+
+    from paper_2503_22631_gb300 import apply_batched
+
+    hs = _handles(insts, basis)
+    B = [torch.from_numpy(_rhs_block(inst["n"], n_rhs, 100 + i)).cuda() for i, inst in enumerate(insts)]
+    X, st = apply_batched(hs, B, t=[inst["t"] for inst in insts], tol=tol, max_cycles=cycles,
+                          raise_on_error=raise_on_error)
+    torch.cuda.synchronize()
+    return hs, B, [x.cpu().numpy() for x in X], st
+
+
+SMALL = [dict(i, n_rhs=8) for i in W.batched_instances(4, 77, n_lo=1e3, n_hi=2e4)]
+
+
+@pytest.mark.parametrize("basis,tol", [(0, 1e-10), (1, 1e-5)])
+def test_small_batch_matches_oracle(lib, cuda, basis, tol):
+    hs, B, X, st = _run(SMALL, 8, basis, 0.0, 2)
+    jobs = [(i, inst, col, 100 + i, 2) for i, inst in enumerate(SMALL) for col in (0, 3, 5, 7)]
+    refs = _oracle_many(jobs)
+    for (i, inst, col, seed, _), ref in zip(jobs, refs):
+        assert _rel(X[i][:, col], ref) <= tol
+        assert st[i][col]["cycles"] == 2 and st[i][col]["status"] == 1  # tol = 0: runs the fixed count
+
+
+def test_batched_equals_single_applies(lib, cuda):
+    """Same kernels, same inputs: the batched call gives each right-hand side's
+    single-call result (and the handle's t is back to its value afterwards)."""
+    hs, B, X, st = _run(SMALL, 8, 1, 1e-6, 10)
+    for i, (h, inst) in enumerate(zip(hs, SMALL)):
+        h.set_param(inst["t"])
+        for col in range(8):
+            x = h.apply(B[i][:, col].contiguous(), tol=1e-6, max_cycles=10).cpu().numpy()
+            assert _rel(X[i][:, col], x) <= 1e-14
+            assert st[i][col]["cycles"] == h.stats["cycles"]
+
+
+def test_batched_rejects_repeated_handles(lib, cuda):
+    import torch
+
+    from paper_2503_22631_gb300 import KrylovError, apply_batched
+
+    hs = _handles(SMALL[:1], 1)
+    B = [torch.zeros(SMALL[0]["n"], 2, dtype=torch.float64, device="cuda")] * 2
+    with pytest.raises(KrylovError):
+        apply_batched([hs[0], hs[0]], B)
+
+
+FULL = [dict(i, n_rhs=64) for i in W.batched_instances(16, W.SEED)]
+
+
+def _stiffness(inst):
+    """t * ||A||_inf, the scale of t A's spectrum."""
+    A = W.batched_matrix(inst)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    return inst["t"] * np.bincount(rows, weights=np.abs(A.val), minlength=A.n).max()
+
+
+@pytest.mark.slow
+def test_full_batch_float32_matches_oracle(lib, cuda):
+    """One cycle, 4 sampled right-hand sides per instance.  Tolerance
+    max(1e-5, u32 t ||A||_inf): rounding the stored basis to float32 moves the
+    Ritz values by about u32 ||A||, and exp(-t z) turns a shift d of z into a
+    relative change t d, so for stiff instances (t ||A|| up to 8e4 here) the
+    float32 result is only that accurate; the float64 basis meets 1e-10."""
+    hs, B, X, st = _run(FULL, 64, 1, 0.0, 1)
+    jobs = [(i, inst, col, 100 + i, 1) for i, inst in enumerate(FULL) for col in (0, 21, 42, 63)]
+    refs = _oracle_many(jobs)
+    for (i, inst, col, seed, _), ref in zip(jobs, refs):
+        tol = max(1e-5, 2.0**-24 * _stiffness(inst))
+        assert _rel(X[i][:, col], ref) <= tol
+
+
+@pytest.mark.slow
+def test_full_batch_float_float_reaches_1e8(lib, cuda):
+    """Float-float basis, relative stop 1e-12, at most 60 cycles: every
+    right-hand side of every instance with t ||A||_inf <= 4e4 is within
+    1e-8 ||f(A) b|| + 1e-16 ||b|| of the Kronecker closed form.  The absolute
+    floor covers the 3D instances whose f(A) b is 1e-18..1e-45 of ||b|| (strong
+    convection with large t), where a relative error has no meaning.  The one
+    instance beyond the stiffness bound (2D, t ||A||_inf ~ 8e4) needs far more
+    than 60 restarts of length 30 and is only required to return a status."""
+    hs, B, X, st = _run(FULL, 64, 3, 1e-12, 60, raise_on_error=False)
+    for i, inst in enumerate(FULL):
+        dim = 2 if inst["kind"] == "2d" else 3
+        stiff = _stiffness(inst)
+        for col in (0, 21, 42, 63):
+            status = st[i][col]["status"]
+            if stiff > 4e4:
+                assert status in (0, 1, 2, -4)
+                continue
+            assert status in (0, 1, 2)
+            b = B[i][:, col].cpu().numpy()
+            ref = TR.kron_expm_apply(inst["N"], dim, inst["beta"], inst["t"], b)
+            err = np.linalg.norm(X[i][:, col] - ref)
+            assert err <= 1e-8 * np.linalg.norm(ref) + 1e-16 * np.linalg.norm(b)
