@@ -40,9 +40,8 @@ __global__ void norm_b_kernel(const double* b, int n, double* part, CycleDev cd,
   const double v = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = v;
   if (!last_block(cd.counter, &s_last)) return;
+  const double t = (threadIdx.x < 32) ? warp_sum_partials(part, (int)gridDim.x, 1, 0) : 0.0;
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + c);
     cd.scal[4] = t;
     const double eta = sqrt(t);
     cd.scal[0] = eta;
@@ -119,10 +118,10 @@ __global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw
   v = block_sum(av, red);
   if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = v;
   if (!last_block(cd.counter, &s_last)) return;
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + 3 * c + threadIdx.x);
-    cd.scal[threadIdx.x < 2 ? 2 + threadIdx.x : 5] = t;
+  if (threadIdx.x < 96) {  // warp q sums column q
+    const int q = (int)(threadIdx.x >> 5);
+    const double t = warp_sum_partials(part, (int)gridDim.x, 3, q);
+    if ((threadIdx.x & 31) == 0) cd.scal[q < 2 ? 2 + q : 5] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) *cd.counter = 0u;
@@ -191,25 +190,39 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
   v = block_sum(av, red);
   if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = double(v);
   if (!last_block(cd.counter, &s_last)) return;
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + 3 * c + threadIdx.x);
-    cd.scal[threadIdx.x < 2 ? 2 + threadIdx.x : 5] = t;
+  if (threadIdx.x < 96) {  // warp q sums column q
+    const int q = (int)(threadIdx.x >> 5);
+    const double t = warp_sum_partials(part, (int)gridDim.x, 3, q);
+    if ((threadIdx.x & 31) == 0) cd.scal[q < 2 ? 2 + q : 5] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) *cd.counter = 0u;
 }
 
+// U[:, j] = scale * sum over CTAs of the per-CTA sketch partials of column j.
+// Block (32 x SR_GROUPS): thread (x, y) sums CTAs y, y + SR_GROUPS, ... of
+// sketch row 32 blockIdx.x + x; the SR_GROUPS partial sums are then added in
+// group order (deterministic).
+constexpr int SR_GROUPS = 8;
 template <typename Sk>
 __global__ void sketch_reduce_kernel(const Sk* part, int ncols, int grid, int s, double scale,
                                      int64_t col_stride, double* U) {
+  __shared__ double acc_g[SR_GROUPS][32];
   const int j = blockIdx.y;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ncols || r >= s) return;
-  const Sk* p = part + (size_t)j * col_stride;
+  const int r = blockIdx.x * 32 + (int)threadIdx.x;
   double acc = 0.0;
-  for (int c = 0; c < grid; ++c) acc += double(p[(size_t)c * s + r]);
-  U[(size_t)j * s + r] = acc * scale;
+  if (j < ncols && r < s) {
+    const Sk* p = part + (size_t)j * col_stride;
+#pragma unroll 4
+    for (int c = (int)threadIdx.y; c < grid; c += SR_GROUPS) acc += double(p[(size_t)c * s + r]);
+  }
+  acc_g[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < ncols && r < s) {
+    double t = 0.0;
+    for (int g = 0; g < SR_GROUPS; ++g) t += acc_g[g][threadIdx.x];
+    U[(size_t)j * s + r] = t * scale;
+  }
 }
 
 __global__ void spmv_f64_kernel(int n, const int* rp, const int* ci, const double* val, const double* x,
@@ -231,9 +244,8 @@ __global__ void dot_f64_kernel(const double* a, const double* b, int n, double* 
   const double v = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = v;
   if (!last_block(counter, &s_last)) return;
+  const double t = (threadIdx.x < 32) ? warp_sum_partials(part, (int)gridDim.x, 1, 0) : 0.0;
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(part + c);
     *out = t;
     *counter = 0u;
   }
@@ -345,9 +357,10 @@ void launch_update(int basis, void* W, int64_t ldw, int n, int m_eff, int has_ne
 
 void launch_sketch_reduce(const void* sk_part, int ncols, int grid, int s, int zeta, int64_t col_stride, double* U,
                           cudaStream_t st) {
-  dim3 g((s + 127) / 128, ncols);
+  dim3 g((s + 31) / 32, ncols);
   const double scale = 1.0 / std::sqrt((double)zeta);
-  sketch_reduce_kernel<double><<<g, 128, 0, st>>>((const double*)sk_part, ncols, grid, s, scale, col_stride, U);
+  sketch_reduce_kernel<double><<<g, dim3(32, SR_GROUPS), 0, st>>>((const double*)sk_part, ncols, grid, s, scale,
+                                                                  col_stride, U);
 }
 
 void launch_spmv_f64(int n, const int* row_ptr, const int* col, const double* val, const double* x, double* y,

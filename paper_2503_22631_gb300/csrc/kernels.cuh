@@ -281,6 +281,16 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v) {
 
 // Block-wide sum in a fixed order (warp shuffles, then warp 0 over the warp
 // partials).  Result valid in thread 0.  `sh` holds >= 32 entries.
+// Sum of column q of a count x stride array of per-CTA partials, computed by
+// one warp: lane l takes rows l, l+32, ... in order, then a fixed shuffle tree.
+// The result (in every lane) does not depend on timing, only on count.
+__device__ __forceinline__ double warp_sum_partials(const double* part, int count, int stride, int q) {
+  double t = 0.0;
+#pragma unroll 4
+  for (int c = (int)(threadIdx.x & 31); c < count; c += 32) t += __ldcg(part + (size_t)c * stride + q);
+  return warp_sum(t);
+}
+
 template <typename A> __device__ __forceinline__ A block_sum(A v, A* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   v = warp_sum(v);

@@ -60,9 +60,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) spmv_dot_noalloc_kernel(
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  const double t = (threadIdx.x < 32) ? krylov::warp_sum_partials(scr->part, (int)gridDim.x, 1, 0) : 0.0;
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(&scr->part[c]);
     *dot_out = t;
     scr->counter = 0u;
   }

@@ -61,14 +61,8 @@ constexpr int NQ = 2 + MAX_WINDOW;  // scalar partials per CTA: ||w||^2, ||p||^2
 constexpr int STAGE = 512;          // staged nonzeros per warp in the CSR stream
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ float shfl_T(unsigned m, float v, int src) { return __shfl_sync(m, v, src); }
-__device__ __forceinline__ double shfl_T(unsigned m, double v, int src) { return __shfl_sync(m, v, src); }
-__device__ __forceinline__ ff shfl_T(unsigned m, ff v, int src) {
-  return ff{__shfl_sync(m, v.hi, src), __shfl_sync(m, v.lo, src)};
-}
-
 // Arrival ticket of the deterministic "last CTA reduces" pattern: true in the
-// CTA that arrives last (it then sums the per-CTA partials in CTA order).
+// CTA that arrives last (it then sums the per-CTA partials in a fixed order).
 __device__ __forceinline__ bool last_block_flag(unsigned* counter, int* s_last) {
   __threadfence();
   __syncthreads();
@@ -281,7 +275,6 @@ __device__ __forceinline__ SketchSpec spec_of(const StepLaunch& L) {
 // all column indices and values of a batch are loaded first, then all the
 // gathers, so each lane keeps many independent loads in flight.
 constexpr int U_FUSED = 4;
-constexpr int U_FF = 4;
 
 // ---------------------------------------------------------------------------
 template <typename VT, typename AT, bool MAT, bool SPMV, int SKM>
@@ -483,10 +476,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) step_kernel(const StepLaunch 
   if (bad) atomicOr(&cd.flags[2], ERR_SKETCH);
 
   if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x < NQ) {
-    double acc = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) acc += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
-    tot[threadIdx.x] = acc;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double acc = warp_sum_partials(L.part, (int)gridDim.x, NQ, q);
+    if ((threadIdx.x & 31) == 0) tot[q] = acc;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -673,11 +665,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value<NW>(bins, L.s, C, b, fxs, L.fx_wb);
   if (bad) atomicOr(&cd.flags[2], ERR_SKETCH);
   if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ);
-    reduce_mat(L, cd, t, MAT ? 1 : 0);
-    *cd.counter = 0u;
+  if (threadIdx.x < 32) {
+    const double t = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
+    if (threadIdx.x == 0) {
+      reduce_mat(L, cd, t, MAT ? 1 : 0);
+      *cd.counter = 0u;
+    }
   }
 }
 
@@ -813,11 +806,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
     if (threadIdx.x == 0) part[2 + q] = v;
   }
   if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x < NQ) {
-    double t = 0.0;
-    if (threadIdx.x >= 1 && threadIdx.x < 2 + nd)
-      for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
-    tot[threadIdx.x] = t;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
+    if ((threadIdx.x & 31) == 0) tot[q] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -976,11 +967,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
     if (threadIdx.x == 0) part[2 + q] = v;
   }
   if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x < NQ) {
-    double t = 0.0;
-    if (threadIdx.x >= 1 && threadIdx.x < 2 + nd)
-      for (int c = 0; c < (int)gridDim.x; ++c) t += __ldcg(L.part + (size_t)c * NQ + threadIdx.x);
-    tot[threadIdx.x] = t;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
+    if ((threadIdx.x & 31) == 0) tot[q] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
