@@ -14,7 +14,8 @@ struct CycleDev {
   double* coef;    // (m+1) x (MAX_WINDOW+1): window coefficients then rho
   double* R;       // (m+1) x m column-major, leading dimension m+1
   double* scal;    // [0] eta, [1] 1/eta, [2] ||y||^2, [3] ||x||^2, [4] ||b||^2,
-                   // [5] bound on ||w_1||^2 of the next cycle
+                   // [5] bound on ||w_1||^2 of the next cycle, [6] bound on
+                   // ||w_{j+1}|| for the next materialized column (fixed-point sketch scale)
   unsigned* counter;  // arrival counters of the last-block reducers (zeroed)
 };
 

@@ -120,6 +120,12 @@ __device__ __forceinline__ void reduce_spmv(const StepLaunch& L, const CycleDev&
   }
   est = fmax(est, 1e-20 * pi);
   c[MAX_WINDOW] = (pi > 0.0) ? 1.0 / sqrt(est) : 1.0;
+  // bound on |w_{j+1}[i]| for the next materialization's fixed-point sketch:
+  // ||w_{j+1}|| <= rho (||p_j|| + sum_q |h_q| ||w_q||) (triangle inequality)
+  double B = sqrt(pi);
+  for (int q = 0; q < MAX_WINDOW; ++q)
+    if (dlo + q <= j) B += fabs(c[q]) * sqrt(cd.sig2[dlo + q]);
+  cd.scal[6] = B * fabs(c[MAX_WINDOW]);
 }
 
 // Column i of S held by one lane: the entries (row, negative) e = 0..zeta-1,
@@ -223,13 +229,16 @@ __device__ __forceinline__ void fx_emit(int* bins, int sC, int row, int cp, cons
 }
 
 // Value of bin b of this CTA: sum of its words over the copies, as a double.
+// Thread b starts at copy b mod C, so the lanes of a warp read C different
+// banks at every step instead of all hitting one (integer sums: any order).
 template <int NW>
 __device__ __forceinline__ double fx_value(const int* bins, int s, int C, int b, const FxScale& f, int WB) {
   double v = 0.0;
 #pragma unroll
   for (int w = 0; w < NW; ++w) {
     long long t = 0;
-    for (int c = 0; c < C; ++c) t += bins[(w * s + b) * C + c];
+    const int* col = bins + (w * s + b) * C;
+    for (int c = 0; c < C; ++c) t += col[(c + b) & (C - 1)];
     v += ldexp((double)t, f.E - (w + 1) * WB);
   }
   return v;
@@ -237,19 +246,12 @@ __device__ __forceinline__ double fx_value(const int* bins, int s, int C, int b,
 
 // Scale for the contributions of column j: |w_j[i]| <= ||w_j|| <= B where, for a
 // materialized column, B = rho (||p_{j-1}|| + sum_q |h_q| ||w_q||) (triangle
-// inequality on the orthogonalization), else the stored bound of slot 0.
+// inequality on the orthogonalization, computed once by the reducer of p_{j-1}),
+// else the stored bound of slot 0.
 __device__ __forceinline__ FxScale fx_scale(const StepLaunch& L, const CycleDev& cd, int mat) {
-  double B;
-  const int j = L.j;
-  if (mat) {
-    const double* c = cd.coef + (size_t)(j - 1) * (MAX_WINDOW + 1);
-    const int lo = max(0, j - L.k);
-    B = sqrt(cd.pi[j - 1]);
-    for (int q = 0; q < j - lo; ++q) B += fabs(c[q]) * sqrt(cd.sig2[lo + q]);
-    B *= fabs(c[MAX_WINDOW]);
-  } else {
-    B = sqrt(cd.scal[5]);
-  }
+  // materialized column: the bound the previous product's reducer stored;
+  // first column of a cycle: the bound of the start vector
+  double B = mat ? cd.scal[6] : sqrt(cd.scal[5]);
   B = B * 1.0001 + 1e-300;
   FxScale f;
   f.E = ilogb(B) + 2;  // 2^(E-1) > B
