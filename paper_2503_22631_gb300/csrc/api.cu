@@ -55,7 +55,8 @@ struct krylov_handle {
   cudaStream_t st = nullptr;
   int num_sms = 0;
   int device = 0;
-  int grid = 0;
+  int grid = 0;                    // CTAs of the step kernels (one resident wave)
+  int grid_spmv = 0, grid_spmv_t = 0;  // CTAs of the float-float product kernel for A, A^T
 
   // matrix (and its transpose, built on first adjoint use)
   int* rp = nullptr;
@@ -64,6 +65,7 @@ struct krylov_handle {
   float* val32 = nullptr;
   float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
+  int part_cap = 0;                // per-CTA partial slots (8 doubles each)
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
   int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
@@ -220,6 +222,11 @@ krylov_status build_transpose(krylov_handle* h) {
   dfree(h, work);
   CK(tile_span_max(h->n, h->rpt, h->d_flag, h->h_flags, h->st));
   h->tma_cap_t = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 4) : 0;
+  if (h->opt.basis_dtype == 3) {
+    const int vals32 = h->vals_exact_f32 && h->opt.narrow_values_if_exact;
+    h->grid_spmv_t = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap_t),
+                                          std::min(h->part_cap, (h->n + STEP_THREADS - 1) / STEP_THREADS)));
+  }
   h->have_t = 1;
   return KRYLOV_OK;
 }
@@ -304,6 +311,8 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       L.zeta = h->opt.zeta;
       L.seed = h->seed;
       L.grid = h->grid;
+      L.grid_spmv = transpose ? h->grid_spmv_t : h->grid_spmv;
+      L.rows_spmv = ((n + L.grid_spmv - 1) / L.grid_spmv + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
       // whole 256-row tiles per CTA (tiles then start at multiples of 256)
       L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
       L.m = M;
@@ -621,7 +630,13 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   h->sk_col_stride = (int64_t)h->grid * s;
   CKF(cudaMalloc(&h->sk_part, (size_t)(m + 1) * h->sk_col_stride * sizeof(double)));
   h->allocs.push_back(h->sk_part);
-  CKF(dalloc(h, &h->part, (size_t)h->grid * 8));
+  h->grid_spmv = h->grid;
+  if (opt.basis_dtype == 3)
+    h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap),
+                                        (n + STEP_THREADS - 1) / STEP_THREADS));
+  h->grid_spmv_t = h->grid_spmv;
+  h->part_cap = std::max(h->grid, std::min(h->num_sms * 32, (n + STEP_THREADS - 1) / STEP_THREADS));
+  CKF(dalloc(h, &h->part, (size_t)h->part_cap * 8));
   CKF(dalloc(h, &h->cd.flags, 4));
   CKF(dalloc(h, &h->cd.sig2, (size_t)m + 1));
   CKF(dalloc(h, &h->cd.pi, (size_t)m + 1));

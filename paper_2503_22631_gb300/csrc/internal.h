@@ -60,9 +60,12 @@ struct StepLaunch {
   int sk_copies;     // lane-private copies of each sketch bin in shared memory
   int fx_wb;         // bits per fixed-point word of the sketch bins
   int tma_cap;       // staged nonzeros per 256-row tile (0: no bulk-copy staging)
+  int grid_spmv;     // CTAs of the separate product kernel (float-float basis)
+  int rows_spmv;     // rows per CTA of that kernel (a multiple of 256)
 };
 
 // basis dtype codes (krylov_basis)
+int spmv_ctas_per_sm(int vals_f32, int tma_cap);
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
 void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st);

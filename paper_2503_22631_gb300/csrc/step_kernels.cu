@@ -722,8 +722,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
   ffacc acc_pi;
   ffacc acc_dot[KW];
   float2* mystage = stage + wid * STAGE;
-  const int r0 = blockIdx.x * L.rows_per_cta;
-  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  const int r0 = blockIdx.x * L.rows_spmv;
+  const int r1 = min(L.n, r0 + L.rows_spmv);
   for (int t0 = r0; t0 < r1; t0 += STEP_THREADS) {
     const int i0 = t0 + wid * 32;
     if (i0 >= r1) continue;  // warp-uniform
@@ -870,8 +870,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   const float2* Wd[KW];
 #pragma unroll
   for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
-  const int r0 = blockIdx.x * L.rows_per_cta;
-  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  const int r0 = blockIdx.x * L.rows_spmv;
+  const int r1 = min(L.n, r0 + L.rows_spmv);
   const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
@@ -1042,12 +1042,12 @@ void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) 
     auto k = ff_spmv_tma_kernel<AT, KW>;
     const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
-    k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
+    k<<<L.grid_spmv, STEP_THREADS, smem, st>>>(L, cd);
     return;
   }
   auto k = ff_spmv_kernel<AT, KW>;
   raise_smem_limit((const void*)k, FF_STAGE_SMEM);
-  k<<<L.grid, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
+  k<<<L.grid_spmv, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
 }
 
 void launch_ff_step(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
@@ -1092,13 +1092,17 @@ int sketch_word_bits(int rows_per_cta, int copies) {
 }
 
 // Resident CTAs per SM of the main step kernel(s) (one persistent wave).
+// Resident CTAs per SM of the float-float product kernel for this operator.
+int spmv_ctas_per_sm(int vals_f32, int tma_cap) {
+  if (tma_cap > 0)
+    return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2>, 2 * tma_stage_bytes<float>(tma_cap))
+                    : occ(ff_spmv_tma_kernel<float2, 2>, 2 * tma_stage_bytes<float2>(tma_cap));
+  return vals_f32 ? occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM) : occ(ff_spmv_kernel<float2, 2>, FF_STAGE_SMEM);
+}
+
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
   (void)sk_mode;
-  if (basis == 3) {
-    const int a = occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
-    const int b = occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM);
-    return std::min(a, b);
-  }
+  if (basis == 3) return occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
   const size_t smem = fused_smem(basis, s, copies);
   if (basis == 0)
     return vals_f32 ? occ(step_kernel<double, float, true, true, SK_TAB8>, smem)
