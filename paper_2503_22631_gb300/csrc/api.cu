@@ -532,6 +532,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   krylov_handle* h = new (std::nothrow) krylov_handle();
   if (!h) return KRYLOV_ENOMEM;
   h->n = (int)A->n;
+  h->ldw = (A->n + 63) / 64 * 64;  // basis slot stride (also the padded length of row arrays)
   h->nnz = A->nnz;
   h->m = m;
   h->k = k;
@@ -600,8 +601,9 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
     h->sk_mode = packed ? SK_TAB8 : SK_TAB16;
     h->sk_tab.packed = packed ? 1 : 0;
     if (packed) {
-      CKF(dalloc(h, &h->sk_tab.rows8, (size_t)n));
-      CKF(dalloc(h, &h->sk_tab.neg8, (size_t)n));
+      // padded to the slot stride: staged copies read whole 16-row groups
+      CKF(dalloc(h, &h->sk_tab.rows8, (size_t)h->ldw));
+      CKF(dalloc(h, &h->sk_tab.neg8, (size_t)h->ldw));
     } else {
       CKF(dalloc(h, &h->sk_tab.rows16, (size_t)n * opt.zeta));
       CKF(dalloc(h, &h->sk_tab.neg32, (size_t)n));
@@ -619,12 +621,11 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   h->grid = std::max(1, std::min(h->num_sms * step_ctas_per_sm(opt.basis_dtype, h->sk_mode, s, h->sk_copies, vals32),
                                  (n + STEP_THREADS - 1) / STEP_THREADS));
   const int bb = basis_bytes(opt.basis_dtype);
-  h->ldw = ((int64_t)n + 63) / 64 * 64;
   CKF(cudaMalloc(&h->W, (size_t)(m + 1) * h->ldw * bb));
   h->allocs.push_back(h->W);
   const int pb = wide(opt.basis_dtype) ? 8 : 4;
   for (int i = 0; i < 2; ++i) {
-    CKF(cudaMalloc(&h->p[i], (size_t)n * pb));
+    CKF(cudaMalloc(&h->p[i], (size_t)h->ldw * pb));
     h->allocs.push_back(h->p[i]);
   }
   h->sk_col_stride = (int64_t)h->grid * s;

@@ -262,6 +262,12 @@ __device__ __forceinline__ FxScale fx_scale(const StepLaunch& L, const CycleDev&
 
 __host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+// fixed-point sketch bins of a CTA: words x s x copies ints
+__host__ __device__ __forceinline__ int fx_words(int basis) { return (basis == 0 || basis == 3) ? 3 : 2; }
+__host__ __device__ __forceinline__ size_t bins_bytes(int basis, int s, int copies) {
+  return (size_t)fx_words(basis) * s * copies * sizeof(int);
+}
+
 __device__ __forceinline__ SketchSpec spec_of(const StepLaunch& L) {
   SketchSpec t;
   t.s = L.s;
@@ -676,6 +682,152 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   }
 }
 
+// Materialize + sketch with the row streams staged in shared memory (packed
+// sketch table).  Tiles of 256 rows: thread 0 copies the tile's slices of
+// p_{j-1} (or w_0), the window vectors and the sketch table (8 row bytes and
+// a sign byte per column) with bulk asynchronous copies completing on an
+// mbarrier, MT_STAGES tiles ahead; each thread then handles one row from
+// shared memory exactly as ff_mat_kernel does.  Row slices start at multiples
+// of 256 rows (16-byte aligned) and a partial last tile is copied rounded up
+// to 16 rows (the row arrays are padded to the slot stride).
+constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
+constexpr int MT_ROWS = STEP_THREADS;
+constexpr int MT_STAGES = 3;
+__host__ __device__ constexpr size_t mt_stage_bytes(int kw) {
+  return (size_t)MT_ROWS * 8 * (2 + kw) + MT_ROWS;
+}
+
+template <bool MAT, int KW>
+__global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
+  constexpr int NW = 3;
+  constexpr size_t SB = mt_stage_bytes(KW);
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[MT_STAGES];
+  __shared__ float red[64];
+  __shared__ int s_last;
+  __shared__ FxScale s_fx;
+  __shared__ ff s_h[MAX_WINDOW + 1];
+  const int lane = threadIdx.x & 31;
+  const int C = L.sk_copies;
+  int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
+  unsigned char* stages = smem + align16(bins_bytes(3, L.s, C));
+  const int j = L.j;
+  if (cd.flags[0] < j) return;
+  const int lo = MAT ? max(0, j - L.k) : j;
+  const int nl = j - lo;
+  const int r0 = blockIdx.x * L.rows_per_cta;
+  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + MT_ROWS - 1) / MT_ROWS : 0;
+
+  const float2* W = static_cast<const float2*>(L.W);
+  float2* Wj = static_cast<float2*>(L.W) + (int64_t)j * L.ldw;
+  const float2* src0 = MAT ? static_cast<const float2*>(L.p_prev) : Wj;
+  const float2* Wq[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * L.ldw;
+  auto st_p = [&](int st) { return reinterpret_cast<const float2*>(stages + st * SB); };
+  auto st_w = [&](int st, int q) { return reinterpret_cast<const float2*>(stages + st * SB + (size_t)MT_ROWS * 8 * (1 + q)); };
+  auto st_r = [&](int st) { return reinterpret_cast<const uint2*>(stages + st * SB + (size_t)MT_ROWS * 8 * (1 + KW)); };
+  auto st_n = [&](int st) { return stages + st * SB + (size_t)MT_ROWS * 8 * (2 + KW); };
+  auto issue = [&](int t) {  // thread 0
+    const int st = t % MT_STAGES;
+    const int ts = r0 + t * MT_ROWS;
+    const uint32_t rc = (uint32_t)((min(MT_ROWS, r1 - ts) + 15) & ~15);
+    const uint32_t nvec = MAT ? 1u + (uint32_t)nl : 1u;
+    unsigned char* base = stages + st * SB;
+    mbar_arrive_expect_tx(&bars[st], rc * 8u * (nvec + 1u) + rc);
+    bulk_g2s(base, src0 + ts, rc * 8u, &bars[st]);
+    if (MAT) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nl) bulk_g2s(base + (size_t)MT_ROWS * 8 * (1 + q), Wq[q] + ts, rc * 8u, &bars[st]);
+    }
+    bulk_g2s(base + (size_t)MT_ROWS * 8 * (1 + KW), L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
+    bulk_g2s(base + (size_t)MT_ROWS * 8 * (2 + KW), L.sk_tab.neg8 + ts, rc, &bars[st]);
+  };
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < MT_STAGES; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+    for (int t = 0; t < min(ntiles, MT_STAGES); ++t) issue(t);
+    s_fx = fx_scale(L, cd, MAT ? 1 : 0);  // per-CTA prologue, overlapping the first copies
+    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
+    s_h[MAX_WINDOW] = MAT ? ff_from_double(c[MAX_WINDOW]) : ff{1.f, 0.f};
+  }
+  {
+    const int nb = NW * L.s * C;
+    int4* b4 = reinterpret_cast<int4*>(bins);
+    for (int e = threadIdx.x; e < nb / 4; e += blockDim.x) b4[e] = make_int4(0, 0, 0, 0);
+    for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
+  }
+  __syncthreads();
+  const FxScale fxs = s_fx;
+  const int cp = lane & (C - 1);
+  const int sC = L.s * C;
+  ff h[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) h[q] = s_h[q];
+  const ff rho = s_h[MAX_WINDOW];
+  ffacc acc_sig;
+  bool timed_out = false;
+  int last_issued = min(ntiles, MT_STAGES) - 1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % MT_STAGES;
+    const uint32_t par = (uint32_t)(t / MT_STAGES) & 1u;
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
+    const int k = (int)threadIdx.x;
+    const int i = r0 + t * MT_ROWS + k;
+    if (i < r1 && !timed_out) {
+      const float2 p2 = st_p(st)[k];
+      ff wj{p2.x, p2.y};
+      if (MAT) {
+        ff acc = wj;
+#pragma unroll
+        for (int q = 0; q < KW; ++q)
+          if (q < nl) {
+            const float2 w2 = st_w(st, q)[k];
+            acc = ff_add(acc, ff_mul(h[q], ff{w2.x, w2.y}));
+          }
+        wj = ff_mul(acc, rho);
+        st_ff(Wj + i, wj);
+      }
+      acc_sig.add_prod(wj, wj);
+      const uint2 rr = st_r(st)[k];
+      const uint32_t ng = st_n(st)[k];
+      const FxWords<NW> xw = fx_split<NW>(wj.hi, wj.lo, fxs);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (e < L.zeta)
+          fx_emit<NW>(bins, sC, (int)(((e < 4 ? rr.x : rr.y) >> (8 * (e & 3))) & 0xFFu), cp, xw, (ng >> e) & 1u, C);
+    }
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && t + MT_STAGES < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue(t + MT_STAGES);
+      last_issued = t + MT_STAGES;
+    }
+  }
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    for (int t = max(0, last_issued - MT_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % MT_STAGES], (uint32_t)(t / MT_STAGES) & 1u, TMA_WAIT_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  const double v = block_sum_ff(acc_sig.result(), red, red + 32);
+  if (threadIdx.x == 0) part[0] = v;
+  __syncthreads();
+  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
+  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value<NW>(bins, L.s, C, b, fxs, L.fx_wb);
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  if (threadIdx.x < 32) {
+    const double tsum = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
+    if (threadIdx.x == 0) {
+      reduce_mat(L, cd, tsum, MAT ? 1 : 0);
+      *cd.counter = 0u;
+    }
+  }
+}
+
 // Four consecutive matrix values, read as one aligned 16-byte (float) or two
 // 16-byte (float-float pair) loads.
 template <typename AT> struct Vals4;
@@ -831,7 +983,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
 constexpr int TMA_ROWS = STEP_THREADS;     // rows per staged tile
 constexpr int TMA_RP = TMA_ROWS + 4;       // staged row_ptr entries (16-byte multiple)
 constexpr int TMA_ROW_FAST = 8;            // rows up to this length issue all gathers together
-constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
 
 template <typename AT>
 __host__ __device__ __forceinline__ size_t tma_stage_bytes(int cap) {
@@ -981,9 +1132,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
 }
 
 // ---------------------------------------------------------------------------
-// fixed-point sketch bins of a CTA: words x s x copies ints
-int fx_words(int basis) { return (basis == 0 || basis == 3) ? 3 : 2; }
-size_t bins_bytes(int basis, int s, int copies) { return (size_t)fx_words(basis) * s * copies * sizeof(int); }
 
 size_t fused_smem(int basis, int s, int copies) {
   const size_t a = (basis == 0) ? 8 : 4;
@@ -1024,10 +1172,19 @@ void launch_ff_mat_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
 }
 
+size_t mt_smem(int s, int copies, int kw) { return align16(bins_bytes(3, s, copies)) + MT_STAGES * mt_stage_bytes(kw); }
+
 template <bool MAT>
 void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   switch (L.sk_mode) {
-    case SK_TAB8: launch_ff_mat_t<MAT, SK_TAB8>(L, cd, st); break;
+    case SK_TAB8: {  // packed table: row streams staged by bulk copies
+      const int kw = (L.k <= 2) ? 2 : MAX_WINDOW;
+      const size_t smem = mt_smem(L.s, L.sk_copies, kw);
+      auto k = (L.k <= 2) ? ff_mat_tma_kernel<MAT, 2> : ff_mat_tma_kernel<MAT, MAX_WINDOW>;
+      raise_smem_limit((const void*)k, smem);
+      k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
+      break;
+    }
     case SK_TAB16: launch_ff_mat_t<MAT, SK_TAB16>(L, cd, st); break;
     case SK_GEN8: launch_ff_mat_t<MAT, SK_GEN8>(L, cd, st); break;
     default: launch_ff_mat_t<MAT, SK_GEN>(L, cd, st); break;
@@ -1075,9 +1232,9 @@ int occ(K kern, size_t smem) {
 }  // namespace
 
 int sketch_bin_copies(int basis, int s) {
-  // lane-private copies: the largest power of two <= 32 whose bins fit in 64 KB
+  // lane-private copies: the largest power of two <= 32 whose bins fit in 32 KB
   int c = 32;
-  while (c > 1 && bins_bytes(basis, s, c) > 64 * 1024) c >>= 1;
+  while (c > 1 && bins_bytes(basis, s, c) > 32 * 1024) c >>= 1;
   return c;
 }
 
@@ -1101,8 +1258,9 @@ int spmv_ctas_per_sm(int vals_f32, int tma_cap) {
 }
 
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
-  (void)sk_mode;
-  if (basis == 3) return occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
+  if (basis == 3)
+    return (sk_mode == SK_TAB8) ? occ(ff_mat_tma_kernel<true, 2>, mt_smem(s, copies, 2))
+                                : occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
   const size_t smem = fused_smem(basis, s, copies);
   if (basis == 0)
     return vals_f32 ? occ(step_kernel<double, float, true, true, SK_TAB8>, smem)
