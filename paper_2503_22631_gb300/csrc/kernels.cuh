@@ -243,6 +243,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// ---- programmatic dependent launch ------------------------------------------
+// A kernel launched with programmatic stream serialization may start while the
+// previous kernel in the stream is still running: pdl_wait() blocks until that
+// kernel (and so everything before it) has completed and its writes are
+// visible; pdl_trigger() lets the next kernel start launching.  Both are no-ops
+// for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- storage conversions --------------------------------------------------
 template <typename T> struct Store;
 template <> struct Store<double> {

@@ -712,7 +712,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
   unsigned char* stages = smem + align16(bins_bytes(3, L.s, C));
   const int j = L.j;
-  if (cd.flags[0] < j) return;
   const int lo = MAT ? max(0, j - L.k) : j;
   const int nl = j - lo;
   const int r0 = blockIdx.x * L.rows_per_cta;
@@ -748,17 +747,23 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   if (threadIdx.x == 0) {
     for (int q = 0; q < MT_STAGES; ++q) mbar_init(&bars[q], 1);
     fence_mbar_init();
-    for (int t = 0; t < min(ntiles, MT_STAGES); ++t) issue(t);
-    s_fx = fx_scale(L, cd, MAT ? 1 : 0);  // per-CTA prologue, overlapping the first copies
-    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
-    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
-    s_h[MAX_WINDOW] = MAT ? ff_from_double(c[MAX_WINDOW]) : ff{1.f, 0.f};
   }
   {
     const int nb = NW * L.s * C;
     int4* b4 = reinterpret_cast<int4*>(bins);
     for (int e = threadIdx.x; e < nb / 4; e += blockDim.x) b4[e] = make_int4(0, 0, 0, 0);
     for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
+  }
+  // everything above is independent of earlier kernels; p_{j-1}, the window
+  // and the coefficients are not
+  pdl_wait();
+  if (cd.flags[0] < j) return;  // the cycle ended before column j (breakdown)
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < min(ntiles, MT_STAGES); ++t) issue(t);
+    s_fx = fx_scale(L, cd, MAT ? 1 : 0);  // per-CTA prologue, overlapping the first copies
+    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
+    s_h[MAX_WINDOW] = MAT ? ff_from_double(c[MAX_WINDOW]) : ff{1.f, 0.f};
   }
   __syncthreads();
   const FxScale fxs = s_fx;
@@ -807,6 +812,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
       last_issued = t + MT_STAGES;
     }
   }
+  pdl_trigger();
   if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
   if (threadIdx.x == 0 && timed_out) {
     for (int t = max(0, last_issued - MT_STAGES + 1); t <= last_issued; ++t)
@@ -1006,7 +1012,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   __shared__ int s_last;
   __shared__ double tot[NQ];
   const int j = L.j;
-  if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
   const int cap = L.tma_cap;
   const size_t sb = tma_stage_bytes<AT>(cap);
   // stage st: row_ptr slice (TMA_RP ints), columns (cap ints), values (cap AT)
@@ -1047,6 +1052,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   if (threadIdx.x == 0) {
     if (ntiles > 0) issue(0, __ldg(L.row_ptr + r0), __ldg(L.row_ptr + tile_end(0)));
     if (ntiles > 1) issue(1, __ldg(L.row_ptr + r0 + TMA_ROWS), __ldg(L.row_ptr + tile_end(1)));
+  }
+  // the CSR stream does not depend on earlier kernels: its first tiles are on
+  // their way before waiting for the kernel that produced w_j
+  pdl_wait();
+  if (cd.flags[1] != 0) {  // breakdown in this cycle: no further products
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(ntiles, 2); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+    return;
   }
   ffacc acc_pi;
   ffacc acc_dot[KW];
@@ -1104,6 +1117,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
       last_issued = t + 2;
     }
   }
+  pdl_trigger();
   if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
   if (threadIdx.x == 0 && timed_out) {
     // let copies still in flight land before the CTA exits (bounded again)
@@ -1172,6 +1186,23 @@ void launch_ff_mat_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
 }
 
+// Launch with programmatic stream serialization (the kernel calls pdl_wait()
+// before touching anything an earlier kernel produced).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(STEP_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 size_t mt_smem(int s, int copies, int kw) { return align16(bins_bytes(3, s, copies)) + MT_STAGES * mt_stage_bytes(kw); }
 
 template <bool MAT>
@@ -1182,7 +1213,7 @@ void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
       const size_t smem = mt_smem(L.s, L.sk_copies, kw);
       auto k = (L.k <= 2) ? ff_mat_tma_kernel<MAT, 2> : ff_mat_tma_kernel<MAT, MAX_WINDOW>;
       raise_smem_limit((const void*)k, smem);
-      k<<<L.grid, STEP_THREADS, smem, st>>>(L, cd);
+      launch_pdl(k, L.grid, smem, st, L, cd);
       break;
     }
     case SK_TAB16: launch_ff_mat_t<MAT, SK_TAB16>(L, cd, st); break;
@@ -1199,7 +1230,7 @@ void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) 
     auto k = ff_spmv_tma_kernel<AT, KW>;
     const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
-    k<<<L.grid_spmv, STEP_THREADS, smem, st>>>(L, cd);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
   }
   auto k = ff_spmv_kernel<AT, KW>;
