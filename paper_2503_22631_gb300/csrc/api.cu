@@ -93,6 +93,11 @@ struct krylov_handle {
   double* stage_b = nullptr;  // device staging of krylov_apply_host
   double* stage_x = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // the m + 1 step launches of a cycle for A (0) and A^T (1), captured once
+  // (their arguments do not change between cycles or calls) and replayed
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+  int step_runs[2] = {0, 0};
+  cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
   SketchTable sk_tab{};
   int sk_mode = SK_TAB8;
   int sk_copies = 32;
@@ -237,6 +242,43 @@ double model_bytes_step(const krylov_handle* h, int use32) {
   return (double)h->nnz * (ba + 4.0) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
 }
 
+// Arguments of the step launch for column j of a cycle (the same in every cycle).
+StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, int use32, double thr, int j) {
+  const int n = h->n, M = h->m, basis = h->opt.basis_dtype;
+  StepLaunch L{};
+  L.n = n;
+  L.row_ptr = op.rp;
+  L.col = op.ci;
+  L.val = use32 ? (const void*)op.val32 : (basis == 3 ? (const void*)op.valff : (const void*)op.val);
+  L.val_f32 = use32;
+  L.W = h->W;
+  L.ldw = h->ldw;
+  L.j = j;
+  L.k = h->k;
+  L.mat = (j > 0);
+  L.spmv = (j < M);
+  L.p_prev = h->p[(j + 1) & 1];
+  L.p_out = h->p[j & 1];
+  L.sk_part = (char*)h->sk_part + (size_t)j * h->sk_col_stride * sizeof(double);
+  L.part = h->part;
+  L.thr = thr;
+  L.s = h->s;
+  L.zeta = h->opt.zeta;
+  L.seed = h->seed;
+  L.grid = h->grid;
+  L.grid_spmv = transpose ? h->grid_spmv_t : h->grid_spmv;
+  L.rows_spmv = ((n + L.grid_spmv - 1) / L.grid_spmv + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
+  // whole 256-row tiles per CTA (tiles then start at multiples of 256)
+  L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
+  L.m = M;
+  L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : 0;
+  L.sk_tab = h->sk_tab;
+  L.sk_mode = h->sk_mode;
+  L.sk_copies = h->sk_copies;
+  L.fx_wb = sketch_word_bits(L.rows_per_cta, h->sk_copies);
+  return L;
+}
+
 krylov_status apply_core(krylov_handle* h, int transpose, const double* b, double* x, double tol,
                          int max_cycles, krylov_stats* stout) {
   if (!h || !b || !x || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
@@ -289,39 +331,32 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   for (int c = 1; c <= max_cycles; ++c) {
     launch_cycle_reset(h->cd, M, st);
     CK(cudaEventRecord(h->ev[0], st));
-    for (int j = 0; j <= M; ++j) {
-      StepLaunch L{};
-      L.n = n;
-      L.row_ptr = op.rp;
-      L.col = op.ci;
-      L.val = use32 ? (const void*)op.val32 : (basis == 3 ? (const void*)op.valff : (const void*)op.val);
-      L.val_f32 = use32;
-      L.W = h->W;
-      L.ldw = h->ldw;
-      L.j = j;
-      L.k = h->k;
-      L.mat = (j > 0);
-      L.spmv = (j < M);
-      L.p_prev = h->p[(j + 1) & 1];
-      L.p_out = h->p[j & 1];
-      L.sk_part = (char*)h->sk_part + (size_t)j * h->sk_col_stride * sizeof(double);
-      L.part = h->part;
-      L.thr = thr;
-      L.s = h->s;
-      L.zeta = h->opt.zeta;
-      L.seed = h->seed;
-      L.grid = h->grid;
-      L.grid_spmv = transpose ? h->grid_spmv_t : h->grid_spmv;
-      L.rows_spmv = ((n + L.grid_spmv - 1) / L.grid_spmv + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
-      // whole 256-row tiles per CTA (tiles then start at multiples of 256)
-      L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
-      L.m = M;
-      L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : 0;
-      L.sk_tab = h->sk_tab;
-      L.sk_mode = h->sk_mode;
-      L.sk_copies = h->sk_copies;
-      L.fx_wb = sketch_word_bits(L.rows_per_cta, h->sk_copies);
-      launch_step(basis, L, h->cd, M, st);
+    // the first run is eager (it also raises the kernels' shared-memory
+    // limits); later cycles replay a graph of the same launches
+    const bool use_graph = h->opt.use_graph && h->step_runs[transpose] > 0;
+    if (use_graph && !h->step_graph[transpose]) {
+      // captured on a private stream (the caller's may be the legacy default
+      // stream, which cannot be captured); the graph is launched on st
+      if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      for (int j = 0; j <= M; ++j)
+        launch_step(basis, step_args(h, op, transpose, use32, thr, j), h->cd, M, h->cap_stream);
+      const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+      cudaError_t ie = cudaErrorUnknown;
+      if (ce == cudaSuccess) ie = cudaGraphInstantiate(&h->step_graph[transpose], g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {  // no graph: the same launches stay eager
+        h->step_graph[transpose] = nullptr;
+        h->opt.use_graph = 0;
+        (void)cudaGetLastError();
+      }
+    }
+    if (use_graph && h->step_graph[transpose]) {
+      CK(cudaGraphLaunch(h->step_graph[transpose], st));
+    } else {
+      for (int j = 0; j <= M; ++j) launch_step(basis, step_args(h, op, transpose, use32, thr, j), h->cd, M, st);
+      h->step_runs[transpose] += 1;
     }
     CK(cudaEventRecord(h->ev[1], st));
     stats.launches += (basis == 3 ? 2 * M + 1 : M + 1) + 1;
@@ -483,7 +518,7 @@ void krylov_options_default(krylov_options* opt) {
   opt->basis_dtype = KRYLOV_BASIS_F64;
   opt->ortho = KRYLOV_ORTHO_TRUNC;
   opt->narrow_values_if_exact = 1;
-  opt->use_graph = 0;
+  opt->use_graph = 1;
   opt->abs_tol = 0;
   opt->stream = nullptr;
 }
@@ -509,6 +544,9 @@ void krylov_destroy(krylov_handle* h) {
     if (p) cudaFree(p);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& g : h->step_graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   delete h;
