@@ -66,6 +66,7 @@ struct krylov_handle {
   float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
   int part_cap = 0;                // per-CTA partial slots (8 doubles each)
+  int grid_update = 0;             // CTAs of the cycle-end update pass
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
   int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
@@ -413,7 +414,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     } else {
       return KRYLOV_EUNSUPPORTED;
     }
-    launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid, h->cd, M, st);
+    launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid_update, h->cd, M, st);
     stats.launches += 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -676,6 +677,8 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   h->grid_spmv_t = h->grid_spmv;
   h->part_cap = std::max(h->grid, std::min(h->num_sms * 32, (n + STEP_THREADS - 1) / STEP_THREADS));
   CKF(dalloc(h, &h->part, (size_t)h->part_cap * 8));
+  // the update pass streams m + 2 vectors: 8 resident CTAs per SM
+  h->grid_update = std::max(1, std::min(h->part_cap, std::min(h->num_sms * 8, (n + STEP_THREADS - 1) / STEP_THREADS)));
   CKF(dalloc(h, &h->cd.flags, 4));
   CKF(dalloc(h, &h->cd.sig2, (size_t)m + 1));
   CKF(dalloc(h, &h->cd.pi, (size_t)m + 1));

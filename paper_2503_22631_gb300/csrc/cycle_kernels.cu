@@ -70,41 +70,99 @@ __global__ void ff_start_kernel(const double* b, float2* W0, int n, CycleDev cd)
   }
 }
 
+// Compensated accumulation of products (float-float): S + E tracks sum a * w.
+struct ffsum {
+  float S = 0.f, E = 0.f;
+  __device__ __forceinline__ void add_prod(ff a, ff w) {
+    const float p = __fmul_rn(a.hi, w.hi);
+    float e = __fmaf_rn(a.hi, w.hi, -p);
+    e = __fmaf_rn(a.hi, w.lo, e);
+    e = __fmaf_rn(a.lo, w.hi, e);
+    const ff t = two_sum(S, p);
+    S = t.hi;
+    E = __fadd_rn(E, __fadd_rn(t.lo, e));
+  }
+  __device__ __forceinline__ ff result() const { return fast_two_sum(S, E); }
+};
+
+// Cycle end for the float64 / float32 / bfloat16 bases: x += W_m z and the
+// next start vector v = (w_{m+1} - W_m g) tau^{-1}, one pass over the basis.
+// Basis slices are loaded UPD_BATCH at a time (all in flight before use).
+// float64: float64 arithmetic.  float32 / bfloat16: products of the stored
+// value with z (and g) held as float-float pairs, summed with error-free
+// transformations on the FP32 pipes (the result is float64-accurate for the
+// stored basis; float64 FMAs here would make the pass FP64-bound on GB300).
+constexpr int UPD_BATCH = 8;
+
 template <typename VT>
 __global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw, int n, int m_eff,
                                                               int has_next, const double* zg, int m,
                                                               double* x, double* part, CycleDev cd,
                                                               int rows_per_cta) {
+  constexpr bool WIDE = sizeof(VT) == 8;
   __shared__ double zs[256], gs[256];
+  __shared__ ff zf[256], gf[256];
   __shared__ double red[32];
   __shared__ int s_last;
   for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
     zs[q] = zg[q];
     gs[q] = zg[m + q];
+    zf[q] = ff_from_double(zg[q]);
+    gf[q] = ff_neg(ff_from_double(zg[m + q]));
   }
   const double tau_inv = zg[2 * m];
   __syncthreads();
   double ay = 0.0, ax = 0.0, av = 0.0;
   const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
   for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
-    double y = 0.0;
-    double v = has_next ? double(Store<VT>::load(W + (int64_t)m_eff * ldw + i)) : 0.0;
-    for (int q = 0; q < m_eff; ++q) {
-      const double w = double(Store<VT>::load(W + (int64_t)q * ldw + i));
-      y = fma(w, zs[q], y);
-      v = fma(-w, gs[q], v);
+    double y, v;
+    if constexpr (WIDE) {
+      y = 0.0;
+      v = has_next ? double(Store<VT>::load(W + (int64_t)m_eff * ldw + i)) : 0.0;
+      for (int q0 = 0; q0 < m_eff; q0 += UPD_BATCH) {
+        double wv[UPD_BATCH];
+#pragma unroll
+        for (int u = 0; u < UPD_BATCH; ++u)
+          if (q0 + u < m_eff) wv[u] = double(Store<VT>::load(W + (int64_t)(q0 + u) * ldw + i));
+#pragma unroll
+        for (int u = 0; u < UPD_BATCH; ++u)
+          if (q0 + u < m_eff) {
+            y = fma(wv[u], zs[q0 + u], y);
+            v = fma(-wv[u], gs[q0 + u], v);
+          }
+      }
+    } else {
+      ffsum fy, fv;
+      if (has_next) fv.S = Store<VT>::load(W + (int64_t)m_eff * ldw + i);
+      for (int q0 = 0; q0 < m_eff; q0 += UPD_BATCH) {
+        float wv[UPD_BATCH];
+#pragma unroll
+        for (int u = 0; u < UPD_BATCH; ++u)
+          if (q0 + u < m_eff) wv[u] = Store<VT>::load(W + (int64_t)(q0 + u) * ldw + i);
+#pragma unroll
+        for (int u = 0; u < UPD_BATCH; ++u)
+          if (q0 + u < m_eff) {
+            const ff w{wv[u], 0.f};
+            fy.add_prod(zf[q0 + u], w);
+            if (has_next) fv.add_prod(gf[q0 + u], w);
+          }
+      }
+      const ff ry = fy.result(), rv = fv.result();
+      y = (double)ry.hi + (double)ry.lo;
+      v = (double)rv.hi + (double)rv.lo;
     }
     const double xn = x[i] + y;
     x[i] = xn;
     if (has_next) {
       const double vn = v * tau_inv;
       double vs;
-      if constexpr (sizeof(VT) == 8) {
+      if constexpr (WIDE) {
         W[i] = vn;
         vs = vn;
       } else {
-        Store<VT>::put(W + i, __double2float_rn(vn));
-        vs = (double)Store<VT>::load(W + i);
+        const float f = __double2float_rn(vn);
+        Store<VT>::put(W + i, f);
+        vs = (double)stored<VT, float>(f);
       }
       av = fma(vs, vs, av);
     }
@@ -126,21 +184,6 @@ __global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw
   __syncthreads();
   if (threadIdx.x == 0) *cd.counter = 0u;
 }
-
-// Compensated accumulation of products (float-float): S + E tracks sum a * w.
-struct ffsum {
-  float S = 0.f, E = 0.f;
-  __device__ __forceinline__ void add_prod(ff a, ff w) {
-    const float p = __fmul_rn(a.hi, w.hi);
-    float e = __fmaf_rn(a.hi, w.hi, -p);
-    e = __fmaf_rn(a.hi, w.lo, e);
-    e = __fmaf_rn(a.lo, w.hi, e);
-    const ff t = two_sum(S, p);
-    S = t.hi;
-    E = __fadd_rn(E, __fadd_rn(t.lo, e));
-  }
-  __device__ __forceinline__ ff result() const { return fast_two_sum(S, E); }
-};
 
 // Cycle end for the float-float basis (x stays float64).
 __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int64_t ldw, int n, int m_eff,
@@ -164,12 +207,18 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
       v.S = wm.x;
       v.E = wm.y;
     }
-#pragma unroll 4
-    for (int q = 0; q < m_eff; ++q) {
-      const float2 w2 = W[(int64_t)q * ldw + i];
-      const ff w{w2.x, w2.y};
-      y.add_prod(zs[q], w);
-      if (has_next) v.add_prod(gs[q], w);
+    for (int q0 = 0; q0 < m_eff; q0 += UPD_BATCH) {
+      float2 wv[UPD_BATCH];
+#pragma unroll
+      for (int u = 0; u < UPD_BATCH; ++u)
+        if (q0 + u < m_eff) wv[u] = W[(int64_t)(q0 + u) * ldw + i];
+#pragma unroll
+      for (int u = 0; u < UPD_BATCH; ++u)
+        if (q0 + u < m_eff) {
+          const ff w{wv[u].x, wv[u].y};
+          y.add_prod(zs[q0 + u], w);
+          if (has_next) v.add_prod(gs[q0 + u], w);
+        }
     }
     const ff yy = y.result();
     const double xn = x[i] + ((double)yy.hi + (double)yy.lo);
