@@ -91,12 +91,19 @@ typedef enum {
   KRYLOV_BASIS_BF16 = 2,
   KRYLOV_BASIS_DF64 = 3
 } krylov_basis;
-typedef enum { KRYLOV_ORTHO_TRUNC = 0 } krylov_ortho;
+/* Orthogonalization of a cycle:
+ *   TRUNC  classical Gram-Schmidt against the last k stored vectors, then the
+ *          sketched basis is whitened (App. A, Eq. A.1) for the restart;
+ *   RGS    Algorithm 1: Gram-Schmidt in sketch space against the last k
+ *          sketches (all of them when k >= m: the paper's randomized restart),
+ *          one basis update per step; float64 and float-float bases only
+ *          (KRYLOV_EUNSUPPORTED otherwise). */
+typedef enum { KRYLOV_ORTHO_TRUNC = 0, KRYLOV_ORTHO_RGS = 1 } krylov_ortho;
 
 typedef struct {
   int zeta;        /* nonzeros per sketch column (Eq. 3); 1 <= zeta <= min(s, 32). Default 8 */
   int basis_dtype; /* krylov_basis: storage of the Krylov basis and step vectors. Default F64 */
-  int ortho;       /* krylov_ortho: truncated classical Gram-Schmidt + whitening (App. A) */
+  int ortho;       /* krylov_ortho: TRUNC (default) or RGS */
   int narrow_values_if_exact; /* F64 basis: stream A's values as float32 when every value
                                  round-trips exactly (lossless). Default 1 */
   int use_graph;   /* capture the m steps of a cycle in a CUDA graph. Default 1 */
@@ -135,8 +142,9 @@ void krylov_options_default(krylov_options* opt);
  * vectors, the s x (m+1) sketch, the projected-problem history).
  *   f      : the function and its parameter;
  *   m      : restart length (Algorithm 2), 1 <= m <= 256;
- *   k      : orthogonalization window, 1 <= k <= 4 (Sec. 5: incomplete
- *            orthogonalization against the last k vectors);
+ *   k      : orthogonalization window: 1 <= k <= 4 with TRUNC (Sec. 5:
+ *            incomplete orthogonalization against the last k vectors),
+ *            1 <= k <= m with RGS (k = m: full sketch orthogonalization);
  *   s      : sketch rows d of Eq. (3), m+1 <= s <= 1024;
  *   seed   : keys the counter-based generator of S;
  *   opt    : may be NULL (defaults);

@@ -17,10 +17,11 @@ import numpy as np
 
 from . import _lib
 from ._lib import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_EXP_NEG, F_INV, F_INVSQRT,
-                   NOT_CONVERGED, OK, KrylovError, status_string)
+                   NOT_CONVERGED, OK, ORTHO_RGS, ORTHO_TRUNC, KrylovError, status_string)
 
 __all__ = ["Krylov", "KrylovExpm", "krylov_expm", "apply_batched", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT",
-           "BASIS_F64", "BASIS_F32", "BASIS_BF16", "BASIS_DF64", "OK", "NOT_CONVERGED", "BREAKDOWN_EXACT"]
+           "BASIS_F64", "BASIS_F32", "BASIS_BF16", "BASIS_DF64", "ORTHO_TRUNC", "ORTHO_RGS", "OK", "NOT_CONVERGED",
+           "BREAKDOWN_EXACT"]
 
 _SUCCESS = (OK, NOT_CONVERGED, BREAKDOWN_EXACT)
 
@@ -41,7 +42,7 @@ class Krylov:
 
     def __init__(self, row_ptr, col_idx, val, *, f=F_EXP_NEG, t=1.0, m=30, k=2, s=None, seed=0, zeta=8,
                  basis=BASIS_F64, narrow_values_if_exact=True, abs_tol=False, sketch_regenerate=False,
-                 stream=None):
+                 ortho=ORTHO_TRUNC, use_graph=True, stream=None):
         lib = _lib.load()
         torch = _torch()
         self._keep = []
@@ -71,6 +72,8 @@ class Krylov:
         opt.narrow_values_if_exact = 1 if narrow_values_if_exact else 0
         opt.abs_tol = 1 if abs_tol else 0
         opt.sketch_regenerate = 1 if sketch_regenerate else 0
+        opt.ortho = int(ortho)
+        opt.use_graph = 1 if use_graph else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -81,7 +84,7 @@ class Krylov:
         _lib.check(st, "krylov_create")
         self._h = h
         self.n, self.nnz, self.m, self.k, self.s, self.zeta = n, nnz, m, k, s, zeta
-        self.f, self.t, self.basis, self.seed = f, t, basis, seed
+        self.f, self.t, self.basis, self.seed, self.ortho = f, t, basis, seed, ortho
         self.stats = None
         self._keep = []  # the library copied the matrix
 

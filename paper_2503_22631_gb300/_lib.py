@@ -24,6 +24,9 @@ ETIMEOUT = -5
 EUNSUPPORTED = -6
 
 # krylov_fkind
+ORTHO_TRUNC = 0
+ORTHO_RGS = 1
+
 F_EXP_NEG = 0
 F_INVSQRT = 1
 F_INV = 2

@@ -66,6 +66,7 @@ struct krylov_handle {
   float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
   int part_cap = 0;                // per-CTA partial slots (8 doubles each)
+  long long* rgs_acc = nullptr;    // randomized Gram-Schmidt: exact sketch sums [3][s]
   int grid_update = 0;             // CTAs of the cycle-end update pass
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
@@ -280,6 +281,56 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   return L;
 }
 
+// The m steps of a randomized Gram-Schmidt cycle (Algorithm 1): sketch and
+// normalize the start vector, then per column the product, the sketch-space
+// orthogonalization and the materialization of the next column.  Returns the
+// number of kernels launched.
+int rgs_cycle_steps(krylov_handle* h, const Operator& op, int transpose, int use32, double thr, int cycle,
+                    cudaStream_t st) {
+  const int M = h->m, basis = h->opt.basis_dtype;
+  RgsArgs a{};
+  a.n = h->n;
+  a.m = M;
+  a.k = h->k;
+  a.s = h->s;
+  a.zeta = h->opt.zeta;
+  a.grid = h->grid;
+  a.rows_per_cta = ((h->n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
+  a.sk_mode = h->sk_mode;
+  a.copies = h->sk_copies;
+  a.fx_wb = sketch_word_bits(a.rows_per_cta, h->sk_copies);
+  a.basis = basis;
+  a.ldw = h->ldw;
+  a.seed = h->seed;
+  a.sk_tab = h->sk_tab;
+  a.W = h->W;
+  a.part = h->part;
+  a.acc = h->rgs_acc;
+  a.U = h->sd.U;
+  a.misc = h->sd.misc;
+  a.thr = thr;
+  int launches = 0;
+  launch_rgs_start(a, h->cd, cycle, st);
+  launches += 2;
+  for (int j = 0; j < M; ++j) {
+    StepLaunch L = step_args(h, op, transpose, use32, thr, j);
+    L.rgs = 1;
+    L.spmv = 1;
+    L.mat = 0;
+    L.p_out = h->p[j & 1];
+    if (basis == 3) {
+      launch_ff_product(L, h->cd, st);
+    } else {
+      L.rows_per_cta = (h->n + h->grid - 1) / h->grid;
+      launch_rgs_product_f64(L, h->cd, st);
+    }
+    launch_rgs_orth(a, h->cd, h->p[j & 1], j, st);
+    launch_rgs_mat(a, h->cd, h->p[j & 1], j, st);
+    launches += 3;
+  }
+  return launches;
+}
+
 krylov_status apply_core(krylov_handle* h, int transpose, const double* b, double* x, double tol,
                          int max_cycles, krylov_stats* stout) {
   if (!h || !b || !x || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
@@ -332,9 +383,13 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   for (int c = 1; c <= max_cycles; ++c) {
     launch_cycle_reset(h->cd, M, st);
     CK(cudaEventRecord(h->ev[0], st));
+    const bool rgs = (h->opt.ortho == KRYLOV_ORTHO_RGS);
+    if (rgs) {
+      stats.launches += rgs_cycle_steps(h, op, transpose, use32, thr, c, st);
+    }
     // the first run is eager (it also raises the kernels' shared-memory
     // limits); later cycles replay a graph of the same launches
-    const bool use_graph = h->opt.use_graph && h->step_runs[transpose] > 0;
+    const bool use_graph = !rgs && h->opt.use_graph && h->step_runs[transpose] > 0;
     if (use_graph && !h->step_graph[transpose]) {
       // captured on a private stream (the caller's may be the legacy default
       // stream, which cannot be captured); the graph is launched on st
@@ -353,15 +408,19 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
         (void)cudaGetLastError();
       }
     }
-    if (use_graph && h->step_graph[transpose]) {
+    if (rgs) {
+      // launched above
+    } else if (use_graph && h->step_graph[transpose]) {
       CK(cudaGraphLaunch(h->step_graph[transpose], st));
     } else {
       for (int j = 0; j <= M; ++j) launch_step(basis, step_args(h, op, transpose, use32, thr, j), h->cd, M, st);
       h->step_runs[transpose] += 1;
     }
     CK(cudaEventRecord(h->ev[1], st));
-    stats.launches += (basis == 3 ? 2 * M + 1 : M + 1) + 1;
-    stats.step_launches += (basis == 3 ? 2 * M + 1 : M + 1);
+    if (!rgs) {
+      stats.launches += (basis == 3 ? 2 * M + 1 : M + 1) + 1;
+      stats.step_launches += (basis == 3 ? 2 * M + 1 : M + 1);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -380,9 +439,14 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       stats.ms_steps += ms_s;
       stats.step_bytes += me * model_bytes_step(h, use32);
     }
-    launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
-    launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->f.t, st);
-    stats.launches += 2;
+    if (rgs) {
+      launch_rgs_small(h->sd, h->cd, M, me, has_next, c, h->f.t, st);
+      stats.launches += 1;
+    } else {
+      launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
+      launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->f.t, st);
+      stats.launches += 2;
+    }
     const int a = c - 1;
     if (h->f.kind == KRYLOV_F_EXP_NEG) {
       CK(cudaMemcpyAsync(h->h_scal, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -562,9 +626,14 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   if (opt_in) opt = *opt_in;
   if (A->n < 1 || A->n > 0x7FF00000LL || A->nnz < 0 || A->nnz > 0x7FFFFFF0LL) return KRYLOV_EINVAL;
   if (!A->row_ptr || (A->nnz > 0 && (!A->col_idx || !A->val))) return KRYLOV_EINVAL;
-  if (m < 1 || m > 256 || k < 1 || k > MAX_WINDOW || s < m + 1 || s > 1024) return KRYLOV_EINVAL;
+  if (m < 1 || m > 256 || k < 1 || s < m + 1 || s > 1024) return KRYLOV_EINVAL;
+  if (k > ((opt.ortho == KRYLOV_ORTHO_RGS) ? m : MAX_WINDOW)) return KRYLOV_EINVAL;
   if (opt.zeta < 1 || opt.zeta > std::min(s, MAX_ZETA)) return KRYLOV_EINVAL;
-  if (opt.basis_dtype < 0 || opt.basis_dtype > 3 || opt.ortho != KRYLOV_ORTHO_TRUNC) return KRYLOV_EINVAL;
+  if (opt.basis_dtype < 0 || opt.basis_dtype > 3) return KRYLOV_EINVAL;
+  if (opt.ortho != KRYLOV_ORTHO_TRUNC && opt.ortho != KRYLOV_ORTHO_RGS) return KRYLOV_EINVAL;
+  // the randomized Gram-Schmidt cycle runs with the float64 and float-float bases
+  if (opt.ortho == KRYLOV_ORTHO_RGS && opt.basis_dtype != KRYLOV_BASIS_F64 && opt.basis_dtype != KRYLOV_BASIS_DF64)
+    return KRYLOV_EUNSUPPORTED;
   if (f.kind != KRYLOV_F_EXP_NEG && f.kind != KRYLOV_F_INV && f.kind != KRYLOV_F_INVSQRT) return KRYLOV_EINVAL;
   if (!std::isfinite(f.t)) return KRYLOV_EINVAL;
 
@@ -694,6 +763,10 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(dalloc(h, &h->sd.zg, (size_t)2 * m + 1));
   CKF(dalloc(h, &h->sd.misc, 8));
   CKF(dalloc(h, &h->sd.fcol, (size_t)m));
+  if (opt.ortho == KRYLOV_ORTHO_RGS) {
+    CKF(dalloc(h, &h->rgs_acc, (size_t)3 * s));
+    CKF(cudaMemsetAsync(h->rgs_acc, 0, sizeof(long long) * 3 * (size_t)s, h->st));
+  }
   if (f.kind == KRYLOV_F_INVSQRT) {
     double alpha = 0.0;
     CKF(norm_inf(n, h->rp, h->val, h->d_flag, h->h_flags, &alpha, h->st));

@@ -21,6 +21,8 @@ struct CycleDev {
 
 enum : int { ERR_SKETCH = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
+struct SmallDev;
+
 // Stored sparse sign embedding (generated once per handle on the device).
 struct SketchTable {
   int packed;          // 1: rows8/neg8 (s <= 255, zeta <= 8); 0: rows16/neg32
@@ -62,12 +64,39 @@ struct StepLaunch {
   int tma_cap;       // staged nonzeros per 256-row tile (0: no bulk-copy staging)
   int grid_spmv;     // CTAs of the separate product kernel (float-float basis)
   int rows_spmv;     // rows per CTA of that kernel (a multiple of 256)
+  int rgs;           // 1: randomized Gram-Schmidt cycle (the product kernel forms p and ||p||^2 only)
+};
+
+// Arguments of the randomized Gram-Schmidt cycle kernels (Algorithm 1).
+struct RgsArgs {
+  int n, m, k, s, zeta;
+  int grid, rows_per_cta;   // sketch / materialize kernels
+  int sk_mode, copies, fx_wb;
+  int basis;                // 0 float64, 3 float-float
+  int64_t ldw;
+  uint64_t seed;
+  SketchTable sk_tab;
+  void* W;                  // basis slots
+  double* part;             // per-CTA partials
+  long long* acc;           // [3][s] exact fixed-point sums over CTAs (zero between uses)
+  double* U;                // s x (m+1) sketched basis, column-major (U_j = S w_j)
+  double* misc;             // small-problem scalars ([0] beta)
+  double thr;               // breakdown threshold relative to ||S A w_j||
 };
 
 // basis dtype codes (krylov_basis)
 int spmv_ctas_per_sm(int vals_f32, int tma_cap);
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
+// float-float product kernel alone (p_j = A w_j, window dots unless L.rgs)
+void launch_ff_product(const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
+// randomized Gram-Schmidt cycle (rgs_kernels.cu)
+void launch_rgs_start(const RgsArgs& a, const CycleDev& cd, int cycle, cudaStream_t st);
+void launch_rgs_product_f64(const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
+void launch_rgs_orth(const RgsArgs& a, const CycleDev& cd, const void* p, int j, cudaStream_t st);
+void launch_rgs_mat(const RgsArgs& a, const CycleDev& cd, const void* p, int j, cudaStream_t st);
+void launch_rgs_small(const SmallDev& sd, const CycleDev& cd, int m, int me, int has_next, int cycle, double t,
+                      cudaStream_t st);
 void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st);
 void launch_start(int basis, const double* b, void* W0, int n, const CycleDev& cd, int grid,
                   cudaStream_t st);

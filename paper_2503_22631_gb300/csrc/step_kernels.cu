@@ -7,15 +7,13 @@
 //                 orthogonalization of the previous product, rounded to the
 //                 basis storage type and stored in slot j
 //   sketch        u_j += S e_i w_j[i] for the zeta entries of column i of S,
-//                 accumulated in warp-private bins in shared memory: lanes
-//                 that hit the same bin in a round are combined first (match
-//                 + shuffles, lane order), then one plain read-modify-write
-//                 per bin -- no atomics, deterministic
-//   product       p_j = A w_j by a warp-cooperative CSR stream: a warp loads
-//                 the nonzeros of its 32 consecutive rows with coalesced
-//                 loads (batches of U per lane, indices first, then gathers),
-//                 stages the products in shared memory and sums each row's
-//                 segment in storage order
+//                 accumulated exactly as fixed-point integer words (a scale
+//                 from a bound on |w_j[i]|) with shared-memory integer atomics
+//                 into lane-private copies of the bins: deterministic in any
+//                 arrival order
+//   product       p_j = A w_j, each row's products summed in storage order
+//                 (CSR tiles staged in shared memory by bulk asynchronous
+//                 copies, or a warp-cooperative CSR stream)
 //   dots          <w_q, p_j> for the window of the next column, ||p_j||^2,
 //                 ||w_j||^2
 //
@@ -34,7 +32,7 @@
 // for whatever rho_j was used.  The whitening absorbs the column scaling.
 //
 // Reductions are deterministic: per-CTA partials in fixed slots, then the
-// last CTA to arrive (atomic ticket) sums them in CTA order and writes the
+// last CTA to arrive (atomic ticket) sums them in a fixed order and writes the
 // next column's coefficients.  Sketch partials stay per CTA and are summed
 // once per cycle by sketch_reduce_kernel.
 #include <algorithm>
@@ -42,6 +40,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "step_common.cuh"
 
 namespace krylov {
 namespace {
@@ -57,20 +56,7 @@ template <> struct Types<double> {
   using Sk = double;
 };
 
-constexpr int NQ = 2 + MAX_WINDOW;  // scalar partials per CTA: ||w||^2, ||p||^2, dots
 constexpr int STAGE = 512;          // staged nonzeros per warp in the CSR stream
-constexpr unsigned FULL = 0xffffffffu;
-
-// Arrival ticket of the deterministic "last CTA reduces" pattern: true in the
-// CTA that arrives last (it then sums the per-CTA partials in a fixed order).
-__device__ __forceinline__ bool last_block_flag(unsigned* counter, int* s_last) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) *s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (*s_last) __threadfence();
-  return *s_last != 0;
-}
 
 // Reducer of a materialized column j: record ||w_j||^2 and R[j, j-1] = 1/rho_j,
 // and flag a happy breakdown when ||w_j|| / rho_j (the norm of the
@@ -104,6 +90,7 @@ __device__ __forceinline__ void reduce_spmv(const StepLaunch& L, const CycleDev&
   const double pi = tot[1];
   cd.pi[j] = pi;
   if (!isfinite(pi)) cd.flags[2] |= ERR_NONFINITE;
+  if (L.rgs) return;  // the sketch-space orthogonalization takes it from here
   const int dlo = max(0, j - L.k + 1);
   double est = pi;
   double* c = cd.coef + (size_t)j * (MAX_WINDOW + 1);
@@ -126,157 +113,6 @@ __device__ __forceinline__ void reduce_spmv(const StepLaunch& L, const CycleDev&
   for (int q = 0; q < MAX_WINDOW; ++q)
     if (dlo + q <= j) B += fabs(c[q]) * sqrt(cd.sig2[dlo + q]);
   cd.scal[6] = B * fabs(c[MAX_WINDOW]);
-}
-
-// Column i of S held by one lane: the entries (row, negative) e = 0..zeta-1,
-// from the stored table or regenerated with the counter-based generator.
-template <int SKM> struct SkCol {
-  uint32_t p0 = 0xFFFFFFFFu, p1 = 0xFFFFFFFFu, ng = 0u;
-  int got = 0;
-  const uint16_t* r16 = nullptr;
-  __device__ __forceinline__ void load(const StepLaunch& L, const SketchSpec& sp, uint32_t inv_s, int i) {
-    if constexpr (SKM == SK_TAB8) {
-      const uint2 r = __ldg(L.sk_tab.rows8 + i);
-      p0 = r.x;
-      p1 = r.y;
-      ng = __ldg(L.sk_tab.neg8 + i);
-      got = sp.zeta;
-    } else if constexpr (SKM == SK_TAB16) {
-      r16 = L.sk_tab.rows16 + (size_t)i * sp.zeta;
-      ng = __ldg(L.sk_tab.neg32 + i);
-      got = sp.zeta;
-    } else if constexpr (SKM == SK_GEN8) {
-      got = sketch_column_packed((uint32_t)i, sp, inv_s, &p0, &p1, &ng);
-    }
-  }
-  __device__ __forceinline__ int row(int e) const {
-    if constexpr (SKM == SK_TAB16) return (int)__ldg(r16 + e);
-    return (int)(((e < 4 ? p0 : p1) >> (8 * (e & 3))) & 0xFFu);
-  }
-  __device__ __forceinline__ bool neg(int e) const { return (ng >> e) & 1u; }
-};
-
-// Generic regeneration (any s <= 32768, zeta <= 32): entries kept in a local array.
-struct SkColGen {
-  int rows[MAX_ZETA];
-  uint32_t ng = 0u;
-  int got = 0;
-  __device__ __forceinline__ void load(const StepLaunch& L, const SketchSpec& sp, uint32_t inv_s, int i) {
-    (void)L;
-    (void)inv_s;
-    got = 0;
-    ng = 0u;
-    sketch_column<MAX_ZETA>((uint32_t)i, sp, [&](int r, bool n) {
-      rows[got] = r;
-      ng |= (n ? 1u : 0u) << got;
-      ++got;
-    });
-  }
-  __device__ __forceinline__ int row(int e) const { return rows[e]; }
-  __device__ __forceinline__ bool neg(int e) const { return (ng >> e) & 1u; }
-};
-
-template <int SKM> struct SkColOf { using type = SkCol<SKM>; };
-template <> struct SkColOf<SK_GEN> { using type = SkColGen; };
-
-// ---- exact fixed-point sketch bins ---------------------------------------
-// A contribution v with |v| <= B is scaled by the power of two 2^(WB - E),
-// E = ceil(log2 B) + 1, so |x| <= 2^(WB-1), and split into NW integer words
-// x = q_0 + 2^-WB q_1 + 2^-2WB q_2 + ... (each |q_w| <= 2^(WB-1)), rounding
-// with the 1.5 * 2^23 addition trick on the FP32 pipes.  Word w of bin b
-// lives in a lane-private column (address (w s + b) C + copy), so the integer
-// atomic adds of a warp hit distinct banks; integer sums are exact and
-// independent of the order in which threads arrive.  WB is chosen on the host
-// so that no column can overflow (entries per column <= rows per CTA / C).
-struct FxScale {
-  float to_fixed;  // 2^(WB - E)
-  float word;      // 2^WB
-  int E;
-};
-
-template <int NW> struct FxWords {
-  int q[NW];
-};
-
-// Split the contribution (h + l) of one row into its fixed-point words (once
-// per row: every entry of the row adds the same value up to its sign).
-template <int NW>
-__device__ __forceinline__ FxWords<NW> fx_split(float h, float l, const FxScale& f) {
-  const float magic = 12582912.0f;  // 1.5 * 2^23
-  FxWords<NW> out;
-  h = __fmul_rn(h, f.to_fixed);
-  l = __fmul_rn(l, f.to_fixed);
-#pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const float r = __fadd_rn(h, magic);
-    out.q[w] = __float_as_int(r) - 0x4B400000;
-    if (w + 1 < NW) {
-      const ff d = two_sum(__fsub_rn(h, __fsub_rn(r, magic)), l);
-      h = __fmul_rn(d.hi, f.word);
-      l = __fmul_rn(d.lo, f.word);
-    }
-  }
-  return out;
-}
-
-// Add +-words to bin `row` in this lane's column.
-template <int NW>
-__device__ __forceinline__ void fx_emit(int* bins, int sC, int row, int cp, const FxWords<NW>& x, bool neg,
-                                        int C) {
-  int* b = bins + row * C + cp;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) atomicAdd(b + w * sC, neg ? -x.q[w] : x.q[w]);
-}
-
-// Value of bin b of this CTA: sum of its words over the copies, as a double.
-// Thread b starts at copy b mod C, so the lanes of a warp read C different
-// banks at every step instead of all hitting one (integer sums: any order).
-template <int NW>
-__device__ __forceinline__ double fx_value(const int* bins, int s, int C, int b, const FxScale& f, int WB) {
-  double v = 0.0;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    long long t = 0;
-    const int* col = bins + (w * s + b) * C;
-    for (int c = 0; c < C; ++c) t += col[(c + b) & (C - 1)];
-    v += ldexp((double)t, f.E - (w + 1) * WB);
-  }
-  return v;
-}
-
-// Scale for the contributions of column j: |w_j[i]| <= ||w_j|| <= B where, for a
-// materialized column, B = rho (||p_{j-1}|| + sum_q |h_q| ||w_q||) (triangle
-// inequality on the orthogonalization, computed once by the reducer of p_{j-1}),
-// else the stored bound of slot 0.
-__device__ __forceinline__ FxScale fx_scale(const StepLaunch& L, const CycleDev& cd, int mat) {
-  // materialized column: the bound the previous product's reducer stored;
-  // first column of a cycle: the bound of the start vector
-  double B = mat ? cd.scal[6] : sqrt(cd.scal[5]);
-  B = B * 1.0001 + 1e-300;
-  FxScale f;
-  f.E = ilogb(B) + 2;  // 2^(E-1) > B
-  f.to_fixed = ldexpf(1.0f, L.fx_wb - f.E);
-  f.word = ldexpf(1.0f, L.fx_wb);
-  return f;
-}
-
-__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
-
-// fixed-point sketch bins of a CTA: words x s x copies ints
-__host__ __device__ __forceinline__ int fx_words(int basis) { return (basis == 0 || basis == 3) ? 3 : 2; }
-__host__ __device__ __forceinline__ size_t bins_bytes(int basis, int s, int copies) {
-  return (size_t)fx_words(basis) * s * copies * sizeof(int);
-}
-
-__device__ __forceinline__ SketchSpec spec_of(const StepLaunch& L) {
-  SketchSpec t;
-  t.s = L.s;
-  t.zeta = L.zeta;
-  t.lim = 32768u - 32768u % (uint32_t)L.s;
-  t.k0 = (uint32_t)(L.seed & 0xFFFFFFFFull);
-  t.k1 = (uint32_t)(L.seed >> 32);
-  t.scale = 1.f;
-  return t;
 }
 
 // Products of the CSR stream are formed in batches of U nonzeros per lane:
@@ -332,7 +168,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) step_kernel(const StepLaunch 
   }
   const A rho = s_h[MAX_WINDOW];
   const int dlo = max(0, j - L.k + 1);
-  const int nd = j - dlo + 1;
+  const int nd = L.rgs ? 0 : j - dlo + 1;  // window dots (none in a randomized Gram-Schmidt cycle)
   const int off = dlo - lo;
   const SketchSpec sp = spec_of(L);
   const uint32_t inv_s = sketch_inv_s(L.s);
@@ -500,69 +336,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) step_kernel(const StepLaunch 
 // Float-float basis ("df64"): (hi, lo) float pairs, arithmetic on the FP32
 // pipes.  The sums that define the Arnoldi relation (products and
 // orthogonalization), the sketch and the dots are float-float accurate.
-
-__device__ __forceinline__ ff ld_ff(const float2* p) {
-  const float2 v = __ldg(p);
-  return {v.x, v.y};
-}
-__device__ __forceinline__ void st_ff(float2* p, ff v) { *p = make_float2(v.hi, v.lo); }
-
-// Compensated accumulation: S + E tracks a sum of float-float products.
-struct ffacc {
-  float S = 0.f, E = 0.f;
-  __device__ __forceinline__ void add_prod(ff a, ff w) {
-    const float p = __fmul_rn(a.hi, w.hi);
-    float e = __fmaf_rn(a.hi, w.hi, -p);
-    e = __fmaf_rn(a.hi, w.lo, e);
-    e = __fmaf_rn(a.lo, w.hi, e);
-    add_pe(p, e);
-  }
-  __device__ __forceinline__ void add_pe(float p, float e) {
-    const ff t = two_sum(S, p);
-    S = t.hi;
-    E = __fadd_rn(E, __fadd_rn(t.lo, e));
-  }
-  __device__ __forceinline__ ff result() const { return fast_two_sum(S, E); }
-};
-
-// product of a matrix value and a float-float entry as (p, e), p + e accurate
-// to float-float precision
-__device__ __forceinline__ float2 prod_pe(float a, ff w) {
-  const float p = __fmul_rn(a, w.hi);
-  float e = __fmaf_rn(a, w.hi, -p);
-  e = __fmaf_rn(a, w.lo, e);
-  return make_float2(p, e);
-}
-__device__ __forceinline__ float2 prod_pe(float2 a, ff w) {
-  const float p = __fmul_rn(a.x, w.hi);
-  float e = __fmaf_rn(a.x, w.hi, -p);
-  e = __fmaf_rn(a.x, w.lo, e);
-  e = __fmaf_rn(a.y, w.hi, e);
-  return make_float2(p, e);
-}
-
-// Block-wide float-float sum, result (as double) in thread 0.
-__device__ __forceinline__ double block_sum_ff(ff v, float* sh_hi, float* sh_lo) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const ff u{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
-    v = ff_add(v, u);
-  }
-  __syncthreads();
-  if (lane == 0) {
-    sh_hi[wid] = v.hi;
-    sh_lo[wid] = v.lo;
-  }
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0) {
-    ff a{0.f, 0.f};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = ff_add(a, ff{sh_hi[w], sh_lo[w]});
-    r = ff_to_double(a);
-  }
-  return r;
-}
 
 // Inputs of one row of ff_mat_kernel, loaded before any use so that two rows
 // per thread have their loads in flight together.
@@ -873,7 +646,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
   const AT* val = static_cast<const AT*>(L.val);
   const int4* col4 = reinterpret_cast<const int4*>(L.col);
   const int dlo = max(0, j - L.k + 1);
-  const int nd = j - dlo + 1;
+  const int nd = L.rgs ? 0 : j - dlo + 1;  // window dots (none in a randomized Gram-Schmidt cycle)
   const float2* Wd[KW];
 #pragma unroll
   for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
@@ -1022,7 +795,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   const float2* Wj = W + (int64_t)j * L.ldw;
   const AT* val = static_cast<const AT*>(L.val);
   const int dlo = max(0, j - L.k + 1);
-  const int nd = j - dlo + 1;
+  const int nd = L.rgs ? 0 : j - dlo + 1;  // window dots (none in a randomized Gram-Schmidt cycle)
   const float2* Wd[KW];
 #pragma unroll
   for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
@@ -1238,6 +1011,16 @@ void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) 
   k<<<L.grid_spmv, STEP_THREADS, FF_STAGE_SMEM, st>>>(L, cd);
 }
 
+void launch_ff_prod(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (L.val_f32) {
+    if (L.k <= 2 || L.rgs) launch_ff_spmv_t<float, 2>(L, cd, st);
+    else launch_ff_spmv_t<float, MAX_WINDOW>(L, cd, st);
+  } else {
+    if (L.k <= 2 || L.rgs) launch_ff_spmv_t<float2, 2>(L, cd, st);
+    else launch_ff_spmv_t<float2, MAX_WINDOW>(L, cd, st);
+  }
+}
+
 void launch_ff_step(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   if (L.mat) launch_ff_mat<true>(L, cd, st);
   else launch_ff_mat<false>(L, cd, st);
@@ -1299,6 +1082,8 @@ int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
   if (basis == 1) return occ(step_kernel<float, float, true, true, SK_TAB8>, smem);
   return occ(step_kernel<__nv_bfloat16, float, true, true, SK_TAB8>, smem);
 }
+
+void launch_ff_product(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) { launch_ff_prod(L, cd, st); }
 
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st) {
   (void)m;
