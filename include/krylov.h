@@ -115,6 +115,10 @@ typedef struct {
                             with the counter-based generator instead (no table, more
                             arithmetic per step).  Both give bit-identical S. */
   void* stream;    /* cudaStream_t for all work; NULL = legacy default stream */
+  int autotune;    /* float-float basis: 1 (default) times the two product kernels on the
+                      operator at create (w_j pieces staged in shared memory from a per-tile
+                      segment plan, or w_j gathered through L1/L2) and keeps the faster;
+                      0 uses the staged pieces whenever the operator has a segment plan */
 } krylov_options;
 
 typedef struct {

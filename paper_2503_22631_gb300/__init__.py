@@ -42,7 +42,7 @@ class Krylov:
 
     def __init__(self, row_ptr, col_idx, val, *, f=F_EXP_NEG, t=1.0, m=30, k=2, s=None, seed=0, zeta=8,
                  basis=BASIS_F64, narrow_values_if_exact=True, abs_tol=False, sketch_regenerate=False,
-                 ortho=ORTHO_TRUNC, use_graph=True, stream=None):
+                 ortho=ORTHO_TRUNC, use_graph=True, autotune=True, stream=None):
         lib = _lib.load()
         torch = _torch()
         self._keep = []
@@ -74,6 +74,7 @@ class Krylov:
         opt.sketch_regenerate = 1 if sketch_regenerate else 0
         opt.ortho = int(ortho)
         opt.use_graph = 1 if use_graph else 0
+        opt.autotune = 1 if autotune else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

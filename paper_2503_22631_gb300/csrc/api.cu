@@ -45,6 +45,98 @@ struct DevBuf {
 
 }  // namespace
 
+namespace {
+
+// Segment plan of an operator (see ff_spmv_seg_kernel): device arrays and caps.
+struct SegPlan {
+  int4* seg = nullptr;
+  int* seg_n = nullptr;
+  uint16_t* lcol = nullptr;
+  int seg_cap = 0;
+  int lcap = 0;
+};
+
+// Host construction of a segment plan from a host CSR: per 256-row tile the
+// sorted distinct columns are cut into pieces wherever two consecutive columns
+// are more than SEG_GAP apart; each piece is widened to an even start and an
+// even length (16-byte copies of float-float entries) and placed after the
+// previous one.  Returns false when some tile needs more than SEG_MAX pieces
+// or SEG_CAP_MAX staged entries (the operator then keeps the gather kernel).
+bool build_seg_plan(int n, int64_t nnz, const int* rp, const int* ci, std::vector<int4>& seg, std::vector<int>& segn,
+                    std::vector<uint16_t>& lcol, int& seg_cap, int& lcap) {
+  const int ntiles = (n + STEP_THREADS - 1) / STEP_THREADS;
+  seg.assign((size_t)ntiles * SEG_MAX, make_int4(0, 0, 0, 0));
+  segn.assign((size_t)ntiles, 0);
+  lcol.assign((size_t)nnz + 16, 0);
+  std::atomic<bool> ok{true};
+  std::atomic<int> cap_w{0}, cap_l{0};
+  auto work = [&](int t0, int t1) {
+    std::vector<int> cols, starts, ends;
+    int my_w = 0, my_l = 0;
+    for (int t = t0; t < t1 && ok.load(std::memory_order_relaxed); ++t) {
+      const int ts = t * STEP_THREADS, te = std::min(n, ts + STEP_THREADS);
+      const int e0 = rp[ts], e1 = rp[te];
+      my_l = std::max(my_l, ((e1 + 7) & ~7) - (e0 & ~7));
+      cols.assign(ci + e0, ci + e1);
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      starts.clear();
+      ends.clear();
+      for (int c : cols) {
+        if (starts.empty() || c > ends.back() + SEG_GAP) {
+          starts.push_back(c);
+          ends.push_back(c);
+        } else {
+          ends.back() = c;
+        }
+      }
+      if ((int)starts.size() > SEG_MAX) {
+        ok = false;
+        break;
+      }
+      int off = 0;
+      for (size_t q = 0; q < starts.size(); ++q) {
+        const int a = starts[q] & ~1;
+        const int len = ((ends[q] + 1 - a) + 1) & ~1;
+        seg[(size_t)t * SEG_MAX + q] = make_int4(a, len, off, 0);
+        starts[q] = a;
+        off += len;
+      }
+      if (off > SEG_CAP_MAX) {
+        ok = false;
+        break;
+      }
+      my_w = std::max(my_w, off);
+      segn[(size_t)t] = (int)starts.size();
+      for (int e = e0; e < e1; ++e) {
+        const int c = ci[e];
+        const int q = (int)(std::upper_bound(starts.begin(), starts.end(), c) - starts.begin()) - 1;
+        const int4 sg = seg[(size_t)t * SEG_MAX + q];
+        lcol[(size_t)e] = (uint16_t)(sg.z + (c - sg.x));
+      }
+    }
+    int w = cap_w.load();
+    while (my_w > w && !cap_w.compare_exchange_weak(w, my_w)) {
+    }
+    int l = cap_l.load();
+    while (my_l > l && !cap_l.compare_exchange_weak(l, my_l)) {
+    }
+  };
+  const int nth = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  const int per = (ntiles + nth - 1) / nth;
+  for (int w = 0; w < nth; ++w) {
+    const int t0 = w * per, t1 = std::min(ntiles, t0 + per);
+    if (t0 < t1) pool.emplace_back(work, t0, t1);
+  }
+  for (auto& th : pool) th.join();
+  seg_cap = cap_w.load();
+  lcap = std::max(8, cap_l.load());
+  return ok.load();
+}
+
+}  // namespace
+
 struct krylov_handle {
   int n = 0;
   int64_t nnz = 0;
@@ -70,7 +162,8 @@ struct krylov_handle {
   int grid_update = 0;             // CTAs of the cycle-end update pass
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
-  int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
+  int tma_cap = 0, tma_cap_t = 0;
+  SegPlan seg_a, seg_t;            // segment plans of A and A^T (float-float basis)  // staged span per tile for A and A^T (0: no staging)
   int* rpt = nullptr;
   int* cit = nullptr;
   double* valt = nullptr;
@@ -204,6 +297,31 @@ struct Operator {
   const float2* valff;
 };
 
+// Build the segment plan of an operator held on the device (copied to the
+// host for the construction) and upload it; no plan when a tile does not fit.
+krylov_status install_seg_plan(krylov_handle* h, SegPlan& plan, const int* rp_dev, const int* ci_dev) {
+  std::vector<int> rp((size_t)h->n + 1), ci((size_t)std::max<int64_t>(h->nnz, 1));
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(rp.data(), rp_dev, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+  if (h->nnz > 0) CK(cudaMemcpy(ci.data(), ci_dev, sizeof(int) * (size_t)h->nnz, cudaMemcpyDeviceToHost));
+  std::vector<int4> seg;
+  std::vector<int> segn;
+  std::vector<uint16_t> lcol;
+  int seg_cap = 0, lcap = 0;
+  if (!build_seg_plan(h->n, h->nnz, rp.data(), ci.data(), seg, segn, lcol, seg_cap, lcap)) return KRYLOV_OK;
+  CK(dalloc(h, &plan.seg, seg.size()));
+  CK(dalloc(h, &plan.seg_n, segn.size()));
+  CK(dalloc(h, &plan.lcol, lcol.size()));
+  CK(cudaMemcpy(plan.seg, seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(plan.seg_n, segn.data(), sizeof(int) * segn.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(plan.lcol, lcol.data(), sizeof(uint16_t) * lcol.size(), cudaMemcpyHostToDevice));
+  plan.seg_cap = std::max(seg_cap, 2);
+  plan.lcap = lcap;
+  return KRYLOV_OK;
+}
+
+krylov_status choose_product_kernel(krylov_handle* h, int transpose);
+
 krylov_status build_transpose(krylov_handle* h) {
   if (h->have_t) return KRYLOV_OK;
   int* work = nullptr;
@@ -231,10 +349,18 @@ krylov_status build_transpose(krylov_handle* h) {
   h->tma_cap_t = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 4) : 0;
   if (h->opt.basis_dtype == 3) {
     const int vals32 = h->vals_exact_f32 && h->opt.narrow_values_if_exact;
-    h->grid_spmv_t = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap_t),
+    krylov_status ps = install_seg_plan(h, h->seg_t, h->rpt, h->cit);
+    if (ps != KRYLOV_OK) return ps;
+    const SegPlan& sp = h->seg_t;
+    h->grid_spmv_t = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap_t, sp.seg ? sp.seg_cap : 0,
+                                                                        sp.lcap),
                                           std::min(h->part_cap, (h->n + STEP_THREADS - 1) / STEP_THREADS)));
   }
   h->have_t = 1;
+  {
+    const krylov_status cs = choose_product_kernel(h, 1);
+    if (cs != KRYLOV_OK) return cs;
+  }
   return KRYLOV_OK;
 }
 
@@ -274,6 +400,14 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
   L.m = M;
   L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : 0;
+  if (basis == 3) {
+    const SegPlan& sp = transpose ? h->seg_t : h->seg_a;
+    L.seg = sp.seg;
+    L.seg_n = sp.seg_n;
+    L.lcol = sp.lcol;
+    L.seg_cap = sp.seg_cap;
+    L.lcap = sp.lcap;
+  }
   L.sk_tab = h->sk_tab;
   L.sk_mode = h->sk_mode;
   L.sk_copies = h->sk_copies;
@@ -329,6 +463,55 @@ int rgs_cycle_steps(krylov_handle* h, const Operator& op, int transpose, int use
     launches += 3;
   }
   return launches;
+}
+
+// Autotuning of the float-float product kernel for one operator: time the
+// kernel that stages the pieces of w_j in shared memory (segment plan) against
+// the one that gathers w_j through L1/L2, a few launches each on zeroed
+// vectors, and keep the faster (stencils with float32 values favour the
+// gathers, wider rows with float-float values the staged pieces).
+krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
+  SegPlan& sp = transpose ? h->seg_t : h->seg_a;
+  int& grid = transpose ? h->grid_spmv_t : h->grid_spmv;
+  if (h->opt.basis_dtype != 3 || !sp.seg || !h->opt.autotune) return KRYLOV_OK;
+  const int use32 = (h->opt.narrow_values_if_exact && h->vals_exact_f32) ? 1 : 0;
+  Operator op{transpose ? h->rpt : h->rp, transpose ? h->cit : h->ci, transpose ? h->valt : h->val,
+              transpose ? h->valt32 : h->val32, transpose ? h->valtff : h->valff};
+  const int n = h->n;
+  const int tcap = transpose ? h->tma_cap_t : h->tma_cap;
+  const int grid_seg = grid;
+  const int grid_gather = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(use32, tcap, 0, 0),
+                                               std::min(h->part_cap, (n + STEP_THREADS - 1) / STEP_THREADS)));
+  cudaStream_t st = h->st;
+  CK(cudaMemsetAsync(h->W, 0, sizeof(float2) * 2 * (size_t)h->ldw, st));
+  CK(cudaMemsetAsync(h->cd.flags, 0, 4 * sizeof(int), st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_variant = [&](bool seg) -> float {
+    StepLaunch L = step_args(h, op, transpose, use32, 1e-12, 1);
+    L.grid_spmv = seg ? grid_seg : grid_gather;
+    L.rows_spmv = ((n + L.grid_spmv - 1) / L.grid_spmv + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
+    if (!seg) L.seg = nullptr;
+    for (int r = 0; r < 2; ++r) launch_ff_product(L, h->cd, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5; ++r) launch_ff_product(L, h->cd, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  const float t_seg = time_variant(true);
+  const float t_gather = time_variant(false);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  if (t_gather < t_seg) {
+    sp.seg = nullptr;
+    grid = grid_gather;
+  }
+  return KRYLOV_OK;
 }
 
 krylov_status apply_core(krylov_handle* h, int transpose, const double* b, double* x, double tol,
@@ -584,6 +767,7 @@ void krylov_options_default(krylov_options* opt) {
   opt->ortho = KRYLOV_ORTHO_TRUNC;
   opt->narrow_values_if_exact = 1;
   opt->use_graph = 1;
+  opt->autotune = 1;
   opt->abs_tol = 0;
   opt->stream = nullptr;
 }
@@ -740,9 +924,14 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(cudaMalloc(&h->sk_part, (size_t)(m + 1) * h->sk_col_stride * sizeof(double)));
   h->allocs.push_back(h->sk_part);
   h->grid_spmv = h->grid;
-  if (opt.basis_dtype == 3)
-    h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap),
+  if (opt.basis_dtype == 3) {
+    const krylov_status ps = install_seg_plan(h, h->seg_a, h->rp, h->ci);
+    if (ps != KRYLOV_OK) return fail(ps);
+    const SegPlan& sp = h->seg_a;
+    h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap, sp.seg ? sp.seg_cap : 0,
+                                                                      sp.lcap),
                                         (n + STEP_THREADS - 1) / STEP_THREADS));
+  }
   h->grid_spmv_t = h->grid_spmv;
   h->part_cap = std::max(h->grid, std::min(h->num_sms * 32, (n + STEP_THREADS - 1) / STEP_THREADS));
   CKF(dalloc(h, &h->part, (size_t)h->part_cap * 8));
@@ -783,6 +972,10 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   }
   CKF(dalloc(h, &h->d_dot, 1));
   CKF(cudaStreamSynchronize(h->st));
+  {
+    const krylov_status cs = choose_product_kernel(h, 0);
+    if (cs != KRYLOV_OK) return fail(cs);
+  }
 #undef CKF
   *out = h;
   return KRYLOV_OK;

@@ -65,7 +65,19 @@ struct StepLaunch {
   int grid_spmv;     // CTAs of the separate product kernel (float-float basis)
   int rows_spmv;     // rows per CTA of that kernel (a multiple of 256)
   int rgs;           // 1: randomized Gram-Schmidt cycle (the product kernel forms p and ||p||^2 only)
+  // segment plan of the operator (float-float basis; seg null: no plan): per
+  // 256-row tile the contiguous pieces of w_j that its columns touch and, per
+  // nonzero, the 16-bit position of its column among the staged pieces
+  const int4* seg;          // [tiles][SEG_MAX]: start, length, offset, unused
+  const int* seg_n;         // [tiles] pieces per tile
+  const uint16_t* lcol;     // [nnz + 16] tile-local column positions
+  int seg_cap;              // max staged entries of w_j per tile (even)
+  int lcap;                 // max aligned nonzero span per tile (multiple of 8)
 };
+
+constexpr int SEG_MAX = 16;        // pieces of w_j per tile
+constexpr int SEG_CAP_MAX = 3072;  // staged entries of w_j per tile (24 KB float-float)
+constexpr int SEG_GAP = 64;        // columns closer than this join one piece
 
 // Arguments of the randomized Gram-Schmidt cycle kernels (Algorithm 1).
 struct RgsArgs {
@@ -85,7 +97,7 @@ struct RgsArgs {
 };
 
 // basis dtype codes (krylov_basis)
-int spmv_ctas_per_sm(int vals_f32, int tma_cap);
+int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap);
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
 // float-float product kernel alone (p_j = A w_j, window dots unless L.rgs)

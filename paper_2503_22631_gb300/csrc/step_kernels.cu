@@ -995,10 +995,180 @@ void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Product kernel with the w_j gathers served from shared memory (float-float
+// basis, operators with a segment plan).  For each 256-row tile a plan built
+// at create lists the few contiguous pieces of w_j that the tile's columns
+// touch (a stencil tile touches three: its own neighbourhood and the two
+// planes at +-N^2) and stores, per nonzero, the 16-bit position of its column
+// among the staged pieces.  Thread 0 copies the tile's row_ptr slice, its
+// 16-bit positions, its values and the pieces of w_j into shared memory with
+// bulk asynchronous copies (two tiles in flight); each thread then forms its
+// row with shared-memory loads only.  The CSR parts do not depend on earlier
+// kernels and are issued before the dependent-launch wait, the pieces of w_j
+// after it.
+template <typename AT>
+__host__ __device__ __forceinline__ size_t seg_stage_bytes(int lcap, int seg_cap) {
+  return (size_t)TMA_RP * 4 + (size_t)lcap * (2 + sizeof(AT)) + (size_t)seg_cap * sizeof(float2);
+}
+
+template <typename AT, int KW>
+__global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const StepLaunch L, const CycleDev cd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ float rhi[32], rlo[32];
+  __shared__ int s_last;
+  __shared__ double tot[NQ];
+  const int j = L.j;
+  const int lcap = L.lcap;
+  const size_t sb = seg_stage_bytes<AT>(lcap, L.seg_cap);
+  auto rp_st = [&](int st) { return reinterpret_cast<int*>(smem + (size_t)st * sb); };
+  auto lc_st = [&](int st) { return reinterpret_cast<uint16_t*>(smem + (size_t)st * sb + (size_t)TMA_RP * 4); };
+  auto val_st = [&](int st) {
+    return reinterpret_cast<AT*>(smem + (size_t)st * sb + (size_t)TMA_RP * 4 + (size_t)lcap * 2);
+  };
+  auto w_st = [&](int st) {
+    return reinterpret_cast<float2*>(smem + (size_t)st * sb + (size_t)TMA_RP * 4 + (size_t)lcap * (2 + sizeof(AT)));
+  };
+  const float2* W = static_cast<const float2*>(L.W);
+  const float2* Wj = W + (int64_t)j * L.ldw;
+  const AT* val = static_cast<const AT*>(L.val);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = L.rgs ? 0 : j - dlo + 1;  // window dots (none in a randomized Gram-Schmidt cycle)
+  const float2* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
+  const int r0 = blockIdx.x * L.rows_spmv;
+  const int r1 = min(L.n, r0 + L.rows_spmv);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto tile_end = [&](int t) { return min(r0 + (t + 1) * TMA_ROWS, r1); };
+  // thread 0: announce all bytes of tile t and copy its CSR parts
+  auto issue_csr = [&](int t) {
+    const int st = t & 1;
+    const int ts = r0 + t * TMA_ROWS;
+    const int g = ts / TMA_ROWS;
+    const int e0 = __ldg(L.row_ptr + ts), e1 = __ldg(L.row_ptr + tile_end(t));
+    const int ea = e0 & ~7, eb = (e1 + 7) & ~7;
+    const int ns = __ldg(L.seg_n + g);
+    uint32_t wbytes = 0;
+    for (int q = 0; q < ns; ++q) wbytes += (uint32_t)__ldg(&L.seg[(size_t)g * SEG_MAX + q].y) * 8u;
+    const uint32_t brp = TMA_RP * 4u, blc = (uint32_t)(eb - ea) * 2u, bval = (uint32_t)(eb - ea) * sizeof(AT);
+    mbar_arrive_expect_tx(&bars[st], brp + blc + bval + wbytes);
+    bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
+    if (eb > ea) {
+      bulk_g2s(lc_st(st), L.lcol + ea, blc, &bars[st]);
+      bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
+    }
+  };
+  // thread 0: copy the pieces of w_j of tile t (after w_j is complete)
+  auto issue_w = [&](int t) {
+    const int st = t & 1;
+    const int g = (r0 + t * TMA_ROWS) / TMA_ROWS;
+    const int ns = __ldg(L.seg_n + g);
+    for (int q = 0; q < ns; ++q) {
+      const int4 sg = __ldg(&L.seg[(size_t)g * SEG_MAX + q]);
+      bulk_g2s(w_st(st) + sg.z, Wj + sg.x, (uint32_t)sg.y * 8u, &bars[st]);
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(ntiles, 2); ++t) issue_csr(t);
+  pdl_wait();
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(ntiles, 2); ++t) issue_w(t);  // also on breakdown: the phases must complete
+  if (cd.flags[1] != 0) {  // breakdown in this cycle: no further products
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(ntiles, 2); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+    return;
+  }
+  ffacc acc_pi;
+  ffacc acc_dot[KW];
+  bool timed_out = false;
+  int last_issued = min(ntiles, 2) - 1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t & 1;
+    const uint32_t par = (uint32_t)(t >> 1) & 1u;
+    const int ts = r0 + t * TMA_ROWS;
+    const int i = ts + (int)threadIdx.x;
+    const bool valid = i < tile_end(t);
+    ff wq[KW];
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) wq[q] = ld_ff(Wd[q] + i);
+    }
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
+    if (valid && !timed_out) {
+      const int* rps = rp_st(st);
+      const uint16_t* lcs = lc_st(st);
+      const AT* vs = val_st(st);
+      const float2* ws = w_st(st);
+      const int ea = rps[0] & ~7;
+      const int rb = rps[threadIdx.x] - ea, re = rps[threadIdx.x + 1] - ea;
+      ffacc acc;
+#pragma unroll 4
+      for (int e = rb; e < re; ++e) {
+        const float2 w2 = ws[lcs[e]];
+        acc_val(acc, vs[e], ff{w2.x, w2.y});
+      }
+      const ff p = acc.result();
+      st_ff(static_cast<float2*>(L.p_out) + i, p);
+      acc_pi.add_prod(p, p);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) acc_dot[q].add_prod(wq[q], p);
+    }
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && t + 2 < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue_csr(t + 2);
+      issue_w(t + 2);
+      last_issued = t + 2;
+    }
+  }
+  pdl_trigger();
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    for (int t = max(0, last_issued - 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t & 1], (uint32_t)(t >> 1) & 1u, TMA_WAIT_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
+  if (threadIdx.x == 0) part[1] = v;
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;  // nd is uniform across the block
+    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
+    if (threadIdx.x == 0) part[2 + q] = v;
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double tq = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
+    if ((threadIdx.x & 31) == 0) tot[q] = tq;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    reduce_spmv(L, cd, tot);
+    *cd.counter = 0u;
+  }
+}
+
 constexpr size_t FF_STAGE_SMEM = (size_t)(STEP_THREADS / 32) * STAGE * sizeof(float2);
 
 template <typename AT, int KW>
 void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (L.seg != nullptr) {
+    auto k = ff_spmv_seg_kernel<AT, KW>;
+    const size_t smem = 2 * seg_stage_bytes<AT>(L.lcap, L.seg_cap);
+    raise_smem_limit((const void*)k, smem);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+    return;
+  }
   if (L.tma_cap > 0) {
     auto k = ff_spmv_tma_kernel<AT, KW>;
     const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
@@ -1064,7 +1234,10 @@ int sketch_word_bits(int rows_per_cta, int copies) {
 
 // Resident CTAs per SM of the main step kernel(s) (one persistent wave).
 // Resident CTAs per SM of the float-float product kernel for this operator.
-int spmv_ctas_per_sm(int vals_f32, int tma_cap) {
+int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap) {
+  if (seg_cap > 0)
+    return vals_f32 ? occ(ff_spmv_seg_kernel<float, 2>, 2 * seg_stage_bytes<float>(lcap, seg_cap))
+                    : occ(ff_spmv_seg_kernel<float2, 2>, 2 * seg_stage_bytes<float2>(lcap, seg_cap));
   if (tma_cap > 0)
     return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2>, 2 * tma_stage_bytes<float>(tma_cap))
                     : occ(ff_spmv_tma_kernel<float2, 2>, 2 * tma_stage_bytes<float2>(tma_cap));

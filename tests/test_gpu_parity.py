@@ -176,3 +176,45 @@ def test_sketch_table_equals_regeneration(lib, cuda, basis, tol, s, zeta):
                     basis=basis, sketch_regenerate=regen)
         out.append(kr.apply(b, max_cycles=3).cpu().numpy())
     assert _rel(out[1], out[0]) <= tol
+
+
+def test_product_kernel_variants_agree_bitwise(lib, cuda):
+    """Float-float basis: the product kernel that stages the pieces of w_j in
+    shared memory (autotune off: always when a segment plan exists) and the
+    autotuned choice sum every row in the same order: identical results."""
+    import torch
+
+    from paper_2503_22631_gb300 import BASIS_DF64, F_EXP_NEG, Krylov
+
+    A = W.convdiff3d(20, (50.0, 50.0, 50.0))
+    b = torch.from_numpy(W.rhs_uniform(A.n, 3)).cuda()
+    xs = []
+    for autotune in (False, True):
+        kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=2e-3, m=20, k=2, s=60, seed=5, zeta=8,
+                    basis=BASIS_DF64, autotune=autotune)
+        xs.append(kr.apply(b, tol=0.0, max_cycles=3).cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
+
+
+def test_random_sparse_matrix_gather_path(lib, cuda):
+    """Columns spread over the whole range (no segment plan fits): the
+    gather kernel, against the oracle."""
+    rng = np.random.default_rng(17)
+    n, per = 6000, 9
+    cols = np.sort(rng.choice(n, size=(n, per - 1), replace=True), axis=1)
+    rows = []
+    for i in range(n):
+        c = np.unique(np.concatenate([[i], cols[i]]))
+        rows.append(c)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(c) for c in rows])
+    ci = np.concatenate(rows).astype(np.int32)
+    val = rng.standard_normal(ci.size) * 0.1
+    diag = rp[:-1] + np.array([np.searchsorted(c, i) for i, c in enumerate(rows)])
+    val[diag] = 4.0 + np.abs(val[diag])
+    A = W.Csr(n, rp.astype(np.int32), ci, val)
+    b = W.rhs_normal(n, 4)
+    args = (D.EXP_NEG, 0.1, 20, 2, 60, 8, 21)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=2)
+    x, _ = _gpu(A, b, *args, 2, basis=3)
+    assert _rel(x, ref.x) <= 1e-10
