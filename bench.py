@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cycles", type=int, default=None, help="override the cycle count (profiling)")
+    ap.add_argument("--workload", default="convdiff3d_128",
+                    choices=["convdiff3d_128", "convdiff3d_128_rgs", "fem_kuhn_160", "batched16",
+                             "convdiff3d_96_adjoint"],
+                    help="convdiff3d_128 is the headline; the others time the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: no warm-up floor, no e2e, no CPU baseline, no clock sampling")
     return ap.parse_args()
@@ -245,12 +249,144 @@ def seconds_per_solve(ms_max: float, steps: int, world: int) -> float:
     return ms_max / 1e3 / (steps * world)
 
 
+# ------------------------------------------------------- other configurations --
+def _timed(fn, steps, warmup, stream):
+    """CUDA-event time of `steps` calls of fn() after `warmup` calls (ms)."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def secondary_main(args):
+    """One JSON line for a non-headline configuration (one GPU; the config names
+    what a step is)."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2503_22631_gb300 import (BASIS_DF64, F_EXP_NEG, F_INVSQRT, ORTHO_RGS, Krylov, apply_batched, build,
+                                        krylov_expm)
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    warmup = max(args.warmup, 3)
+    wl = args.workload
+    stats = []
+    if wl == "convdiff3d_128_rgs":
+        A, b = make_inputs()
+        kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=WORKLOAD["t"], m=WORKLOAD["m"], k=WORKLOAD["m"],
+                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=BASIS_DF64, ortho=ORTHO_RGS)
+        bd = torch.from_numpy(b).cuda()
+        cycles = 10
+
+        def fn():
+            kr.apply(bd, tol=0.0, max_cycles=cycles)
+            stats.append(dict(kr.stats))
+
+        metric = "seconds to 1e-8 rel err per f(A)b at n=2.1M, randomized Gram-Schmidt with the full window"
+        config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": 40, "k": 40, "s": 160, "zeta": 8, "t": 1e-2,
+                  "cycles": cycles, "basis": "df64", "ortho": "rgs"}
+        units = 1
+    elif wl == "fem_kuhn_160":
+        cfg = W.CONFIGS["fem_kuhn_160"]
+        A = cfg["matrix"]()
+        b = cfg["rhs"](A.n)
+        kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_INVSQRT, t=1.0, m=cfg["m"], k=cfg["k"], s=cfg["s"], seed=W.SEED,
+                    zeta=cfg["zeta"], basis=BASIS_DF64)
+        bd = torch.from_numpy(b).cuda()
+        cycles = 20
+
+        def fn():
+            kr.apply(bd, tol=0.0, max_cycles=cycles)
+            stats.append(dict(kr.stats))
+
+        metric = "seconds per 20 restart cycles of A^{-1/2} b at n=4.0M (P1 FEM, k=4)"
+        config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": cfg["m"], "k": cfg["k"], "s": cfg["s"],
+                  "zeta": cfg["zeta"], "cycles": cycles, "basis": "df64", "f": "invsqrt"}
+        units = 1
+    elif wl == "batched16":
+        insts = W.batched_instances(16, W.SEED)
+        hs, B = [], []
+        for i, inst in enumerate(insts):
+            Ai = W.batched_matrix(inst)
+            hs.append(Krylov(Ai.row_ptr, Ai.col_idx, Ai.val, f=F_EXP_NEG, t=inst["t"], m=30, k=2, s=120, seed=W.SEED,
+                             zeta=8, basis=BASIS_DF64))
+            B.append(torch.from_numpy(W.rhs_normal(inst["n"] * 64, 100 + i).reshape(inst["n"], 64)).cuda())
+        cycles = 2
+        ts = [inst["t"] for inst in insts]
+
+        def fn():
+            _, st = apply_batched(hs, B, t=ts, tol=0.0, max_cycles=cycles, raise_on_error=False)
+            stats.extend(x for row in st for x in row)
+
+        metric = "seconds per batched call: 16 matrices x 64 right-hand sides, 2 restart cycles each"
+        config = {"workload": wl, "instances": 16, "rhs": 64, "n_total": int(sum(i["n"] for i in insts)),
+                  "m": 30, "k": 2, "s": 120, "zeta": 8, "cycles": cycles, "basis": "df64"}
+        units = 1
+    else:  # convdiff3d_96_adjoint
+        cfg = W.CONFIGS["convdiff3d_96_adjoint"]
+        A = cfg["matrix"]()
+        kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=cfg["t"], m=cfg["m"], k=cfg["k"], s=cfg["s"],
+                    seed=W.SEED, zeta=cfg["zeta"], basis=BASIS_DF64)
+        b0 = torch.from_numpy(cfg["rhs"](A.n)).cuda()
+        y = torch.from_numpy(W.rhs_normal(A.n, W.SEED + 1)).cuda()
+
+        def fn():
+            bb = b0.clone().requires_grad_(True)
+            tt = torch.tensor(cfg["t"], dtype=torch.float64, requires_grad=True)
+            x = krylov_expm(bb, tt, kr, 1e-10, 40)
+            ((x - y) ** 2).sum().backward()
+            stats.append(dict(kr.stats))
+
+        metric = "seconds per loss gradient (grad_b and grad_t of ||exp(-tA)b - y||^2) at n=885K"
+        config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": cfg["m"], "k": 2, "s": 160, "zeta": 8,
+                  "t": cfg["t"], "tol": 1e-10, "basis": "df64"}
+        units = 1
+    with ClockSampler(0, enabled=not args.profile) as clk:
+        ms = _timed(fn, args.steps, warmup, stream)
+    per_call = max(1, len(stats) // (warmup + args.steps))
+    stats = stats[-per_call * args.steps:]  # the timed calls only
+    steps_ms = sum(x.get("ms_steps", 0.0) for x in stats)
+    step_bytes = sum(x.get("step_bytes", 0.0) for x in stats)
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = step_bytes / (steps_ms / 1e3) / 1e9 if steps_ms > 0 else None
+    value = ms / 1e3 / (args.steps * units)
+    line = {
+        "metric": metric, "value": value, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "df64", "data": "synthetic", "config": config,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "Arnoldi-step phase (step kernels of every cycle)",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
+        "cpu_baseline": None, "e2e": None,
+        "gpu_launches": int(sum(x.get("launches", 0) for x in stats)),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------- main ---
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_main(args, rank)
+        return
+    if args.workload != "convdiff3d_128":
+        if rank == 0:
+            secondary_main(args)
         return
 
     import numpy as np
