@@ -370,6 +370,18 @@ double model_bytes_step(const krylov_handle* h, int use32) {
   return (double)h->nnz * (ba + 4.0) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
 }
 
+// Randomized Gram-Schmidt step j: read A and w_j, write p; the sketch reads p
+// and S's table (9 bytes per column); the materialization reads p and the
+// window (min(j + 1, k) vectors) and writes w_{j+1}.
+double model_bytes_rgs_step(const krylov_handle* h, int use32, int j) {
+  const double bv = basis_bytes(h->opt.basis_dtype);
+  const double ba = use32 ? 4.0 : 8.0;
+  const double n = (double)h->n;
+  const int nwin = std::min(j + 1, h->k);
+  return (double)h->nnz * (ba + 4.0) + 4.0 * (n + 1) + n * bv + n * bv + (n * bv + 9.0 * n) +
+         (n * bv + nwin * n * bv + n * bv);
+}
+
 // Arguments of the step launch for column j of a cycle (the same in every cycle).
 StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, int use32, double thr, int j) {
   const int n = h->n, M = h->m, basis = h->opt.basis_dtype;
@@ -620,7 +632,11 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       float ms_s = 0.f;
       CK(cudaEventElapsedTime(&ms_s, h->ev[0], h->ev[1]));
       stats.ms_steps += ms_s;
-      stats.step_bytes += me * model_bytes_step(h, use32);
+      if (h->opt.ortho == KRYLOV_ORTHO_RGS) {
+        for (int j = 0; j < me; ++j) stats.step_bytes += model_bytes_rgs_step(h, use32, j);
+      } else {
+        stats.step_bytes += me * model_bytes_step(h, use32);
+      }
     }
     if (rgs) {
       launch_rgs_small(h->sd, h->cd, M, me, has_next, c, h->f.t, st);
