@@ -167,6 +167,47 @@ struct SmallDev {
 constexpr size_t INVSQRT_SMEM_MAX = 100 * 1024;
 size_t invsqrt_smem(int m);
 
+// Per-right-hand-side strides (in elements) of the small-problem and cycle
+// arrays when several independent problems are laid out one after another
+// (the block form); all zero for one problem.
+struct BatchStride {
+  int64_t U, Tw, Tinv, zg, Xblk, gam, misc, G, S0, fcol;  // SmallDev arrays
+  int64_t flags, sig2, pi, coef, R, scal;                 // CycleDev arrays
+};
+__host__ __device__ inline SmallDev offset_sd(SmallDev sd, const BatchStride& b, int r) {
+  sd.U += b.U * r;
+  sd.Tw += b.Tw * r;
+  sd.Tinv += b.Tinv * r;
+  sd.zg += b.zg * r;
+  sd.Xblk += b.Xblk * r;
+  sd.gam += b.gam * r;
+  sd.misc += b.misc * r;
+  sd.G += b.G * r;
+  sd.S0 += b.S0 * r;
+  sd.fcol += b.fcol * r;
+  return sd;
+}
+__host__ __device__ inline CycleDev offset_cd(CycleDev cd, const BatchStride& b, int r) {
+  cd.flags += b.flags * r;
+  cd.sig2 += b.sig2 * r;
+  cd.pi += b.pi * r;
+  cd.coef += b.coef * r;
+  cd.R += b.R * r;
+  cd.scal += b.scal * r;
+  return cd;
+}
+
+// Batched small problem (block form): one problem per CTA (whiten, z) or per
+// grid z-slice (exp), problems r = 0..nb-1 at offsets r * stride.
+void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
+                           int ncols, int m_eff, int has_next, int cycle, double t, cudaStream_t st);
+void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
+                               double scale, int first, int src, double* dst0, int dst_in_g, cudaStream_t st);
+void launch_exp_square_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int level,
+                               int64_t level_stride, cudaStream_t st);
+void launch_z_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int m_eff, const double* fcol0,
+                      int64_t fcol_stride, cudaStream_t st);
+
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
                    int has_next, int cycle, double t, cudaStream_t st);
 void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first,

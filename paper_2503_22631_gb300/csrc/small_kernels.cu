@@ -33,7 +33,11 @@ __device__ __forceinline__ double& Tat(double* Tw, int s, int a, int b) { return
 
 __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, CycleDev cd, int s, int M,
                                                                int nc, int me, int has_next, int cycle,
-                                                               double t, double* scratch) {
+                                                               double t, double* scratch, const BatchStride bs) {
+  // problem blockIdx.x of a batch (strides are zero for a single problem)
+  sd = offset_sd(sd, bs, blockIdx.x);
+  cd = offset_cd(cd, bs, blockIdx.x);
+  scratch += bs.S0 * blockIdx.x;
   __shared__ double red[32];
   __shared__ double sh_beta_h, sh_alpha;
   __shared__ double diag[1024];
@@ -190,7 +194,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
 // with E the block row of the identity (E[a] = I).  first: S_old = E.
 __global__ void exp_taylor_kernel(const double* __restrict__ Xblk, const double* __restrict__ gam, int M,
                                   int a, double kinv, double scale, int first, const double* __restrict__ Sold,
-                                  double* __restrict__ Snew) {
+                                  double* __restrict__ Snew, int64_t sx, int64_t sg, int64_t s_old, int64_t s_new) {
+  // problem blockIdx.z of a batch: X blocks, couplings and the Horner buffers
+  // at strides sx, sg, s_old, s_new (zero for a single problem)
+  Xblk += sx * blockIdx.z;
+  gam += sg * blockIdx.z;
+  Sold += s_old * blockIdx.z;
+  Snew += s_new * blockIdx.z;
   const int j = blockIdx.y;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (j > a || e >= M * M) return;
@@ -213,7 +223,10 @@ __global__ void exp_taylor_kernel(const double* __restrict__ Xblk, const double*
 
 // Squaring for block row a: N[j] = sum_{l=j}^{a} G[a][l] G[l][j], blocks of
 // the lower triangle stored row-major by (row, col) pairs.
-__global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restrict__ Go, int M, int a) {
+__global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restrict__ Go, int M, int a,
+                                  int64_t sgm) {
+  Gi += sgm * blockIdx.z;  // problem blockIdx.z of a batch (stride 0 for one problem)
+  Go += sgm * blockIdx.z;
   const int j = blockIdx.y;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (j > a || e >= M * M) return;
@@ -341,7 +354,9 @@ __global__ void invsqrt_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, int 
   }
 }
 
-__global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc) {
+__global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc, const BatchStride bs, int64_t fstride) {
+  sd = offset_sd(sd, bs, blockIdx.x);  // problem blockIdx.x of a batch
+  fsrc += fstride * blockIdx.x;
   const double beta = sd.misc[0];
   for (int a = threadIdx.x; a < me; a += blockDim.x) {
     double acc = 0.0;
@@ -355,7 +370,35 @@ __global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc) {
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff, int has_next,
                    int cycle, double t, cudaStream_t st) {
   // scratch for T_m R_m: reuse the Horner buffer area (not in use at this point)
-  whiten_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0);
+  whiten_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, BatchStride{});
+}
+
+void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
+                           int ncols, int m_eff, int has_next, int cycle, double t, cudaStream_t st) {
+  whiten_kernel<<<nb, SMALL_THREADS, 0, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, bs);
+}
+
+void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
+                               double scale, int first, int src, double* dst0, int dst_in_g, cudaStream_t st) {
+  const int MM = m * m;
+  dim3 g((MM + 127) / 128, a + 1, nb);
+  const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
+  // dst0 lies in problem 0's Horner buffer or (last step) its exp rows
+  exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst0, bs.Xblk, bs.gam,
+                                       bs.S0, dst_in_g ? bs.G : bs.S0);
+}
+
+void launch_exp_square_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int level,
+                               int64_t level_stride, cudaStream_t st) {
+  const int MM = m * m;
+  dim3 g((MM + 127) / 128, a + 1, nb);
+  exp_square_kernel<<<g, 128, 0, st>>>(sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride,
+                                      m, a, bs.G);
+}
+
+void launch_z_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int m_eff, const double* fcol0,
+                      int64_t fcol_stride, cudaStream_t st) {
+  z_kernel<<<nb, 256, 0, st>>>(sd, m, m_eff, fcol0, bs, fcol_stride);
 }
 
 void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first, int last,
@@ -364,14 +407,14 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double s
   const int MM = m * m;
   dim3 g((MM + 127) / 128, a + 1);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
-  exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst);
+  exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0, 0, 0, 0);
 }
 
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st) {
   const int MM = m * m;
   dim3 g((MM + 127) / 128, a + 1);
   exp_square_kernel<<<g, 128, 0, st>>>(sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride,
-                                      m, a);
+                                      m, a, 0);
 }
 
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
@@ -393,7 +436,7 @@ void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_e
 }
 
 void launch_z(const SmallDev& sd, int m, int m_eff, const double* fcol_src, cudaStream_t st) {
-  z_kernel<<<1, 256, 0, st>>>(sd, m, m_eff, fcol_src);
+  z_kernel<<<1, 256, 0, st>>>(sd, m, m_eff, fcol_src, BatchStride{}, 0);
 }
 
 }  // namespace krylov
