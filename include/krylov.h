@@ -119,6 +119,9 @@ typedef struct {
                       operator at create (w_j pieces staged in shared memory from a per-tile
                       segment plan, or w_j gathered through L1/L2) and keeps the faster;
                       0 uses the staged pieces whenever the operator has a segment plan */
+  int block_rhs;   /* batched form: 1 (default) advances up to 64 right-hand sides of a matrix
+                      together through the block kernels (float-float basis, TRUNC, exp, packed
+                      sketch table, m <= 64, max_cycles <= 16); 0 solves them one by one */
 } krylov_options;
 
 typedef struct {

@@ -42,7 +42,7 @@ class Krylov:
 
     def __init__(self, row_ptr, col_idx, val, *, f=F_EXP_NEG, t=1.0, m=30, k=2, s=None, seed=0, zeta=8,
                  basis=BASIS_F64, narrow_values_if_exact=True, abs_tol=False, sketch_regenerate=False,
-                 ortho=ORTHO_TRUNC, use_graph=True, autotune=True, stream=None):
+                 ortho=ORTHO_TRUNC, use_graph=True, autotune=True, block_rhs=True, stream=None):
         lib = _lib.load()
         torch = _torch()
         self._keep = []
@@ -75,6 +75,7 @@ class Krylov:
         opt.ortho = int(ortho)
         opt.use_graph = 1 if use_graph else 0
         opt.autotune = 1 if autotune else 0
+        opt.block_rhs = 1 if block_rhs else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

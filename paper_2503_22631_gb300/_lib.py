@@ -67,7 +67,8 @@ class Func(C.Structure):
 class Options(C.Structure):
     _fields_ = [("zeta", C.c_int), ("basis_dtype", C.c_int), ("ortho", C.c_int),
                 ("narrow_values_if_exact", C.c_int), ("use_graph", C.c_int), ("abs_tol", C.c_int),
-                ("sketch_regenerate", C.c_int), ("stream", C.c_void_p), ("autotune", C.c_int)]
+                ("sketch_regenerate", C.c_int), ("stream", C.c_void_p), ("autotune", C.c_int),
+                ("block_rhs", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -135,6 +135,8 @@ bool build_seg_plan(int n, int64_t nnz, const int* rp, const int* ci, std::vecto
   return ok.load();
 }
 
+struct BlockWs;
+
 }  // namespace
 
 struct krylov_handle {
@@ -159,6 +161,7 @@ struct krylov_handle {
   int vals_exact_f32 = 0;
   int part_cap = 0;                // per-CTA partial slots (8 doubles each)
   long long* rgs_acc = nullptr;    // randomized Gram-Schmidt: exact sketch sums [3][s]
+  BlockWs* bk = nullptr;           // block form workspace (allocated on first use)
   int grid_update = 0;             // CTAs of the cycle-end update pass
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
@@ -732,6 +735,305 @@ krylov_status apply_impl(krylov_handle* h, int transpose, const double* b, doubl
   return r;
 }
 
+constexpr int NQ_HOST = 2 + MAX_WINDOW;  // per-CTA scalar slots of the product kernels
+
+// ---- block form (several right-hand sides of one matrix together) ----------
+
+// Workspace of the block form for up to nb_cap right-hand sides: vectors
+// row-major n x nb, per-right-hand-side cycle and small-problem state at the
+// strides of bs.
+struct BlockWs {
+  int nb_cap = 0, rows_cap = 0, levels_cap = 0;
+  int64_t level_stride = 0;
+  float2* W = nullptr;
+  float2* P[2] = {nullptr, nullptr};
+  double* part = nullptr;
+  long long* acc = nullptr;
+  int* E = nullptr;
+  int* active = nullptr;
+  unsigned* counter = nullptr;
+  CycleDev cd{};
+  SmallDev sd{};
+  BatchStride bs{};
+  int* h_flags = nullptr;    // pinned: nb x 4
+  double* h_scal = nullptr;  // pinned: nb x 8 (scal) then nb x 8 (misc)
+  int* h_active = nullptr;   // pinned: nb
+  std::vector<void*> allocs;
+};
+
+constexpr int BK_NB = 64;
+constexpr int BK_MAX_CYCLES = 16;  // block exp rows stored for at most this many cycles
+
+template <typename T>
+cudaError_t balloc(BlockWs& b, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  b.allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaMemset(q, 0, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_block_ws(BlockWs& b) {
+  for (void* p : b.allocs) cudaFree(p);
+  b.allocs.clear();
+  if (b.h_flags) cudaFreeHost(b.h_flags);
+  if (b.h_scal) cudaFreeHost(b.h_scal);
+  if (b.h_active) cudaFreeHost(b.h_active);
+  b = BlockWs{};
+}
+
+// Can the block kernels run this configuration?
+bool block_eligible(const krylov_handle* h, int n_rhs, int max_cycles) {
+  return h->opt.block_rhs && n_rhs > 1 && h->opt.basis_dtype == KRYLOV_BASIS_DF64 &&
+         h->opt.ortho == KRYLOV_ORTHO_TRUNC && h->f.kind == KRYLOV_F_EXP_NEG && h->sk_mode == SK_TAB8 &&
+         max_cycles <= BK_MAX_CYCLES && h->m <= 64 && bk_mat_smem(h->s, BK_NB) <= 200 * 1024;
+}
+
+krylov_status ensure_block_ws(krylov_handle* h, int levels) {
+  BlockWs& b = *h->bk;
+  const int M = h->m, s = h->s;
+  const size_t MM = (size_t)M * M;
+  if (b.nb_cap == 0) {
+    const size_t n = (size_t)h->n;
+    b.nb_cap = BK_NB;
+    b.rows_cap = BK_MAX_CYCLES;
+    CK(balloc(b, &b.W, (size_t)(M + 1) * n * BK_NB));
+    CK(balloc(b, &b.P[0], n * BK_NB));
+    CK(balloc(b, &b.P[1], n * BK_NB));
+    CK(balloc(b, &b.part, (size_t)h->num_sms * 2 * NQ_HOST * BK_NB));
+    CK(balloc(b, &b.acc, (size_t)(M + 1) * 3 * s * BK_NB));
+    CK(balloc(b, &b.E, (size_t)(M + 1) * BK_NB));
+    CK(balloc(b, &b.active, (size_t)BK_NB));
+    CK(balloc(b, &b.counter, 4));
+    BatchStride& bs = b.bs;
+    bs.flags = 4;
+    bs.sig2 = M + 1;
+    bs.pi = M + 1;
+    bs.coef = (int64_t)(M + 1) * (MAX_WINDOW + 1);
+    bs.R = (int64_t)(M + 1) * M;
+    bs.scal = 8;
+    bs.U = (int64_t)s * (M + 1);
+    bs.Tw = (int64_t)s * (M + 1);
+    bs.Tinv = (int64_t)MM;
+    bs.zg = 2 * M + 1;
+    bs.Xblk = (int64_t)b.rows_cap * MM;
+    bs.gam = b.rows_cap;
+    bs.misc = 8;
+    bs.S0 = (int64_t)std::max<size_t>(2 * (size_t)b.rows_cap * MM, MM);
+    bs.fcol = M;
+    CK(balloc(b, &b.cd.flags, (size_t)bs.flags * BK_NB));
+    CK(balloc(b, &b.cd.sig2, (size_t)bs.sig2 * BK_NB));
+    CK(balloc(b, &b.cd.pi, (size_t)bs.pi * BK_NB));
+    CK(balloc(b, &b.cd.coef, (size_t)bs.coef * BK_NB));
+    CK(balloc(b, &b.cd.R, (size_t)bs.R * BK_NB));
+    CK(balloc(b, &b.cd.scal, (size_t)bs.scal * BK_NB));
+    b.cd.counter = b.counter;
+    CK(balloc(b, &b.sd.U, (size_t)bs.U * BK_NB));
+    CK(balloc(b, &b.sd.Tw, (size_t)bs.Tw * BK_NB));
+    CK(balloc(b, &b.sd.Tinv, (size_t)bs.Tinv * BK_NB));
+    CK(balloc(b, &b.sd.zg, (size_t)bs.zg * BK_NB));
+    CK(balloc(b, &b.sd.Xblk, (size_t)bs.Xblk * BK_NB));
+    CK(balloc(b, &b.sd.gam, (size_t)bs.gam * BK_NB));
+    CK(balloc(b, &b.sd.misc, (size_t)bs.misc * BK_NB));
+    CK(balloc(b, &b.sd.S0, (size_t)bs.S0 * BK_NB));
+    CK(balloc(b, &b.sd.fcol, (size_t)bs.fcol * BK_NB));
+    if (cudaMallocHost(&b.h_flags, sizeof(int) * 4 * BK_NB) != cudaSuccess) return KRYLOV_ENOMEM;
+    if (cudaMallocHost(&b.h_scal, sizeof(double) * 16 * BK_NB) != cudaSuccess) return KRYLOV_ENOMEM;
+    if (cudaMallocHost(&b.h_active, sizeof(int) * BK_NB) != cudaSuccess) return KRYLOV_ENOMEM;
+  }
+  if (levels > b.levels_cap) {
+    const int nl = std::max(levels, b.levels_cap + 4);
+    if (b.sd.G) {
+      cudaFree(b.sd.G);
+      b.allocs.erase(std::find(b.allocs.begin(), b.allocs.end(), (void*)b.sd.G));
+      b.sd.G = nullptr;
+    }
+    b.level_stride = (int64_t)b.rows_cap * (b.rows_cap + 1) / 2 * (int64_t)MM;
+    b.bs.G = (int64_t)nl * b.level_stride;
+    CK(balloc(b, &b.sd.G, (size_t)b.bs.G * BK_NB));
+    b.levels_cap = nl;
+  }
+  return KRYLOV_OK;
+}
+
+// Block row a of exp(-t H_r) for every right-hand side r at scale levels 0..sl.
+int exp_row_block(krylov_handle* h, int nb, int a, int sl, cudaStream_t st) {
+  BlockWs& b = *h->bk;
+  const int M = h->m;
+  const size_t MM = (size_t)M * M;
+  const double scale = -h->f.t / std::ldexp(1.0, sl);
+  double* g0row = b.sd.G + (size_t)a * (a + 1) / 2 * MM;
+  int src = 0;
+  for (int kdeg = EXP_TAYLOR_DEG; kdeg >= 1; --kdeg) {
+    const int first = (kdeg == EXP_TAYLOR_DEG);
+    double* dst = (kdeg == 1) ? g0row : b.sd.S0 + (size_t)(1 - src) * (size_t)(a + 1) * MM;
+    launch_exp_taylor_batched(b.sd, b.bs, nb, M, a, kdeg, scale, first, src, dst, kdeg == 1 ? 1 : 0, st);
+    src = 1 - src;
+  }
+  for (int lv = 0; lv < sl; ++lv) launch_exp_square_batched(b.sd, b.bs, nb, M, a, lv, b.level_stride, st);
+  return EXP_TAYLOR_DEG + sl;
+}
+
+// nb (<= 64) right-hand sides of the caller's row-major block B (column c0
+// on, leading dimension ldb) through the block kernels; results into X (same
+// layout).  Right-hand sides that meet a breakdown are flagged in `redo` and
+// solved afterwards by the single-vector path.
+krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t ldb, int nb, double tol,
+                          int max_cycles, krylov_stats* st, std::vector<int>& redo) {
+  if (!h->bk) h->bk = new (std::nothrow) BlockWs();
+  if (!h->bk) return KRYLOV_ENOMEM;
+  BlockWs& b = *h->bk;
+  cudaStream_t s_ = h->st;
+  const int M = h->m, n = h->n;
+  const size_t MM = (size_t)M * M;
+  krylov_status cs = ensure_block_ws(h, std::max(1, b.levels_cap));
+  if (cs != KRYLOV_OK) return cs;
+  const int use32 = (h->opt.narrow_values_if_exact && h->vals_exact_f32) ? 1 : 0;
+  BlockLaunch L{};
+  L.n = n;
+  L.nb = nb;
+  L.m = M;
+  L.k = h->k;
+  L.s = h->s;
+  L.zeta = h->opt.zeta;
+  L.rp = h->rp;
+  L.ci = h->ci;
+  L.val = use32 ? (const void*)h->val32 : (const void*)h->valff;
+  L.val_f32 = use32;
+  L.W = b.W;
+  L.slot = (int64_t)n * nb;
+  L.part = b.part;
+  L.cd = b.cd;
+  L.bs = b.bs;
+  L.counter = b.counter;
+  L.acc = b.acc;
+  L.E = b.E;
+  L.tab = h->sk_tab;
+  L.grid = std::max(1, std::min(h->num_sms * 2, (n + 7) / 8));
+  L.rows_per_cta = (n + L.grid - 1) / L.grid;
+  L.fx_wb = sketch_word_bits(L.rows_per_cta, 1);
+  L.thr = 1e-12;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s_));
+  // x = 0 in the block's columns; flags, misc cleared
+  launch_zero_columns(X, n, ldb, nb, s_);
+  CK(cudaMemsetAsync(b.cd.flags, 0, sizeof(int) * 4 * BK_NB, s_));
+  CK(cudaMemsetAsync(b.sd.misc, 0, sizeof(double) * 8 * BK_NB, s_));
+  launch_bk_norm_start(L, B, ldb, s_);
+  CK(cudaMemcpyAsync(b.h_scal, b.cd.scal, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s_));
+  CK(cudaStreamSynchronize(s_));
+  std::vector<int> active((size_t)nb, 1), done((size_t)nb, 0);
+  std::vector<double> maxX((size_t)nb, 0.0), maxG((size_t)nb, 0.0);
+  for (int r = 0; r < nb; ++r) {
+    std::memset(&st[r], 0, sizeof(krylov_stats));
+    st[r].status = KRYLOV_NOT_CONVERGED;
+    if (!(b.h_scal[8 * r] > 0.0) || !std::isfinite(b.h_scal[8 * r])) {  // b_r = 0 (or invalid): one by one
+      active[r] = 0;
+      redo.push_back(r);
+    }
+  }
+  int s_lv = -1, launches = 2;
+  for (int c = 1; c <= max_cycles; ++c) {
+    int n_active = 0;
+    for (int r = 0; r < nb; ++r) {
+      b.h_active[r] = active[r];
+      n_active += active[r];
+      b.h_flags[4 * r] = M;
+      b.h_flags[4 * r + 1] = 0;
+      b.h_flags[4 * r + 2] = 0;
+      b.h_flags[4 * r + 3] = 0;
+    }
+    if (n_active == 0) break;
+    CK(cudaMemcpyAsync(b.active, b.h_active, sizeof(int) * nb, cudaMemcpyHostToDevice, s_));
+    CK(cudaMemcpyAsync(b.cd.flags, b.h_flags, sizeof(int) * 4 * nb, cudaMemcpyHostToDevice, s_));
+    for (int j = 0; j <= M; ++j) {
+      L.j = j;
+      L.p_prev = b.P[(j + 1) & 1];
+      L.p_out = b.P[j & 1];
+      launch_bk_step(L, j > 0, j < M, s_);
+      launches += (j < M) ? 2 : 1;
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(b.h_flags, b.cd.flags, sizeof(int) * 4 * nb, cudaMemcpyDeviceToHost, s_));
+    CK(cudaStreamSynchronize(s_));
+    for (int r = 0; r < nb; ++r) {
+      if (!active[r]) continue;
+      if (b.h_flags[4 * r + 1] != 0 || (b.h_flags[4 * r + 2] & (ERR_NONFINITE | ERR_SKETCH))) {
+        active[r] = 0;  // breakdown (or trouble): this right-hand side is redone alone
+        redo.push_back(r);
+      }
+    }
+    launch_bk_sketch_fin(L, b.sd, M + 1, s_);
+    launch_whiten_batched(b.sd, b.cd, b.bs, nb, h->s, M, M + 1, M, 1, c, h->f.t, s_);
+    CK(cudaMemcpyAsync(b.h_scal + 8 * BK_NB, b.sd.misc, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s_));
+    CK(cudaStreamSynchronize(s_));
+    launches += 2;
+    int need = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (!active[r]) continue;
+      const double* mi = b.h_scal + 8 * BK_NB + 8 * r;
+      maxX[r] = std::max(maxX[r], mi[2]);
+      maxG[r] = std::max(maxG[r], mi[3]);
+      st[r].kappa_T_max = std::max(st[r].kappa_T_max, mi[4]);
+      if (!std::isfinite(maxX[r]) || !std::isfinite(maxG[r])) {
+        active[r] = 0;
+        redo.push_back(r);
+        continue;
+      }
+      need = std::max(need, scale_levels_for(maxX[r] + maxG[r]));
+    }
+    const int a = c - 1;
+    if (need > s_lv) {
+      s_lv = need;
+      cs = ensure_block_ws(h, s_lv + 1);
+      if (cs != KRYLOV_OK) return cs;
+      for (int ap = 0; ap < a; ++ap) launches += exp_row_block(h, nb, ap, s_lv, s_);
+    }
+    launches += exp_row_block(h, nb, a, s_lv, s_);
+    const double* fsrc = b.sd.G + (size_t)s_lv * b.level_stride + (size_t)a * (a + 1) / 2 * MM;
+    launch_z_batched(b.sd, b.bs, nb, M, M, fsrc, b.bs.G, s_);
+    for (int r = 0; r < nb; ++r) b.h_active[r] = active[r];
+    CK(cudaMemcpyAsync(b.active, b.h_active, sizeof(int) * nb, cudaMemcpyHostToDevice, s_));
+    launch_bk_update(L, b.sd, M, 1, X, ldb, b.active, s_);
+    launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(b.h_scal, b.cd.scal, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s_));
+    CK(cudaStreamSynchronize(s_));
+    for (int r = 0; r < nb; ++r) {
+      if (!active[r]) continue;
+      const double yn = std::sqrt(b.h_scal[8 * r + 2]), xn = std::sqrt(b.h_scal[8 * r + 3]);
+      st[r].cycles = c;
+      st[r].steps += M;
+      st[r].last_update_norm = yn;
+      st[r].x_norm = xn;
+      if (!std::isfinite(yn) || !std::isfinite(xn)) {
+        active[r] = 0;
+        redo.push_back(r);
+        continue;
+      }
+      const double lim = h->opt.abs_tol ? tol : tol * xn;
+      if (yn <= lim && (h->opt.abs_tol || xn > 0.0)) {
+        active[r] = 0;
+        st[r].status = KRYLOV_OK;
+      }
+    }
+  }
+  CK(cudaEventRecord(e1, s_));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int r = 0; r < nb; ++r) {
+    st[r].ms_total = ms;
+    st[r].launches = launches;
+  }
+  return KRYLOV_OK;
+}
+
 // One instance of the batched form: its right-hand sides in order, on a
 // stream of its own ordered after (and, at the end, before) the handle's stream.
 krylov_status run_instance(krylov_handle* h, int n_rhs, const double* B, double* X, const double* t_new, double tol,
@@ -753,9 +1055,32 @@ krylov_status run_instance(krylov_handle* h, int n_rhs, const double* B, double*
     if (dalloc(h, &h->stage_b, (size_t)h->n) != cudaSuccess || dalloc(h, &h->stage_x, (size_t)h->n) != cudaSuccess)
       worst = KRYLOV_ENOMEM;
   }
+  // block kernels: up to 64 right-hand sides advance together; those that meet
+  // a breakdown (or a zero right-hand side) are redone one by one below
+  std::vector<char> todo((size_t)n_rhs, 1);
+  if (worst == KRYLOV_OK && block_eligible(h, n_rhs, max_cycles)) {
+    std::vector<krylov_stats> bst((size_t)n_rhs);
+    for (int c0 = 0; c0 < n_rhs && worst == KRYLOV_OK; c0 += BK_NB) {
+      const int nb = std::min(BK_NB, n_rhs - c0);
+      std::vector<int> redo;
+      const krylov_status s = block_solve(h, B + c0, X + c0, n_rhs, nb, tol, max_cycles, bst.data() + c0, redo);
+      if (s != KRYLOV_OK) {
+        worst = s;
+        break;
+      }
+      for (int r = 0; r < nb; ++r) todo[(size_t)(c0 + r)] = 0;
+      for (int r : redo) todo[(size_t)(c0 + r)] = 1;
+    }
+    for (int r = 0; r < n_rhs; ++r) {
+      if (todo[(size_t)r]) continue;
+      if (st) st[r] = bst[(size_t)r];
+      if (bst[(size_t)r].status == KRYLOV_NOT_CONVERGED && worst == KRYLOV_OK) worst = KRYLOV_NOT_CONVERGED;
+    }
+  }
   // every right-hand side runs even if an earlier one failed (its status is in
   // its stats); only a CUDA error stops the instance
   for (int r = 0; r < n_rhs && worst != KRYLOV_ECUDA && worst != KRYLOV_ENOMEM; ++r) {
+    if (!todo[(size_t)r]) continue;
     launch_gather_column(B, h->n, n_rhs, r, h->stage_b, bs);
     krylov_status s = apply_impl(h, 0, h->stage_b, h->stage_x, tol, max_cycles, st ? st + r : nullptr);
     launch_scatter_column(h->stage_x, h->n, n_rhs, r, X, bs);
@@ -784,6 +1109,7 @@ void krylov_options_default(krylov_options* opt) {
   opt->narrow_values_if_exact = 1;
   opt->use_graph = 1;
   opt->autotune = 1;
+  opt->block_rhs = 1;
   opt->abs_tol = 0;
   opt->stream = nullptr;
 }
@@ -812,6 +1138,10 @@ void krylov_destroy(krylov_handle* h) {
   for (auto& g : h->step_graph)
     if (g) cudaGraphExecDestroy(g);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->bk) {
+    free_block_ws(*h->bk);
+    delete h->bk;
+  }
   if (h->h_flags) cudaFreeHost(h->h_flags);
   if (h->h_scal) cudaFreeHost(h->h_scal);
   delete h;

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
                                                                  int has_next, const double* zg, int m, double* x,
                                                                  double* part, CycleDev cd, int rows_per_cta) {
   __shared__ ff zs[256], gs[256];
-  __shared__ float red[32];
+  __shared__ double red[32];
   __shared__ int s_last;
   for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
     zs[q] = ff_from_double(zg[q]);
@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
   }
   const ff tau_inv = ff_from_double(zg[2 * m]);
   __syncthreads();
-  float ay = 0.f, ax = 0.f, av = 0.f;
+  // squared norms in float64: a float square of a tiny update would underflow
+  // to zero and read as a converged cycle
+  double ay = 0.0, ax = 0.0, av = 0.0;
   const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
   for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
     ffsum y, v;
@@ -226,18 +228,18 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
     if (has_next) {
       const ff vn = ff_mul(v.result(), tau_inv);
       W[i] = make_float2(vn.hi, vn.lo);
-      av = __fmaf_rn(vn.hi, vn.hi, av);
+      av = fma((double)vn.hi, (double)vn.hi, av);
     }
-    ay = __fmaf_rn(yy.hi, yy.hi, ay);
-    const float xf = __double2float_rn(xn);
-    ax = __fmaf_rn(xf, xf, ax);
+    const double yd = (double)yy.hi + (double)yy.lo;
+    ay = fma(yd, yd, ay);
+    ax = fma(xn, xn, ax);
   }
-  float v = block_sum(ay, red);
-  if (threadIdx.x == 0) part[3 * blockIdx.x] = double(v);
+  double v = block_sum(ay, red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x] = v;
   v = block_sum(ax, red);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = double(v);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = v;
   v = block_sum(av, red);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = double(v);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = v;
   if (!last_block(cd.counter, &s_last)) return;
   if (threadIdx.x < 96) {  // warp q sums column q
     const int q = (int)(threadIdx.x >> 5);
@@ -449,6 +451,19 @@ __global__ void scatter_column_kernel(const double* __restrict__ x, int64_t n, i
 }
 int column_grid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 }  // namespace
+
+namespace {
+__global__ void zero_columns_kernel(double* X, int64_t n, int64_t ld, int ncols) {
+  const int64_t total = n * ncols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    X[(e / ncols) * ld + e % ncols] = 0.0;
+}
+}  // namespace
+
+void launch_zero_columns(double* X, int64_t n, int64_t ld, int ncols, cudaStream_t st) {
+  const int64_t total = n * ncols;
+  zero_columns_kernel<<<(int)std::min<int64_t>(4096, (total + 255) / 256), 256, 0, st>>>(X, n, ld, ncols);
+}
 
 void launch_gather_column(const double* B, int64_t n, int ncols, int r, double* b, cudaStream_t st) {
   gather_column_kernel<<<column_grid(n), 256, 0, st>>>(B, n, ncols, r, b);

@@ -79,6 +79,37 @@ constexpr int SEG_MAX = 16;        // pieces of w_j per tile
 constexpr int SEG_CAP_MAX = 3072;  // staged entries of w_j per tile (24 KB float-float)
 constexpr int SEG_GAP = 64;        // columns closer than this join one piece
 
+// Per-right-hand-side strides (in elements) of the small-problem and cycle
+// arrays when several independent problems are laid out one after another
+// (the block form); all zero for one problem.
+struct BatchStride {
+  int64_t U, Tw, Tinv, zg, Xblk, gam, misc, G, S0, fcol;  // SmallDev arrays
+  int64_t flags, sig2, pi, coef, R, scal;                 // CycleDev arrays
+};
+
+// Arguments of the block-form kernels (nb right-hand sides of one matrix,
+// vectors row-major n x nb, float-float basis).
+struct BlockLaunch {
+  int n, nb, m, k, s, zeta, j;
+  const int* rp;
+  const int* ci;
+  const void* val;
+  int val_f32;
+  float2* W;            // (m+1) slots of n x nb
+  int64_t slot;         // n * nb
+  const float2* p_prev;
+  float2* p_out;
+  double* part;         // per-CTA partials [grid][NQ][64]
+  CycleDev cd;          // right-hand side 0's cycle state; others at offsets bs
+  BatchStride bs;
+  unsigned* counter;
+  long long* acc;       // [m+1][3][s][64] exact sketch sums
+  int* E;               // [m+1][64] fixed-point exponents of the sketch words
+  SketchTable tab;
+  int grid, rows_per_cta, fx_wb;
+  double thr;
+};
+
 // Arguments of the randomized Gram-Schmidt cycle kernels (Algorithm 1).
 struct RgsArgs {
   int n, m, k, s, zeta;
@@ -142,6 +173,7 @@ cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, cons
                           int* cit, double* vt, int* work, cudaStream_t st);
 void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st);
 void launch_gather_column(const double* B, int64_t n, int ncols, int r, double* b, cudaStream_t st);
+void launch_zero_columns(double* X, int64_t n, int64_t ld, int ncols, cudaStream_t st);
 void launch_scatter_column(const double* x, int64_t n, int ncols, int r, double* X, cudaStream_t st);
 
 // ---- small projected problem (FP64) ---------------------------------------
@@ -167,13 +199,6 @@ struct SmallDev {
 constexpr size_t INVSQRT_SMEM_MAX = 100 * 1024;
 size_t invsqrt_smem(int m);
 
-// Per-right-hand-side strides (in elements) of the small-problem and cycle
-// arrays when several independent problems are laid out one after another
-// (the block form); all zero for one problem.
-struct BatchStride {
-  int64_t U, Tw, Tinv, zg, Xblk, gam, misc, G, S0, fcol;  // SmallDev arrays
-  int64_t flags, sig2, pi, coef, R, scal;                 // CycleDev arrays
-};
 __host__ __device__ inline SmallDev offset_sd(SmallDev sd, const BatchStride& b, int r) {
   sd.U += b.U * r;
   sd.Tw += b.Tw * r;
@@ -207,6 +232,14 @@ void launch_exp_square_batched(const SmallDev& sd, const BatchStride& bs, int nb
                                int64_t level_stride, cudaStream_t st);
 void launch_z_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int m_eff, const double* fcol0,
                       int64_t fcol_stride, cudaStream_t st);
+
+// block form (block_kernels.cu)
+size_t bk_mat_smem(int s, int nb);
+void launch_bk_norm_start(const BlockLaunch& B, const double* b, int64_t ldb, cudaStream_t st);
+void launch_bk_step(const BlockLaunch& B, int mat, int spmv, cudaStream_t st);
+void launch_bk_sketch_fin(const BlockLaunch& B, const SmallDev& sd, int ncols, cudaStream_t st);
+void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int has_next, double* x, int64_t ldx,
+                      const int* active, cudaStream_t st);
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
                    int has_next, int cycle, double t, cudaStream_t st);

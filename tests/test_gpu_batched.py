@@ -154,3 +154,70 @@ def test_full_batch_float_float_reaches_1e8(lib, cuda):
             ref = TR.kron_expm_apply(inst["N"], dim, inst["beta"], inst["t"], b)
             err = np.linalg.norm(X[i][:, col] - ref)
             assert err <= 1e-8 * np.linalg.norm(ref) + 1e-16 * np.linalg.norm(b)
+
+
+def _run_df64(insts, n_rhs, tol, cycles, block_rhs):
+    import torch
+
+    from paper_2503_22631_gb300 import BASIS_DF64, F_EXP_NEG, Krylov, apply_batched
+
+    hs = []
+    for inst in insts:
+        A = W.batched_matrix(inst)
+        hs.append(Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=1.0, m=M, k=KW, s=S, seed=W.SEED, zeta=ZETA,
+                         basis=BASIS_DF64, block_rhs=block_rhs))
+    B = [torch.from_numpy(_rhs_block(inst["n"], n_rhs, 100 + i)).cuda() for i, inst in enumerate(insts)]
+    X, st = apply_batched(hs, B, t=[inst["t"] for inst in insts], tol=tol, max_cycles=cycles)
+    torch.cuda.synchronize()
+    return [x.cpu().numpy() for x in X], st
+
+
+@pytest.mark.parametrize("n_rhs", [8, 40, 70])
+def test_block_kernels_match_one_by_one(lib, cuda, n_rhs):
+    """Float-float basis: the block kernels (right-hand sides advanced together,
+    chunks of at most 64) agree with the single-vector kernels to rounding."""
+    insts = SMALL[:2]
+    Xb, stb = _run_df64(insts, n_rhs, 0.0, 3, True)
+    Xs, sts = _run_df64(insts, n_rhs, 0.0, 3, False)
+    for i in range(len(insts)):
+        for col in range(n_rhs):
+            assert _rel(Xb[i][:, col], Xs[i][:, col]) <= 1e-12
+            assert stb[i][col]["cycles"] == sts[i][col]["cycles"] == 3
+
+
+def test_block_kernels_match_oracle_and_stop_rule(lib, cuda):
+    insts = SMALL[2:4]
+    Xb, stb = _run_df64(insts, 16, 0.0, 2, True)
+    jobs = [(i, dict(inst, n_rhs=16), col, 100 + i, 2) for i, inst in enumerate(insts) for col in (0, 7, 15)]
+    refs = _oracle_many(jobs)
+    for (i, inst, col, seed, _), ref in zip(jobs, refs):
+        assert _rel(Xb[i][:, col], ref) <= 1e-10
+    # relative stop: every right-hand side stops at its own cycle, as one by one
+    Xb, stb = _run_df64(insts, 12, 1e-9, 16, True)
+    Xs, sts = _run_df64(insts, 12, 1e-9, 16, False)
+    for i in range(len(insts)):
+        for col in range(12):
+            assert stb[i][col]["cycles"] == sts[i][col]["cycles"]
+            assert _rel(Xb[i][:, col], Xs[i][:, col]) <= 1e-10
+
+
+def test_block_kernels_redo_breakdown_alone(lib, cuda):
+    """A right-hand side that is an eigenvector breaks down in the first step:
+    the block form hands it to the single-vector kernels (exact result)."""
+    import torch
+
+    from paper_2503_22631_gb300 import BASIS_DF64, F_EXP_NEG, Krylov, apply_batched
+
+    N = 32
+    A = W.poisson2d(N)
+    mode, c, p, q = W.sine_mode_mixture_2d(N, 1, 9)
+    Bn = _rhs_block(A.n, 6, 3)
+    Bn[:, 2] = mode
+    kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=1e-3, m=10, k=2, s=30, seed=1, zeta=8, basis=BASIS_DF64)
+    X, st = apply_batched([kr], [torch.from_numpy(Bn).cuda()], t=[1e-3], tol=0.0, max_cycles=3)
+    x = X[0].cpu().numpy()
+    assert st[0][2]["breakdown"] == 1
+    assert _rel(x[:, 2], TR.sine_mode_exp(N, c, p, q, 1e-3)) <= 1e-12
+    kr1 = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=1e-3, m=10, k=2, s=30, seed=1, zeta=8, basis=BASIS_DF64)
+    x0 = kr1.apply(torch.from_numpy(Bn[:, 0].copy()).cuda(), tol=0.0, max_cycles=3).cpu().numpy()
+    assert _rel(x[:, 0], x0) <= 1e-12
