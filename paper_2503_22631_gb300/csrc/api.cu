@@ -162,6 +162,7 @@ struct krylov_handle {
   int part_cap = 0;                // per-CTA partial slots (8 doubles each)
   long long* rgs_acc = nullptr;    // randomized Gram-Schmidt: exact sketch sums [3][s]
   BlockWs* bk = nullptr;           // block form workspace (allocated on first use)
+  int bk_concurrent = 1;           // instances running concurrently in the current batched call
   int grid_update = 0;             // CTAs of the cycle-end update pass
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
@@ -801,7 +802,7 @@ krylov_status ensure_block_ws(krylov_handle* h, int levels) {
     CK(balloc(b, &b.W, (size_t)(M + 1) * n * BK_NB));
     CK(balloc(b, &b.P[0], n * BK_NB));
     CK(balloc(b, &b.P[1], n * BK_NB));
-    CK(balloc(b, &b.part, (size_t)h->num_sms * 2 * NQ_HOST * BK_NB));
+    CK(balloc(b, &b.part, (size_t)h->num_sms * 8 * NQ_HOST * BK_NB));
     CK(balloc(b, &b.acc, (size_t)(M + 1) * 3 * s * BK_NB));
     CK(balloc(b, &b.E, (size_t)(M + 1) * BK_NB));
     CK(balloc(b, &b.active, (size_t)BK_NB));
@@ -910,8 +911,17 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
   L.acc = b.acc;
   L.E = b.E;
   L.tab = h->sk_tab;
-  L.grid = std::max(1, std::min(h->num_sms * 2, (n + 7) / 8));
+  // grids from the kernels' occupancy (the materialize kernel holds nb-wide
+  // sketch bins in shared memory, the product and update kernels none)
+  // (a full wave each for one instance; two CTAs per SM when several
+  // instances run concurrently and fill the GPU between them)
+  const int part_ctas = h->num_sms * 8;
+  const int per_sm_mat = (h->bk_concurrent > 1) ? 2 : bk_ctas_per_sm(0, bk_mat_smem(h->s, nb));
+  const int per_sm_p = (h->bk_concurrent > 1) ? 2 : bk_ctas_per_sm(1, 0);
+  L.grid = std::max(1, std::min(std::min(part_ctas, h->num_sms * per_sm_mat), (n + 7) / 8));
   L.rows_per_cta = (n + L.grid - 1) / L.grid;
+  L.grid_p = std::max(1, std::min(std::min(part_ctas, h->num_sms * per_sm_p), (n + 7) / 8));
+  L.rows_p = (n + L.grid_p - 1) / L.grid_p;
   L.fx_wb = sketch_word_bits(L.rows_per_cta, 1);
   L.thr = 1e-12;
   cudaEvent_t e0, e1;
@@ -936,6 +946,7 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
     }
   }
   int s_lv = -1, launches = 2;
+  double ms_steps = 0.0, step_bytes = 0.0;
   for (int c = 1; c <= max_cycles; ++c) {
     int n_active = 0;
     for (int r = 0; r < nb; ++r) {
@@ -949,6 +960,7 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
     if (n_active == 0) break;
     CK(cudaMemcpyAsync(b.active, b.h_active, sizeof(int) * nb, cudaMemcpyHostToDevice, s_));
     CK(cudaMemcpyAsync(b.cd.flags, b.h_flags, sizeof(int) * 4 * nb, cudaMemcpyHostToDevice, s_));
+    CK(cudaEventRecord(h->ev[0], s_));
     for (int j = 0; j <= M; ++j) {
       L.j = j;
       L.p_prev = b.P[(j + 1) & 1];
@@ -956,9 +968,19 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
       launch_bk_step(L, j > 0, j < M, s_);
       launches += (j < M) ? 2 : 1;
     }
+    CK(cudaEventRecord(h->ev[1], s_));
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(b.h_flags, b.cd.flags, sizeof(int) * 4 * nb, cudaMemcpyDeviceToHost, s_));
     CK(cudaStreamSynchronize(s_));
+    {
+      float ms_s = 0.f;
+      CK(cudaEventElapsedTime(&ms_s, h->ev[0], h->ev[1]));
+      ms_steps += ms_s;
+      // per step: A once, and per right-hand side the vectors of a single step
+      step_bytes += M * ((double)h->nnz * ((use32 ? 4.0 : 8.0) + 4.0) + 4.0 * (n + 1) +
+                         (double)nb * (model_bytes_step(h, use32) - (double)h->nnz * ((use32 ? 4.0 : 8.0) + 4.0) -
+                                       4.0 * (n + 1)));
+    }
     for (int r = 0; r < nb; ++r) {
       if (!active[r]) continue;
       if (b.h_flags[4 * r + 1] != 0 || (b.h_flags[4 * r + 2] & (ERR_NONFINITE | ERR_SKETCH))) {
@@ -1027,9 +1049,13 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // block-wide figures are reported once, on the block's first right-hand side
   for (int r = 0; r < nb; ++r) {
     st[r].ms_total = ms;
-    st[r].launches = launches;
+    st[r].launches = (r == 0) ? launches : 0;
+    st[r].step_launches = (r == 0) ? launches : 0;
+    st[r].ms_steps = (r == 0) ? ms_steps : 0.0;
+    st[r].step_bytes = (r == 0) ? step_bytes : 0.0;
   }
   return KRYLOV_OK;
 }
@@ -1348,6 +1374,7 @@ krylov_status krylov_apply_batched(krylov_handle* const* hs, int n_inst, int n_r
       if (hs[j] == hs[i]) return KRYLOV_EINVAL;  // a handle is not thread-safe
   }
   std::vector<krylov_status> res((size_t)n_inst, KRYLOV_OK);
+  for (int i = 0; i < n_inst; ++i) hs[i]->bk_concurrent = std::min(n_inst, 16);
   std::atomic<int> next{0};
   auto worker = [&]() {
     for (int i = next.fetch_add(1); i < n_inst; i = next.fetch_add(1))

@@ -206,22 +206,39 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_spmv_kernel(const BlockLaunch
   for (int q = 0; q < KW; ++q) Wd[q] = B.W + (int64_t)(dlo + (q < nd ? q : 0)) * B.slot;
   const AT* val = static_cast<const AT*>(B.val);
   ffacc pi[2], dots[KW][2];
-  const int r0 = blockIdx.x * B.rows_per_cta, r1 = min(B.n, r0 + B.rows_per_cta);
+  const int r0 = blockIdx.x * B.rows_p, r1 = min(B.n, r0 + B.rows_p);
   for (int i = r0 + wid; i < r1; i += BK_WARPS) {
     const int eb = __ldg(B.rp + i), ee = __ldg(B.rp + i + 1);
     ffacc acc[2];
-    for (int e = eb; e < ee; ++e) {
-      const int c = __ldg(B.ci + e);
-      const AT a = __ldg(val + e);
-      const float2* wc = Wj + (int64_t)c * nb;
+    // nonzeros in batches of 4: indices and values first, then the gathers,
+    // then the sums (storage order)
+    for (int e0 = eb; e0 < ee; e0 += 4) {
+      int cc[4];
+      AT av[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = lane + 32 * h;
-        if (r < nb) {
-          const float2 pe = prod_pe(a, ldf(wc + r));
-          acc[h].add_pe(pe.x, pe.y);
+      for (int u = 0; u < 4; ++u)
+        if (e0 + u < ee) {
+          cc[u] = __ldg(B.ci + e0 + u);
+          av[u] = __ldg(val + e0 + u);
         }
-      }
+      float2 wv[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e0 + u < ee) {
+          const float2* wc = Wj + (int64_t)cc[u] * nb;
+          if (lane < nb) wv[u][0] = wc[lane];
+          if (lane + 32 < nb) wv[u][1] = wc[lane + 32];
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e0 + u < ee) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (lane + 32 * h < nb) {
+              const float2 pe = prod_pe(av[u], ff{wv[u][h].x, wv[u][h].y});
+              acc[h].add_pe(pe.x, pe.y);
+            }
+        }
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -343,7 +360,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
   for (int r = threadIdx.x; r < nb; r += blockDim.x) s_tinv[r] = ff_from_double(offset_sd(sd, B.bs, r).zg[2 * M]);
   __syncthreads();
   double ay[2] = {0.0, 0.0}, ax[2] = {0.0, 0.0}, av[2] = {0.0, 0.0};
-  const int r0 = blockIdx.x * B.rows_per_cta, r1 = min(B.n, r0 + B.rows_per_cta);
+  const int r0 = blockIdx.x * B.rows_p, r1 = min(B.n, r0 + B.rows_p);
   for (int i = r0 + wid; i < r1; i += BK_WARPS) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -408,6 +425,15 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
 
 size_t bk_mat_smem(int s, int nb) { return (size_t)NWB * s * nb * sizeof(int); }
 
+int bk_ctas_per_sm(int kernel, size_t smem) {
+  const void* k = (kernel == 0) ? (const void*)bk_mat_kernel<true, 2>
+                  : (kernel == 1) ? (const void*)bk_spmv_kernel<float2, 2> : (const void*)bk_update_kernel;
+  raise_smem_limit(k, smem);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, STEP_THREADS, smem);
+  return std::max(1, b);
+}
+
 void launch_bk_norm_start(const BlockLaunch& B, const double* b, int64_t ldb, cudaStream_t st) {
   bk_norm_kernel<<<B.grid, STEP_THREADS, 0, st>>>(B, b, ldb);
   const int64_t total = (int64_t)B.n * B.nb;
@@ -428,11 +454,11 @@ void launch_bk_step(const BlockLaunch& B, int mat, int spmv, cudaStream_t st) {
   }
   if (spmv) {
     if (B.val_f32) {
-      if (B.k <= 2) bk_spmv_kernel<float, 2><<<B.grid, STEP_THREADS, 0, st>>>(B);
-      else bk_spmv_kernel<float, MAX_WINDOW><<<B.grid, STEP_THREADS, 0, st>>>(B);
+      if (B.k <= 2) bk_spmv_kernel<float, 2><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
+      else bk_spmv_kernel<float, MAX_WINDOW><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
     } else {
-      if (B.k <= 2) bk_spmv_kernel<float2, 2><<<B.grid, STEP_THREADS, 0, st>>>(B);
-      else bk_spmv_kernel<float2, MAX_WINDOW><<<B.grid, STEP_THREADS, 0, st>>>(B);
+      if (B.k <= 2) bk_spmv_kernel<float2, 2><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
+      else bk_spmv_kernel<float2, MAX_WINDOW><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
     }
   }
 }
@@ -446,7 +472,7 @@ void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int h
                       const int* active, cudaStream_t st) {
   const size_t smem = 2 * (size_t)m_eff * B.nb * sizeof(ff);
   raise_smem_limit((const void*)bk_update_kernel, smem);
-  bk_update_kernel<<<B.grid, STEP_THREADS, smem, st>>>(B, sd, m_eff, has_next, x, ldx, active);
+  bk_update_kernel<<<B.grid_p, STEP_THREADS, smem, st>>>(B, sd, m_eff, has_next, x, ldx, active);
 }
 
 }  // namespace krylov

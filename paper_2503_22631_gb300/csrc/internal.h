@@ -106,7 +106,8 @@ struct BlockLaunch {
   long long* acc;       // [m+1][3][s][64] exact sketch sums
   int* E;               // [m+1][64] fixed-point exponents of the sketch words
   SketchTable tab;
-  int grid, rows_per_cta, fx_wb;
+  int grid, rows_per_cta, fx_wb;   // materialize/sketch kernel (and norms)
+  int grid_p, rows_p;              // product and update kernels
   double thr;
 };
 
@@ -235,6 +236,7 @@ void launch_z_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, 
 
 // block form (block_kernels.cu)
 size_t bk_mat_smem(int s, int nb);
+int bk_ctas_per_sm(int kernel, size_t smem);  // 0: materialize/sketch, 1: product, 2: update
 void launch_bk_norm_start(const BlockLaunch& B, const double* b, int64_t ldb, cudaStream_t st);
 void launch_bk_step(const BlockLaunch& B, int mat, int spmv, cudaStream_t st);
 void launch_bk_sketch_fin(const BlockLaunch& B, const SmallDev& sd, int ncols, cudaStream_t st);
