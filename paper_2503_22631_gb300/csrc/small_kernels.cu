@@ -28,6 +28,12 @@ namespace krylov {
 namespace {
 
 constexpr int SMALL_THREADS = 256;
+// the whitening QR works in shared memory when s x (m+1) doubles fit in this
+constexpr int WHITEN_SMEM_DOUBLES = 20 * 1024;  // 160 KB
+size_t whiten_smem(int s, int nc) {
+  const size_t d = (size_t)s * nc;
+  return d <= (size_t)WHITEN_SMEM_DOUBLES ? d * sizeof(double) : 0;
+}
 
 __device__ __forceinline__ double& Tat(double* Tw, int s, int a, int b) { return Tw[(size_t)b * s + a]; }
 
@@ -38,11 +44,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
   sd = offset_sd(sd, bs, blockIdx.x);
   cd = offset_cd(cd, bs, blockIdx.x);
   scratch += bs.S0 * blockIdx.x;
+  extern __shared__ double sA[];  // the sketched basis in shared memory when it fits
   __shared__ double red[32];
   __shared__ double sh_beta_h, sh_alpha;
   __shared__ double diag[1024];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
-  double* A = sd.Tw;  // s x nc, leading dimension s
+  const bool in_smem = (size_t)s * nc <= (size_t)WHITEN_SMEM_DOUBLES;
+  double* A = in_smem ? sA : sd.Tw;  // s x nc, leading dimension s
 
   for (size_t e = tid; e < (size_t)s * nc; e += blockDim.x) A[e] = sd.U[e];
   __syncthreads();
@@ -85,6 +93,9 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
   __syncthreads();
   for (int a = tid; a < nc; a += blockDim.x) Tat(A, s, a, a) = fabs(diag[a]);
   __syncthreads();
+  if (in_smem) {  // T (upper nc x nc of A) stays readable in global memory
+    for (size_t e = tid; e < (size_t)s * nc; e += blockDim.x) sd.Tw[e] = A[e];
+  }
 
   // ---- T_m^{-1} (upper triangular), one column per thread ----
   double* Ti = sd.Tinv;  // me x me, leading dimension M
@@ -233,13 +244,17 @@ __global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restr
   const int r = e % M, col = e / M;
   const size_t MM = (size_t)M * M;
   const size_t rowa = (size_t)a * (a + 1) / 2;
-  double acc = 0.0;
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};  // four independent chains
   for (int l = j; l <= a; ++l) {
     const double* L = Gi + (rowa + l) * MM;                      // G[a][l]
     const double* Rb = Gi + ((size_t)l * (l + 1) / 2 + j) * MM;  // G[l][j]
-    for (int p = 0; p < M; ++p) acc = fma(L[(size_t)p * M + r], Rb[(size_t)col * M + p], acc);
+    int p = 0;
+    for (; p + 3 < M; p += 4)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a4[u] = fma(L[(size_t)(p + u) * M + r], Rb[(size_t)col * M + p + u], a4[u]);
+    for (; p < M; ++p) a4[0] = fma(L[(size_t)p * M + r], Rb[(size_t)col * M + p], a4[0]);
   }
-  Go[(rowa + j) * MM + e] = acc;
+  Go[(rowa + j) * MM + e] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
 }
 
 // f(z) = 1/z: y_a = X_a^{-1} rhs, rhs = e_1 (a = 0) or -gamma_{a-1} y_{a-1}[M-1] e_1
@@ -370,12 +385,17 @@ __global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc, const B
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff, int has_next,
                    int cycle, double t, cudaStream_t st) {
   // scratch for T_m R_m: reuse the Horner buffer area (not in use at this point)
-  whiten_kernel<<<1, SMALL_THREADS, 0, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, BatchStride{});
+  const size_t smem = whiten_smem(s, ncols);
+  raise_smem_limit((const void*)whiten_kernel, smem);
+  whiten_kernel<<<1, SMALL_THREADS, smem, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0,
+                                                BatchStride{});
 }
 
 void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
                            int ncols, int m_eff, int has_next, int cycle, double t, cudaStream_t st) {
-  whiten_kernel<<<nb, SMALL_THREADS, 0, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, bs);
+  const size_t smem = whiten_smem(s, ncols);
+  raise_smem_limit((const void*)whiten_kernel, smem);
+  whiten_kernel<<<nb, SMALL_THREADS, smem, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, bs);
 }
 
 void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
