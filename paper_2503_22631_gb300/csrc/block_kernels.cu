@@ -13,6 +13,7 @@
 // coefficients, R, flags) live in the single-vector layout repeated nb times
 // (BatchStride), so the small-problem kernels run unchanged per problem.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "internal.h"
@@ -349,12 +350,26 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nb = B.nb, M = B.m;
-  ff* zf = reinterpret_cast<ff*>(smem);  // [m_eff][nb]: z_r
+  ff* zf = reinterpret_cast<ff*>(smem);  // [m_eff][nb]: z_r scaled by 2^-ez_r
   ff* gf = zf + (size_t)m_eff * nb;     // [m_eff][nb]: -g_r
+  __shared__ int s_ez[BK_MAXNB];
+  // each z_r enters the float pairs scaled so that max |z_r| is in [1, 2) (a
+  // tiny update must not underflow in float); sums are scaled back in float64
+  for (int r = threadIdx.x; r < nb; r += blockDim.x) s_ez[r] = INT_MIN;
+  __syncthreads();
+  for (int e = threadIdx.x; e < m_eff * nb; e += blockDim.x) {
+    const int q = e / nb, r = e % nb;
+    const double z = offset_sd(sd, B.bs, r).zg[q];
+    if (z != 0.0 && isfinite(z)) atomicMax(&s_ez[r], ilogb(z));
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nb; r += blockDim.x)
+    if (s_ez[r] == INT_MIN) s_ez[r] = 0;
+  __syncthreads();
   for (int e = threadIdx.x; e < m_eff * nb; e += blockDim.x) {
     const int q = e / nb, r = e % nb;
     const SmallDev d = offset_sd(sd, B.bs, r);
-    zf[e] = ff_from_double(d.zg[q]);
+    zf[e] = ff_from_double(ldexp(d.zg[q], -s_ez[r]));
     gf[e] = ff_neg(ff_from_double(d.zg[M + q]));
   }
   for (int r = threadIdx.x; r < nb; r += blockDim.x) s_tinv[r] = ff_from_double(offset_sd(sd, B.bs, r).zg[2 * M]);
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
           }
       }
       const ff yy = y.result();
-      const double yd = (double)yy.hi + (double)yy.lo;
+      const double yd = ldexp((double)yy.hi + (double)yy.lo, s_ez[r]);
       double* xp = x + (int64_t)i * ldx + r;
       const double xn = active[r] ? *xp + yd : *xp;
       *xp = xn;

@@ -14,6 +14,7 @@
 //                         generator (S is likewise generated once per run and
 //                         stored in App. A)
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "internal.h"
@@ -103,11 +104,20 @@ __global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw
   __shared__ double zs[256], gs[256];
   __shared__ ff zf[256], gf[256];
   __shared__ double red[32];
-  __shared__ int s_last;
+  __shared__ int s_last, s_ez;
+  // z enters the float pairs scaled by 2^-ez (max |z| in [1, 2)): a tiny
+  // update (z ~ 1e-50 for a very stiff first cycle) must not underflow in
+  // float; the sum is scaled back in float64
+  if (threadIdx.x == 0) s_ez = INT_MIN;
+  __syncthreads();
+  for (int q = threadIdx.x; q < m_eff; q += blockDim.x)
+    if (zg[q] != 0.0 && isfinite(zg[q])) atomicMax(&s_ez, ilogb(zg[q]));
+  __syncthreads();
+  const int ez = (s_ez == INT_MIN) ? 0 : s_ez;
   for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
     zs[q] = zg[q];
     gs[q] = zg[m + q];
-    zf[q] = ff_from_double(zg[q]);
+    zf[q] = ff_from_double(ldexp(zg[q], -ez));
     gf[q] = ff_neg(ff_from_double(zg[m + q]));
   }
   const double tau_inv = zg[2 * m];
@@ -148,7 +158,7 @@ __global__ void __launch_bounds__(STEP_THREADS) update_kernel(VT* W, int64_t ldw
           }
       }
       const ff ry = fy.result(), rv = fv.result();
-      y = (double)ry.hi + (double)ry.lo;
+      y = ldexp((double)ry.hi + (double)ry.lo, ez);
       v = (double)rv.hi + (double)rv.lo;
     }
     const double xn = x[i] + y;
@@ -191,9 +201,16 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
                                                                  double* part, CycleDev cd, int rows_per_cta) {
   __shared__ ff zs[256], gs[256];
   __shared__ double red[32];
-  __shared__ int s_last;
+  __shared__ int s_last, s_ez;
+  // z scaled by 2^-ez in the float pairs (see update_kernel), scaled back in float64
+  if (threadIdx.x == 0) s_ez = INT_MIN;
+  __syncthreads();
+  for (int q = threadIdx.x; q < m_eff; q += blockDim.x)
+    if (zg[q] != 0.0 && isfinite(zg[q])) atomicMax(&s_ez, ilogb(zg[q]));
+  __syncthreads();
+  const int ez = (s_ez == INT_MIN) ? 0 : s_ez;
   for (int q = threadIdx.x; q < m_eff; q += blockDim.x) {
-    zs[q] = ff_from_double(zg[q]);
+    zs[q] = ff_from_double(ldexp(zg[q], -ez));
     gs[q] = ff_neg(ff_from_double(zg[m + q]));
   }
   const ff tau_inv = ff_from_double(zg[2 * m]);
@@ -223,14 +240,14 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_update_kernel(float2* W, int6
         }
     }
     const ff yy = y.result();
-    const double xn = x[i] + ((double)yy.hi + (double)yy.lo);
+    const double yd = ldexp((double)yy.hi + (double)yy.lo, ez);
+    const double xn = x[i] + yd;
     x[i] = xn;
     if (has_next) {
       const ff vn = ff_mul(v.result(), tau_inv);
       W[i] = make_float2(vn.hi, vn.lo);
       av = fma((double)vn.hi, (double)vn.hi, av);
     }
-    const double yd = (double)yy.hi + (double)yy.lo;
     ay = fma(yd, yd, ay);
     ax = fma(xn, xn, ax);
   }
