@@ -257,6 +257,46 @@ __global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restr
   Go[(rowa + j) * MM + e] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
 }
 
+// The same squaring with the sum over l spread over the grid: one CTA row per
+// (j, l) pair (j <= l <= a) forms the partial product G[a][l] G[l][j] into
+// P[pair]; exp_square_reduce_kernel then sums the pairs of each j in order of
+// l (deterministic).  Every pair is one m x m product, so the grid is
+// balanced and the FP64 work is spread over (a+1)(a+2)/2 CTA rows instead of
+// a+1.
+__global__ void exp_square_pairs_kernel(const double* __restrict__ Gi, double* __restrict__ P, int M, int a) {
+  int k = blockIdx.y, j = 0;
+  while (k > a - j) {  // pair index -> (j, l): pairs of j are l = j..a
+    k -= a - j + 1;
+    ++j;
+  }
+  const int l = j + k;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * M) return;
+  const int r = e % M, col = e / M;
+  const size_t MM = (size_t)M * M;
+  const double* L = Gi + ((size_t)a * (a + 1) / 2 + l) * MM;   // G[a][l]
+  const double* Rb = Gi + ((size_t)l * (l + 1) / 2 + j) * MM;  // G[l][j]
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};
+  int p = 0;
+  for (; p + 3 < M; p += 4)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a4[u] = fma(L[(size_t)(p + u) * M + r], Rb[(size_t)col * M + p + u], a4[u]);
+  for (; p < M; ++p) a4[0] = fma(L[(size_t)p * M + r], Rb[(size_t)col * M + p], a4[0]);
+  P[(size_t)blockIdx.y * MM + e] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+}
+
+__global__ void exp_square_reduce_kernel(const double* __restrict__ P, double* __restrict__ Go, int M, int a) {
+  const int j = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > a || e >= M * M) return;
+  const size_t MM = (size_t)M * M;
+  size_t pair = 0;  // first pair of j
+  for (int jj = 0; jj < j; ++jj) pair += (size_t)(a - jj + 1);
+  double acc = 0.0;
+  for (int l = j; l <= a; ++l) acc += P[(pair + (l - j)) * MM + e];
+  Go[((size_t)a * (a + 1) / 2 + j) * MM + e] = acc;
+}
+
 // f(z) = 1/z: y_a = X_a^{-1} rhs, rhs = e_1 (a = 0) or -gamma_{a-1} y_{a-1}[M-1] e_1
 // (block forward substitution on the block lower-bidiagonal H).  X_a is me x me
 // (me < M only in a cycle that ended in breakdown).  LU with partial pivoting in
@@ -430,11 +470,15 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double s
   exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0, 0, 0, 0);
 }
 
-void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st) {
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, double* pairs,
+                       cudaStream_t st) {
   const int MM = m * m;
-  dim3 g((MM + 127) / 128, a + 1);
-  exp_square_kernel<<<g, 128, 0, st>>>(sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride,
-                                      m, a, 0);
+  const int npairs = (a + 1) * (a + 2) / 2;
+  exp_square_pairs_kernel<<<dim3((MM + 127) / 128, npairs), 128, 0, st>>>(sd.G + (size_t)level * level_stride, pairs,
+                                                                          m, a);
+  exp_square_reduce_kernel<<<dim3((MM + 127) / 128, a + 1), 128, 0, st>>>(pairs,
+                                                                         sd.G + (size_t)(level + 1) * level_stride, m,
+                                                                         a);
 }
 
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
