@@ -649,7 +649,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       stats.launches += 1;
     } else {
       launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
-      launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->f.t, st);
+      launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->k, h->f.t, st);
       stats.launches += 2;
     }
     const int a = c - 1;
@@ -991,7 +991,7 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
       }
     }
     launch_bk_sketch_fin(L, b.sd, M + 1, s_);
-    launch_whiten_batched(b.sd, b.cd, b.bs, nb, h->s, M, M + 1, M, 1, c, h->f.t, s_);
+    launch_whiten_batched(b.sd, b.cd, b.bs, nb, h->s, M, M + 1, M, 1, c, h->k, h->f.t, s_);
     CK(cudaMemcpyAsync(b.h_scal + 8 * BK_NB, b.sd.misc, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s_));
     CK(cudaStreamSynchronize(s_));
     launches += 2;

@@ -223,10 +223,11 @@ __host__ __device__ inline CycleDev offset_cd(CycleDev cd, const BatchStride& b,
   return cd;
 }
 
-// Batched small problem (block form): one problem per CTA (whiten, z) or per
-// grid z-slice (exp), problems r = 0..nb-1 at offsets r * stride.
+// Batched small problem (block form): one problem per cluster (whiten), per
+// CTA (z) or per grid z-slice (exp), problems r = 0..nb-1 at offsets r * stride.
+// kw: window of the truncated recurrence (band of R_m).
 void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
-                           int ncols, int m_eff, int has_next, int cycle, double t, cudaStream_t st);
+                           int ncols, int m_eff, int has_next, int cycle, int kw, double t, cudaStream_t st);
 void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
                                double scale, int first, int src, double* dst0, int dst_in_g, cudaStream_t st);
 void launch_exp_square_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int level,
@@ -244,7 +245,7 @@ void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int h
                       const int* active, cudaStream_t st);
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
-                   int has_next, int cycle, double t, cudaStream_t st);
+                   int has_next, int cycle, int kw, double t, cudaStream_t st);
 void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first,
                             int last, int src, double* dst, cudaStream_t st);
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, double* pairs,

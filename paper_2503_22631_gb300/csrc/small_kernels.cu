@@ -19,13 +19,20 @@
 // inv_block       f(z) = 1/z: block forward substitution for H_{cm}^{-1} e_1,
 //                 which needs only the last entry of the previous block.
 // z_kernel        z = beta T_m^{-1} F[(c-1)m+1 : cm, 1] (Algorithm 2, update y).
+#include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 #include "kernels.cuh"
 
 namespace krylov {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int SMALL_THREADS = 256;
 // the whitening QR works in shared memory when s x (m+1) doubles fit in this
@@ -37,6 +44,42 @@ size_t whiten_smem(int s, int nc) {
 
 __device__ __forceinline__ double& Tat(double* Tw, int s, int a, int b) { return Tw[(size_t)b * s + a]; }
 
+// Small dense products on GB300 are bound by the FP64 pipe (about two FMAs
+// per clock per SM): each FP64 warp instruction occupies its SM sub-partition
+// for many cycles, so a product is spread over as many SMs as possible and
+// the dependent chain of each output is kept short.  One CTA forms 32
+// consecutive entries e = col m + r of L R (m x m, column-major); the sum over
+// p is cut into KS_WARPS contiguous ranges, one per warp, and warp 0 adds the
+// partial sums in warp order (a fixed order: the result is deterministic).
+constexpr int KS_WARPS = 4;
+constexpr int KS_THREADS = 32 * KS_WARPS;
+
+// Every thread of the CTA calls this (it holds a barrier); the sum is
+// returned in warp 0, other warps get 0.
+__device__ __forceinline__ double ks_product(const double* __restrict__ L, const double* __restrict__ R, int M,
+                                             int e, double (*red)[32]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int chunk = (M + KS_WARPS - 1) / KS_WARPS;
+  const int p0 = w * chunk, p1 = min(M, p0 + chunk);
+  double acc = 0.0;
+  if (e < M * M) {
+    const int r = e % M, col = e / M;
+    const double* Lr = L + r;
+    const double* Rc = R + (size_t)col * M;
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) acc = fma(Lr[(size_t)p * M], Rc[p], acc);
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  double sum = 0.0;
+  if (w == 0) {
+    sum = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < KS_WARPS; ++q) sum += red[q][lane];
+  }
+  return sum;
+}
+
 __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, CycleDev cd, int s, int M,
                                                                int nc, int me, int has_next, int cycle,
                                                                double t, double* scratch, const BatchStride bs) {
@@ -46,7 +89,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
   scratch += bs.S0 * blockIdx.x;
   extern __shared__ double sA[];  // the sketched basis in shared memory when it fits
   __shared__ double red[32];
-  __shared__ double sh_beta_h, sh_alpha;
+  __shared__ double sh_beta_h;
   __shared__ double diag[1024];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
   const bool in_smem = (size_t)s * nc <= (size_t)WHITEN_SMEM_DOUBLES;
@@ -56,11 +99,22 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
   __syncthreads();
 
   // ---- Householder QR, T only ----
-  for (int jj = 0; jj < nc; ++jj) {
+  // Two barriers per column: the reflector of column jj is formed by thread 0
+  // from the squared norm that the warp updating column jj (in the previous
+  // pass) left in sh_nrm2; the trailing update then applies it, and the warp
+  // that updates column jj + 1 also forms that column's squared norm below
+  // the diagonal for the next pass.
+  __shared__ double sh_nrm2;
+  {
     double acc = 0.0;
-    for (int r = jj + tid; r < s; r += blockDim.x) acc = fma(A[(size_t)jj * s + r], A[(size_t)jj * s + r], acc);
-    const double nrm2 = block_sum(acc, red);
+    for (int r = tid; r < s; r += blockDim.x) acc = fma(A[r], A[r], acc);
+    const double v = block_sum(acc, red);
+    if (tid == 0) sh_nrm2 = v;
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nc; ++jj) {
     if (tid == 0) {
+      const double nrm2 = sh_nrm2;
       const double x0 = A[(size_t)jj * s + jj];
       const double nx = sqrt(nrm2);
       const double alpha = (x0 >= 0.0) ? -nx : nx;
@@ -68,7 +122,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
       const double vn2 = nrm2 - x0 * x0 + v0 * v0;
       A[(size_t)jj * s + jj] = v0;
       sh_beta_h = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
-      sh_alpha = alpha;
+      diag[jj] = alpha;
     }
     __syncthreads();
     const double bh = sh_beta_h;
@@ -76,10 +130,19 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
       double d = 0.0;
       for (int r = jj + lane; r < s; r += 32) d = fma(A[(size_t)jj * s + r], A[(size_t)l * s + r], d);
       d = warp_sum(d) * bh;
-      for (int r = jj + lane; r < s; r += 32) A[(size_t)l * s + r] = fma(-d, A[(size_t)jj * s + r], A[(size_t)l * s + r]);
+      if (l == jj + 1) {  // also the squared norm of the updated column below row jj
+        double q = 0.0;
+        for (int r = jj + lane; r < s; r += 32) {
+          const double u = fma(-d, A[(size_t)jj * s + r], A[(size_t)l * s + r]);
+          A[(size_t)l * s + r] = u;
+          if (r > jj) q = fma(u, u, q);
+        }
+        q = warp_sum(q);
+        if (lane == 0) sh_nrm2 = q;
+      } else {
+        for (int r = jj + lane; r < s; r += 32) A[(size_t)l * s + r] = fma(-d, A[(size_t)jj * s + r], A[(size_t)l * s + r]);
+      }
     }
-    __syncthreads();
-    if (tid == 0) diag[jj] = sh_alpha;
     __syncthreads();
   }
   // sign fix: row a of T times sign(diag[a]); write diagonal
@@ -200,36 +263,294 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
   }
 }
 
+// ---- whitening on a thread-block cluster ----
+// The whitening is a chain of nc Householder reflectors whose FP64 work
+// (each FP64 warp instruction holds its SM sub-partition for many cycles on
+// this part) overwhelms one SM.  Here the columns of U are dealt round-robin
+// to the CL CTAs of a cluster (column l lives in the shared memory of CTA
+// l mod CL); reflector jj is formed by the warp that owns column jj, every
+// CTA reads it from the owner's shared memory (distributed shared memory)
+// and applies it to its own columns, one cluster barrier per column.  The
+// warp that updates column jj + 1 also forms its squared norm below the
+// diagonal and the next reflector, so the chain between two barriers is one
+// column update.  Then every CTA gathers T (signs fixed so that diag(T) > 0)
+// and each warp takes one column b: the column sweep of T x = e_b gives
+// column b of T_m^{-1}, and column b of X = T_m (R_m T_m^{-1}) + (r / T_mm)
+// t e_m^T is formed from it with the band of R_m (rows p - 1 .. p + k - 1 of
+// column p hold the only nonzeros of the truncated recurrence); the extra
+// column b = me solves T_m g = t.
+constexpr int WC_THREADS = 256;
+constexpr size_t WC_SMEM_MAX = 200 * 1024;
+
+size_t whiten_cluster_smem(int s, int nc, int cl) {
+  const size_t ncl = (size_t)((nc + cl - 1) / cl);
+  return ((size_t)s * ncl + 4 * (size_t)nc + (size_t)nc * nc + (size_t)(WC_THREADS / 32) * 2 * nc) * sizeof(double);
+}
+
+// Householder reflector of column col below row jj: v = x - alpha e_1 written
+// over the column (row jj holds v_0), beta = 2 / (v^T v), alpha = -sign(x_0) |x|.
+__device__ __forceinline__ void wc_reflector(double* col, int jj, double nrm2, double* sbeta, double* salpha) {
+  const double x0 = col[jj];
+  const double nx = sqrt(nrm2);
+  const double alpha = (x0 >= 0.0) ? -nx : nx;
+  const double v0 = x0 - alpha;
+  const double vn2 = nrm2 - x0 * x0 + v0 * v0;
+  col[jj] = v0;
+  sbeta[jj] = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+  salpha[jj] = alpha;
+}
+
+// Back substitution T[0..top][0..top] x = rhs by columns (rhs in x on entry):
+// x_l = x_l / T_ll, then x_a -= T_al x_l for every a < l (lanes over a).
+__device__ __forceinline__ void wc_sweep(double* x, const double* sT, int ldt, const double* dinv, int top,
+                                         int lane) {
+  for (int l = top; l >= 0; --l) {
+    const double xl = x[l] * dinv[l];
+    __syncwarp();
+    for (int a = lane; a < l; a += 32) x[a] = fma(-sT[(size_t)l * ldt + a], xl, x[a]);
+    if (lane == 0) x[l] = xl;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(WC_THREADS) whiten_cluster_kernel(SmallDev sd, CycleDev cd, int s, int M, int nc,
+                                                                    int me, int has_next, int cycle, int kw,
+                                                                    double t, const BatchStride bs) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int prob = (int)(blockIdx.x / (unsigned)CL);  // problem of a batch (one cluster each)
+  sd = offset_sd(sd, bs, prob);
+  cd = offset_cd(cd, bs, prob);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+  const int ncl = (nc + CL - 1) / CL;
+  extern __shared__ double wsm[];
+  double* Aloc = wsm;                      // s x ncl: slot q holds column q CL + rank
+  double* sbeta = Aloc + (size_t)s * ncl;  // [nc] reflector scalars of own columns
+  double* salpha = sbeta + nc;             // [nc] alpha of own columns
+  double* diag = salpha + nc;              // [nc] alpha of every column
+  double* dinv = diag + nc;                // [nc] 1 / T_aa
+  double* sT = dinv + nc;                  // nc x nc, T (upper triangle, leading dimension nc)
+  double* xw = sT + (size_t)nc * nc;       // per warp: x [nc], z [nc]
+  __shared__ double wmax[3][WC_THREADS / 32];
+  __shared__ double cta_max[3];
+
+  for (int q = 0; q < ncl; ++q) {
+    const int l = q * CL + rank;
+    if (l >= nc) break;
+    for (int r = tid; r < s; r += blockDim.x) Aloc[(size_t)q * s + r] = sd.U[(size_t)l * s + r];
+  }
+  __syncthreads();
+  if (rank == 0 && wid == 0) {
+    double acc = 0.0;
+    for (int r = lane; r < s; r += 32) acc = fma(Aloc[r], Aloc[r], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) wc_reflector(Aloc, 0, acc, sbeta, salpha);
+  }
+  // ---- Householder QR, one reflector per cluster barrier ----
+  for (int jj = 0; jj < nc; ++jj) {
+    cluster.sync();  // reflector jj is formed (and visible) in CTA jj mod CL
+    const int o = jj % CL;
+    const double* v = cluster.map_shared_rank(Aloc, o) + (size_t)(jj / CL) * s;
+    const double beta = cluster.map_shared_rank(sbeta, o)[jj];
+    const int q0 = (jj + 1 > rank) ? (jj + 1 - rank + CL - 1) / CL : 0;  // first own column after jj
+    for (int q = q0 + wid; q < ncl; q += nwarp) {
+      const int l = q * CL + rank;
+      if (l >= nc) break;
+      double* u = Aloc + (size_t)q * s;
+      double d = 0.0;
+      for (int r = jj + lane; r < s; r += 32) d = fma(v[r], u[r], d);
+      d = warp_sum(d) * beta;
+      if (l == jj + 1) {  // the next column: its norm below row jj and its reflector
+        double nq = 0.0;
+        for (int r = jj + lane; r < s; r += 32) {
+          const double x = fma(-d, v[r], u[r]);
+          u[r] = x;
+          if (r > jj) nq = fma(x, x, nq);
+        }
+        nq = warp_sum(nq);
+        __syncwarp();
+        if (lane == 0) wc_reflector(u, l, nq, sbeta, salpha);
+      } else {
+        for (int r = jj + lane; r < s; r += 32) u[r] = fma(-d, v[r], u[r]);
+      }
+    }
+  }
+  // ---- T with diag(T) > 0: gathered by every CTA; own columns to global ----
+  for (int a = tid; a < nc; a += blockDim.x) {
+    const double al = cluster.map_shared_rank(salpha, a % CL)[a];
+    diag[a] = al;
+    dinv[a] = 1.0 / fabs(al);
+  }
+  __syncthreads();
+  for (size_t e = tid; e < (size_t)nc * nc; e += blockDim.x) {
+    const int a = (int)(e % nc), b = (int)(e / nc);
+    double x = 0.0;
+    if (a < b) {
+      x = cluster.map_shared_rank(Aloc, b % CL)[(size_t)(b / CL) * s + a];
+      if (diag[a] < 0.0) x = -x;
+    } else if (a == b) {
+      x = fabs(diag[a]);
+    }
+    sT[e] = x;
+  }
+  for (int q = 0; q < ncl; ++q) {
+    const int l = q * CL + rank;
+    if (l >= nc) break;
+    for (int r = tid; r < s; r += blockDim.x) {
+      double x = Aloc[(size_t)q * s + r];
+      if (r < l) x = (diag[r] < 0.0) ? -x : x;
+      else if (r == l) x = fabs(diag[l]);
+      sd.Tw[(size_t)l * s + r] = x;
+    }
+  }
+  __syncthreads();
+
+  // ---- per column b: T_m^{-1} e_b, X e_b, norms; b = me: g = T_m^{-1} t ----
+  const int ldr = M + 1;
+  const double r_next = has_next ? cd.R[(size_t)(me - 1) * ldr + me] : 0.0;
+  const double rt = has_next ? r_next / sT[(size_t)(me - 1) * nc + me - 1] : 0.0;
+  double* X = sd.Xblk + (size_t)(cycle - 1) * M * M;
+  double* x = xw + (size_t)wid * 2 * nc;
+  double* z = x + nc;
+  double cmax = 0.0, tmax = 0.0, timax = 0.0;
+  const int ntask = max(M, me + 1);
+  for (int b = rank * nwarp + wid; b < ntask; b += CL * nwarp) {
+    if (b < me) {
+      for (int a = lane; a <= b; a += 32) x[a] = (a == b) ? 1.0 : 0.0;
+      __syncwarp();
+      wc_sweep(x, sT, nc, dinv, b, lane);
+      double ci = 0.0, ct = 0.0;
+      for (int a = lane; a < me; a += 32) {
+        const double y = (a <= b) ? x[a] : 0.0;
+        sd.Tinv[(size_t)b * M + a] = y;
+        ci += fabs(y);
+        if (a <= b) ct += fabs(sT[(size_t)b * nc + a]);
+      }
+      ci = warp_sum(ci);
+      ct = warp_sum(ct);
+      timax = fmax(timax, ci);
+      tmax = fmax(tmax, ct);
+      // z = R_m y (y = x, zero below row b), then X e_b = T_m z (+ the rank-one term)
+      for (int l = lane; l < me; l += 32) {
+        const int p0 = max(l - 1, 0), p1 = min(min(l + kw - 1, b), me - 1);
+        double acc = 0.0;
+        for (int p = p0; p <= p1; ++p) acc = fma(cd.R[(size_t)p * ldr + l], x[p], acc);
+        z[l] = acc;
+      }
+      __syncwarp();
+      double cs = 0.0;
+      for (int a = lane; a < M; a += 32) {
+        double acc = 0.0;
+        if (a < me) {
+          for (int l = a; l < me; ++l) acc = fma(sT[(size_t)l * nc + a], z[l], acc);
+          if (b == me - 1 && has_next) acc = fma(rt, sT[(size_t)me * nc + a], acc);
+        }
+        X[(size_t)b * M + a] = acc;
+        cs += fabs(acc);
+      }
+      cmax = fmax(cmax, warp_sum(cs));
+      __syncwarp();
+    } else {
+      if (b < M)
+        for (int a = lane; a < M; a += 32) X[(size_t)b * M + a] = 0.0;
+      if (b == me) {
+        if (has_next) {
+          for (int a = lane; a < me; a += 32) x[a] = sT[(size_t)me * nc + a];
+          __syncwarp();
+          wc_sweep(x, sT, nc, dinv, me - 1, lane);
+        }
+        for (int a = lane; a < me; a += 32) sd.zg[M + a] = has_next ? x[a] : 0.0;
+        __syncwarp();
+      }
+    }
+  }
+  if (lane == 0) {
+    wmax[0][wid] = cmax;
+    wmax[1][wid] = tmax;
+    wmax[2][wid] = timax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    for (int w = 0; w < nwarp; ++w) {
+      c0 = fmax(c0, wmax[0][w]);
+      c1 = fmax(c1, wmax[1][w]);
+      c2 = fmax(c2, wmax[2][w]);
+    }
+    cta_max[0] = c0;
+    cta_max[1] = c1;
+    cta_max[2] = c2;
+  }
+  cluster.sync();  // every CTA's maxima are in place
+  if (rank == 0 && tid == 0) {
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    for (int q = 0; q < CL; ++q) {
+      const double* cm = cluster.map_shared_rank(cta_max, q);
+      c0 = fmax(c0, cm[0]);
+      c1 = fmax(c1, cm[1]);
+      c2 = fmax(c2, cm[2]);
+    }
+    const double T11 = sT[0];
+    double* misc = sd.misc;
+    if (cycle == 1) {
+      misc[0] = cd.scal[0] * T11;  // beta = ||b|| T[1,1]
+      misc[3] = 0.0;
+    } else {
+      const double gam = misc[1] * T11;  // gamma of the previous coupling
+      sd.gam[cycle - 2] = gam;
+      misc[3] = fabs(t * gam);
+    }
+    if (has_next) {
+      const double tau = sT[(size_t)me * nc + me];
+      misc[1] = r_next * tau / sT[(size_t)(me - 1) * nc + me - 1];
+      sd.zg[2 * M] = 1.0 / tau;
+    } else {
+      misc[1] = 0.0;
+      sd.zg[2 * M] = 0.0;
+    }
+    misc[2] = fabs(t) * c0;
+    misc[4] = c1 * c2;
+    const bool ok = isfinite(c0) && isfinite(c1) && isfinite(c2) && isfinite(misc[0]) && isfinite(misc[1]);
+    if (!ok) cd.flags[2] |= ERR_NONFINITE;
+  }
+  cluster.sync();  // no CTA leaves while rank 0 reads its shared memory
+}
+
 // One Horner step for block row a of T_q(B), B = scale * H (scale = -t/2^s):
 //   S_new[j] = (S_old[j] X_j scale + S_old[j+1](:,1) scale gamma_j e_m^T) / kdeg + E[j]
 // with E the block row of the identity (E[a] = I).  first: S_old = E.
-__global__ void exp_taylor_kernel(const double* __restrict__ Xblk, const double* __restrict__ gam, int M,
-                                  int a, double kinv, double scale, int first, const double* __restrict__ Sold,
-                                  double* __restrict__ Snew, int64_t sx, int64_t sg, int64_t s_old, int64_t s_new) {
+__global__ void __launch_bounds__(KS_THREADS) exp_taylor_kernel(const double* __restrict__ Xblk,
+                                                                const double* __restrict__ gam, int M, int a,
+                                                                double kinv, double scale, int first,
+                                                                const double* __restrict__ Sold,
+                                                                double* __restrict__ Snew, int64_t sx, int64_t sg,
+                                                                int64_t s_old, int64_t s_new) {
   // problem blockIdx.z of a batch: X blocks, couplings and the Horner buffers
   // at strides sx, sg, s_old, s_new (zero for a single problem)
   Xblk += sx * blockIdx.z;
   gam += sg * blockIdx.z;
   Sold += s_old * blockIdx.z;
   Snew += s_new * blockIdx.z;
-  const int j = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j > a || e >= M * M) return;
-  const int r = e % M, col = e / M;
-  const double* Xj = Xblk + (size_t)j * M * M;
+  __shared__ double red[KS_WARPS][32];
+  const int j = blockIdx.y;  // j <= a (grid rows)
+  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
+  const size_t MM = (size_t)M * M;
+  const double* Xj = Xblk + (size_t)j * MM;
   double acc = 0.0;
+  if (!first) acc = ks_product(Sold + (size_t)j * MM, Xj, M, e, red);  // uniform branch: whole CTA
+  if (threadIdx.x >= 32 || e >= M * M) return;
+  const int r = e % M, col = e / M;
   if (first) {
     if (j == a) acc = Xj[(size_t)col * M + r] * scale;
     if (j + 1 == a && col == M - 1 && r == 0) acc += scale * gam[j];
   } else {
-    const double* Sj = Sold + (size_t)j * M * M;
-    for (int l = 0; l < M; ++l) acc = fma(Sj[(size_t)l * M + r], Xj[(size_t)col * M + l], acc);
     acc *= scale;
-    if (col == M - 1 && j < a) acc = fma(Sold[(size_t)(j + 1) * M * M + r], scale * gam[j], acc);
+    if (col == M - 1 && j < a) acc = fma(Sold[(size_t)(j + 1) * MM + r], scale * gam[j], acc);
   }
   acc *= kinv;
   if (j == a && r == col) acc += 1.0;
-  Snew[(size_t)j * M * M + e] = acc;
+  Snew[(size_t)j * MM + e] = acc;
 }
 
 // Squaring for block row a: N[j] = sum_{l=j}^{a} G[a][l] G[l][j], blocks of
@@ -263,26 +584,21 @@ __global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restr
 // l (deterministic).  Every pair is one m x m product, so the grid is
 // balanced and the FP64 work is spread over (a+1)(a+2)/2 CTA rows instead of
 // a+1.
-__global__ void exp_square_pairs_kernel(const double* __restrict__ Gi, double* __restrict__ P, int M, int a) {
+__global__ void __launch_bounds__(KS_THREADS) exp_square_pairs_kernel(const double* __restrict__ Gi,
+                                                                      double* __restrict__ P, int M, int a) {
   int k = blockIdx.y, j = 0;
   while (k > a - j) {  // pair index -> (j, l): pairs of j are l = j..a
     k -= a - j + 1;
     ++j;
   }
   const int l = j + k;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= M * M) return;
-  const int r = e % M, col = e / M;
+  __shared__ double red[KS_WARPS][32];
+  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
   const size_t MM = (size_t)M * M;
   const double* L = Gi + ((size_t)a * (a + 1) / 2 + l) * MM;   // G[a][l]
   const double* Rb = Gi + ((size_t)l * (l + 1) / 2 + j) * MM;  // G[l][j]
-  double a4[4] = {0.0, 0.0, 0.0, 0.0};
-  int p = 0;
-  for (; p + 3 < M; p += 4)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a4[u] = fma(L[(size_t)(p + u) * M + r], Rb[(size_t)col * M + p + u], a4[u]);
-  for (; p < M; ++p) a4[0] = fma(L[(size_t)p * M + r], Rb[(size_t)col * M + p], a4[0]);
-  P[(size_t)blockIdx.y * MM + e] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+  const double acc = ks_product(L, Rb, M, e, red);
+  if (threadIdx.x < 32 && e < M * M) P[(size_t)blockIdx.y * MM + e] = acc;
 }
 
 __global__ void exp_square_reduce_kernel(const double* __restrict__ P, double* __restrict__ Go, int M, int a) {
@@ -422,8 +738,87 @@ __global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc, const B
 
 }  // namespace
 
+namespace {
+
+// Largest cluster (16, 8, 4, 2 or 1 CTAs) the device schedules for the
+// cluster whitening at the largest shared-memory footprint it is given, and
+// the SM count; found once per device.
+struct WcDevice {
+  int cl_max = 1;
+  int sms = 1;
+};
+
+WcDevice whiten_cluster_device() {
+  static std::mutex mu;
+  static std::map<int, WcDevice> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return WcDevice{};
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  WcDevice d;
+  cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* kern = (const void*)whiten_cluster_kernel;
+  if (raise_smem_limit(kern, WC_SMEM_MAX) == cudaSuccess &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    for (int cl = 16; cl >= 2; cl >>= 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(WC_THREADS);
+      cfg.dynamicSmemBytes = WC_SMEM_MAX;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cl;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n > 0) {
+        d.cl_max = cl;
+        break;
+      }
+    }
+  }
+  cudaGetLastError();  // a refused size leaves no error behind
+  cache[dev] = d;
+  return d;
+}
+
+// Cluster whitening of nb problems (one cluster each): the cluster size is
+// the device's largest, cut to about (SM count / nb) when many problems run
+// at once.  Returns false (nothing launched) when the shared-memory footprint
+// does not fit; the single-CTA kernel then runs.
+bool launch_whiten_cluster(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
+                           int ncols, int m_eff, int has_next, int cycle, int kw, double t, cudaStream_t st) {
+  const WcDevice d = whiten_cluster_device();
+  int cl = d.cl_max;
+  const int target = std::max(1, d.sms / std::max(nb, 1));
+  while (cl > 1 && cl > target) cl >>= 1;
+  const size_t smem = whiten_cluster_smem(s, ncols, cl);
+  if (smem > WC_SMEM_MAX) return false;
+  if (raise_smem_limit((const void*)whiten_cluster_kernel, smem) != cudaSuccess) return false;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nb * cl));
+  cfg.blockDim = dim3(WC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, whiten_cluster_kernel, sd, cd, s, m, ncols, m_eff, has_next, cycle, kw, t, bs) ==
+         cudaSuccess;
+}
+
+}  // namespace
+
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff, int has_next,
-                   int cycle, double t, cudaStream_t st) {
+                   int cycle, int kw, double t, cudaStream_t st) {
+  if (launch_whiten_cluster(sd, cd, BatchStride{}, 1, s, m, ncols, m_eff, has_next, cycle, kw, t, st)) return;
   // scratch for T_m R_m: reuse the Horner buffer area (not in use at this point)
   const size_t smem = whiten_smem(s, ncols);
   raise_smem_limit((const void*)whiten_kernel, smem);
@@ -432,7 +827,8 @@ void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int nco
 }
 
 void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
-                           int ncols, int m_eff, int has_next, int cycle, double t, cudaStream_t st) {
+                           int ncols, int m_eff, int has_next, int cycle, int kw, double t, cudaStream_t st) {
+  if (launch_whiten_cluster(sd, cd, bs, nb, s, m, ncols, m_eff, has_next, cycle, kw, t, st)) return;
   const size_t smem = whiten_smem(s, ncols);
   raise_smem_limit((const void*)whiten_kernel, smem);
   whiten_kernel<<<nb, SMALL_THREADS, smem, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, bs);
@@ -441,10 +837,10 @@ void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchSt
 void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
                                double scale, int first, int src, double* dst0, int dst_in_g, cudaStream_t st) {
   const int MM = m * m;
-  dim3 g((MM + 127) / 128, a + 1, nb);
+  dim3 g((MM + 31) / 32, a + 1, nb);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
   // dst0 lies in problem 0's Horner buffer or (last step) its exp rows
-  exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst0, bs.Xblk, bs.gam,
+  exp_taylor_kernel<<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst0, bs.Xblk, bs.gam,
                                        bs.S0, dst_in_g ? bs.G : bs.S0);
 }
 
@@ -465,16 +861,16 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double s
                             int src, double* dst, cudaStream_t st) {
   (void)last;
   const int MM = m * m;
-  dim3 g((MM + 127) / 128, a + 1);
+  dim3 g((MM + 31) / 32, a + 1);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
-  exp_taylor_kernel<<<g, 128, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0, 0, 0, 0);
+  exp_taylor_kernel<<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0, 0, 0, 0);
 }
 
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, double* pairs,
                        cudaStream_t st) {
   const int MM = m * m;
   const int npairs = (a + 1) * (a + 2) / 2;
-  exp_square_pairs_kernel<<<dim3((MM + 127) / 128, npairs), 128, 0, st>>>(sd.G + (size_t)level * level_stride, pairs,
+  exp_square_pairs_kernel<<<dim3((MM + 31) / 32, npairs), KS_THREADS, 0, st>>>(sd.G + (size_t)level * level_stride, pairs,
                                                                           m, a);
   exp_square_reduce_kernel<<<dim3((MM + 127) / 128, a + 1), 128, 0, st>>>(pairs,
                                                                          sd.G + (size_t)(level + 1) * level_stride, m,
