@@ -264,8 +264,7 @@ krylov_status ensure_small_capacity(krylov_handle* h, int rows, int levels) {
     int nl = std::max(levels, h->cap_levels + 4);
     dfree(h, h->sd.G);
     h->level_stride = (int64_t)h->cap_rows * (h->cap_rows + 1) / 2 * (int64_t)MM;
-    // one extra level holds the pair products of a squaring
-    CK(dalloc(h, &h->sd.G, (size_t)(nl + 1) * h->level_stride));
+    CK(dalloc(h, &h->sd.G, (size_t)nl * h->level_stride));
     h->cap_levels = nl;
   }
   return KRYLOV_OK;
@@ -290,9 +289,8 @@ int exp_row(krylov_handle* h, int a, int sl) {
     launch_exp_taylor_step(h->sd, M, a, kdeg, scale, first, kdeg == 1, src, dst, h->st);
     src = 1 - src;
   }
-  double* pairs = h->sd.G + (size_t)h->cap_levels * h->level_stride;
-  for (int lv = 0; lv < sl; ++lv) launch_exp_square(h->sd, M, a, lv, h->level_stride, pairs, h->st);
-  return EXP_TAYLOR_DEG + 2 * sl;
+  for (int lv = 0; lv < sl; ++lv) launch_exp_square(h->sd, M, a, lv, h->level_stride, h->st);
+  return EXP_TAYLOR_DEG + sl;
 }
 
 struct Operator {

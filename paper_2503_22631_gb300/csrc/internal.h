@@ -248,8 +248,7 @@ void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int nco
                    int has_next, int cycle, int kw, double t, cudaStream_t st);
 void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first,
                             int last, int src, double* dst, cudaStream_t st);
-void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, double* pairs,
-                       cudaStream_t st);
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st);
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st);
 void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double u0, double hq,
                           int nodes, cudaStream_t st);

@@ -578,39 +578,46 @@ __global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restr
   Go[(rowa + j) * MM + e] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
 }
 
-// The same squaring with the sum over l spread over the grid: one CTA row per
-// (j, l) pair (j <= l <= a) forms the partial product G[a][l] G[l][j] into
-// P[pair]; exp_square_reduce_kernel then sums the pairs of each j in order of
-// l (deterministic).  Every pair is one m x m product, so the grid is
-// balanced and the FP64 work is spread over (a+1)(a+2)/2 CTA rows instead of
-// a+1.
-__global__ void __launch_bounds__(KS_THREADS) exp_square_pairs_kernel(const double* __restrict__ Gi,
-                                                                      double* __restrict__ P, int M, int a) {
-  int k = blockIdx.y, j = 0;
-  while (k > a - j) {  // pair index -> (j, l): pairs of j are l = j..a
-    k -= a - j + 1;
-    ++j;
-  }
-  const int l = j + k;
-  __shared__ double red[KS_WARPS][32];
-  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
-  const size_t MM = (size_t)M * M;
-  const double* L = Gi + ((size_t)a * (a + 1) / 2 + l) * MM;   // G[a][l]
-  const double* Rb = Gi + ((size_t)l * (l + 1) / 2 + j) * MM;  // G[l][j]
-  const double acc = ks_product(L, Rb, M, e, red);
-  if (threadIdx.x < 32 && e < M * M) P[(size_t)blockIdx.y * MM + e] = acc;
-}
+// The same squaring for one problem with the whole inner sum of an output
+// block spread over the warps of a CTA: the flattened index (l - j) m + p over
+// the (a - j + 1) m terms of N[j] is cut into SQ_WARPS contiguous ranges, one
+// per warp, and warp 0 adds the partial sums in warp order (deterministic).
+// One CTA per (j, 32 consecutive entries): the dependent chain of a warp is at
+// most (a + 1) m / SQ_WARPS terms and the grid holds every block of the row.
+constexpr int SQ_WARPS = 8;
 
-__global__ void exp_square_reduce_kernel(const double* __restrict__ P, double* __restrict__ Go, int M, int a) {
+__global__ void __launch_bounds__(SQ_WARPS * 32) exp_square_row_kernel(const double* __restrict__ Gi,
+                                                                     double* __restrict__ Go, int M, int a) {
+  __shared__ double red[SQ_WARPS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j > a || e >= M * M) return;
+  const int e = blockIdx.x * 32 + lane;
   const size_t MM = (size_t)M * M;
-  size_t pair = 0;  // first pair of j
-  for (int jj = 0; jj < j; ++jj) pair += (size_t)(a - jj + 1);
+  const size_t rowa = (size_t)a * (a + 1) / 2;
+  const int K = (a - j + 1) * M;
+  const int chunk = (K + SQ_WARPS - 1) / SQ_WARPS;
+  const int k0 = w * chunk, k1 = min(K, k0 + chunk);
   double acc = 0.0;
-  for (int l = j; l <= a; ++l) acc += P[(pair + (l - j)) * MM + e];
-  Go[((size_t)a * (a + 1) / 2 + j) * MM + e] = acc;
+  if (e < M * M && k0 < k1) {
+    const int r = e % M, col = e / M;
+    int k = k0;
+    while (k < k1) {  // one (l, p-range) segment at a time
+      const int l = j + k / M, p0 = k % M, p1 = min(M, p0 + (k1 - k));
+      const double* L = Gi + (rowa + l) * MM + r;                         // G[a][l], row r
+      const double* Rb = Gi + ((size_t)l * (l + 1) / 2 + j) * MM + (size_t)col * M;  // G[l][j], column col
+#pragma unroll 4
+      for (int p = p0; p < p1; ++p) acc = fma(L[(size_t)p * M], Rb[p], acc);
+      k += p1 - p0;
+    }
+  }
+  red[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && e < M * M) {
+    double sum = red[0][lane];
+#pragma unroll
+    for (int q = 1; q < SQ_WARPS; ++q) sum += red[q][lane];
+    Go[(rowa + j) * MM + e] = sum;
+  }
 }
 
 // f(z) = 1/z: y_a = X_a^{-1} rhs, rhs = e_1 (a = 0) or -gamma_{a-1} y_{a-1}[M-1] e_1
@@ -866,15 +873,10 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double s
   exp_taylor_kernel<<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0, 0, 0, 0);
 }
 
-void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, double* pairs,
-                       cudaStream_t st) {
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st) {
   const int MM = m * m;
-  const int npairs = (a + 1) * (a + 2) / 2;
-  exp_square_pairs_kernel<<<dim3((MM + 31) / 32, npairs), KS_THREADS, 0, st>>>(sd.G + (size_t)level * level_stride, pairs,
-                                                                          m, a);
-  exp_square_reduce_kernel<<<dim3((MM + 127) / 128, a + 1), 128, 0, st>>>(pairs,
-                                                                         sd.G + (size_t)(level + 1) * level_stride, m,
-                                                                         a);
+  exp_square_row_kernel<<<dim3((MM + 31) / 32, a + 1), SQ_WARPS * 32, 0, st>>>(
+      sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride, m, a);
 }
 
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
