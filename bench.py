@@ -66,6 +66,9 @@ def parse():
                     help="convdiff3d_128 is the headline; the others time the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: no warm-up floor, no e2e, no CPU baseline, no clock sampling")
+    ap.add_argument("--product", default="auto", choices=["auto", "gather"],
+                    help="float-float product kernel: timed choice at create (default) or always the "
+                         "gather kernel (a fixed launch sequence for ncu captures)")
     return ap.parse_args()
 
 
@@ -166,12 +169,14 @@ def step_traffic():
     import hashlib
 
     tf = ROOT / "profiles" / "step_kernel_traffic.txt"
-    src = ROOT / "paper_2503_22631_gb300" / "csrc" / "step_kernels.cu"
-    if not tf.exists() or not src.exists():
+    csrc = ROOT / "paper_2503_22631_gb300" / "csrc"
+    srcs = [csrc / "step_kernels.cu", csrc / "step_common.cuh"]
+    if not tf.exists() or not all(p.exists() for p in srcs):
         return None
     kv = dict(line.split("=", 1) for line in tf.read_text().splitlines()
               if "=" in line and not line.startswith("#"))
-    if kv.get("step_kernels_sha256_16") != hashlib.sha256(src.read_bytes()).hexdigest()[:16]:
+    digest = hashlib.sha256(b"".join(p.read_bytes() for p in srcs)).hexdigest()[:16]
+    if kv.get("step_kernels_sha256_16") != digest:
         return None
     return float(kv["bytes_per_launch"])
 
@@ -411,7 +416,8 @@ def main():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=WORKLOAD["t"], m=WORKLOAD["m"], k=WORKLOAD["k"],
-                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=basis, stream=stream)
+                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=basis, stream=stream,
+                    autotune="gather" if args.product == "gather" else True)
         bd = torch.from_numpy(b).cuda()
         x = torch.empty_like(bd)
         stream.synchronize()

@@ -117,8 +117,10 @@ typedef struct {
   void* stream;    /* cudaStream_t for all work; NULL = legacy default stream */
   int autotune;    /* float-float basis: 1 (default) times the two product kernels on the
                       operator at create (w_j pieces staged in shared memory from a per-tile
-                      segment plan, or w_j gathered through L1/L2) and keeps the faster;
-                      0 uses the staged pieces whenever the operator has a segment plan */
+                      segment plan, or w_j gathered through L1/L2) and keeps the staged
+                      pieces only when they are faster by more than 3 %; 0 uses the staged
+                      pieces whenever the operator has a segment plan; 2 always gathers
+                      (a fixed kernel choice, e.g. for profiling); other values: EINVAL */
   int block_rhs;   /* batched form: 1 (default) advances up to 64 right-hand sides of a matrix
                       together through the block kernels (float-float basis, TRUNC, exp, packed
                       sketch table, m <= 64, max_cycles <= 16); 0 solves them one by one */

@@ -74,7 +74,7 @@ class Krylov:
         opt.sketch_regenerate = 1 if sketch_regenerate else 0
         opt.ortho = int(ortho)
         opt.use_graph = 1 if use_graph else 0
-        opt.autotune = 1 if autotune else 0
+        opt.autotune = 2 if autotune == "gather" else (1 if autotune else 0)
         opt.block_rhs = 1 if block_rhs else 0
         if stream is None:
             stream = torch.cuda.current_stream()

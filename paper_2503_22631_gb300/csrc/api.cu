@@ -489,7 +489,7 @@ int rgs_cycle_steps(krylov_handle* h, const Operator& op, int transpose, int use
 krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
   SegPlan& sp = transpose ? h->seg_t : h->seg_a;
   int& grid = transpose ? h->grid_spmv_t : h->grid_spmv;
-  if (h->opt.basis_dtype != 3 || !sp.seg || !h->opt.autotune) return KRYLOV_OK;
+  if (h->opt.basis_dtype != 3 || !sp.seg || h->opt.autotune == 0) return KRYLOV_OK;
   const int use32 = (h->opt.narrow_values_if_exact && h->vals_exact_f32) ? 1 : 0;
   Operator op{transpose ? h->rpt : h->rp, transpose ? h->cit : h->ci, transpose ? h->valt : h->val,
               transpose ? h->valt32 : h->val32, transpose ? h->valtff : h->valff};
@@ -498,6 +498,11 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
   const int grid_seg = grid;
   const int grid_gather = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(use32, tcap, 0, 0),
                                                std::min(h->part_cap, (n + STEP_THREADS - 1) / STEP_THREADS)));
+  if (h->opt.autotune == 2) {  // fixed choice: the gather kernel
+    sp.seg = nullptr;
+    grid = grid_gather;
+    return KRYLOV_OK;
+  }
   cudaStream_t st = h->st;
   CK(cudaMemsetAsync(h->W, 0, sizeof(float2) * 2 * (size_t)h->ldw, st));
   CK(cudaMemsetAsync(h->cd.flags, 0, 4 * sizeof(int), st));
@@ -518,12 +523,18 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
     cudaEventElapsedTime(&ms, e0, e1);
     return ms;
   };
-  const float t_seg = time_variant(true);
-  const float t_gather = time_variant(false);
+  // alternate the variants over a few rounds and keep each one's best time:
+  // one round alone flips with the box's state; the segment plan must win by
+  // a clear margin over the plain gather kernel to be kept
+  float t_seg = 1e30f, t_gather = 1e30f;
+  for (int round = 0; round < 3; ++round) {
+    t_seg = std::min(t_seg, time_variant(true));
+    t_gather = std::min(t_gather, time_variant(false));
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CK(cudaGetLastError());
-  if (t_gather < t_seg) {
+  if (!(t_seg < 0.97f * t_gather)) {
     sp.seg = nullptr;
     grid = grid_gather;
   }
@@ -1187,6 +1198,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   if (opt.zeta < 1 || opt.zeta > std::min(s, MAX_ZETA)) return KRYLOV_EINVAL;
   if (opt.basis_dtype < 0 || opt.basis_dtype > 3) return KRYLOV_EINVAL;
   if (opt.ortho != KRYLOV_ORTHO_TRUNC && opt.ortho != KRYLOV_ORTHO_RGS) return KRYLOV_EINVAL;
+  if (opt.autotune < 0 || opt.autotune > 2) return KRYLOV_EINVAL;
   // the randomized Gram-Schmidt cycle runs with the float64 and float-float bases
   if (opt.ortho == KRYLOV_ORTHO_RGS && opt.basis_dtype != KRYLOV_BASIS_F64 && opt.basis_dtype != KRYLOV_BASIS_DF64)
     return KRYLOV_EUNSUPPORTED;

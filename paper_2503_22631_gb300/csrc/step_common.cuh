@@ -125,26 +125,36 @@ __device__ __forceinline__ void fx_emit(int* bins, int sC, int row, int cp, cons
   for (int w = 0; w < NW; ++w) atomicAdd(b + w * sC, neg ? -x.q[w] : x.q[w]);
 }
 
+// 2^k as a double, built from its exponent field (no FP64 arithmetic) in the
+// normal range; ldexp outside it.
+__device__ __forceinline__ double pow2d(int k) {
+  return (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(k + 1023) << 52) : ldexp(1.0, k);
+}
+
 // Value of bin b of this CTA: sum of its words over the copies, as a double.
 // Thread b starts at copy b mod C, so the lanes of a warp read C different
 // banks at every step instead of all hitting one (integer sums: any order).
+// The last two word sums are merged exactly in 64-bit integers (a word sum is
+// below 2^35 in magnitude and WB <= 21, so t 2^WB + t' stays below 2^57),
+// which leaves two conversions and power-of-two scalings: the FP64 pipe,
+// shared by the CTAs of an SM, is what this per-CTA epilogue waits on.
 template <int NW>
 __device__ __forceinline__ double fx_value(const int* bins, int s, int C, int b, const FxScale& f, int WB) {
-  double v = 0.0;
+  static_assert(NW == 2 || NW == 3, "two or three fixed-point words");
+  long long t[NW];
 #pragma unroll
   for (int w = 0; w < NW; ++w) {
-    long long t = 0;
+    long long u = 0;
     const int* col = bins + (w * s + b) * C;
-    for (int c = 0; c < C; ++c) t += col[(c + b) & (C - 1)];
-    v += ldexp((double)t, f.E - (w + 1) * WB);
+    for (int c = 0; c < C; ++c) u += col[(c + b) & (C - 1)];
+    t[w] = u;
   }
-  return v;
+  const long long low = t[NW - 2] * (1ll << WB) + t[NW - 1];
+  const double vlow = (double)low * pow2d(f.E - NW * WB);
+  if (NW == 2) return vlow;
+  return fma((double)t[0], pow2d(f.E - WB), vlow);
 }
 
-// Scale for the contributions of column j: |w_j[i]| <= ||w_j|| <= B where, for a
-// materialized column, B = rho (||p_{j-1}|| + sum_q |h_q| ||w_q||) (triangle
-// inequality on the orthogonalization, computed once by the reducer of p_{j-1}),
-// else the stored bound of slot 0.
 __device__ __forceinline__ FxScale fx_scale(const StepLaunch& L, const CycleDev& cd, int mat) {
   // materialized column: the bound the previous product's reducer stored;
   // first column of a cycle: the bound of the start vector
