@@ -210,6 +210,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// Expect `bytes` more transaction bytes in the current phase, without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Arrive without expecting transaction bytes.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
 // Global -> shared bulk copy whose completion is reported to `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -294,9 +303,21 @@ template <typename A> __device__ __forceinline__ A warp_sum(A v) {
 // one warp: lane l takes rows l, l+32, ... in order, then a fixed shuffle tree.
 // The result (in every lane) does not depend on timing, only on count.
 __device__ __forceinline__ double warp_sum_partials(const double* part, int count, int stride, int q) {
+  // up to 16 loads per lane in flight at once (one round trip to L2 for up to
+  // 512 partials), then added in the order c = lane, lane + 32, ...
+  constexpr int B = 16;
+  const int lane = (int)(threadIdx.x & 31);
   double t = 0.0;
-#pragma unroll 4
-  for (int c = (int)(threadIdx.x & 31); c < count; c += 32) t += __ldcg(part + (size_t)c * stride + q);
+  for (int c0 = lane; c0 < count; c0 += 32 * B) {
+    double v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int c = c0 + 32 * u;
+      v[u] = (c < count) ? __ldcg(part + (size_t)c * stride + q) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) t += v[u];
+  }
   return warp_sum(t);
 }
 

@@ -275,10 +275,12 @@ __global__ void __launch_bounds__(SMALL_THREADS) whiten_kernel(SmallDev sd, Cycl
 // diagonal and the next reflector, so the chain between two barriers is one
 // column update.  Then every CTA gathers T (signs fixed so that diag(T) > 0)
 // and each warp takes one column b: the column sweep of T x = e_b gives
-// column b of T_m^{-1}, and column b of X = T_m (R_m T_m^{-1}) + (r / T_mm)
-// t e_m^T is formed from it with the band of R_m (rows p - 1 .. p + k - 1 of
-// column p hold the only nonzeros of the truncated recurrence); the extra
-// column b = me solves T_m g = t.
+// column b of T_m^{-1}, and column b of T_m R_m comes from the band of R_m
+// (rows b - k + 1 .. b + 1 of column b hold the only nonzeros of the
+// truncated recurrence); the extra column b = me solves T_m g = t.  After a
+// cluster barrier each warp forms its columns of X = (T_m R_m) T_m^{-1} +
+// (r / T_mm) t e_m^T in that association (the product T_m R_m first, then
+// the inverse), the order of the definition in App. A.
 constexpr int WC_THREADS = 256;
 constexpr size_t WC_SMEM_MAX = 200 * 1024;
 
@@ -315,13 +317,14 @@ __device__ __forceinline__ void wc_sweep(double* x, const double* sT, int ldt, c
 
 __global__ void __launch_bounds__(WC_THREADS) whiten_cluster_kernel(SmallDev sd, CycleDev cd, int s, int M, int nc,
                                                                     int me, int has_next, int cycle, int kw,
-                                                                    double t, const BatchStride bs) {
+                                                                    double t, double* scratch, const BatchStride bs) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int prob = (int)(blockIdx.x / (unsigned)CL);  // problem of a batch (one cluster each)
   sd = offset_sd(sd, bs, prob);
   cd = offset_cd(cd, bs, prob);
+  scratch += bs.S0 * prob;  // T_m R_m (leading dimension M)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
   const int ncl = (nc + CL - 1) / CL;
   extern __shared__ double wsm[];
@@ -406,13 +409,12 @@ __global__ void __launch_bounds__(WC_THREADS) whiten_cluster_kernel(SmallDev sd,
   }
   __syncthreads();
 
-  // ---- per column b: T_m^{-1} e_b, X e_b, norms; b = me: g = T_m^{-1} t ----
+  // ---- per column b: T_m^{-1} e_b, (T_m R_m) e_b, norms; b = me: g = T_m^{-1} t ----
   const int ldr = M + 1;
   const double r_next = has_next ? cd.R[(size_t)(me - 1) * ldr + me] : 0.0;
   const double rt = has_next ? r_next / sT[(size_t)(me - 1) * nc + me - 1] : 0.0;
   double* X = sd.Xblk + (size_t)(cycle - 1) * M * M;
   double* x = xw + (size_t)wid * 2 * nc;
-  double* z = x + nc;
   double cmax = 0.0, tmax = 0.0, timax = 0.0;
   const int ntask = max(M, me + 1);
   for (int b = rank * nwarp + wid; b < ntask; b += CL * nwarp) {
@@ -426,44 +428,43 @@ __global__ void __launch_bounds__(WC_THREADS) whiten_cluster_kernel(SmallDev sd,
         sd.Tinv[(size_t)b * M + a] = y;
         ci += fabs(y);
         if (a <= b) ct += fabs(sT[(size_t)b * nc + a]);
+        // (T_m R_m)[a, b]: R_m has its nonzeros in rows b - k + 1 .. b + 1 of column b
+        const int l0 = max(a, b - kw + 1), l1 = min(b + 1, me - 1);
+        double tr = 0.0;
+        for (int l = l0; l <= l1; ++l) tr = fma(sT[(size_t)l * nc + a], cd.R[(size_t)b * ldr + l], tr);
+        scratch[(size_t)b * M + a] = tr;
       }
       ci = warp_sum(ci);
       ct = warp_sum(ct);
       timax = fmax(timax, ci);
       tmax = fmax(tmax, ct);
-      // z = R_m y (y = x, zero below row b), then X e_b = T_m z (+ the rank-one term)
-      for (int l = lane; l < me; l += 32) {
-        const int p0 = max(l - 1, 0), p1 = min(min(l + kw - 1, b), me - 1);
-        double acc = 0.0;
-        for (int p = p0; p <= p1; ++p) acc = fma(cd.R[(size_t)p * ldr + l], x[p], acc);
-        z[l] = acc;
-      }
       __syncwarp();
-      double cs = 0.0;
-      for (int a = lane; a < M; a += 32) {
-        double acc = 0.0;
-        if (a < me) {
-          for (int l = a; l < me; ++l) acc = fma(sT[(size_t)l * nc + a], z[l], acc);
-          if (b == me - 1 && has_next) acc = fma(rt, sT[(size_t)me * nc + a], acc);
-        }
-        X[(size_t)b * M + a] = acc;
-        cs += fabs(acc);
-      }
-      cmax = fmax(cmax, warp_sum(cs));
-      __syncwarp();
-    } else {
-      if (b < M)
-        for (int a = lane; a < M; a += 32) X[(size_t)b * M + a] = 0.0;
-      if (b == me) {
-        if (has_next) {
-          for (int a = lane; a < me; a += 32) x[a] = sT[(size_t)me * nc + a];
-          __syncwarp();
-          wc_sweep(x, sT, nc, dinv, me - 1, lane);
-        }
-        for (int a = lane; a < me; a += 32) sd.zg[M + a] = has_next ? x[a] : 0.0;
+    } else if (b == me) {
+      if (has_next) {
+        for (int a = lane; a < me; a += 32) x[a] = sT[(size_t)me * nc + a];
         __syncwarp();
+        wc_sweep(x, sT, nc, dinv, me - 1, lane);
       }
+      for (int a = lane; a < me; a += 32) sd.zg[M + a] = has_next ? x[a] : 0.0;
+      __syncwarp();
     }
+  }
+  cluster.sync();  // T_m^{-1} and T_m R_m complete (global memory)
+  // ---- X = (T_m R_m) T_m^{-1} + (r / T_mm) t e_m^T, column b per warp ----
+  for (int b = rank * nwarp + wid; b < M; b += CL * nwarp) {
+    double cs = 0.0;
+    for (int a = lane; a < M; a += 32) {
+      double acc = 0.0;
+      if (a < me && b < me) {
+        for (int l = 0; l <= b; ++l)
+          acc = fma(__ldcg(scratch + (size_t)l * M + a), __ldcg(sd.Tinv + (size_t)b * M + l), acc);
+        if (b == me - 1 && has_next) acc = fma(rt, sT[(size_t)me * nc + a], acc);
+      }
+      X[(size_t)b * M + a] = acc;
+      cs += fabs(acc);
+    }
+    cs = warp_sum(cs);
+    if (b < me) cmax = fmax(cmax, cs);
   }
   if (lane == 0) {
     wmax[0][wid] = cmax;
@@ -817,8 +818,9 @@ bool launch_whiten_cluster(const SmallDev& sd, const CycleDev& cd, const BatchSt
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, whiten_cluster_kernel, sd, cd, s, m, ncols, m_eff, has_next, cycle, kw, t, bs) ==
-         cudaSuccess;
+  // T_m R_m goes to the Horner buffer area (not in use at this point)
+  return cudaLaunchKernelEx(&cfg, whiten_cluster_kernel, sd, cd, s, m, ncols, m_eff, has_next, cycle, kw, t, sd.S0,
+                            bs) == cudaSuccess;
 }
 
 }  // namespace

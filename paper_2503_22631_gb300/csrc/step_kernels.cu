@@ -524,14 +524,19 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   auto st_w = [&](int st, int q) { return reinterpret_cast<const float2*>(stages + st * SB + (size_t)MT_ROWS * 8 * (1 + q)); };
   auto st_r = [&](int st) { return reinterpret_cast<const uint2*>(stages + st * SB + (size_t)MT_ROWS * 8 * (1 + KW)); };
   auto st_n = [&](int st) { return stages + st * SB + (size_t)MT_ROWS * 8 * (2 + KW); };
-  auto issue = [&](int t) {  // thread 0
+  // Tile t's copies come in two parts: the window columns and the sketch
+  // table (written two or more kernels back, or never) and the product p_{j-1}
+  // (written by the kernel just before).  The first part of the first tiles is
+  // issued before the programmatic-launch wait, overlapping the previous
+  // kernel's reduction tail; the phase completes only once the second part
+  // has arrived as well (its arrive carries the last byte count).
+  auto rows_of = [&](int t) { return (uint32_t)((min(MT_ROWS, r1 - (r0 + t * MT_ROWS)) + 15) & ~15); };
+  auto issue_static = [&](int t) {  // thread 0: expects its bytes, does not arrive
     const int st = t % MT_STAGES;
     const int ts = r0 + t * MT_ROWS;
-    const uint32_t rc = (uint32_t)((min(MT_ROWS, r1 - ts) + 15) & ~15);
-    const uint32_t nvec = MAT ? 1u + (uint32_t)nl : 1u;
+    const uint32_t rc = rows_of(t);
     unsigned char* base = stages + st * SB;
-    mbar_arrive_expect_tx(&bars[st], rc * 8u * (nvec + 1u) + rc);
-    bulk_g2s(base, src0 + ts, rc * 8u, &bars[st]);
+    mbar_expect_tx(&bars[st], rc * 8u * (MAT ? 1u + (uint32_t)nl : 1u) + rc);
     if (MAT) {
 #pragma unroll
       for (int q = 0; q < KW; ++q)
@@ -539,6 +544,16 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
     }
     bulk_g2s(base + (size_t)MT_ROWS * 8 * (1 + KW), L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
     bulk_g2s(base + (size_t)MT_ROWS * 8 * (2 + KW), L.sk_tab.neg8 + ts, rc, &bars[st]);
+  };
+  auto issue_p = [&](int t) {  // thread 0: arrives with the product's bytes
+    const int st = t % MT_STAGES;
+    const uint32_t rc = rows_of(t);
+    mbar_arrive_expect_tx(&bars[st], rc * 8u);
+    bulk_g2s(stages + st * SB, src0 + r0 + t * MT_ROWS, rc * 8u, &bars[st]);
+  };
+  auto issue = [&](int t) {
+    issue_static(t);
+    issue_p(t);
   };
   if (threadIdx.x == 0) {
     for (int q = 0; q < MT_STAGES; ++q) mbar_init(&bars[q], 1);
@@ -550,12 +565,22 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
     for (int e = threadIdx.x; e < nb / 4; e += blockDim.x) b4[e] = make_int4(0, 0, 0, 0);
     for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
   }
-  // everything above is independent of earlier kernels; p_{j-1}, the window
-  // and the coefficients are not
+  const int npre = min(ntiles, MT_STAGES);
+  if (threadIdx.x == 0)
+    for (int t = 0; t < npre; ++t) issue_static(t);
+  // everything above is independent of the kernel just before; p_{j-1} and
+  // the coefficients are not
   pdl_wait();
-  if (cd.flags[0] < j) return;  // the cycle ended before column j (breakdown)
+  if (cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
+    if (threadIdx.x == 0)  // complete the phases and let the copies land before leaving
+      for (int t = 0; t < npre; ++t) {
+        mbar_arrive(&bars[t]);
+        (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+      }
+    return;
+  }
   if (threadIdx.x == 0) {
-    for (int t = 0; t < min(ntiles, MT_STAGES); ++t) issue(t);
+    for (int t = 0; t < npre; ++t) issue_p(t);
     s_fx = fx_scale(L, cd, MAT ? 1 : 0);  // per-CTA prologue, overlapping the first copies
     const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
     for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
