@@ -166,8 +166,10 @@ struct krylov_handle {
   int grid_update = 0;             // CTAs of the cycle-end update pass
   int q_nodes = 0;                 // z^{-1/2} quadrature nodes
   double q_u0 = 0.0;               // first node
-  int tma_cap = 0, tma_cap_t = 0;
-  SegPlan seg_a, seg_t;            // segment plans of A and A^T (float-float basis)  // staged span per tile for A and A^T (0: no staging)
+  int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
+  int16_t* dcol = nullptr;         // col - row per nonzero of A (bandwidth < 2^15, staged float-float product)
+  int16_t* dcolt = nullptr;        // the same for A^T
+  SegPlan seg_a, seg_t;            // segment plans of A and A^T (float-float basis)
   int* rpt = nullptr;
   int* cit = nullptr;
   double* valt = nullptr;
@@ -326,6 +328,23 @@ krylov_status install_seg_plan(krylov_handle* h, SegPlan& plan, const int* rp_de
 
 krylov_status choose_product_kernel(krylov_handle* h, int transpose);
 
+// Column offsets col - row as 2-byte integers for the staged float-float
+// product kernel, when every |col - row| fits (banded operators: stencils and
+// meshes in a banded ordering); they replace the 4-byte column indices in
+// its copies.  Null otherwise.
+krylov_status install_delta16(krylov_handle* h, const int* rp_dev, const int* ci_dev, int16_t** out) {
+  *out = nullptr;
+  if (h->opt.basis_dtype != 3 || h->nnz == 0) return KRYLOV_OK;
+  CK(csr_bandwidth(h->n, rp_dev, ci_dev, h->d_flag, h->h_flags, h->st));
+  if (h->h_flags[0] > 32767) return KRYLOV_OK;
+  int16_t* d = nullptr;
+  CK(dalloc(h, &d, (size_t)h->nnz + CSR_PAD));
+  CK(cudaMemsetAsync(d + h->nnz, 0, CSR_PAD * sizeof(int16_t), h->st));
+  CK(csr_delta16(h->n, rp_dev, ci_dev, d, h->st));
+  *out = d;
+  return KRYLOV_OK;
+}
+
 krylov_status build_transpose(krylov_handle* h) {
   if (h->have_t) return KRYLOV_OK;
   int* work = nullptr;
@@ -350,10 +369,12 @@ krylov_status build_transpose(krylov_handle* h) {
   CK(cudaStreamSynchronize(h->st));
   dfree(h, work);
   CK(tile_span_max(h->n, h->rpt, h->d_flag, h->h_flags, h->st));
-  h->tma_cap_t = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 4) : 0;
+  h->tma_cap_t = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 8) : 0;
   if (h->opt.basis_dtype == 3) {
     const int vals32 = h->vals_exact_f32 && h->opt.narrow_values_if_exact;
     krylov_status ps = install_seg_plan(h, h->seg_t, h->rpt, h->cit);
+    if (ps != KRYLOV_OK) return ps;
+    ps = install_delta16(h, h->rpt, h->cit, &h->dcolt);
     if (ps != KRYLOV_OK) return ps;
     const SegPlan& sp = h->seg_t;
     h->grid_spmv_t = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap_t, sp.seg ? sp.seg_cap : 0,
@@ -371,7 +392,9 @@ krylov_status build_transpose(krylov_handle* h) {
 double model_bytes_step(const krylov_handle* h, int use32) {
   const double bv = basis_bytes(h->opt.basis_dtype);
   const double ba = use32 ? 4.0 : 8.0;
-  return (double)h->nnz * (ba + 4.0) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
+  // column entries as stored for the product: 2-byte offsets for a banded operator
+  const double bi = (h->dcol != nullptr) ? 2.0 : 4.0;
+  return (double)h->nnz * (ba + bi) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
 }
 
 // Randomized Gram-Schmidt step j: read A and w_j, write p; the sketch reads p
@@ -416,6 +439,7 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
   L.m = M;
   L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : 0;
+  L.dcol = (basis == 3) ? (transpose ? h->dcolt : h->dcol) : nullptr;
   if (basis == 3) {
     const SegPlan& sp = transpose ? h->seg_t : h->seg_a;
     L.seg = sp.seg;
@@ -1258,7 +1282,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(narrow_values(nnz, h->val, h->val32, h->d_flag, h->h_flags, h->st));
   h->vals_exact_f32 = (h->h_flags[0] == 0);
   CKF(tile_span_max(n, h->rp, h->d_flag, h->h_flags, h->st));
-  h->tma_cap = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 4) : 0;
+  h->tma_cap = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 8) : 0;
   if (opt.basis_dtype == KRYLOV_BASIS_DF64 && !(h->vals_exact_f32 && opt.narrow_values_if_exact)) {
     CKF(dalloc(h, &h->valff, (size_t)nnz + CSR_PAD));
     CKF(cudaMemsetAsync(h->valff + nnz, 0, CSR_PAD * sizeof(float2), h->st));
@@ -1309,7 +1333,9 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   h->allocs.push_back(h->sk_part);
   h->grid_spmv = h->grid;
   if (opt.basis_dtype == 3) {
-    const krylov_status ps = install_seg_plan(h, h->seg_a, h->rp, h->ci);
+    krylov_status ps = install_seg_plan(h, h->seg_a, h->rp, h->ci);
+    if (ps != KRYLOV_OK) return fail(ps);
+    ps = install_delta16(h, h->rp, h->ci, &h->dcol);
     if (ps != KRYLOV_OK) return fail(ps);
     const SegPlan& sp = h->seg_a;
     h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap, sp.seg ? sp.seg_cap : 0,

@@ -62,6 +62,8 @@ struct StepLaunch {
   int sk_copies;     // lane-private copies of each sketch bin in shared memory
   int fx_wb;         // bits per fixed-point word of the sketch bins
   int tma_cap;       // staged nonzeros per 256-row tile (0: no bulk-copy staging)
+  const int16_t* dcol;  // [nnz + 8] col - row per nonzero when the bandwidth is below 2^15 (staged
+                        // product kernel: 2 bytes per column instead of 4), else null
   int grid_spmv;     // CTAs of the separate product kernel (float-float basis)
   int rows_spmv;     // rows per CTA of that kernel (a multiple of 256)
   int rgs;           // 1: randomized Gram-Schmidt cycle (the product kernel forms p and ||p||^2 only)
@@ -169,6 +171,10 @@ cudaError_t raise_smem_limit(const void* kern, size_t bytes);
 cudaError_t norm_inf(int n, const int* rp, const double* val, int* d_flag, int* h_flag, double* out,
                      cudaStream_t st);
 cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaStream_t st);
+// max |col - row| over the nonzeros into h_flag[0] (synchronizes st)
+cudaError_t csr_bandwidth(int n, const int* rp, const int* ci, int* d_flag, int* h_flag, cudaStream_t st);
+// dcol[e] = col[e] - row(e); the caller has checked the bandwidth is below 2^15
+cudaError_t csr_delta16(int n, const int* rp, const int* ci, int16_t* dcol, cudaStream_t st);
 cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st);
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
                           int* cit, double* vt, int* work, cudaStream_t st);

@@ -112,14 +112,33 @@ __global__ void sort_rows_kernel(int n, const int* rpt, int* cit, double* vt) {
 
 // Largest 16-byte-aligned nonzero span of a 256-row tile (tiles start at
 // multiples of 256): ((rp[end] + 3) & ~3) - (rp[start] & ~3).
+// Largest nonzero span of a 256-row tile, both ends rounded out to multiples
+// of 8 entries (the staged copies start on 16-byte boundaries for 2-byte
+// column offsets as well as 4-byte columns).
 __global__ void tile_span_kernel(int n, const int* rp, int* out) {
   const int stride = gridDim.x * blockDim.x;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; (int64_t)t * 256 < n; t += stride) {
     const int ts = t * 256;
     const int te = min(ts + 256, n);
-    const int span = ((rp[te] + 3) & ~3) - (rp[ts] & ~3);
+    const int span = ((rp[te] + 7) & ~7) - (rp[ts] & ~7);
     atomicMax(out, span);
   }
+}
+
+// max over nonzeros of |col - row| (the bandwidth of the operator).
+__global__ void band_kernel(int n, const int* rp, const int* ci, int* out) {
+  const int stride = gridDim.x * blockDim.x;
+  int b = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) b = max(b, abs(ci[e] - i));
+  if (b > 0) atomicMax(out, b);
+}
+
+// dcol[e] = col[e] - row(e) (requires a bandwidth below 2^15).
+__global__ void delta16_kernel(int n, const int* rp, const int* ci, int16_t* dcol) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) dcol[e] = (int16_t)(ci[e] - i);
 }
 
 // max_i sum_j |a_ij| (the infinity norm), as the bit pattern of a nonnegative
@@ -176,6 +195,20 @@ cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag,
   if (nnz > 0) narrow_kernel<<<grid_for(nnz), 256, 0, st>>>(nnz, v, v32, d_flag);
   cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   return cudaStreamSynchronize(st);
+}
+
+cudaError_t csr_bandwidth(int n, const int* rp, const int* ci, int* d_flag, int* h_flag, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  band_kernel<<<grid_for(n), 256, 0, st>>>(n, rp, ci, d_flag);
+  e = cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t csr_delta16(int n, const int* rp, const int* ci, int16_t* dcol, cudaStream_t st) {
+  delta16_kernel<<<grid_for(n), 256, 0, st>>>(n, rp, ci, dcol);
+  return cudaGetLastError();
 }
 
 cudaError_t tile_span_max(int n, const int* rp, int* d_flag, int* h_flag, cudaStream_t st) {

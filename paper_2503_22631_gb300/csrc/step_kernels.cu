@@ -38,6 +38,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "kernels.cuh"
 #include "step_common.cuh"
@@ -811,9 +813,11 @@ constexpr int TMA_ROWS = STEP_THREADS;     // rows per staged tile
 constexpr int TMA_RP = TMA_ROWS + 4;       // staged row_ptr entries (16-byte multiple)
 constexpr int TMA_ROW_FAST = 8;            // rows up to this length issue all gathers together
 
-template <typename AT>
+// Stage of the staged product kernel: row_ptr slice, columns (4-byte indices,
+// or 2-byte offsets col - row when DI), values.  cap is a multiple of 8.
+template <typename AT, bool DI = false>
 __host__ __device__ __forceinline__ size_t tma_stage_bytes(int cap) {
-  return (size_t)TMA_RP * 4 + (size_t)cap * 4 + (size_t)cap * sizeof(AT);
+  return (size_t)TMA_RP * 4 + (size_t)cap * (DI ? 2 : 4) + (size_t)cap * sizeof(AT);
 }
 
 __device__ __forceinline__ void acc_val(ffacc& acc, float a, ff w) {
@@ -825,8 +829,10 @@ __device__ __forceinline__ void acc_val(ffacc& acc, float2 a, ff w) {
   acc.add_pe(pe.x, pe.y);
 }
 
-template <typename AT, int KW>
+template <typename AT, int KW, bool DI>
 __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const StepLaunch L, const CycleDev cd) {
+  using CT = typename std::conditional<DI, int16_t, int>::type;  // staged column entry
+  constexpr int EA = DI ? 8 : 4;  // staged nonzero ranges start on 16-byte boundaries
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ float rhi[32], rlo[32];
@@ -834,11 +840,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   __shared__ double tot[NQ];
   const int j = L.j;
   const int cap = L.tma_cap;
-  const size_t sb = tma_stage_bytes<AT>(cap);
-  // stage st: row_ptr slice (TMA_RP ints), columns (cap ints), values (cap AT)
+  const size_t sb = tma_stage_bytes<AT, DI>(cap);
+  // stage st: row_ptr slice (TMA_RP ints), columns (cap CT), values (cap AT)
   auto rp_st = [&](int st) { return reinterpret_cast<int*>(smem + (size_t)st * sb); };
-  auto col_st = [&](int st) { return rp_st(st) + TMA_RP; };
+  auto col_st = [&](int st) { return reinterpret_cast<CT*>(rp_st(st) + TMA_RP); };
   auto val_st = [&](int st) { return reinterpret_cast<AT*>(col_st(st) + cap); };
+  const CT* colsrc = DI ? reinterpret_cast<const CT*>(L.dcol) : reinterpret_cast<const CT*>(L.col);
   const float2* W = static_cast<const float2*>(L.W);
   const float2* Wj = W + (int64_t)j * L.ldw;
   const AT* val = static_cast<const AT*>(L.val);
@@ -860,12 +867,13 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   auto issue = [&](int t, int e0, int e1) {
     const int st = t & 1;
     const int ts = r0 + t * TMA_ROWS;
-    const int ea = e0 & ~3, eb = (e1 + 3) & ~3;
-    const uint32_t brp = TMA_RP * 4u, bcol = (uint32_t)(eb - ea) * 4u, bval = (uint32_t)(eb - ea) * sizeof(AT);
+    const int ea = e0 & ~(EA - 1), eb = (e1 + EA - 1) & ~(EA - 1);
+    const uint32_t brp = TMA_RP * 4u, bcol = (uint32_t)(eb - ea) * (uint32_t)sizeof(CT),
+                   bval = (uint32_t)(eb - ea) * sizeof(AT);
     mbar_arrive_expect_tx(&bars[st], brp + bcol + bval);
     bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
     if (eb > ea) {
-      bulk_g2s(col_st(st), L.col + ea, bcol, &bars[st]);
+      bulk_g2s(col_st(st), colsrc + ea, bcol, &bars[st]);
       bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
     }
   };
@@ -906,23 +914,24 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
     if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
     if (valid && !timed_out) {
       const int* rps = rp_st(st);
-      const int* cs = col_st(st);
+      const CT* cs = col_st(st);
       const AT* vs = val_st(st);
-      const int ea = rps[0] & ~3;
+      const int ea = rps[0] & ~(EA - 1);
       const int rb = rps[threadIdx.x] - ea, re = rps[threadIdx.x + 1] - ea;
+      const int cbase = DI ? i : 0;  // column = cbase + staged entry
       ffacc acc;
       if (re - rb <= TMA_ROW_FAST) {
         // short rows: every gather of the row in flight at once
         float2 wv[TMA_ROW_FAST];
 #pragma unroll
         for (int q = 0; q < TMA_ROW_FAST; ++q)
-          if (rb + q < re) wv[q] = __ldg(Wj + cs[rb + q]);
+          if (rb + q < re) wv[q] = __ldg(Wj + (cbase + (int)cs[rb + q]));
 #pragma unroll
         for (int q = 0; q < TMA_ROW_FAST; ++q)
           if (rb + q < re) acc_val(acc, vs[rb + q], ff{wv[q].x, wv[q].y});
       } else {
 #pragma unroll 4
-        for (int e = rb; e < re; ++e) acc_val(acc, vs[e], ld_ff(Wj + cs[e]));
+        for (int e = rb; e < re; ++e) acc_val(acc, vs[e], ld_ff(Wj + (cbase + (int)cs[e])));
       }
       const ff p = acc.result();
       st_ff(static_cast<float2*>(L.p_out) + i, p);
@@ -1217,8 +1226,15 @@ void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) 
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
   }
+  if (L.tma_cap > 0 && L.dcol != nullptr) {
+    auto k = ff_spmv_tma_kernel<AT, KW, true>;
+    const size_t smem = 2 * tma_stage_bytes<AT, true>(L.tma_cap);
+    raise_smem_limit((const void*)k, smem);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+    return;
+  }
   if (L.tma_cap > 0) {
-    auto k = ff_spmv_tma_kernel<AT, KW>;
+    auto k = ff_spmv_tma_kernel<AT, KW, false>;
     const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
@@ -1287,8 +1303,8 @@ int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap) {
     return vals_f32 ? occ(ff_spmv_seg_kernel<float, 2>, 2 * seg_stage_bytes<float>(lcap, seg_cap))
                     : occ(ff_spmv_seg_kernel<float2, 2>, 2 * seg_stage_bytes<float2>(lcap, seg_cap));
   if (tma_cap > 0)
-    return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2>, 2 * tma_stage_bytes<float>(tma_cap))
-                    : occ(ff_spmv_tma_kernel<float2, 2>, 2 * tma_stage_bytes<float2>(tma_cap));
+    return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2, false>, 2 * tma_stage_bytes<float>(tma_cap))
+                    : occ(ff_spmv_tma_kernel<float2, 2, false>, 2 * tma_stage_bytes<float2>(tma_cap));
   return vals_f32 ? occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM) : occ(ff_spmv_kernel<float2, 2>, FF_STAGE_SMEM);
 }
 

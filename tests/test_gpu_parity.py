@@ -218,3 +218,26 @@ def test_random_sparse_matrix_gather_path(lib, cuda):
     ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=2)
     x, _ = _gpu(A, b, *args, 2, basis=3)
     assert _rel(x, ref.x) <= 1e-10
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_wide_band_operator_parity(lib, cuda, adjoint):
+    """A 2D Poisson matrix (bandwidth 200) with two couplings 39,999 rows apart:
+    the bandwidth is at least 2^15, so the staged product kernel reads 4-byte
+    column indices (a narrower band gets 2-byte offsets col - row); the
+    operator and its transpose against the oracle."""
+    import scipy.sparse as sp
+
+    P = W.poisson2d(200)
+    n = P.n
+    Ps = sp.csr_matrix((P.val, P.col_idx, P.row_ptr), shape=(n, n))
+    far = sp.csr_matrix((np.array([-2048.0, -1024.0]), (np.array([0, n - 1]), np.array([n - 1, 0]))), shape=(n, n))
+    Aw = (Ps + far).tocsr()
+    Aw.sort_indices()
+    A = W.Csr(n, Aw.indptr.astype(np.int32), Aw.indices.astype(np.int32), Aw.data.astype(np.float64))
+    assert np.abs(np.repeat(np.arange(n), np.diff(A.row_ptr)) - A.col_idx).max() >= 2**15
+    b = W.rhs_normal(n, 6, normalize=True)
+    args = (D.EXP_NEG, 1e-5, 20, 2, 60, 8, 9)
+    ref = K.restarted(A.transpose() if adjoint else A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=2)
+    x, _ = _gpu(A, b, *args, 2, basis=3, adjoint=adjoint)
+    assert _rel(x, ref.x) <= 1e-10
