@@ -1280,9 +1280,13 @@ int occ(K kern, size_t smem) {
 }  // namespace
 
 int sketch_bin_copies(int basis, int s) {
-  // lane-private copies: the largest power of two <= 32 whose bins fit in 32 KB
+  // lane-private copies: the largest power of two <= 32 whose bins fit in
+  // 32 KB, or 64 KB for the float-float materialize kernel, where 32 copies
+  // (one per lane: the bank of every atomic is its lane) remove the conflicts
+  // of lanes l and l + 16 that 16 copies leave (2.35 wavefronts per shared
+  // atomic); that costs resident CTAs and still wins 1.5 % per step
   int c = 32;
-  while (c > 1 && bins_bytes(basis, s, c) > 32 * 1024) c >>= 1;
+  while (c > 1 && bins_bytes(basis, s, c) > (basis == 3 ? 64 : 32) * 1024) c >>= 1;
   return c;
 }
 
