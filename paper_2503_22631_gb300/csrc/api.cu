@@ -723,6 +723,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     CK(cudaMemcpyAsync(h->h_scal + 8, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (h->h_flags[2] & ERR_TIMEOUT) return KRYLOV_ETIMEOUT;  // a bounded wait of the small problem
     if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
     stats.kappa_T_max = std::max(stats.kappa_T_max, h->h_scal[8 + 4]);
     const double ynorm = std::sqrt(h->h_scal[2]);
@@ -1018,7 +1019,7 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
     }
     for (int r = 0; r < nb; ++r) {
       if (!active[r]) continue;
-      if (b.h_flags[4 * r + 1] != 0 || (b.h_flags[4 * r + 2] & (ERR_NONFINITE | ERR_SKETCH))) {
+      if (b.h_flags[4 * r + 1] != 0 || (b.h_flags[4 * r + 2] & (ERR_NONFINITE | ERR_SKETCH | ERR_TIMEOUT))) {
         active[r] = 0;  // breakdown (or trouble): this right-hand side is redone alone
         redo.push_back(r);
       }
