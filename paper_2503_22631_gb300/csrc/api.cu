@@ -1025,7 +1025,7 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
       }
     }
     launch_bk_sketch_fin(L, b.sd, M + 1, s_);
-    launch_whiten_batched(b.sd, b.cd, b.bs, nb, h->s, M, M + 1, M, 1, c, h->k, h->f.t, s_);
+    launch_whiten_batched(b.sd, b.cd, b.bs, nb, h->bk_concurrent, h->s, M, M + 1, M, 1, c, h->k, h->f.t, s_);
     CK(cudaMemcpyAsync(b.h_scal + 8 * BK_NB, b.sd.misc, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s_));
     CK(cudaStreamSynchronize(s_));
     launches += 2;

@@ -232,8 +232,10 @@ __host__ __device__ inline CycleDev offset_cd(CycleDev cd, const BatchStride& b,
 // Batched small problem (block form): one problem per cluster (whiten), per
 // CTA (z) or per grid z-slice (exp), problems r = 0..nb-1 at offsets r * stride.
 // kw: window of the truncated recurrence (band of R_m).
-void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
-                           int ncols, int m_eff, int has_next, int cycle, int kw, double t, cudaStream_t st);
+// concurrent: such batched launches running at once on other streams
+void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int concurrent,
+                           int s, int m, int ncols, int m_eff, int has_next, int cycle, int kw, double t,
+                           cudaStream_t st);
 void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
                                double scale, int first, int src, double* dst0, int dst_in_g, cudaStream_t st);
 void launch_exp_square_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int level,

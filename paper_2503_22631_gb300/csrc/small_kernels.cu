@@ -521,12 +521,18 @@ __global__ void __launch_bounds__(WC_THREADS) whiten_cluster_kernel(SmallDev sd,
 // One Horner step for block row a of T_q(B), B = scale * H (scale = -t/2^s):
 //   S_new[j] = (S_old[j] X_j scale + S_old[j+1](:,1) scale gamma_j e_m^T) / kdeg + E[j]
 // with E the block row of the identity (E[a] = I).  first: S_old = E.
+// KSW = KS_WARPS: the CTA forms one chunk of 32 entries with the inner sum
+// split over its warps (one problem: latency first).  KSW = 1: each warp forms
+// its own chunk with whole inner sums (a batch of problems: the FP64 pipe is
+// saturated anyway, and the split's partial sums are extra FP64 work).
+template <int KSW>
 __global__ void __launch_bounds__(KS_THREADS) exp_taylor_kernel(const double* __restrict__ Xblk,
                                                                 const double* __restrict__ gam, int M, int a,
                                                                 double kinv, double scale, int first,
                                                                 const double* __restrict__ Sold,
                                                                 double* __restrict__ Snew, int64_t sx, int64_t sg,
                                                                 int64_t s_old, int64_t s_new) {
+  static_assert(KSW == KS_WARPS || KSW == 1, "inner sum split over all warps of the CTA or none");
   // problem blockIdx.z of a batch: X blocks, couplings and the Horner buffers
   // at strides sx, sg, s_old, s_new (zero for a single problem)
   Xblk += sx * blockIdx.z;
@@ -535,12 +541,25 @@ __global__ void __launch_bounds__(KS_THREADS) exp_taylor_kernel(const double* __
   Snew += s_new * blockIdx.z;
   __shared__ double red[KS_WARPS][32];
   const int j = blockIdx.y;  // j <= a (grid rows)
-  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
+  const int chunk = (KSW == 1) ? (int)blockIdx.x * KS_WARPS + w : (int)blockIdx.x;
+  const int e = chunk * 32 + (threadIdx.x & 31);
   const size_t MM = (size_t)M * M;
   const double* Xj = Xblk + (size_t)j * MM;
   double acc = 0.0;
-  if (!first) acc = ks_product(Sold + (size_t)j * MM, Xj, M, e, red);  // uniform branch: whole CTA
-  if (threadIdx.x >= 32 || e >= M * M) return;
+  if (KSW == 1) {
+    if (e >= M * M) return;
+    if (!first) {
+      const int r = e % M, col = e / M;
+      const double* Lr = Sold + (size_t)j * MM + r;
+      const double* Rc = Xj + (size_t)col * M;
+#pragma unroll 4
+      for (int p = 0; p < M; ++p) acc = fma(Lr[(size_t)p * M], Rc[p], acc);
+    }
+  } else {
+    if (!first) acc = ks_product(Sold + (size_t)j * MM, Xj, M, e, red);  // uniform branch: whole CTA
+    if (w != 0 || e >= M * M) return;
+  }
   const int r = e % M, col = e / M;
   if (first) {
     if (j == a) acc = Xj[(size_t)col * M + r] * scale;
@@ -794,14 +813,16 @@ WcDevice whiten_cluster_device() {
 }
 
 // Cluster whitening of nb problems (one cluster each): the cluster size is
-// the device's largest, cut to about (SM count / nb) when many problems run
-// at once.  Returns false (nothing launched) when the shared-memory footprint
-// does not fit; the single-CTA kernel then runs.
-bool launch_whiten_cluster(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
-                           int ncols, int m_eff, int has_next, int cycle, int kw, double t, cudaStream_t st) {
+// the device's largest, cut to about (SM count / problems) when many problems
+// run at once (nb in this launch times `concurrent` such launches on other
+// streams).  Returns false (nothing launched) when the shared-memory
+// footprint does not fit; the single-CTA kernel then runs.
+bool launch_whiten_cluster(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int concurrent,
+                           int s, int m, int ncols, int m_eff, int has_next, int cycle, int kw, double t,
+                           cudaStream_t st) {
   const WcDevice d = whiten_cluster_device();
   int cl = d.cl_max;
-  const int target = std::max(1, d.sms / std::max(nb, 1));
+  const int target = std::max(1, d.sms / std::max(nb * std::max(concurrent, 1), 1));
   while (cl > 1 && cl > target) cl >>= 1;
   const size_t smem = whiten_cluster_smem(s, ncols, cl);
   if (smem > WC_SMEM_MAX) return false;
@@ -827,7 +848,7 @@ bool launch_whiten_cluster(const SmallDev& sd, const CycleDev& cd, const BatchSt
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff, int has_next,
                    int cycle, int kw, double t, cudaStream_t st) {
-  if (launch_whiten_cluster(sd, cd, BatchStride{}, 1, s, m, ncols, m_eff, has_next, cycle, kw, t, st)) return;
+  if (launch_whiten_cluster(sd, cd, BatchStride{}, 1, 1, s, m, ncols, m_eff, has_next, cycle, kw, t, st)) return;
   // scratch for T_m R_m: reuse the Horner buffer area (not in use at this point)
   const size_t smem = whiten_smem(s, ncols);
   raise_smem_limit((const void*)whiten_kernel, smem);
@@ -835,9 +856,10 @@ void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int nco
                                                 BatchStride{});
 }
 
-void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int s, int m,
-                           int ncols, int m_eff, int has_next, int cycle, int kw, double t, cudaStream_t st) {
-  if (launch_whiten_cluster(sd, cd, bs, nb, s, m, ncols, m_eff, has_next, cycle, kw, t, st)) return;
+void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchStride& bs, int nb, int concurrent,
+                           int s, int m, int ncols, int m_eff, int has_next, int cycle, int kw, double t,
+                           cudaStream_t st) {
+  if (launch_whiten_cluster(sd, cd, bs, nb, concurrent, s, m, ncols, m_eff, has_next, cycle, kw, t, st)) return;
   const size_t smem = whiten_smem(s, ncols);
   raise_smem_limit((const void*)whiten_kernel, smem);
   whiten_kernel<<<nb, SMALL_THREADS, smem, st>>>(sd, cd, s, m, ncols, m_eff, has_next, cycle, t, sd.S0, bs);
@@ -846,10 +868,10 @@ void launch_whiten_batched(const SmallDev& sd, const CycleDev& cd, const BatchSt
 void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int kdeg,
                                double scale, int first, int src, double* dst0, int dst_in_g, cudaStream_t st) {
   const int MM = m * m;
-  dim3 g((MM + 31) / 32, a + 1, nb);
+  dim3 g((MM + KS_THREADS - 1) / KS_THREADS, a + 1, nb);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
   // dst0 lies in problem 0's Horner buffer or (last step) its exp rows
-  exp_taylor_kernel<<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst0, bs.Xblk, bs.gam,
+  exp_taylor_kernel<1><<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst0, bs.Xblk, bs.gam,
                                        bs.S0, dst_in_g ? bs.G : bs.S0);
 }
 
@@ -872,7 +894,8 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double s
   const int MM = m * m;
   dim3 g((MM + 31) / 32, a + 1);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
-  exp_taylor_kernel<<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0, 0, 0, 0);
+  exp_taylor_kernel<KS_WARPS><<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0,
+                                                         0, 0, 0);
 }
 
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st) {
