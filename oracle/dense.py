@@ -11,7 +11,14 @@
   scaling (E. D. Denman, A. N. Beavers, 1976; N. J. Higham, "Functions of
   Matrices", 2008, Sec. 6.3 and 6.5).  Not in the paper: the inverse square
   root workload is an extension.
-* ``f_dense``      f(H) for the three supported kinds.
+* ``phi1m``        phi_1(A) = sum_k A^k / (k+1)!  (the paper's phi function,
+  Sec. 5, phi_1(z) = (e^z - 1)/z) as the top-right block of exp of the block
+  triangular [[A, I], [0, 0]], whose exponential is [[e^A, phi_1(A)], [0, I]]
+  (the series of the two sides agree term by term; the identity is the usual
+  way to evaluate phi functions with an exponential, see Hochbruck and
+  Ostermann, "Exponential integrators", Acta Numerica 2010, which the paper
+  cites for phi_1).
+* ``f_dense``      f(H) for the four supported kinds.
 """
 import math
 from fractions import Fraction
@@ -21,6 +28,7 @@ import numpy as np
 EXP_NEG = 0      # f(z) = exp(-t z)
 INVSQRT = 1      # f(z) = z^{-1/2}
 INV = 2          # f(z) = 1/z
+PHI1_NEG = 3     # f(z) = phi_1(-t z) = (1 - e^{-t z}) / (t z)
 
 
 def qr_positive(U):
@@ -120,10 +128,22 @@ def invsqrtm(A, tol=1e-14, max_iter=100):
     return Z
 
 
+def phi1m(A):
+    """phi_1(A): the top-right n x n block of exp([[A, I], [0, 0]])."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    Z = np.zeros((2 * n, 2 * n))
+    Z[:n, :n] = A
+    Z[:n, n:] = np.eye(n)
+    return expm(Z)[:n, n:]
+
+
 def f_dense(kind, H, t=1.0):
-    """f(H) for f(z) = exp(-t z), z^{-1/2} or 1/z (dense, FP64)."""
+    """f(H) for f(z) = exp(-t z), z^{-1/2}, 1/z or phi_1(-t z) (dense, FP64)."""
     if kind == EXP_NEG:
         return expm(-t * H)
+    if kind == PHI1_NEG:
+        return phi1m(-t * H)
     if kind == INVSQRT:
         return invsqrtm(H)
     if kind == INV:

@@ -51,12 +51,32 @@ def sine_mode_exp(N, c, p, q, t):
     return out.reshape(-1)
 
 
+def phi1_neg(x):
+    """phi_1(-x) = (1 - e^{-x}) / x elementwise (1 at x = 0), from expm1."""
+    x = np.asarray(x, dtype=np.float64)
+    safe = np.where(x == 0.0, 1.0, x)
+    return np.where(x == 0.0, 1.0, -np.expm1(-safe) / safe)
+
+
+def sine_mode_phi1(N, c, p, q, t):
+    """phi_1(-t A) b for b = sum_l c_l phi_{p_l q_l} on the 5-point Laplacian."""
+    h = 1.0 / (N + 1)
+    ii = np.arange(1, N + 1)
+    lam = (4.0 / h**2) * (np.sin(np.asarray(p) * np.pi * h / 2) ** 2 + np.sin(np.asarray(q) * np.pi * h / 2) ** 2)
+    out = np.zeros((N, N))
+    for cl, pl, ql, ll in zip(c, p, q, lam):
+        out += cl * phi1_neg(t * ll) * np.outer(np.sin(ql * np.pi * ii * h), np.sin(pl * np.pi * ii * h))
+    return out.reshape(-1)
+
+
 def dense_fAb(Adense, b, fkind, t=1.0, symmetric=False):
     """f(A) b on a small dense matrix."""
     if symmetric:
         lam, Q = np.linalg.eigh(Adense)
         if fkind == dense.EXP_NEG:
             fl = np.exp(-t * lam)
+        elif fkind == dense.PHI1_NEG:
+            fl = phi1_neg(t * lam)
         elif fkind == dense.INVSQRT:
             fl = lam ** -0.5
         else:

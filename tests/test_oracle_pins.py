@@ -171,6 +171,33 @@ def test_invsqrtm():
     assert rel(Z, np.linalg.inv(sl.sqrtm(N))) < 1e-11
 
 
+def test_phi1m_closed_forms():
+    """phi_1 on a diagonal (expm1(l)/l, 1 at l = 0), on a 2 x 2 Jordan block
+    (phi_1' on the superdiagonal), and A phi_1(A) = e^A - I for a random A."""
+    lam = np.array([-30.0, -2.5, -1e-9, 0.0, 1e-9, 0.7, 3.0])
+    P = D.phi1m(np.diag(lam))
+    ref = np.where(lam == 0.0, 1.0, np.expm1(lam) / np.where(lam == 0.0, 1.0, lam))
+    assert np.allclose(np.diag(P), ref, rtol=1e-14, atol=0)
+    assert np.abs(P - np.diag(np.diag(P))).max() == 0.0
+    l = -1.7
+    J = np.array([[l, 1.0], [0.0, l]])
+    dphi = (l * math.exp(l) - math.exp(l) + 1.0) / l**2
+    assert np.allclose(D.phi1m(J), [[math.expm1(l) / l, dphi], [0.0, math.expm1(l) / l]], rtol=1e-14, atol=1e-16)
+    A = np.random.default_rng(11).standard_normal((14, 14))
+    assert rel(A @ D.phi1m(A), D.expm(A) - np.eye(14)) < 1e-12
+    # f_dense applies the parameter: phi_1(-t H)
+    H = np.diag([2.0, 5.0])
+    assert np.allclose(np.diag(D.f_dense(D.PHI1_NEG, H, 0.3)), -np.expm1(-0.3 * np.array([2.0, 5.0])) / (0.3 * np.array([2.0, 5.0])), rtol=1e-14)
+
+
+def test_phi1m_matches_eigendecomposition():
+    S = W.poisson2d(6).to_dense()
+    lam, Q = np.linalg.eigh(S)
+    t = 3e-3
+    ref = Q @ np.diag(-np.expm1(-t * lam) / (t * lam)) @ Q.T
+    assert rel(D.f_dense(D.PHI1_NEG, S, t), ref) < 1e-13
+
+
 # ---------------------------------------------------------------- truth -----
 def test_kronecker_truth_matches_dense_exponential():
     """exp(-tA) of the Kronecker-sum grid operator applied by mode products
@@ -248,7 +275,7 @@ def test_single_mode_breaks_down_exactly(mode):
     assert rel(r.x, TR.sine_mode_exp(N, c, p, q, 2e-3)) < 1e-13
 
 
-@pytest.mark.parametrize("fkind", [D.EXP_NEG, D.INV, D.INVSQRT])
+@pytest.mark.parametrize("fkind", [D.EXP_NEG, D.INV, D.INVSQRT, D.PHI1_NEG])
 def test_exact_when_m_reaches_n(fkind):
     """With m = n the Krylov space is the whole space: one cycle is exact."""
     A = W.fem_p1_kuhn(4, 1.0, 2)  # 27 unknowns, SPD
@@ -329,3 +356,16 @@ def test_stopping_estimate_decreases():
     ys = [ci.update_norm for ci in r.info]
     assert ys[-1] <= 1e-10 * r.info[-1].x_norm
     assert all(ys[i + 1] < ys[i] for i in range(1, len(ys) - 1))
+
+
+@pytest.mark.parametrize("mode", [K.TRUNC, K.RGS])
+def test_restarted_phi1_converges_to_sine_modes(mode):
+    """phi_1(-t A) b (the paper's phi function, Sec. 5) on the 5-point Laplacian
+    for a mixture of eigenmodes: closed form phi_1(-t lambda) per mode."""
+    N = 24
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 6, 13)
+    t = 2e-3
+    r = K.restarted(A, b, D.PHI1_NEG, t, 10, 2 if mode == K.TRUNC else 10, 40, 8, 5, mode=mode, tol=1e-13,
+                    max_cycles=40)
+    assert rel(r.x, TR.sine_mode_phi1(N, c, p, q, t)) < 1e-10
