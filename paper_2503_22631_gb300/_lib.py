@@ -30,6 +30,7 @@ ORTHO_RGS = 1
 F_EXP_NEG = 0
 F_INVSQRT = 1
 F_INV = 2
+F_PHI1_NEG = 3
 
 # krylov_basis
 BASIS_F64 = 0

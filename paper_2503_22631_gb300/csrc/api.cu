@@ -188,6 +188,7 @@ struct krylov_handle {
   SmallDev sd{};
   int cap_rows = 0;     // block rows of the projected-function storage
   int cap_levels = 0;   // scale levels allocated in sd.G
+  int64_t gphi_stride = 0;  // phi_1 vectors: doubles per scale level in sd.gphi
   int64_t level_stride = 0;
   int* d_flag = nullptr;
   double* d_dot = nullptr;
@@ -267,6 +268,11 @@ krylov_status ensure_small_capacity(krylov_handle* h, int rows, int levels) {
     dfree(h, h->sd.G);
     h->level_stride = (int64_t)h->cap_rows * (h->cap_rows + 1) / 2 * (int64_t)MM;
     CK(dalloc(h, &h->sd.G, (size_t)nl * h->level_stride));
+    if (h->f.kind == KRYLOV_F_PHI1_NEG) {  // the augmented column: one m-vector per block row and level
+      dfree(h, h->sd.gphi);
+      h->gphi_stride = (int64_t)h->cap_rows * h->m;
+      CK(dalloc(h, &h->sd.gphi, (size_t)nl * h->gphi_stride));
+    }
     h->cap_levels = nl;
   }
   return KRYLOV_OK;
@@ -285,13 +291,20 @@ int exp_row(krylov_handle* h, int a, int sl) {
   const double scale = -h->f.t / std::ldexp(1.0, sl);
   double* g0row = h->sd.G + (size_t)a * (a + 1) / 2 * MM;
   int src = 0;
+  // phi_1: the extra column of exp([[-tH, e_1], [0, 0]]) rides along (level 0
+  // from the Taylor steps, then one vector row per squaring)
+  const bool phi = (h->f.kind == KRYLOV_F_PHI1_NEG);
+  auto gvec = [&](int lv) { return h->sd.gphi + (size_t)lv * h->gphi_stride; };
   for (int kdeg = EXP_TAYLOR_DEG; kdeg >= 1; --kdeg) {
     const int first = (kdeg == EXP_TAYLOR_DEG);
     double* dst = (kdeg == 1) ? g0row : h->sd.S0 + (size_t)(1 - src) * (size_t)(a + 1) * MM;
-    launch_exp_taylor_step(h->sd, M, a, kdeg, scale, first, kdeg == 1, src, dst, h->st);
+    launch_exp_taylor_step(h->sd, M, a, kdeg, scale, first, kdeg == 1, src, dst,
+                           phi ? gvec(0) + (size_t)a * M : nullptr, std::ldexp(1.0, -sl), h->st);
     src = 1 - src;
   }
-  for (int lv = 0; lv < sl; ++lv) launch_exp_square(h->sd, M, a, lv, h->level_stride, h->st);
+  for (int lv = 0; lv < sl; ++lv)
+    launch_exp_square(h->sd, M, a, lv, h->level_stride, phi ? gvec(lv) : nullptr, phi ? gvec(lv + 1) : nullptr,
+                      h->st);
   return EXP_TAYLOR_DEG + sl;
 }
 
@@ -587,7 +600,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   CK(cudaEventRecord(e0, st));
 
   int levels_needed = 1;
-  if (h->f.kind == KRYLOV_F_EXP_NEG) levels_needed = std::max(1, h->cap_levels);
+  if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG) levels_needed = std::max(1, h->cap_levels);
   krylov_status cs = ensure_small_capacity(h, max_cycles, levels_needed);
   if (cs != KRYLOV_OK) return cs;
 
@@ -686,7 +699,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       stats.launches += 2;
     }
     const int a = c - 1;
-    if (h->f.kind == KRYLOV_F_EXP_NEG) {
+    if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG) {
       CK(cudaMemcpyAsync(h->h_scal, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       maxX = std::max(maxX, h->h_scal[2]);
@@ -702,7 +715,10 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       }
       stats.launches += exp_row(h, a, s_lv);
       const size_t MM = (size_t)M * M;
-      const double* fsrc = h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
+      // exp: first column of block (a, 0); phi_1: block row a of the extra column
+      const double* fsrc = (h->f.kind == KRYLOV_F_PHI1_NEG)
+                               ? h->sd.gphi + (size_t)s_lv * h->gphi_stride + (size_t)a * M
+                               : h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
       launch_z(h->sd, M, me, fsrc, st);
       stats.launches += 1;
     } else if (h->f.kind == KRYLOV_F_INVSQRT) {
@@ -1110,7 +1126,7 @@ krylov_status run_instance(krylov_handle* h, int n_rhs, const double* B, double*
   }
   krylov_status worst = KRYLOV_OK;
   const double t_old = h->f.t;
-  if (t_new && h->f.kind == KRYLOV_F_EXP_NEG) h->f.t = *t_new;
+  if (t_new && (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG)) h->f.t = *t_new;
   if (cudaEventRecord(ev, orig) != cudaSuccess || cudaStreamWaitEvent(bs, ev, 0) != cudaSuccess) worst = KRYLOV_ECUDA;
   h->st = bs;
   if (worst == KRYLOV_OK && !h->stage_b) {
@@ -1227,7 +1243,9 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   // the randomized Gram-Schmidt cycle runs with the float64 and float-float bases
   if (opt.ortho == KRYLOV_ORTHO_RGS && opt.basis_dtype != KRYLOV_BASIS_F64 && opt.basis_dtype != KRYLOV_BASIS_DF64)
     return KRYLOV_EUNSUPPORTED;
-  if (f.kind != KRYLOV_F_EXP_NEG && f.kind != KRYLOV_F_INV && f.kind != KRYLOV_F_INVSQRT) return KRYLOV_EINVAL;
+  if (f.kind != KRYLOV_F_EXP_NEG && f.kind != KRYLOV_F_INV && f.kind != KRYLOV_F_INVSQRT &&
+      f.kind != KRYLOV_F_PHI1_NEG)
+    return KRYLOV_EINVAL;
   if (!std::isfinite(f.t)) return KRYLOV_EINVAL;
 
   krylov_handle* h = new (std::nothrow) krylov_handle();

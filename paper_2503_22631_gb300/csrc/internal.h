@@ -200,6 +200,8 @@ struct SmallDev {
   double* qcarry;  // z^{-1/2}: per quadrature node, last entry of the previous block solve
   double* qpart;   // z^{-1/2}: nodes x m weighted block solutions
   double* qwork;   // z^{-1/2}: nodes x m x m LU work when it does not fit in shared memory
+  double* gphi;    // phi_1: per scale level and block row, the m-vector of the augmented
+                   // exponential's extra column (levels x cycles x m)
 };
 
 // z^{-1/2} quadrature nodes keep their m x m LU work in shared memory up to this size.
@@ -254,9 +256,14 @@ void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int h
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
                    int has_next, int cycle, int kw, double t, cudaStream_t st);
+// gout (phi_1, else null): where the last step stores the Taylor polynomial's
+// extra column for block row a, scaled by gscale = 2^-s
 void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first,
-                            int last, int src, double* dst, cudaStream_t st);
-void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st);
+                            int last, int src, double* dst, double* gout, double gscale, cudaStream_t st);
+// gi/go (phi_1, else null): the phi_1 vectors of block rows 0..a at the input
+// level and of block row a at the output level
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, const double* gi,
+                       double* go, cudaStream_t st);
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st);
 void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double u0, double hq,
                           int nodes, cudaStream_t st);

@@ -525,13 +525,21 @@ __global__ void __launch_bounds__(WC_THREADS) whiten_cluster_kernel(SmallDev sd,
 // split over its warps (one problem: latency first).  KSW = 1: each warp forms
 // its own chunk with whole inner sums (a batch of problems: the FP64 pipe is
 // saturated anyway, and the split's partial sums are extra FP64 work).
+//
+// phi_1 (gout non-null, last step only): with the augmented matrix
+// [[B, w], [0, 0]], w = e_1 2^-s, the Horner recurrence S <- S B / k + I
+// carries the extra column S_old w / k, so the Taylor polynomial's extra
+// column is S^(2) w: the first column of block (a, 0) of the iterate before
+// the last step, times 2^-s (gscale).  It is stored as level 0 of the phi_1
+// vector of block row a.
 template <int KSW>
 __global__ void __launch_bounds__(KS_THREADS) exp_taylor_kernel(const double* __restrict__ Xblk,
                                                                 const double* __restrict__ gam, int M, int a,
                                                                 double kinv, double scale, int first,
                                                                 const double* __restrict__ Sold,
                                                                 double* __restrict__ Snew, int64_t sx, int64_t sg,
-                                                                int64_t s_old, int64_t s_new) {
+                                                                int64_t s_old, int64_t s_new,
+                                                                double* __restrict__ gout, double gscale) {
   static_assert(KSW == KS_WARPS || KSW == 1, "inner sum split over all warps of the CTA or none");
   // problem blockIdx.z of a batch: X blocks, couplings and the Horner buffers
   // at strides sx, sg, s_old, s_new (zero for a single problem)
@@ -539,6 +547,8 @@ __global__ void __launch_bounds__(KS_THREADS) exp_taylor_kernel(const double* __
   gam += sg * blockIdx.z;
   Sold += s_old * blockIdx.z;
   Snew += s_new * blockIdx.z;
+  if (gout != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+    for (int r = threadIdx.x; r < M; r += blockDim.x) gout[r] = Sold[r] * gscale;
   __shared__ double red[KS_WARPS][32];
   const int j = blockIdx.y;  // j <= a (grid rows)
   const int w = threadIdx.x >> 5;
@@ -606,14 +616,48 @@ __global__ void exp_square_kernel(const double* __restrict__ Gi, double* __restr
 // most (a + 1) m / SQ_WARPS terms and the grid holds every block of the row.
 constexpr int SQ_WARPS = 8;
 
+//
+// phi_1 (gi non-null): grid row a + 1 squares the augmented matrix's extra
+// column as well, [[E, g], [0, 1]]^2 = [[E^2, E g + g], [0, 1]]: block row a
+// of the new vector is sum_{l <= a} G[a][l] g[l] + g[a], the same flattened
+// (l, p) sum split over the warps (g[l]: the m-vector of block row l at the
+// input level, gi; output go).
 __global__ void __launch_bounds__(SQ_WARPS * 32) exp_square_row_kernel(const double* __restrict__ Gi,
-                                                                     double* __restrict__ Go, int M, int a) {
+                                                                     double* __restrict__ Go, int M, int a,
+                                                                     const double* __restrict__ gi,
+                                                                     double* __restrict__ go) {
   __shared__ double red[SQ_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j = blockIdx.y;
   const int e = blockIdx.x * 32 + lane;
   const size_t MM = (size_t)M * M;
   const size_t rowa = (size_t)a * (a + 1) / 2;
+  if (j == a + 1) {  // the phi_1 vector of block row a
+    if ((int)blockIdx.x * 32 >= M) return;  // whole CTA
+    const int K = (a + 1) * M;
+    const int chunk = (K + SQ_WARPS - 1) / SQ_WARPS;
+    const int k0 = w * chunk, k1 = min(K, k0 + chunk);
+    double acc = 0.0;
+    if (e < M) {
+      int k = k0;
+      while (k < k1) {  // one (l, p-range) segment at a time
+        const int l = k / M, p0 = k % M, p1 = min(M, p0 + (k1 - k));
+        const double* L = Gi + (rowa + l) * MM + e;  // G[a][l], row e
+        const double* gl = gi + (size_t)l * M;
+        for (int p = p0; p < p1; ++p) acc = fma(L[(size_t)p * M], gl[p], acc);
+        k += p1 - p0;
+      }
+    }
+    red[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && e < M) {
+      double sum = red[0][lane];
+#pragma unroll
+      for (int q = 1; q < SQ_WARPS; ++q) sum += red[q][lane];
+      go[(size_t)a * M + e] = sum + gi[(size_t)a * M + e];
+    }
+    return;
+  }
   const int K = (a - j + 1) * M;
   const int chunk = (K + SQ_WARPS - 1) / SQ_WARPS;
   const int k0 = w * chunk, k1 = min(K, k0 + chunk);
@@ -872,7 +916,7 @@ void launch_exp_taylor_batched(const SmallDev& sd, const BatchStride& bs, int nb
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
   // dst0 lies in problem 0's Horner buffer or (last step) its exp rows
   exp_taylor_kernel<1><<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst0, bs.Xblk, bs.gam,
-                                       bs.S0, dst_in_g ? bs.G : bs.S0);
+                                       bs.S0, dst_in_g ? bs.G : bs.S0, nullptr, 0.0);
 }
 
 void launch_exp_square_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, int a, int level,
@@ -889,19 +933,19 @@ void launch_z_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, 
 }
 
 void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first, int last,
-                            int src, double* dst, cudaStream_t st) {
-  (void)last;
+                            int src, double* dst, double* gout, double gscale, cudaStream_t st) {
   const int MM = m * m;
   dim3 g((MM + 31) / 32, a + 1);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
   exp_taylor_kernel<KS_WARPS><<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0,
-                                                         0, 0, 0);
+                                                         0, 0, 0, (last && !first) ? gout : nullptr, gscale);
 }
 
-void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, cudaStream_t st) {
+void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, const double* gi,
+                       double* go, cudaStream_t st) {
   const int MM = m * m;
-  exp_square_row_kernel<<<dim3((MM + 31) / 32, a + 1), SQ_WARPS * 32, 0, st>>>(
-      sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride, m, a);
+  exp_square_row_kernel<<<dim3((MM + 31) / 32, a + 1 + (gi != nullptr ? 1 : 0)), SQ_WARPS * 32, 0, st>>>(
+      sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride, m, a, gi, go);
 }
 
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
