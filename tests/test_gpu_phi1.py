@@ -88,10 +88,10 @@ def test_phi1_converges_to_sine_modes(lib, cuda):
 
 @pytest.mark.slow
 def test_phi1_full_size_identity(lib, cuda):
-    """128^3 convection-diffusion, t = 1e-2, m = 40, k = 2, s = 160: the GPU's
-    phi_1(-tA) b satisfies t A x = b - exp(-tA) b (exponential from the
-    Kronecker closed form) to 1e-7 after 10 cycles; the residual amplifies x's
-    relative error by about t ||A|| = 2.4e3."""
+    """128^3 convection-diffusion, t = 1e-2, m = 40, k = 2, s = 160 (the phi_1
+    bench workload): a 20-cycle solve satisfies t A x = b - exp(-tA) b (the
+    exponential from the Kronecker closed form) to 1e-10 relative, and 9 cycles
+    (the bench's count) are within 1e-8 of it."""
     import torch
 
     from paper_2503_22631_gb300 import F_PHI1_NEG, Krylov
@@ -101,9 +101,10 @@ def test_phi1_full_size_identity(lib, cuda):
     b = W.rhs_uniform(A.n, W.SEED)
     kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_PHI1_NEG, t=t, m=40, k=2, s=160, seed=W.SEED, zeta=8, basis=3)
     bd = torch.from_numpy(b).cuda()
-    x = kr.apply(bd, tol=0.0, max_cycles=10)
-    ax = kr.spmv(x)
+    x20 = kr.apply(bd, tol=0.0, max_cycles=20)
+    ax = kr.spmv(x20)
+    x9 = kr.apply(bd, tol=0.0, max_cycles=9)
     torch.cuda.synchronize()
-    lhs = t * ax.cpu().numpy()
     rhs = b - TR.kron_expm_apply(N, 3, (50.0, 50.0, 50.0), t, b)
-    assert _rel(lhs, rhs) <= 1e-7
+    assert _rel(t * ax.cpu().numpy(), rhs) <= 1e-10
+    assert _rel(x9.cpu().numpy(), x20.cpu().numpy()) <= 1e-8
