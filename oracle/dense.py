@@ -18,7 +18,11 @@
   way to evaluate phi functions with an exponential, see Hochbruck and
   Ostermann, "Exponential integrators", Acta Numerica 2010, which the paper
   cites for phi_1).
-* ``f_dense``      f(H) for the four supported kinds.
+* ``cossqrtm``     cos(t sqrt(A)) (the membrane example of Sec. 5, cos(nu t sqrt(L)))
+  as the top-left block of exp(t [[0, I], [-A, 0]]): that matrix propagates
+  u'' = -A u, whose solution is u(t) = cos(t sqrt(A)) u(0) + ..., and the
+  series of both sides agree term by term.
+* ``f_dense``      f(H) for the five supported kinds.
 """
 import math
 from fractions import Fraction
@@ -29,6 +33,7 @@ EXP_NEG = 0      # f(z) = exp(-t z)
 INVSQRT = 1      # f(z) = z^{-1/2}
 INV = 2          # f(z) = 1/z
 PHI1_NEG = 3     # f(z) = phi_1(-t z) = (1 - e^{-t z}) / (t z)
+COS_SQRT = 4     # f(z) = cos(t sqrt(z))
 
 
 def qr_positive(U):
@@ -138,12 +143,24 @@ def phi1m(A):
     return expm(Z)[:n, n:]
 
 
+def cossqrtm(A, t=1.0):
+    """cos(t sqrt(A)): the top-left n x n block of exp(t [[0, I], [-A, 0]])."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    Z = np.zeros((2 * n, 2 * n))
+    Z[:n, n:] = t * np.eye(n)
+    Z[n:, :n] = -t * A
+    return expm(Z)[:n, :n]
+
+
 def f_dense(kind, H, t=1.0):
-    """f(H) for f(z) = exp(-t z), z^{-1/2}, 1/z or phi_1(-t z) (dense, FP64)."""
+    """f(H) for f(z) = exp(-t z), z^{-1/2}, 1/z, phi_1(-t z) or cos(t sqrt(z)) (dense, FP64)."""
     if kind == EXP_NEG:
         return expm(-t * H)
     if kind == PHI1_NEG:
         return phi1m(-t * H)
+    if kind == COS_SQRT:
+        return cossqrtm(H, t)
     if kind == INVSQRT:
         return invsqrtm(H)
     if kind == INV:

@@ -169,7 +169,7 @@ def restarted(A, b, fkind, t, m, k, s, zeta, seed, mode=TRUNC, tol=0.0, max_cycl
     """Approximate f(A) b by the restarted method of the chosen mode.
 
     A       workloads.Csr; b: (n,) float64.
-    fkind   oracle.dense.EXP_NEG (exp(-t z)), PHI1_NEG (phi_1(-t z)), INVSQRT or INV.
+    fkind   oracle.dense.EXP_NEG (exp(-t z)), PHI1_NEG (phi_1(-t z)), COS_SQRT (cos(t sqrt(z))), INVSQRT or INV.
     m, k    restart length and orthogonalization window.
     s, zeta sketch rows and nonzeros per sketch column; seed keys the sketch.
     tol     stop once ||y|| <= tol * ||x|| (or <= tol if abs_tol).

@@ -69,6 +69,17 @@ def sine_mode_phi1(N, c, p, q, t):
     return out.reshape(-1)
 
 
+def sine_mode_cos(N, c, p, q, t):
+    """cos(t sqrt(A)) b for b = sum_l c_l phi_{p_l q_l} on the 5-point Laplacian."""
+    h = 1.0 / (N + 1)
+    ii = np.arange(1, N + 1)
+    lam = (4.0 / h**2) * (np.sin(np.asarray(p) * np.pi * h / 2) ** 2 + np.sin(np.asarray(q) * np.pi * h / 2) ** 2)
+    out = np.zeros((N, N))
+    for cl, pl, ql, ll in zip(c, p, q, lam):
+        out += cl * np.cos(t * np.sqrt(ll)) * np.outer(np.sin(ql * np.pi * ii * h), np.sin(pl * np.pi * ii * h))
+    return out.reshape(-1)
+
+
 def dense_fAb(Adense, b, fkind, t=1.0, symmetric=False):
     """f(A) b on a small dense matrix."""
     if symmetric:
@@ -77,6 +88,8 @@ def dense_fAb(Adense, b, fkind, t=1.0, symmetric=False):
             fl = np.exp(-t * lam)
         elif fkind == dense.PHI1_NEG:
             fl = phi1_neg(t * lam)
+        elif fkind == dense.COS_SQRT:
+            fl = np.cos(t * np.sqrt(lam))
         elif fkind == dense.INVSQRT:
             fl = lam ** -0.5
         else:

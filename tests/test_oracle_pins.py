@@ -198,6 +198,33 @@ def test_phi1m_matches_eigendecomposition():
     assert rel(D.f_dense(D.PHI1_NEG, S, t), ref) < 1e-13
 
 
+def test_cossqrtm_closed_forms():
+    """cos(t sqrt(l)) on a diagonal (cos(0) = 1; a negative l gives cosh), the
+    Jordan block: d/dl cos(t sqrt(l)) = -t sin(t sqrt(l)) / (2 sqrt(l)) on the
+    superdiagonal, and the double-angle identity C(4A) = 2 C(A)^2 - I."""
+    t = 0.9
+    lam = np.array([0.0, 0.3, 2.0, 17.0, 150.0, -0.5])
+    C = D.cossqrtm(np.diag(lam), t)
+    ref = np.where(lam >= 0, np.cos(t * np.sqrt(np.abs(lam))), np.cosh(t * np.sqrt(np.abs(lam))))
+    assert np.allclose(np.diag(C), ref, rtol=1e-13, atol=1e-14)
+    l = 3.0
+    J = np.array([[l, 1.0], [0.0, l]])
+    d = -t * math.sin(t * math.sqrt(l)) / (2 * math.sqrt(l))
+    assert np.allclose(D.cossqrtm(J, t), [[math.cos(t * math.sqrt(l)), d], [0.0, math.cos(t * math.sqrt(l))]],
+                       rtol=1e-13, atol=1e-15)
+    A = W.convdiff(5, 2, (3.0, 1.0)).to_dense() * 1e-2
+    C1 = D.cossqrtm(A, 1.0)
+    assert rel(D.cossqrtm(4.0 * A, 1.0), 2.0 * C1 @ C1 - np.eye(A.shape[0])) < 1e-12
+    assert rel(D.f_dense(D.COS_SQRT, A, 2.0), D.cossqrtm(4.0 * A, 1.0)) < 1e-12
+
+
+def test_cossqrtm_matches_eigendecomposition():
+    S = W.poisson2d(6).to_dense()
+    lam, Q = np.linalg.eigh(S)
+    t = 0.05
+    assert rel(D.f_dense(D.COS_SQRT, S, t), Q @ np.diag(np.cos(t * np.sqrt(lam))) @ Q.T) < 1e-12
+
+
 # ---------------------------------------------------------------- truth -----
 def test_kronecker_truth_matches_dense_exponential():
     """exp(-tA) of the Kronecker-sum grid operator applied by mode products
@@ -275,7 +302,7 @@ def test_single_mode_breaks_down_exactly(mode):
     assert rel(r.x, TR.sine_mode_exp(N, c, p, q, 2e-3)) < 1e-13
 
 
-@pytest.mark.parametrize("fkind", [D.EXP_NEG, D.INV, D.INVSQRT, D.PHI1_NEG])
+@pytest.mark.parametrize("fkind", [D.EXP_NEG, D.INV, D.INVSQRT, D.PHI1_NEG, D.COS_SQRT])
 def test_exact_when_m_reaches_n(fkind):
     """With m = n the Krylov space is the whole space: one cycle is exact."""
     A = W.fem_p1_kuhn(4, 1.0, 2)  # 27 unknowns, SPD
@@ -369,3 +396,16 @@ def test_restarted_phi1_converges_to_sine_modes(mode):
     r = K.restarted(A, b, D.PHI1_NEG, t, 10, 2 if mode == K.TRUNC else 10, 40, 8, 5, mode=mode, tol=1e-13,
                     max_cycles=40)
     assert rel(r.x, TR.sine_mode_phi1(N, c, p, q, t)) < 1e-10
+
+
+@pytest.mark.parametrize("mode", [K.TRUNC, K.RGS])
+def test_restarted_cos_converges_to_sine_modes(mode):
+    """cos(t sqrt(A)) b (the membrane example, Sec. 5) on the 5-point Laplacian
+    for a mixture of eigenmodes: closed form cos(t sqrt(lambda)) per mode."""
+    N = 24
+    A = W.poisson2d(N)
+    b, c, p, q = W.sine_mode_mixture_2d(N, 6, 17)
+    t = 0.02
+    r = K.restarted(A, b, D.COS_SQRT, t, 12, 2 if mode == K.TRUNC else 12, 40, 8, 5, mode=mode, tol=1e-13,
+                    max_cycles=60)
+    assert rel(r.x, TR.sine_mode_cos(N, c, p, q, t)) < 1e-10
