@@ -53,12 +53,14 @@ typedef enum {
 /* f(z); exp(-t z) is Eq. (19)'s heat kernel and the exponential of Sec. 5.1 with
  * the time folded in; phi_1(-t z) = (1 - e^{-t z}) / (t z) is the phi function of
  * Sec. 5 (u(t) = u_0 + t phi_1(-L t) b for the convection-diffusion problem with a
- * constant load); z^{-1/2} and 1/z are extensions (Stieltjes functions). */
+ * constant load); cos(t sqrt(z)) is the membrane example of Sec. 5 (the wave
+ * equation u'' = -L u); z^{-1/2} and 1/z are extensions (Stieltjes functions). */
 typedef enum {
-  KRYLOV_F_EXP_NEG = 0, /* f(z) = exp(-t z) */
-  KRYLOV_F_INVSQRT = 1, /* f(z) = z^{-1/2}  */
-  KRYLOV_F_INV = 2,     /* f(z) = 1/z       */
-  KRYLOV_F_PHI1_NEG = 3 /* f(z) = phi_1(-t z) = (1 - e^{-t z}) / (t z); phi_1(0) = 1 */
+  KRYLOV_F_EXP_NEG = 0,  /* f(z) = exp(-t z) */
+  KRYLOV_F_INVSQRT = 1,  /* f(z) = z^{-1/2}  */
+  KRYLOV_F_INV = 2,      /* f(z) = 1/z       */
+  KRYLOV_F_PHI1_NEG = 3, /* f(z) = phi_1(-t z) = (1 - e^{-t z}) / (t z); phi_1(0) = 1 */
+  KRYLOV_F_COS_SQRT = 4  /* f(z) = cos(t sqrt(z)) (an entire function of z) */
 } krylov_fkind;
 
 typedef struct {

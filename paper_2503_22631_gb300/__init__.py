@@ -16,10 +16,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_EXP_NEG, F_INV, F_INVSQRT, F_PHI1_NEG,
+from ._lib import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, BREAKDOWN_EXACT, F_COS_SQRT, F_EXP_NEG, F_INV, F_INVSQRT, F_PHI1_NEG,
                    NOT_CONVERGED, OK, ORTHO_RGS, ORTHO_TRUNC, KrylovError, status_string)
 
-__all__ = ["Krylov", "KrylovExpm", "krylov_expm", "apply_batched", "sketch_columns", "KrylovError", "status_string", "F_EXP_NEG", "F_INV", "F_INVSQRT", "F_PHI1_NEG",
+__all__ = ["Krylov", "KrylovExpm", "krylov_expm", "apply_batched", "sketch_columns", "KrylovError", "status_string", "F_COS_SQRT", "F_EXP_NEG", "F_INV", "F_INVSQRT", "F_PHI1_NEG",
            "BASIS_F64", "BASIS_F32", "BASIS_BF16", "BASIS_DF64", "ORTHO_TRUNC", "ORTHO_RGS", "OK", "NOT_CONVERGED",
            "BREAKDOWN_EXACT"]
 

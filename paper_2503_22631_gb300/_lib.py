@@ -31,6 +31,7 @@ F_EXP_NEG = 0
 F_INVSQRT = 1
 F_INV = 2
 F_PHI1_NEG = 3
+F_COS_SQRT = 4
 
 # krylov_basis
 BASIS_F64 = 0

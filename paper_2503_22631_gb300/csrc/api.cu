@@ -24,6 +24,10 @@ using namespace krylov;
 namespace {
 
 constexpr double EXP_THETA = 2.0;  // ||B||_1 bound after scaling
+// cos(t sqrt(z)): Taylor degree 14 in A = t^2 H / 4^s with ||A||_1 <= 4: the
+// first omitted term is below 4^15 / 30! = 4e-24
+constexpr int COS_TAYLOR_DEG = 14;
+constexpr double COS_THETA = 4.0;
 // Column-index and value arrays get CSR_PAD zeroed elements past nnz so the
 // step kernels can read them in aligned 16-byte chunks.
 constexpr size_t CSR_PAD = 8;
@@ -283,29 +287,41 @@ int scale_levels_for(double normH) {
   return (int)std::ceil(std::log2(normH / EXP_THETA));
 }
 
+// cos(t sqrt(H)): double-angle steps s with ||t^2 H|| / 4^s <= COS_THETA
+int cos_levels_for(double normA) {
+  if (!(normA > COS_THETA)) return 0;
+  return (int)std::ceil(0.5 * std::log2(normA / COS_THETA));
+}
+
 // Block row a of exp(-t H) at all scale levels 0..sl (scale 2^-sl).
 // Returns the number of kernels launched.
 int exp_row(krylov_handle* h, int a, int sl) {
   const int M = h->m;
   const size_t MM = (size_t)M * M;
-  const double scale = -h->f.t / std::ldexp(1.0, sl);
+  // exp(-tH) and phi_1(-tH): B = -t H / 2^sl, Taylor-Horner S <- S B / k + I,
+  // squarings.  cos(t sqrt(H)): B = -t^2 H / 4^sl, S <- S B / ((2k-1) 2k) + I
+  // (the series of cos(sqrt(A)) in Horner form), double-angle steps.
+  const bool cosm = (h->f.kind == KRYLOV_F_COS_SQRT);
+  const int q = cosm ? COS_TAYLOR_DEG : EXP_TAYLOR_DEG;
+  const double scale = cosm ? -(h->f.t * h->f.t) / std::ldexp(1.0, 2 * sl) : -h->f.t / std::ldexp(1.0, sl);
   double* g0row = h->sd.G + (size_t)a * (a + 1) / 2 * MM;
   int src = 0;
   // phi_1: the extra column of exp([[-tH, e_1], [0, 0]]) rides along (level 0
   // from the Taylor steps, then one vector row per squaring)
   const bool phi = (h->f.kind == KRYLOV_F_PHI1_NEG);
   auto gvec = [&](int lv) { return h->sd.gphi + (size_t)lv * h->gphi_stride; };
-  for (int kdeg = EXP_TAYLOR_DEG; kdeg >= 1; --kdeg) {
-    const int first = (kdeg == EXP_TAYLOR_DEG);
+  for (int kdeg = q; kdeg >= 1; --kdeg) {
+    const int first = (kdeg == q);
+    const double kinv = cosm ? 1.0 / ((2.0 * kdeg - 1.0) * (2.0 * kdeg)) : 1.0 / kdeg;
     double* dst = (kdeg == 1) ? g0row : h->sd.S0 + (size_t)(1 - src) * (size_t)(a + 1) * MM;
-    launch_exp_taylor_step(h->sd, M, a, kdeg, scale, first, kdeg == 1, src, dst,
+    launch_exp_taylor_step(h->sd, M, a, kinv, scale, first, kdeg == 1, src, dst,
                            phi ? gvec(0) + (size_t)a * M : nullptr, std::ldexp(1.0, -sl), h->st);
     src = 1 - src;
   }
   for (int lv = 0; lv < sl; ++lv)
     launch_exp_square(h->sd, M, a, lv, h->level_stride, phi ? gvec(lv) : nullptr, phi ? gvec(lv + 1) : nullptr,
-                      h->st);
-  return EXP_TAYLOR_DEG + sl;
+                      cosm ? 1 : 0, h->st);
+  return q + sl;
 }
 
 struct Operator {
@@ -600,7 +616,8 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   CK(cudaEventRecord(e0, st));
 
   int levels_needed = 1;
-  if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG) levels_needed = std::max(1, h->cap_levels);
+  if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG || h->f.kind == KRYLOV_F_COS_SQRT)
+    levels_needed = std::max(1, h->cap_levels);
   krylov_status cs = ensure_small_capacity(h, max_cycles, levels_needed);
   if (cs != KRYLOV_OK) return cs;
 
@@ -699,14 +716,16 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       stats.launches += 2;
     }
     const int a = c - 1;
-    if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG) {
+    if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG || h->f.kind == KRYLOV_F_COS_SQRT) {
       CK(cudaMemcpyAsync(h->h_scal, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       maxX = std::max(maxX, h->h_scal[2]);
       maxG = std::max(maxG, h->h_scal[3]);
       stats.kappa_T_max = std::max(stats.kappa_T_max, h->h_scal[4]);
       if (!std::isfinite(maxX) || !std::isfinite(maxG)) return KRYLOV_ENONFINITE;
-      const int need = scale_levels_for(maxX + maxG);
+      // ||t X||_1 + |t gamma| bounds ||t H||_1; cos(t sqrt(H)) scales t^2 H
+      const int need = (h->f.kind == KRYLOV_F_COS_SQRT) ? cos_levels_for(std::fabs(h->f.t) * (maxX + maxG))
+                                                         : scale_levels_for(maxX + maxG);
       if (need > s_lv) {
         s_lv = need;
         cs = ensure_small_capacity(h, max_cycles, s_lv + 1);
@@ -1126,7 +1145,8 @@ krylov_status run_instance(krylov_handle* h, int n_rhs, const double* B, double*
   }
   krylov_status worst = KRYLOV_OK;
   const double t_old = h->f.t;
-  if (t_new && (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG)) h->f.t = *t_new;
+  if (t_new && (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG || h->f.kind == KRYLOV_F_COS_SQRT))
+    h->f.t = *t_new;
   if (cudaEventRecord(ev, orig) != cudaSuccess || cudaStreamWaitEvent(bs, ev, 0) != cudaSuccess) worst = KRYLOV_ECUDA;
   h->st = bs;
   if (worst == KRYLOV_OK && !h->stage_b) {
@@ -1244,7 +1264,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   if (opt.ortho == KRYLOV_ORTHO_RGS && opt.basis_dtype != KRYLOV_BASIS_F64 && opt.basis_dtype != KRYLOV_BASIS_DF64)
     return KRYLOV_EUNSUPPORTED;
   if (f.kind != KRYLOV_F_EXP_NEG && f.kind != KRYLOV_F_INV && f.kind != KRYLOV_F_INVSQRT &&
-      f.kind != KRYLOV_F_PHI1_NEG)
+      f.kind != KRYLOV_F_PHI1_NEG && f.kind != KRYLOV_F_COS_SQRT)
     return KRYLOV_EINVAL;
   if (!std::isfinite(f.t)) return KRYLOV_EINVAL;
 

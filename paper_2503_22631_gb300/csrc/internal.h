@@ -256,14 +256,16 @@ void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int h
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
                    int has_next, int cycle, int kw, double t, cudaStream_t st);
+// One Horner step S <- S B kinv + I for block row a (B = scale H).
 // gout (phi_1, else null): where the last step stores the Taylor polynomial's
 // extra column for block row a, scaled by gscale = 2^-s
-void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first,
+void launch_exp_taylor_step(const SmallDev& sd, int m, int a, double kinv, double scale, int first,
                             int last, int src, double* dst, double* gout, double gscale, cudaStream_t st);
 // gi/go (phi_1, else null): the phi_1 vectors of block rows 0..a at the input
-// level and of block row a at the output level
+// level and of block row a at the output level; dbl (cos(t sqrt(z))): the
+// double-angle step 2 C^2 - I instead of a square
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, const double* gi,
-                       double* go, cudaStream_t st);
+                       double* go, int dbl, cudaStream_t st);
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st);
 void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double u0, double hq,
                           int nodes, cudaStream_t st);

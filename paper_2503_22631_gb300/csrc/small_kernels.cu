@@ -622,10 +622,14 @@ constexpr int SQ_WARPS = 8;
 // of the new vector is sum_{l <= a} G[a][l] g[l] + g[a], the same flattened
 // (l, p) sum split over the warps (g[l]: the m-vector of block row l at the
 // input level, gi; output go).
+//
+// dbl (cos(t sqrt(z))): the double-angle step C(4A) = 2 C(A)^2 - I instead of
+// a plain square: the block sum is doubled and the identity subtracted on the
+// diagonal block.
 __global__ void __launch_bounds__(SQ_WARPS * 32) exp_square_row_kernel(const double* __restrict__ Gi,
                                                                      double* __restrict__ Go, int M, int a,
                                                                      const double* __restrict__ gi,
-                                                                     double* __restrict__ go) {
+                                                                     double* __restrict__ go, int dbl) {
   __shared__ double red[SQ_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j = blockIdx.y;
@@ -680,6 +684,10 @@ __global__ void __launch_bounds__(SQ_WARPS * 32) exp_square_row_kernel(const dou
     double sum = red[0][lane];
 #pragma unroll
     for (int q = 1; q < SQ_WARPS; ++q) sum += red[q][lane];
+    if (dbl) {
+      sum *= 2.0;
+      if (j == a && e % M == e / M) sum -= 1.0;
+    }
     Go[(rowa + j) * MM + e] = sum;
   }
 }
@@ -932,20 +940,20 @@ void launch_z_batched(const SmallDev& sd, const BatchStride& bs, int nb, int m, 
   z_kernel<<<nb, 256, 0, st>>>(sd, m, m_eff, fcol0, bs, fcol_stride);
 }
 
-void launch_exp_taylor_step(const SmallDev& sd, int m, int a, int kdeg, double scale, int first, int last,
+void launch_exp_taylor_step(const SmallDev& sd, int m, int a, double kinv, double scale, int first, int last,
                             int src, double* dst, double* gout, double gscale, cudaStream_t st) {
   const int MM = m * m;
   dim3 g((MM + 31) / 32, a + 1);
   const double* Sold = sd.S0 + (size_t)src * (size_t)(a + 1) * MM;
-  exp_taylor_kernel<KS_WARPS><<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, 1.0 / kdeg, scale, first, Sold, dst, 0,
-                                                         0, 0, 0, (last && !first) ? gout : nullptr, gscale);
+  exp_taylor_kernel<KS_WARPS><<<g, KS_THREADS, 0, st>>>(sd.Xblk, sd.gam, m, a, kinv, scale, first, Sold, dst, 0, 0,
+                                                         0, 0, (last && !first) ? gout : nullptr, gscale);
 }
 
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, const double* gi,
-                       double* go, cudaStream_t st) {
+                       double* go, int dbl, cudaStream_t st) {
   const int MM = m * m;
   exp_square_row_kernel<<<dim3((MM + 31) / 32, a + 1 + (gi != nullptr ? 1 : 0)), SQ_WARPS * 32, 0, st>>>(
-      sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride, m, a, gi, go);
+      sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride, m, a, gi, go, dbl);
 }
 
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
