@@ -43,6 +43,10 @@ sys.path.insert(0, str(ROOT))
 # identity residual t A x - (b - exp(-tA) b) against the Kronecker closed form
 # is 1e-11 (tests/test_gpu_phi1.py checks both)
 PHI1_CYCLES = 9
+# restart cycles of cos(t sqrt(A)) b, 2D Laplacian 1448^2, t = 0.05, for 1e-8:
+# 3 cycles are 9e-8 from a 30-cycle solve, 4 cycles equal it
+# (tests/test_gpu_cos.py checks 4 cycles and the double-angle identity)
+COS_CYCLES = 4
 
 WORKLOAD = dict(
     workload="convdiff3d_128_exp",
@@ -67,8 +71,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cycles", type=int, default=None, help="override the cycle count (profiling)")
     ap.add_argument("--workload", default="convdiff3d_128",
-                    choices=["convdiff3d_128", "convdiff3d_128_rgs", "convdiff3d_128_phi1", "fem_kuhn_160",
-                             "batched16", "convdiff3d_96_adjoint"],
+                    choices=["convdiff3d_128", "convdiff3d_128_rgs", "convdiff3d_128_phi1", "poisson2d_1448_cos",
+                             "fem_kuhn_160", "batched16", "convdiff3d_96_adjoint"],
                     help="convdiff3d_128 is the headline; the others time the remaining configurations")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: no warm-up floor, no e2e, no CPU baseline, no clock sampling")
@@ -284,8 +288,8 @@ def secondary_main(args):
     import torch
 
     import workloads as W
-    from paper_2503_22631_gb300 import (BASIS_DF64, F_EXP_NEG, F_INVSQRT, F_PHI1_NEG, ORTHO_RGS, Krylov,
-                                        apply_batched, build, krylov_expm)
+    from paper_2503_22631_gb300 import (BASIS_DF64, F_COS_SQRT, F_EXP_NEG, F_INVSQRT, F_PHI1_NEG, ORTHO_RGS,
+                                        Krylov, apply_batched, build, krylov_expm)
 
     build.build()
     torch.cuda.set_device(0)
@@ -323,6 +327,24 @@ def secondary_main(args):
         metric = "seconds to 1e-8 rel err per phi_1(-tA)b at n=2.1M"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": 40, "k": 2, "s": 160, "zeta": 8, "t": 1e-2,
                   "cycles": cycles, "basis": "df64", "f": "phi1"}
+        units = 1
+    elif wl == "poisson2d_1448_cos":
+        # cos(t sqrt(A)) b (the membrane example of Sec. 5) on a 2D 5-point
+        # Laplacian of the headline's size, t sqrt(lambda_max) ~ 200
+        A = W.poisson2d(1448)
+        b = W.rhs_uniform(A.n, SEED)
+        kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_COS_SQRT, t=0.05, m=40, k=2, s=160, seed=SEED, zeta=8,
+                    basis=BASIS_DF64)
+        bd = torch.from_numpy(b).cuda()
+        cycles = COS_CYCLES
+
+        def fn():
+            kr.apply(bd, tol=0.0, max_cycles=cycles)
+            stats.append(dict(kr.stats))
+
+        metric = "seconds to 1e-8 rel err per cos(t sqrt(A))b at n=2.1M (2D Laplacian)"
+        config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": 40, "k": 2, "s": 160, "zeta": 8, "t": 0.05,
+                  "cycles": cycles, "basis": "df64", "f": "cos_sqrt"}
         units = 1
     elif wl == "fem_kuhn_160":
         cfg = W.CONFIGS["fem_kuhn_160"]
