@@ -60,6 +60,23 @@ struct SegPlan {
   int lcap = 0;
 };
 
+// Rows with more nonzeros than this go to the long-row product kernel
+// (power-law operators with the float-float basis): a row per thread would
+// leave one thread with a hub's tens of thousands of nonzeros.
+constexpr int LONG_ROW = 256;
+
+struct LongRows {
+  int n_long = 0;
+  int* rows = nullptr;      // [n_long] longest first
+  int* rp = nullptr;        // the operator with these rows emptied
+  int* ci = nullptr;
+  float* val32 = nullptr;
+  float2* valff = nullptr;
+  int tma_cap = 0;          // staged span per tile of the emptied operator (0: no staging)
+  int grid = 0;             // CTAs of the long-row kernel
+  double* part = nullptr;   // [grid][8] its scalar partials
+};
+
 // Host construction of a segment plan from a host CSR: per 256-row tile the
 // sorted distinct columns are cut into pieces wherever two consecutive columns
 // are more than SEG_GAP apart; each piece is widened to an even start and an
@@ -174,6 +191,7 @@ struct krylov_handle {
   int16_t* dcol = nullptr;         // col - row per nonzero of A (bandwidth < 2^15, staged float-float product)
   int16_t* dcolt = nullptr;        // the same for A^T
   SegPlan seg_a, seg_t;            // segment plans of A and A^T (float-float basis)
+  LongRows long_a, long_t;         // long rows of A and A^T (float-float basis, power-law operators)
   int* rpt = nullptr;
   int* cit = nullptr;
   double* valt = nullptr;
@@ -374,6 +392,78 @@ krylov_status install_delta16(krylov_handle* h, const int* rp_dev, const int* ci
   return KRYLOV_OK;
 }
 
+// Long rows of an operator held on the device: if any row has more than
+// LONG_ROW nonzeros (float-float basis), build the operator with those rows
+// emptied (same row count, so every other kernel keeps its layout), the list
+// of long rows (longest first), the staged span of the emptied operator's
+// tiles and the long-row kernel's grid and partials.
+krylov_status install_long_rows(krylov_handle* h, LongRows& lr, const int* rp_dev, const int* ci_dev,
+                                const float* v32_dev, const float2* vff_dev) {
+  lr = LongRows{};
+  if (h->opt.basis_dtype != 3 || h->nnz == 0) return KRYLOV_OK;
+  const int n = h->n;
+  const size_t nnz = (size_t)h->nnz;
+  std::vector<int> rp((size_t)n + 1);
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(rp.data(), rp_dev, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+  std::vector<int> longs;
+  for (int i = 0; i < n; ++i)
+    if (rp[(size_t)i + 1] - rp[i] > LONG_ROW) longs.push_back(i);
+  if (longs.empty()) return KRYLOV_OK;
+  std::stable_sort(longs.begin(), longs.end(),
+                   [&](int a, int b) { return rp[(size_t)a + 1] - rp[a] > rp[(size_t)b + 1] - rp[b]; });
+  std::vector<char> is_long((size_t)n, 0);
+  for (int i : longs) is_long[i] = 1;
+  std::vector<int> ci(nnz);
+  CK(cudaMemcpy(ci.data(), ci_dev, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+  std::vector<float> v32(v32_dev ? nnz : 0);
+  std::vector<float2> vff(vff_dev ? nnz : 0);
+  if (v32_dev) CK(cudaMemcpy(v32.data(), v32_dev, sizeof(float) * nnz, cudaMemcpyDeviceToHost));
+  if (vff_dev) CK(cudaMemcpy(vff.data(), vff_dev, sizeof(float2) * nnz, cudaMemcpyDeviceToHost));
+  std::vector<int> rps((size_t)n + 1 + RP_PAD, 0);
+  std::vector<int> cis;
+  std::vector<float> v32s;
+  std::vector<float2> vffs;
+  cis.reserve(nnz);
+  for (int i = 0; i < n; ++i) {
+    if (!is_long[i]) {
+      for (int e = rp[i]; e < rp[(size_t)i + 1]; ++e) {
+        cis.push_back(ci[e]);
+        if (v32_dev) v32s.push_back(v32[e]);
+        if (vff_dev) vffs.push_back(vff[e]);
+      }
+    }
+    rps[(size_t)i + 1] = (int)cis.size();
+  }
+  const size_t ns = cis.size();
+  for (size_t q = 0; q < CSR_PAD; ++q) {
+    cis.push_back(0);
+    if (v32_dev) v32s.push_back(0.f);
+    if (vff_dev) vffs.push_back(make_float2(0.f, 0.f));
+  }
+  lr.n_long = (int)longs.size();
+  CK(dalloc(h, &lr.rows, longs.size()));
+  CK(dalloc(h, &lr.rp, rps.size()));
+  CK(dalloc(h, &lr.ci, cis.size()));
+  CK(cudaMemcpy(lr.rows, longs.data(), sizeof(int) * longs.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(lr.rp, rps.data(), sizeof(int) * rps.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(lr.ci, cis.data(), sizeof(int) * cis.size(), cudaMemcpyHostToDevice));
+  if (v32_dev) {
+    CK(dalloc(h, &lr.val32, v32s.size()));
+    CK(cudaMemcpy(lr.val32, v32s.data(), sizeof(float) * v32s.size(), cudaMemcpyHostToDevice));
+  }
+  if (vff_dev) {
+    CK(dalloc(h, &lr.valff, vffs.size()));
+    CK(cudaMemcpy(lr.valff, vffs.data(), sizeof(float2) * vffs.size(), cudaMemcpyHostToDevice));
+  }
+  (void)ns;
+  CK(tile_span_max(n, lr.rp, h->d_flag, h->h_flags, h->st));
+  lr.tma_cap = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 8) : 0;
+  lr.grid = std::max(1, std::min(lr.n_long, h->num_sms * 8));
+  CK(dalloc(h, &lr.part, (size_t)lr.grid * 8));
+  return KRYLOV_OK;
+}
+
 krylov_status build_transpose(krylov_handle* h) {
   if (h->have_t) return KRYLOV_OK;
   int* work = nullptr;
@@ -401,12 +491,17 @@ krylov_status build_transpose(krylov_handle* h) {
   h->tma_cap_t = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 8) : 0;
   if (h->opt.basis_dtype == 3) {
     const int vals32 = h->vals_exact_f32 && h->opt.narrow_values_if_exact;
-    krylov_status ps = install_seg_plan(h, h->seg_t, h->rpt, h->cit);
+    krylov_status ps = install_long_rows(h, h->long_t, h->rpt, h->cit, h->valt32, h->valtff);
     if (ps != KRYLOV_OK) return ps;
-    ps = install_delta16(h, h->rpt, h->cit, &h->dcolt);
-    if (ps != KRYLOV_OK) return ps;
+    if (h->long_t.n_long == 0) {  // plans describe the full operator
+      ps = install_seg_plan(h, h->seg_t, h->rpt, h->cit);
+      if (ps != KRYLOV_OK) return ps;
+      ps = install_delta16(h, h->rpt, h->cit, &h->dcolt);
+      if (ps != KRYLOV_OK) return ps;
+    }
     const SegPlan& sp = h->seg_t;
-    h->grid_spmv_t = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap_t, sp.seg ? sp.seg_cap : 0,
+    const int tcap = h->long_t.n_long ? h->long_t.tma_cap : h->tma_cap_t;
+    h->grid_spmv_t = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, tcap, sp.seg ? sp.seg_cap : 0,
                                                                         sp.lcap),
                                           std::min(h->part_cap, (h->n + STEP_THREADS - 1) / STEP_THREADS)));
   }
@@ -476,6 +571,24 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
     L.lcol = sp.lcol;
     L.seg_cap = sp.seg_cap;
     L.lcap = sp.lcap;
+  }
+  if (basis == 3) {
+    const LongRows& lr = transpose ? h->long_t : h->long_a;
+    if (lr.n_long > 0) {  // the product runs on the emptied operator, then on the long rows
+      L.rp_full = L.row_ptr;
+      L.col_full = L.col;
+      L.val_full = L.val;
+      L.row_ptr = lr.rp;
+      L.col = lr.ci;
+      L.val = use32 ? (const void*)lr.val32 : (const void*)lr.valff;
+      L.tma_cap = lr.tma_cap;
+      L.dcol = nullptr;
+      L.seg = nullptr;
+      L.n_long = lr.n_long;
+      L.long_rows = lr.rows;
+      L.grid_long = lr.grid;
+      L.part_long = lr.part;
+    }
   }
   L.sk_tab = h->sk_tab;
   L.sk_mode = h->sk_mode;
@@ -1372,12 +1485,17 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   h->allocs.push_back(h->sk_part);
   h->grid_spmv = h->grid;
   if (opt.basis_dtype == 3) {
-    krylov_status ps = install_seg_plan(h, h->seg_a, h->rp, h->ci);
+    krylov_status ps = install_long_rows(h, h->long_a, h->rp, h->ci, h->val32, h->valff);
     if (ps != KRYLOV_OK) return fail(ps);
-    ps = install_delta16(h, h->rp, h->ci, &h->dcol);
-    if (ps != KRYLOV_OK) return fail(ps);
+    if (h->long_a.n_long == 0) {  // plans describe the full operator
+      ps = install_seg_plan(h, h->seg_a, h->rp, h->ci);
+      if (ps != KRYLOV_OK) return fail(ps);
+      ps = install_delta16(h, h->rp, h->ci, &h->dcol);
+      if (ps != KRYLOV_OK) return fail(ps);
+    }
     const SegPlan& sp = h->seg_a;
-    h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, h->tma_cap, sp.seg ? sp.seg_cap : 0,
+    const int tcap = h->long_a.n_long ? h->long_a.tma_cap : h->tma_cap;
+    h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, tcap, sp.seg ? sp.seg_cap : 0,
                                                                       sp.lcap),
                                         (n + STEP_THREADS - 1) / STEP_THREADS));
   }

@@ -64,6 +64,18 @@ struct StepLaunch {
   int tma_cap;       // staged nonzeros per 256-row tile (0: no bulk-copy staging)
   const int16_t* dcol;  // [nnz + 8] col - row per nonzero when the bandwidth is below 2^15 (staged
                         // product kernel: 2 bytes per column instead of 4), else null
+  // Rows too long for a row per thread (power-law operators, float-float
+  // basis): row_ptr/col/val above then describe a copy of the operator with
+  // these rows emptied, whose product kernel gives p_i = 0 there (no dot
+  // contribution) and leaves the reduction to ff_spmv_long_kernel, which forms
+  // the long rows from the full operator with a CTA per row and reduces.
+  int n_long;                 // 0: no long rows (everything below is unused)
+  const int* long_rows;       // [n_long] row indices, longest first
+  const int* rp_full;         // full operator
+  const int* col_full;
+  const void* val_full;       // float or float2 like val
+  int grid_long;              // CTAs of the long-row kernel
+  double* part_long;          // [grid_long][2 + MAX_WINDOW] its scalar partials
   int grid_spmv;     // CTAs of the separate product kernel (float-float basis)
   int rows_spmv;     // rows per CTA of that kernel (a multiple of 256)
   int rgs;           // 1: randomized Gram-Schmidt cycle (the product kernel forms p and ||p||^2 only)

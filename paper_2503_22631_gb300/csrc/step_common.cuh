@@ -231,6 +231,27 @@ __device__ __forceinline__ float2 prod_pe(float2 a, ff w) {
 }
 
 // Block-wide float-float sum, result (as double) in thread 0.
+// Block-wide float-float sum in a fixed order (warp shuffle tree, then the
+// warp sums in warp order), kept as a pair; valid in thread 0.
+__device__ __forceinline__ ff block_sum_ff_pair(ff v, float* sh_hi, float* sh_lo) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const ff u{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+    v = ff_add(v, u);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh_hi[wid] = v.hi;
+    sh_lo[wid] = v.lo;
+  }
+  __syncthreads();
+  ff a{0.f, 0.f};
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = ff_add(a, ff{sh_hi[w], sh_lo[w]});
+  return a;
+}
+
 __device__ __forceinline__ double block_sum_ff(ff v, float* sh_hi, float* sh_lo) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

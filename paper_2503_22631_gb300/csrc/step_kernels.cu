@@ -788,6 +788,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
     v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
     if (threadIdx.x == 0) part[2 + q] = v;
   }
+  if (L.n_long > 0) return;  // the long-row kernel reduces this step
   if (!last_block_flag(cd.counter, &s_last)) return;
   for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
     const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
@@ -963,6 +964,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
     v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
     if (threadIdx.x == 0) part[2 + q] = v;
   }
+  if (L.n_long > 0) return;  // the long-row kernel reduces this step
   if (!last_block_flag(cd.counter, &s_last)) return;
   for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
     const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
@@ -1203,6 +1205,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const Step
     v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
     if (threadIdx.x == 0) part[2 + q] = v;
   }
+  if (L.n_long > 0) return;  // the long-row kernel reduces this step
   if (!last_block_flag(cd.counter, &s_last)) return;
   for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
     const double tq = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
@@ -1215,10 +1218,89 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const Step
   }
 }
 
+// ---------------------------------------------------------------------------
+// Long rows of a power-law operator (float-float basis).  Runs after the
+// product kernel of the emptied operator (which gave p_i = 0 on these rows
+// and kept its partials): each CTA takes long rows r = blockIdx.x,
+// blockIdx.x + grid, ... (longest first, so the longest rows start at once),
+// its threads stride over the row's nonzeros in the full operator with
+// float-float products, and a fixed block tree sums them into p_i, which
+// overwrites the zero; thread 0 adds p_i's share of ||p||^2 and of the
+// window dots.  The last CTA reduces both kernels' partials (the emptied
+// operator's CTAs, then these, each in CTA order) and runs the reducer.
+template <typename AT, int KW>
+__global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLaunch L, const CycleDev cd) {
+  __shared__ float rhi[32], rlo[32];
+  __shared__ int s_last;
+  __shared__ double tot[NQ];
+  pdl_wait();  // w_j and the products of the other rows are complete
+  if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
+  const int j = L.j;
+  const float2* W = static_cast<const float2*>(L.W);
+  const float2* Wj = W + (int64_t)j * L.ldw;
+  const AT* val = static_cast<const AT*>(L.val_full);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = L.rgs ? 0 : j - dlo + 1;
+  const float2* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
+  ffacc acc_pi;
+  ffacc acc_dot[KW];
+  for (int r = blockIdx.x; r < L.n_long; r += gridDim.x) {
+    const int i = __ldg(L.long_rows + r);
+    const int e0 = __ldg(L.rp_full + i), e1 = __ldg(L.rp_full + i + 1);
+    ffacc acc;
+#pragma unroll 4
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += (int)blockDim.x)
+      acc_val(acc, val[e], ld_ff(Wj + __ldg(L.col_full + e)));
+    const ff p = block_sum_ff_pair(acc.result(), rhi, rlo);
+    if (threadIdx.x == 0) {
+      st_ff(static_cast<float2*>(L.p_out) + i, p);
+      acc_pi.add_prod(p, p);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) acc_dot[q].add_prod(ld_ff(Wd[q] + i), p);
+    }
+  }
+  pdl_trigger();
+  if (threadIdx.x == 0) {
+    double* part = L.part_long + (size_t)blockIdx.x * NQ;
+    part[1] = ff_to_double(acc_pi.result());
+#pragma unroll
+    for (int q = 0; q < KW; ++q)
+      if (q < nd) part[2 + q] = ff_to_double(acc_dot[q].result());
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    double t = 0.0;
+    if (q >= 1 && q < 2 + nd) {
+      t = warp_sum_partials(L.part, L.grid_spmv, NQ, q);
+      t += warp_sum_partials(L.part_long, (int)gridDim.x, NQ, q);
+    }
+    if ((threadIdx.x & 31) == 0) tot[q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
+    if (threadIdx.x == 0) *cd.counter = 0u;
+  }
+}
+
 constexpr size_t FF_STAGE_SMEM = (size_t)(STEP_THREADS / 32) * STAGE * sizeof(float2);
 
 template <typename AT, int KW>
+void launch_ff_spmv_main(const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
+
+// The product of a step: the kernel of the (possibly emptied) operator, then,
+// for a power-law operator, the long-row kernel that completes and reduces it.
+template <typename AT, int KW>
 void launch_ff_spmv_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  launch_ff_spmv_main<AT, KW>(L, cd, st);
+  if (L.n_long > 0) launch_pdl(ff_spmv_long_kernel<AT, KW>, L.grid_long, 0, st, L, cd);
+}
+
+template <typename AT, int KW>
+void launch_ff_spmv_main(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
   if (L.seg != nullptr) {
     auto k = ff_spmv_seg_kernel<AT, KW>;
     const size_t smem = 2 * seg_stage_bytes<AT>(L.lcap, L.seg_cap);

@@ -409,3 +409,30 @@ def test_restarted_cos_converges_to_sine_modes(mode):
     r = K.restarted(A, b, D.COS_SQRT, t, 12, 2 if mode == K.TRUNC else 12, 40, 8, 5, mode=mode, tol=1e-13,
                     max_cycles=60)
     assert rel(r.x, TR.sine_mode_cos(N, c, p, q, t)) < 1e-10
+
+
+def test_rmat_laplacian_properties():
+    """The graph stand-in: symmetric, zero row sums, diagonal = degree,
+    off-diagonals -1, power-law rows (the longest far above the mean)."""
+    L = W.rmat_laplacian(12, 16, 5)
+    Dn = L.to_dense()
+    assert np.array_equal(Dn, Dn.T)
+    assert np.abs(Dn.sum(axis=1)).max() == 0.0
+    off = Dn - np.diag(np.diag(Dn))
+    assert set(np.unique(off)) <= {-1.0, 0.0}
+    assert np.array_equal(np.diag(Dn), -off.sum(axis=1))
+    deg = np.diff(L.row_ptr) - 1
+    assert deg.max() > 256 and deg.max() > 20 * deg.mean()
+
+
+def test_heat_kernel_on_graph_conserves_mass():
+    """exp(-tL) x_0 with 1^T L = 0: the total probability stays 1 and the
+    uniform vector is stationary (oracle, restarted, float64)."""
+    L = W.rmat_laplacian(10, 8, 3)
+    x0 = W.rhs_probability(L.n, 4)
+    r = K.restarted(L, x0, D.EXP_NEG, 0.1, 20, 2, 60, 8, 3, mode=K.TRUNC, tol=1e-13, max_cycles=60)
+    assert abs(r.x.sum() - 1.0) < 1e-12
+    assert rel(r.x, TR.dense_fAb(L.to_dense(), x0, D.EXP_NEG, 0.1, symmetric=True)) < 1e-10
+    ones = np.ones(L.n)
+    r1 = K.restarted(L, ones, D.EXP_NEG, 0.1, 20, 2, 60, 8, 3, mode=K.TRUNC, tol=0.0, max_cycles=2)
+    assert rel(r1.x, ones) < 1e-13

@@ -37,6 +37,8 @@ __all__ = [
     "rhs_uniform",
     "sine_mode_mixture_2d",
     "batched_instances",
+    "rmat_laplacian",
+    "rhs_probability",
     "CONFIGS",
 ]
 
@@ -315,6 +317,53 @@ def batched_matrix(inst) -> Csr:
 # The five workloads (inputs only).  Seeds are fixed so every consumer reads the
 # same bytes.
 SEED = 20250331
+def rmat_laplacian(scale: int, edge_factor: int, seed: int, abc=(0.57, 0.19, 0.19)) -> Csr:
+    """Out-degree Laplacian of an undirected R-MAT graph (the Graph500 Kronecker
+    generator's recursive quadrant choice; a stand-in for the paper's graph
+    networks, Sec. 5): L[i, i] = number of neighbours of i, L[i, j] = -1 per
+    edge, 2^scale nodes, edge_factor 2^scale drawn edges before self loops and
+    duplicates are dropped and the edge set is symmetrized.  Every row stores its
+    diagonal (0 for an isolated node).  Power-law degrees: at scale 20 the largest
+    row has ~65,000 entries and rows longer than 256 entries hold ~60 % of them.
+    """
+    n = 1 << scale
+    m = edge_factor * n
+    a, b, c = abc
+    rng = np.random.default_rng(seed)
+    src = np.zeros(m, dtype=np.int64)
+    dst = np.zeros(m, dtype=np.int64)
+    for lvl in range(scale):  # one bit of both endpoints per level
+        r = rng.random(m, dtype=np.float32)
+        src |= (r >= a + b).astype(np.int64) << lvl
+        dst |= (((r >= a) & (r < a + b)) | (r >= a + b + c)).astype(np.int64) << lvl
+    keep = src != dst
+    key = np.concatenate([src[keep] * n + dst[keep], dst[keep] * n + src[keep]])
+    key.sort()
+    first = np.ones(key.size, dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    key = key[first]
+    rows = key // n
+    cols = key % n
+    deg = np.bincount(rows, minlength=n)
+    # insert the diagonal of every row at its sorted position
+    diag_key = np.arange(n, dtype=np.int64) * n + np.arange(n, dtype=np.int64)
+    allk = np.concatenate([key, diag_key])
+    order = np.argsort(allk, kind="stable")
+    allk = allk[order]
+    vals = np.concatenate([-np.ones(key.size), deg.astype(np.float64)])[order]
+    rows = allk // n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    return Csr(n, row_ptr.astype(np.int32), (allk % n).astype(np.int32), vals)
+
+
+def rhs_probability(n: int, seed: int) -> np.ndarray:
+    """x_0 = y / ||y||_1 with y ~ U(0, 1) i.i.d. (the paper's initial
+    distribution on a graph, Sec. 5)."""
+    y = np.random.default_rng(seed).random(n)
+    return y / y.sum()
+
+
 CONFIGS = {
     "poisson2d_64": dict(matrix=lambda: poisson2d(64), t=1e-3, m=30, k=2, s=60, zeta=8,
                          rhs=lambda n: rhs_normal(n, SEED, normalize=True), tol=1e-10),
