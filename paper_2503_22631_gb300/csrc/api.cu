@@ -62,11 +62,16 @@ struct SegPlan {
 
 // Rows with more nonzeros than this go to the long-row product kernel
 // (power-law operators with the float-float basis): a row per thread would
-// leave one thread with a hub's tens of thousands of nonzeros.
-constexpr int LONG_ROW = 256;
+// leave one thread with a hub's tens of thousands of nonzeros.  48 keeps the
+// emptied operator's 256-row tiles within the staged kernel's span on the
+// R-MAT graphs (the largest tile: 3512 nonzeros at 2^20 nodes).  Long rows
+// with more than LONG_ROW_CTA nonzeros take a CTA each, the others a warp.
+constexpr int LONG_ROW = 48;
+constexpr int LONG_ROW_CTA = 1024;
 
 struct LongRows {
   int n_long = 0;
+  int n_big = 0;            // the first n_big rows have more than LONG_ROW_CTA nonzeros
   int* rows = nullptr;      // [n_long] longest first
   int* rp = nullptr;        // the operator with these rows emptied
   int* ci = nullptr;
@@ -435,13 +440,13 @@ krylov_status install_long_rows(krylov_handle* h, LongRows& lr, const int* rp_de
     }
     rps[(size_t)i + 1] = (int)cis.size();
   }
-  const size_t ns = cis.size();
   for (size_t q = 0; q < CSR_PAD; ++q) {
     cis.push_back(0);
     if (v32_dev) v32s.push_back(0.f);
     if (vff_dev) vffs.push_back(make_float2(0.f, 0.f));
   }
   lr.n_long = (int)longs.size();
+  while (lr.n_big < lr.n_long && rp[(size_t)longs[lr.n_big] + 1] - rp[longs[lr.n_big]] > LONG_ROW_CTA) ++lr.n_big;
   CK(dalloc(h, &lr.rows, longs.size()));
   CK(dalloc(h, &lr.rp, rps.size()));
   CK(dalloc(h, &lr.ci, cis.size()));
@@ -456,10 +461,9 @@ krylov_status install_long_rows(krylov_handle* h, LongRows& lr, const int* rp_de
     CK(dalloc(h, &lr.valff, vffs.size()));
     CK(cudaMemcpy(lr.valff, vffs.data(), sizeof(float2) * vffs.size(), cudaMemcpyHostToDevice));
   }
-  (void)ns;
   CK(tile_span_max(n, lr.rp, h->d_flag, h->h_flags, h->st));
   lr.tma_cap = (h->h_flags[0] <= TMA_MAX_CAP) ? std::max(h->h_flags[0], 8) : 0;
-  lr.grid = std::max(1, std::min(lr.n_long, h->num_sms * 8));
+  lr.grid = std::max(1, std::min(std::max(lr.n_big, (lr.n_long + 7) / 8), h->num_sms * 8));
   CK(dalloc(h, &lr.part, (size_t)lr.grid * 8));
   return KRYLOV_OK;
 }
@@ -585,6 +589,7 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
       L.dcol = nullptr;
       L.seg = nullptr;
       L.n_long = lr.n_long;
+      L.n_big = lr.n_big;
       L.long_rows = lr.rows;
       L.grid_long = lr.grid;
       L.part_long = lr.part;

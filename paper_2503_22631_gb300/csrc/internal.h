@@ -70,6 +70,7 @@ struct StepLaunch {
   // contribution) and leaves the reduction to ff_spmv_long_kernel, which forms
   // the long rows from the full operator with a CTA per row and reduces.
   int n_long;                 // 0: no long rows (everything below is unused)
+  int n_big;                  // the first n_big long rows take a CTA each, the others a warp each
   const int* long_rows;       // [n_long] row indices, longest first
   const int* rp_full;         // full operator
   const int* col_full;

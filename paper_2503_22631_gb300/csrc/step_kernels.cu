@@ -1221,13 +1221,15 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const Step
 // ---------------------------------------------------------------------------
 // Long rows of a power-law operator (float-float basis).  Runs after the
 // product kernel of the emptied operator (which gave p_i = 0 on these rows
-// and kept its partials): each CTA takes long rows r = blockIdx.x,
-// blockIdx.x + grid, ... (longest first, so the longest rows start at once),
-// its threads stride over the row's nonzeros in the full operator with
-// float-float products, and a fixed block tree sums them into p_i, which
-// overwrites the zero; thread 0 adds p_i's share of ||p||^2 and of the
-// window dots.  The last CTA reduces both kernels' partials (the emptied
-// operator's CTAs, then these, each in CTA order) and runs the reducer.
+// and kept its partials).  The rows come longest first: each of the first
+// n_big (more than 1024 nonzeros) takes a whole CTA in turn (rows
+// blockIdx.x, blockIdx.x + grid, ...), its threads striding over the row's
+// nonzeros and a fixed block tree summing them; every other row takes a warp
+// (rows n_big + blockIdx.x * warps + warp, stepping by grid * warps) with a
+// fixed shuffle tree.  p_i overwrites the zero and the thread that holds it
+// adds its shares of ||p||^2 and of the window dots; a fixed block sum makes
+// the CTA's partials, and the last CTA reduces both kernels' partials (the
+// emptied operator's CTAs, then these, each in CTA order).
 template <typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLaunch L, const CycleDev cd) {
   __shared__ float rhi[32], rlo[32];
@@ -1235,6 +1237,7 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLa
   __shared__ double tot[NQ];
   pdl_wait();  // w_j and the products of the other rows are complete
   if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int j = L.j;
   const float2* W = static_cast<const float2*>(L.W);
   const float2* Wj = W + (int64_t)j * L.ldw;
@@ -1246,7 +1249,14 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLa
   for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
   ffacc acc_pi;
   ffacc acc_dot[KW];
-  for (int r = blockIdx.x; r < L.n_long; r += gridDim.x) {
+  auto finish_row = [&](int i, ff p) {
+    st_ff(static_cast<float2*>(L.p_out) + i, p);
+    acc_pi.add_prod(p, p);
+#pragma unroll
+    for (int q = 0; q < KW; ++q)
+      if (q < nd) acc_dot[q].add_prod(ld_ff(Wd[q] + i), p);
+  };
+  for (int r = blockIdx.x; r < L.n_big; r += gridDim.x) {  // a CTA per row
     const int i = __ldg(L.long_rows + r);
     const int e0 = __ldg(L.rp_full + i), e1 = __ldg(L.rp_full + i + 1);
     ffacc acc;
@@ -1254,21 +1264,29 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLa
     for (int e = e0 + (int)threadIdx.x; e < e1; e += (int)blockDim.x)
       acc_val(acc, val[e], ld_ff(Wj + __ldg(L.col_full + e)));
     const ff p = block_sum_ff_pair(acc.result(), rhi, rlo);
-    if (threadIdx.x == 0) {
-      st_ff(static_cast<float2*>(L.p_out) + i, p);
-      acc_pi.add_prod(p, p);
+    if (threadIdx.x == 0) finish_row(i, p);
+  }
+  for (int r = L.n_big + (int)blockIdx.x * nwarp + wid; r < L.n_long; r += (int)gridDim.x * nwarp) {  // a warp per row
+    const int i = __ldg(L.long_rows + r);
+    const int e0 = __ldg(L.rp_full + i), e1 = __ldg(L.rp_full + i + 1);
+    ffacc acc;
+#pragma unroll 4
+    for (int e = e0 + lane; e < e1; e += 32) acc_val(acc, val[e], ld_ff(Wj + __ldg(L.col_full + e)));
+    ff p = acc.result();
 #pragma unroll
-      for (int q = 0; q < KW; ++q)
-        if (q < nd) acc_dot[q].add_prod(ld_ff(Wd[q] + i), p);
-    }
+    for (int o = 16; o > 0; o >>= 1) p = ff_add(p, ff{__shfl_xor_sync(FULL, p.hi, o), __shfl_xor_sync(FULL, p.lo, o)});
+    if (lane == 0) finish_row(i, p);
   }
   pdl_trigger();
-  if (threadIdx.x == 0) {
-    double* part = L.part_long + (size_t)blockIdx.x * NQ;
-    part[1] = ff_to_double(acc_pi.result());
+  // per-CTA partials: only the threads that finished rows hold nonzero sums
+  double* part = L.part_long + (size_t)blockIdx.x * NQ;
+  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
+  if (threadIdx.x == 0) part[1] = v;
 #pragma unroll
-    for (int q = 0; q < KW; ++q)
-      if (q < nd) part[2 + q] = ff_to_double(acc_dot[q].result());
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;  // nd is uniform across the block
+    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
+    if (threadIdx.x == 0) part[2 + q] = v;
   }
   if (!last_block_flag(cd.counter, &s_last)) return;
   for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {

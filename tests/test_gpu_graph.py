@@ -3,8 +3,9 @@ out-degree Laplacian of a network; an undirected R-MAT graph stands in for the
 paper's networks).
 
 Power-law rows: the float-float product runs the operator with its rows longer
-than 256 nonzeros emptied through the usual kernels, then a long-row kernel
-(a CTA per row) completes those rows and reduces.  The method runs as in the
+than 48 nonzeros emptied through the usual kernels, then a long-row kernel
+(a CTA per row above 1024 nonzeros, a warp per row below) completes those rows
+and reduces.  The method runs as in the
 paper's graph example: sketch-space orthogonalization of the whole cycle
 (randomized Gram-Schmidt, k = m = 40, s = 320); a window of k = 2 vectors
 loses the basis on these stiff operators (kappa(T) reaches 1e16 on the oracle
@@ -42,7 +43,8 @@ def test_graph_heat_kernel_parity(lib, cuda, basis, mode):
     import torch
 
     L = W.rmat_laplacian(12, 16, 5)
-    assert np.diff(L.row_ptr).max() > 256  # the long-row path runs
+    deg = np.diff(L.row_ptr)
+    assert (deg > 1024).sum() >= 1 and ((deg > 48) & (deg <= 1024)).sum() > 100  # both long-row paths run
     x0 = W.rhs_probability(L.n, 6)
     if mode == "trunc":
         m, k, s, kmode, ortho = 20, 2, 60, K.TRUNC, 0
