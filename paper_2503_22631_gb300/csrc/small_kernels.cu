@@ -626,17 +626,23 @@ constexpr int SQ_WARPS = 8;
 // dbl (cos(t sqrt(z))): the double-angle step C(4A) = 2 C(A)^2 - I instead of
 // a plain square: the block sum is doubled and the identity subtracted on the
 // diagonal block.
+// MODE: SQ_EXP (squaring), SQ_PHI (squaring and the phi_1 vector row),
+// SQ_COS (double-angle step); a template parameter, so the squaring of the
+// exponential carries no branch for the other two.
+enum : int { SQ_EXP = 0, SQ_PHI = 1, SQ_COS = 2 };
+
+template <int MODE>
 __global__ void __launch_bounds__(SQ_WARPS * 32) exp_square_row_kernel(const double* __restrict__ Gi,
                                                                      double* __restrict__ Go, int M, int a,
                                                                      const double* __restrict__ gi,
-                                                                     double* __restrict__ go, int dbl) {
+                                                                     double* __restrict__ go) {
   __shared__ double red[SQ_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j = blockIdx.y;
   const int e = blockIdx.x * 32 + lane;
   const size_t MM = (size_t)M * M;
   const size_t rowa = (size_t)a * (a + 1) / 2;
-  if (j == a + 1) {  // the phi_1 vector of block row a
+  if (MODE == SQ_PHI && j == a + 1) {  // the phi_1 vector of block row a
     if ((int)blockIdx.x * 32 >= M) return;  // whole CTA
     const int K = (a + 1) * M;
     const int chunk = (K + SQ_WARPS - 1) / SQ_WARPS;
@@ -684,7 +690,7 @@ __global__ void __launch_bounds__(SQ_WARPS * 32) exp_square_row_kernel(const dou
     double sum = red[0][lane];
 #pragma unroll
     for (int q = 1; q < SQ_WARPS; ++q) sum += red[q][lane];
-    if (dbl) {
+    if (MODE == SQ_COS) {
       sum *= 2.0;
       if (j == a && e % M == e / M) sum -= 1.0;
     }
@@ -952,8 +958,15 @@ void launch_exp_taylor_step(const SmallDev& sd, int m, int a, double kinv, doubl
 void launch_exp_square(const SmallDev& sd, int m, int a, int level, int64_t level_stride, const double* gi,
                        double* go, int dbl, cudaStream_t st) {
   const int MM = m * m;
-  exp_square_row_kernel<<<dim3((MM + 31) / 32, a + 1 + (gi != nullptr ? 1 : 0)), SQ_WARPS * 32, 0, st>>>(
-      sd.G + (size_t)level * level_stride, sd.G + (size_t)(level + 1) * level_stride, m, a, gi, go, dbl);
+  const double* Gi = sd.G + (size_t)level * level_stride;
+  double* Go = sd.G + (size_t)(level + 1) * level_stride;
+  const dim3 block(SQ_WARPS * 32);
+  if (gi != nullptr)
+    exp_square_row_kernel<SQ_PHI><<<dim3((MM + 31) / 32, a + 2), block, 0, st>>>(Gi, Go, m, a, gi, go);
+  else if (dbl)
+    exp_square_row_kernel<SQ_COS><<<dim3((MM + 31) / 32, a + 1), block, 0, st>>>(Gi, Go, m, a, nullptr, nullptr);
+  else
+    exp_square_row_kernel<SQ_EXP><<<dim3((MM + 31) / 32, a + 1), block, 0, st>>>(Gi, Go, m, a, nullptr, nullptr);
 }
 
 void launch_inv_block(const SmallDev& sd, int m, int m_eff, int a, cudaStream_t st) {
