@@ -58,6 +58,27 @@ def test_graph_heat_kernel_parity(lib, cuda, basis, mode):
     assert _rel(xa, ref.x) <= 1e-10
 
 
+@pytest.mark.parametrize("basis", [0, 3])
+def test_directed_graph_parity(lib, cuda, basis):
+    """A directed R-MAT graph (the paper's uk-2002 is directed): L is not
+    symmetric, so the adjoint is checked against the oracle on L^T; both
+    directions have long rows (out- and in-degrees are power laws)."""
+    import torch
+
+    L = W.rmat_laplacian(12, 16, 9, directed=True)
+    assert np.diff(L.row_ptr).max() > 48 and np.diff(L.transpose().row_ptr).max() > 48
+    x0 = W.rhs_probability(L.n, 2)
+    args = (D.EXP_NEG, 0.1, 20, 20, 80, 8, 3)
+    ref = K.restarted(L, x0, *args, mode=K.RGS, tol=0.0, max_cycles=3)
+    ref_t = K.restarted(L.transpose(), x0, *args, mode=K.RGS, tol=0.0, max_cycles=3)
+    kr = _kr(L, 0.1, 20, 20, 80, basis, ortho=1)
+    x = kr.apply(torch.from_numpy(x0).cuda(), tol=0.0, max_cycles=3).cpu().numpy()
+    xa = kr.apply(torch.from_numpy(x0).cuda(), tol=0.0, max_cycles=3, adjoint=True).cpu().numpy()
+    assert _rel(x, ref.x) <= 1e-10
+    assert _rel(xa, ref_t.x) <= 1e-10
+    assert _rel(xa, ref.x) > 1e-6  # the two directions differ
+
+
 @pytest.mark.slow
 def test_graph_heat_kernel_full_size(lib, cuda):
     import torch

@@ -436,3 +436,15 @@ def test_heat_kernel_on_graph_conserves_mass():
     ones = np.ones(L.n)
     r1 = K.restarted(L, ones, D.EXP_NEG, 0.1, 20, 2, 60, 8, 3, mode=K.TRUNC, tol=0.0, max_cycles=2)
     assert rel(r1.x, ones) < 1e-13
+
+
+def test_rmat_laplacian_directed():
+    """Directed variant: zero row sums (L 1 = 0), L[i, i] = out-degree, not
+    symmetric; its uniform vector is stationary for the oracle's heat kernel."""
+    L = W.rmat_laplacian(10, 8, 3, directed=True)
+    Dn = L.to_dense()
+    assert np.abs(Dn.sum(axis=1)).max() == 0.0
+    assert not np.array_equal(Dn, Dn.T)
+    ones = np.ones(L.n)
+    r = K.restarted(L, ones, D.EXP_NEG, 0.1, 20, 20, 60, 8, 3, mode=K.RGS, tol=0.0, max_cycles=2)
+    assert rel(r.x, ones) < 1e-13

@@ -317,14 +317,15 @@ def batched_matrix(inst) -> Csr:
 # The five workloads (inputs only).  Seeds are fixed so every consumer reads the
 # same bytes.
 SEED = 20250331
-def rmat_laplacian(scale: int, edge_factor: int, seed: int, abc=(0.57, 0.19, 0.19)) -> Csr:
-    """Out-degree Laplacian of an undirected R-MAT graph (the Graph500 Kronecker
+def rmat_laplacian(scale: int, edge_factor: int, seed: int, abc=(0.57, 0.19, 0.19), directed=False) -> Csr:
+    """Out-degree Laplacian of an R-MAT graph (the Graph500 Kronecker
     generator's recursive quadrant choice; a stand-in for the paper's graph
-    networks, Sec. 5): L[i, i] = number of neighbours of i, L[i, j] = -1 per
-    edge, 2^scale nodes, edge_factor 2^scale drawn edges before self loops and
-    duplicates are dropped and the edge set is symmetrized.  Every row stores its
-    diagonal (0 for an isolated node).  Power-law degrees: at scale 20 the largest
-    row has ~65,000 entries and rows longer than 256 entries hold ~60 % of them.
+    networks, Sec. 5): L[i, i] = out-degree of i, L[i, j] = -1 per edge i -> j,
+    2^scale nodes, edge_factor 2^scale drawn edges before self loops and
+    duplicates are dropped; undirected (the default) symmetrizes the edge set.
+    Every row stores its diagonal (0 for a node without out-edges).  Power-law
+    degrees: undirected at scale 20 the largest row has ~65,000 entries and rows
+    longer than 256 entries hold ~60 % of them.
     """
     n = 1 << scale
     m = edge_factor * n
@@ -337,7 +338,10 @@ def rmat_laplacian(scale: int, edge_factor: int, seed: int, abc=(0.57, 0.19, 0.1
         src |= (r >= a + b).astype(np.int64) << lvl
         dst |= (((r >= a) & (r < a + b)) | (r >= a + b + c)).astype(np.int64) << lvl
     keep = src != dst
-    key = np.concatenate([src[keep] * n + dst[keep], dst[keep] * n + src[keep]])
+    if directed:
+        key = src[keep] * n + dst[keep]
+    else:
+        key = np.concatenate([src[keep] * n + dst[keep], dst[keep] * n + src[keep]])
     key.sort()
     first = np.ones(key.size, dtype=bool)
     first[1:] = key[1:] != key[:-1]
