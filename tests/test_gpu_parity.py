@@ -241,3 +241,41 @@ def test_wide_band_operator_parity(lib, cuda, adjoint):
     ref = K.restarted(A.transpose() if adjoint else A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=2)
     x, _ = _gpu(A, b, *args, 2, basis=3, adjoint=adjoint)
     assert _rel(x, ref.x) <= 1e-10
+
+
+def _odd_matrix(n, seed, long_row=False):
+    """Random rows of 0..8 nonzeros (unaligned row starts), every 7th row
+    empty, random normal values (not float32-exact); long_row adds ~300
+    entries to the middle row."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(n):
+        ln = int(rng.integers(0, 9))
+        if i % 7 == 3:
+            ln = 0
+        cols = np.unique(rng.integers(0, n, size=ln)) if ln else np.zeros(0, dtype=np.int64)
+        if long_row and i == n // 2:
+            cols = np.unique(np.concatenate([cols, rng.choice(n, size=min(n, 300), replace=False)]))
+        rows.append(cols)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(c) for c in rows])
+    ci = np.concatenate(rows).astype(np.int32)
+    return W.Csr(n, rp.astype(np.int32), ci, rng.standard_normal(ci.size))
+
+
+@pytest.mark.parametrize("basis", [0, 3])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 4097])
+def test_odd_shapes_empty_rows(lib, cuda, n, basis):
+    """Sizes around a warp and a tile (n = 1, 31, 32, 33, 4097), empty rows,
+    unaligned row starts, and at n = 4097 a row of ~300 nonzeros (the
+    float-float product's long-row path): 3 cycles against the oracle (n = 1
+    breaks down exactly in its first cycle)."""
+    A = _odd_matrix(n, n, long_row=(n == 4097))
+    b = W.rhs_normal(n, 5)
+    m = min(10, n)
+    s = max(m + 1, 16)
+    args = (D.EXP_NEG, 0.3, m, min(2, m), s, min(4, s), 3)
+    ref = K.restarted(A, b, *args, mode=K.TRUNC, tol=0.0, max_cycles=3)
+    x, kr = _gpu(A, b, *args, 3, basis=basis)
+    assert kr.stats["cycles"] == ref.cycles
+    assert _rel(x, ref.x) <= 1e-10
