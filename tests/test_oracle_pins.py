@@ -60,6 +60,20 @@ def test_philox_matches_independent_implementation():
         assert np.array_equal(got, ref)
 
 
+def test_philox_known_answer_vectors():
+    """The published known-answer vectors of Philox4x32-10
+    (tests/golden/philox4x32_10_kat.txt): an all-zero, an all-ones and a
+    digits-of-pi counter/key, so a wrong constant fails without any other
+    implementation to compare with."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    lines = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(lines) == 3
+    for words in lines:
+        v = [int(w, 16) for w in words]
+        got = [int(w) for w in PH.philox4x32_10(*v[:6])]
+        assert got == v[6:]
+
+
 # ---------------------------------------------------------------- sketch ----
 def test_sketch_columns_invariants():
     """Eq. (3): zeta distinct rows per column, +-1/sqrt(zeta) entries, so every
@@ -82,18 +96,64 @@ def test_sketch_uniform_rows_and_balanced_signs():
     """Rows uniform over [0, s) and Rademacher signs: chi-square and binomial
     checks on 2e5 columns (catches a biased row map such as v % s without
     rejection at large s, or a sign bit tied to the row)."""
-    n, s, zeta = 200_000, 1000, 1
-    rows, signs = OS.sketch_columns(n, s, zeta, 2024)
-    counts = np.bincount(rows.ravel(), minlength=s)
-    expected = n * zeta / s
-    chi2 = ((counts - expected) ** 2 / expected).sum()
-    # chi-square with s-1 dof: mean s-1, sd sqrt(2(s-1)); allow 5 sd
-    assert abs(chi2 - (s - 1)) < 5 * math.sqrt(2 * (s - 1))
+    for n, s in [(200_000, 1000), (300_000, 20000)]:
+        rows, signs = OS.sketch_columns(n, s, 1, 2024)
+        counts = np.bincount(rows.ravel(), minlength=s)
+        expected = n / s
+        chi2 = ((counts - expected) ** 2 / expected).sum()
+        # chi-square with s-1 dof: mean s-1, sd sqrt(2(s-1)); allow 5 sd.  At
+        # s = 20000, v % s without rejection would double the weight of rows
+        # below 12768.
+        assert abs(chi2 - (s - 1)) < 5 * math.sqrt(2 * (s - 1))
     frac_neg = np.mean(signs < 0)
     assert abs(frac_neg - 0.5) < 5 * math.sqrt(0.25 / signs.size)
     # sign independent of row parity
     odd = rows.ravel() % 2 == 1
     assert abs(np.mean(signs.ravel()[odd] < 0) - 0.5) < 5 * math.sqrt(0.25 / odd.sum())
+
+
+def test_sketch_column_from_known_answer_words():
+    """Column 0 under seed 0 uses the Philox counter (0, 0, 0, 0) and key
+    (0, 0), whose output words are the first published known-answer vector
+    6627e8d5 e169c58d bc57ac4c 9b00dbd8.  Taking 16-bit chunks low half first
+    (e8d5, 6627, c58d, e169, ac4c, bc57, dbd8, 9b00), a candidate row
+    (chunk & 0x7fff) mod s and a sign from bit 15, worked by hand:
+    s = 160 (no chunk reaches the rejection limit 32640) gives rows
+    117, 71, 45, 137, 140, 87, 152, 32 with signs - + - - - - - -;
+    s = 20000 (limit 20000 rejects 26837, 26151, 24937 and 23512) gives
+    17805, 11340, 15447, 6912, all negative.  Pins the chunk order, the mask,
+    the sign bit and the rejection rule of the generator's definition."""
+    rows, signs = OS.sketch_columns(1, 160, 8, 0)
+    assert rows[0].tolist() == [117, 71, 45, 137, 140, 87, 152, 32]
+    assert signs[0].tolist() == [-1.0, 1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0]
+    rows, signs = OS.sketch_columns(1, 20000, 4, 0)
+    assert rows[0].tolist() == [17805, 11340, 15447, 6912]
+    assert signs[0].tolist() == [-1.0] * 4
+
+
+def test_sketch_stream_from_independent_philox():
+    """Columns away from 0, seeds with both key words set and sizes that need
+    several counter blocks: rebuilt one candidate at a time from Triton's
+    Philox4x32-10 words for counter (column, block, 0, 0) and key
+    (seed mod 2^32, seed div 2^32).  Pins which counter and key words carry
+    the column, the block and the seed."""
+    cases = [(0x1234_5678_9ABC_DEF0, 20000, 8), (77, 160, 8), (2**40 + 3, 3001, 16)]
+    cols = [1, 2, 12345, 1_000_003]
+    for seed, s, zeta in cases:
+        rows, signs = OS.sketch_columns(cols[-1] + 1, s, zeta, seed, cols=np.array(cols))
+        lim = 32768 - 32768 % s
+        for ci, col in enumerate(cols):
+            want_r, want_s, block = [], [], 0
+            while len(want_r) < zeta:
+                words = _triton_randint4x(seed, [col + (block << 32)])[0]
+                for w in words:
+                    for chunk in (int(w) & 0xFFFF, int(w) >> 16):
+                        v, row = chunk & 0x7FFF, (chunk & 0x7FFF) % s
+                        if len(want_r) < zeta and v < lim and row not in want_r:
+                            want_r.append(row)
+                            want_s.append(-1.0 if chunk >> 15 else 1.0)
+                block += 1
+            assert rows[ci].tolist() == want_r and signs[ci].tolist() == want_s
 
 
 def test_sketch_is_an_embedding_in_expectation():
@@ -154,6 +214,33 @@ def test_expm_closed_forms():
     assert np.allclose(E, ref, rtol=1e-14, atol=1e-16)
     A = np.random.default_rng(5).standard_normal((12, 12))
     assert np.allclose(D.expm(A) @ D.expm(-A), np.eye(12), atol=1e-12)
+
+
+@pytest.mark.parametrize("th", [10.6, 21.2, 42.4, 84.8])
+def test_expm_rotation_at_scaling_boundaries(th):
+    """exp of [[0, th], [-th, 0]] is the rotation by th.  The angles sit just
+    below 2^j * 2 theta_13, where scaling by 2^-s with s = ceil(log2(||A||_1 /
+    theta_13)) brings the norm to theta_13 but one fewer halving leaves it
+    near 2 theta_13, where the degree-13 approximant on the imaginary axis is
+    off by ~1e-8 (catches a floor for the ceil, or one squaring too few)."""
+    R = D.expm(np.array([[0.0, th], [-th, 0.0]]))
+    ref = np.array([[math.cos(th), math.sin(th)], [-math.sin(th), math.cos(th)]])
+    assert np.abs(R - ref).max() < 1e-14 * th
+
+
+def test_qr_positive_column_nearly_along_e1():
+    """Householder QR is backward stable only when the reflector is formed
+    with alpha = -sign(x_1) ||x|| (no cancellation in x_1 - alpha); columns
+    whose trailing parts are tiny relative to the leading entry expose a wrong
+    sign choice as a large ||Q T - U|| or a non-orthogonal Q."""
+    rng = np.random.default_rng(11)
+    for sgn in (1.0, -1.0):
+        U = 1e-9 * rng.standard_normal((30, 6))
+        U[np.arange(6), np.arange(6)] += sgn * np.array([1.0, 2.0, 0.5, 3.0, 1.5, 0.7])
+        Q, T = D.qr_positive(U)
+        assert np.linalg.norm(Q @ T - U) < 1e-14 * np.linalg.norm(U)
+        assert np.linalg.norm(Q.T @ Q - np.eye(6)) < 1e-14
+        assert np.all(np.diag(T) > 0) and np.allclose(np.tril(T, -1), 0)
 
 
 def test_invsqrtm():
@@ -228,8 +315,10 @@ def test_cossqrtm_matches_eigendecomposition():
 # ---------------------------------------------------------------- truth -----
 def test_kronecker_truth_matches_dense_exponential():
     """exp(-tA) of the Kronecker-sum grid operator applied by mode products
-    equals the dense exponential of the assembled CSR matrix."""
-    for N, dim, beta, t in [(6, 3, (50.0, 50.0, 50.0), 1e-2), (9, 2, (0.0, 0.0), 1e-3), (5, 3, (20.0, 0.0, 0.0), 5e-3)]:
+    equals the dense exponential of the assembled CSR matrix (velocities of
+    both signs, so the upwind side and the |beta| on the diagonal count)."""
+    for N, dim, beta, t in [(6, 3, (50.0, 50.0, 50.0), 1e-2), (9, 2, (0.0, 0.0), 1e-3), (5, 3, (20.0, 0.0, 0.0), 5e-3),
+                              (7, 2, (-30.0, 15.0), 2e-3), (5, 3, (-10.0, 40.0, -25.0), 4e-3)]:
         A = W.convdiff(N, dim, beta)
         b = np.random.default_rng(N).standard_normal(A.n)
         ref = sl.expm(-t * A.to_dense()) @ b
@@ -302,6 +391,55 @@ def test_single_mode_breaks_down_exactly(mode):
     assert rel(r.x, TR.sine_mode_exp(N, c, p, q, 2e-3)) < 1e-13
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_near_breakdown_is_not_breakdown(mode):
+    """b = phi_{1,1} + 1e-7 phi_{12,12}: after one step the residual is about
+    1e-5 of ||A w_1||, far above rounding, so the first step is NOT a happy
+    breakdown, and one cycle reproduces the closed form of the sine modes to
+    rounding; a breakdown test that is too loose stops after one column with
+    an error of order 1e-7."""
+    N = 24
+    A = W.poisson2d(N)
+    c, p, q = np.array([1.0, 1e-7]), np.array([1, 12]), np.array([1, 12])
+    h = 1.0 / (N + 1)
+    ii = np.arange(1, N + 1)
+    b = sum(cl * np.outer(np.sin(ql * np.pi * ii * h), np.sin(pl * np.pi * ii * h))
+            for cl, pl, ql in zip(c, p, q)).reshape(-1)
+    k = 2 if mode == K.TRUNC else 10
+    r = K.restarted(A, b, D.EXP_NEG, 1e-3, 10, k, 30, 4, 1, mode=mode, max_cycles=1)
+    assert r.info[0].m_eff > 1
+    assert rel(r.x, TR.sine_mode_exp(N, c, p, q, 1e-3)) < 1e-12
+
+
+def test_stopping_is_invariant_to_the_scale_of_b():
+    """f(A)(a b) = a f(A) b and the stopping test ||y|| <= tol ||x|| is
+    relative (Sec. 4 estimate compared with the iterate's norm), so scaling b
+    by 1e6 or 1e-6 changes neither the number of cycles nor x / a."""
+    A = W.poisson2d(32)
+    b = W.rhs_normal(A.n, 4, normalize=True)
+    runs = [K.restarted(A, a * b, D.EXP_NEG, 1e-3, 10, 2, 40, 8, 3, mode=K.TRUNC, tol=1e-8, max_cycles=60)
+            for a in (1.0, 1e6, 1e-6)]
+    assert runs[0].cycles > 2
+    assert all(r.cycles == runs[0].cycles for r in runs)
+    assert rel(runs[1].x / 1e6, runs[0].x) < 1e-13 and rel(runs[2].x / 1e-6, runs[0].x) < 1e-13
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_update_norm_is_the_norm_of_the_update(mode):
+    """The stopping quantity of cycle c is ||x_c - x_{c-1}|| (the norm of the
+    correction y added in that cycle), checked by running one cycle fewer."""
+    A = W.convdiff(14, 2, (30.0, 10.0))
+    b = W.rhs_uniform(A.n, 6)
+    k = 2 if mode == K.TRUNC else 12
+    r3 = K.restarted(A, b, D.EXP_NEG, 2e-2, 12, k, 48, 8, 3, mode=mode, max_cycles=3)
+    r2 = K.restarted(A, b, D.EXP_NEG, 2e-2, 12, k, 48, 8, 3, mode=mode, max_cycles=2)
+    assert r3.cycles == 3
+    d = np.linalg.norm(r3.x - r2.x)
+    assert d > 1e-6 * np.linalg.norm(r3.x)
+    assert abs(r3.info[2].update_norm - d) <= 1e-12 * d
+    assert abs(r3.info[2].x_norm - np.linalg.norm(r3.x)) <= 1e-14 * np.linalg.norm(r3.x)
+
+
 @pytest.mark.parametrize("fkind", [D.EXP_NEG, D.INV, D.INVSQRT, D.PHI1_NEG, D.COS_SQRT])
 def test_exact_when_m_reaches_n(fkind):
     """With m = n the Krylov space is the whole space: one cycle is exact."""
@@ -337,6 +475,11 @@ def test_arnoldi_like_relations():
             if mode == K.RGS and k >= m:  # full sketch orthogonalization
                 assert ci.sketch_orth_err < 1e-12
         if mode == K.TRUNC:
+            # the next start vector v has S v = q_{m+1} (the last column of Q),
+            # so the second cycle's T[1,1] = ||S v|| is 1 up to rounding and the
+            # coupling rho T^{next}[1,1] reduces to rho
+            assert abs(r.info[1].T[0, 0] - 1.0) < 1e-12
+        if mode == K.TRUNC:
             ci = r.info[0]
             T = ci.T
             Tm = T[:m, :m]
@@ -350,6 +493,34 @@ def test_arnoldi_like_relations():
             SW = Sk.apply(What)
             assert np.allclose(SW.T @ SW, np.eye(m), atol=1e-12)
             assert abs(np.linalg.norm(Sk.apply(v)) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [K.TRUNC, K.RGS])
+def test_orthogonalization_window_holds_exactly_k_vectors(mode):
+    """The truncated orthogonalization of step j involves exactly the last k
+    vectors: column j of R is zero above row j - k + 1 and nonzero on the k
+    rows of the window, and the new vector (TRUNC: w_{j+1}; RGS: its sketch
+    u_{j+1}) is orthogonal to the window's vectors but not to the one just
+    outside it (a non-symmetric operator, so no three-term recurrence makes
+    older vectors orthogonal by accident).  Catches a window one too wide or
+    one too narrow."""
+    A = W.convdiff(16, 2, (60.0, 25.0))
+    b = W.rhs_uniform(A.n, 5)
+    m, k = 10, 3
+    r = K.restarted(A, b, D.EXP_NEG, 1e-3, m, k, 80, 8, 5, mode=mode, max_cycles=1, keep=True)
+    ci = r.info[0]
+    R = ci.R
+    V = ci.W if mode == K.TRUNC else ci.U
+    V = V / np.linalg.norm(V, axis=0)
+    outside = []
+    for j in range(m):
+        lo = max(0, j - k + 1)
+        assert np.all(R[:lo, j] == 0.0)
+        assert np.all(R[lo:j + 1, j] != 0.0)
+        assert np.abs(V[:, lo:j + 1].T @ V[:, j + 1]).max() < 1e-12
+        if lo > 0:
+            outside.append(abs(V[:, lo - 1] @ V[:, j + 1]))
+    assert max(outside) > 1e-3
 
 
 def test_interpolation_property():
