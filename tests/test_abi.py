@@ -86,3 +86,111 @@ def test_struct_mirrors_list_the_header_fields():
         names = re.findall(r"(?:int|int64_t|double|void\*|const int32_t\*|const double\*|const void\*)\s+(\w+)\s*;",
                            body)
         assert names == [f[0] for f in mirror._fields_], cname
+
+
+def _host_csr():
+    """A 4 x 4 tridiagonal matrix in host memory, plus the arrays that keep it alive."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2503_22631_gb300 import _lib
+
+    rp = np.array([0, 2, 5, 8, 10], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1, 2, 1, 2, 3, 2, 3], dtype=np.int32)
+    val = np.array([2.0, -1, -1, 2, -1, -1, 2, -1, -1, 2])
+    csr = _lib.Csr(n=4, nnz=10, row_ptr=rp.ctypes.data_as(C.c_void_p), col_idx=ci.ctypes.data_as(C.c_void_p),
+                   val=val.ctypes.data_as(C.c_void_p), on_device=0)
+    return csr, (rp, ci, val)
+
+
+def test_create_validates_arguments_before_any_device_call(lib):
+    """krylov_create checks every argument on the host before its first CUDA
+    call: each invalid choice returns KRYLOV_EINVAL (the randomized
+    Gram-Schmidt cycle with a float32 basis KRYLOV_EUNSUPPORTED) and leaves
+    *out NULL, with or without a GPU."""
+    import ctypes as C
+
+    from paper_2503_22631_gb300 import _lib
+
+    csr, keep = _host_csr()
+    EINVAL, EUNSUP = -1, -6
+
+    def create(A=csr, kind=0, t=1.0, m=2, k=2, s=8, opt=None, out=True):
+        h = C.c_void_p(0x1234)
+        st = lib.krylov_create(C.byref(A) if A is not None else None, _lib.Func(kind, t), m, k, s, 7,
+                               C.byref(opt) if opt is not None else None, C.byref(h) if out else None)
+        return st, h
+
+    def options(**kw):
+        o = _lib.Options()
+        lib.krylov_options_default(C.byref(o))
+        for key, v in kw.items():
+            setattr(o, key, v)
+        return o
+
+    def bad_csr(**kw):
+        c = _lib.Csr()
+        C.memmove(C.byref(c), C.byref(csr), C.sizeof(c))
+        for key, v in kw.items():
+            setattr(c, key, v)
+        return c
+
+    cases = [
+        dict(A=None), dict(out=False),
+        dict(A=bad_csr(n=0)), dict(A=bad_csr(n=1 << 31)), dict(A=bad_csr(nnz=-1)),
+        dict(A=bad_csr(nnz=1 << 31)), dict(A=bad_csr(row_ptr=None)), dict(A=bad_csr(col_idx=None)),
+        dict(A=bad_csr(val=None)),
+        dict(m=0), dict(m=257, s=300), dict(k=0), dict(s=2), dict(s=1025), dict(k=5, m=8, s=16),
+        dict(opt=options(zeta=0)), dict(opt=options(zeta=9)), dict(opt=options(zeta=33), s=64),
+        dict(opt=options(basis_dtype=4)), dict(opt=options(basis_dtype=-1)), dict(opt=options(ortho=2)),
+        dict(opt=options(autotune=3)), dict(opt=options(ortho=1), k=3),
+        dict(kind=5), dict(kind=-1), dict(t=float("inf")), dict(t=float("nan")),
+    ]
+    for kw in cases:
+        st, h = create(**kw)
+        assert st == EINVAL, kw
+        if kw.get("out", True) and kw.get("A", csr) is not None:
+            assert h.value is None, kw
+    for basis in (1, 2):  # float32 / bfloat16 bases under randomized Gram-Schmidt
+        st, h = create(opt=options(ortho=1, basis_dtype=basis))
+        assert st == EUNSUP and h.value is None
+    # valid arguments with no device: the first CUDA call fails and the status
+    # says so (there is no host fallback)
+    import torch
+
+    if not torch.cuda.is_available():
+        st, h = create()
+        assert st == -3 and h.value is None
+
+
+def test_calls_on_a_null_handle_are_rejected(lib):
+    """Every entry point that takes a handle answers a NULL one with
+    KRYLOV_EINVAL (no device call), and krylov_destroy(NULL) is a no-op."""
+    import ctypes as C
+
+    from paper_2503_22631_gb300 import _lib
+
+    buf = (C.c_double * 4)()
+    p = C.cast(buf, C.c_void_p)
+    st = _lib.Stats()
+    assert lib.krylov_apply(None, p, p, 1e-8, 3, C.byref(st)) == -1
+    assert st.status == -1
+    assert lib.krylov_apply_adjoint(None, p, p, 1e-8, 3, None) == -1
+    assert lib.krylov_apply_host(None, p, p, 1e-8, 3, None) == -1
+    assert lib.krylov_set_param(None, 0.5) == -1
+    assert lib.krylov_spmv(None, p, p, 0, None, None) == -1
+    assert lib.krylov_size(None) == 0
+    assert lib.krylov_last_cycle(None, None, 0, None, 0, None, 0, None) == -1
+    lib.krylov_destroy(None)
+    hs = (C.c_void_p * 1)(None)
+    assert lib.krylov_apply_batched(C.cast(hs, C.c_void_p), 1, 1, p, p, None, 1e-8, 3, None) == -1
+    assert lib.krylov_apply_batched(None, 1, 1, p, p, None, 1e-8, 3, None) == -1
+    # sketch generator arguments out of range
+    rows = (C.c_int32 * 8)()
+    signs = (C.c_int8 * 8)()
+    r, s_ = C.cast(rows, C.c_void_p), C.cast(signs, C.c_void_p)
+    for args in [(0, 8, 1, 0, 0, 1), (8, 0, 1, 0, 0, 1), (8, 40000, 1, 0, 0, 1), (8, 8, 9, 0, 0, 1),
+                 (8, 64, 33, 0, 0, 1), (8, 8, 1, 0, -1, 1), (8, 8, 1, 0, 4, 5), (8, 8, 1, 0, 0, -1)]:
+        assert lib.krylov_sketch_columns(*args, r, s_) == -1, args
+    assert lib.krylov_sketch_columns(8, 8, 1, 0, 0, 0, r, s_) == 0  # nothing to generate
