@@ -65,7 +65,8 @@ typedef enum {
 
 typedef struct {
   int kind;  /* krylov_fkind */
-  double t;  /* time parameter of exp(-t z); ignored otherwise */
+  double t;  /* t of exp(-t z), phi_1(-t z) and cos(t sqrt(z)); finite (EINVAL
+                otherwise); ignored by z^{-1/2} and 1/z */
 } krylov_func;
 
 /* CSR matrix, borrowed for the duration of krylov_create (the library copies
@@ -170,7 +171,9 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
  * App. A).  b: device, n float64, read only; x: device, n float64, overwritten.
  * tol: stopping tolerance (relative unless opt.abs_tol); tol = 0 runs exactly
  * max_cycles cycles.  st may be NULL.  Returns OK, NOT_CONVERGED or
- * BREAKDOWN_EXACT on success. */
+ * BREAKDOWN_EXACT on success; EINVAL for a NULL h, b or x, max_cycles < 1 or
+ * tol < 0 (or NaN); ENONFINITE when b or the projected problem holds NaN/Inf;
+ * ETIMEOUT when a bounded device wait gave up. */
 krylov_status krylov_apply(krylov_handle* h, const double* b, double* x, double tol,
                            int max_cycles, krylov_stats* st);
 
@@ -185,7 +188,8 @@ krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* 
 krylov_status krylov_apply_adjoint(krylov_handle* h, const double* b, double* x, double tol,
                                    int max_cycles, krylov_stats* st);
 
-/* Change the parameter t of f for subsequent calls (e.g. exp(-t z) at a new t). */
+/* Change the parameter t of f for subsequent calls (e.g. exp(-t z) at a new t).
+ * EINVAL for a NULL handle or a non-finite t. */
 krylov_status krylov_set_param(krylov_handle* h, double t);
 
 /* y <- A x (transpose = 0) or A^T x (transpose = 1).  x, y: device float64, n.
@@ -213,13 +217,12 @@ krylov_status krylov_spmv_dot_noalloc(int64_t n, int64_t nnz, const int32_t* row
                                       double* y, const double* dot_with, double* dot_out,
                                       void* stream);
 
-/* Problem size of a handle. */
+/* Problem size n of a handle (0 for NULL). */
 int64_t krylov_size(const krylov_handle* h);
 
 /* Release the handle and all device memory it owns.  NULL is ignored. */
 void krylov_destroy(krylov_handle* h);
 
-/* Static description of a status code. */
 /* Batched form: f(A_i) b_{i,r} for n_inst handles (matrices of uneven size) and
  * n_rhs right-hand sides each.  Algorithm 2 runs independently for every
  * (instance, right-hand side); instances run concurrently, each on a stream of
@@ -228,8 +231,8 @@ void krylov_destroy(krylov_handle* h);
  *   hs         : n_inst distinct handles (one matrix each);
  *   B[i], X[i] : device float64, row-major n_i x n_rhs (column r is b_{i,r} and
  *                x_{i,r}); X[i] is overwritten;
- *   t_per_inst : NULL, or n_inst values of t for f(z) = exp(-t z) (the handle's t
- *                is restored afterwards);
+ *   t_per_inst : NULL, or n_inst finite values of the parameter t of each
+ *                handle's f (the handle's t is restored afterwards);
  *   st         : NULL, or n_inst * n_rhs stats, entry i * n_rhs + r, each with its
  *                own status.
  * Every right-hand side is attempted; one that fails (a negative status in its
@@ -237,11 +240,13 @@ void krylov_destroy(krylov_handle* h);
  * CUDA or allocation error, which ends its instance.  Returns the first negative
  * status met (instances in order), else KRYLOV_NOT_CONVERGED if any right-hand
  * side did not meet tol, else KRYLOV_OK.
- * EINVAL for null or repeated handles, n_inst < 1 or n_rhs < 1. */
+ * EINVAL for null or repeated handles, null B or X, n_inst < 1, n_rhs < 1,
+ * max_cycles < 1, tol < 0 or a non-finite t. */
 krylov_status krylov_apply_batched(krylov_handle* const* hs, int n_inst, int n_rhs, const double* const* B,
                                    double* const* X, const double* t_per_inst, double tol, int max_cycles,
                                    krylov_stats* st);
 
+/* Static description of a status code ("unknown status" for other values). */
 const char* krylov_status_string(krylov_status s);
 
 /* ---- inspection entry points used by the parity tests ------------------ */
@@ -249,7 +254,9 @@ const char* krylov_status_string(krylov_status s);
 /* Sparse sign columns [col0, col0 + count) of S as generated on the device
  * (Sec. 2.1, Eq. 3): rows_out (host, count*zeta int32) and signs_out (host,
  * count*zeta int8, +1/-1), entries of a column in acceptance order.  The same
- * generator feeds every sketch the library computes. */
+ * generator feeds every sketch the library computes.  EINVAL unless
+ * 1 <= s <= 32768, 1 <= zeta <= min(s, 32), col0 >= 0, count >= 0,
+ * col0 + count <= n and both outputs are set; count = 0 writes nothing. */
 krylov_status krylov_sketch_columns(int64_t n, int s, int zeta, uint64_t seed, int64_t col0,
                                     int64_t count, int32_t* rows_out, int8_t* signs_out);
 
