@@ -11,7 +11,7 @@ sparse products, truncated orthogonalization, sketches, whitening, f of the
 projected matrix, solution updates).
 
 Inputs are synthetic and resident in HBM before the timed region; the working
-set (matrix 125 MB + basis 344 MB) is larger than the 129 MB L2, so no flush
+set (matrix 125 MB + float-float basis 688 MB) is larger than the 129 MB L2, so no flush
 is needed between steps.  ``e2e`` repeats the measurement through the host
 entry point (b copied in and x copied out inside the timed region).
 
@@ -288,10 +288,12 @@ def secondary_main(args):
     import torch
 
     import workloads as W
-    from paper_2503_22631_gb300 import (BASIS_DF64, F_COS_SQRT, F_EXP_NEG, F_INVSQRT, F_PHI1_NEG, ORTHO_RGS,
-                                        Krylov, apply_batched, build, krylov_expm)
+    from paper_2503_22631_gb300 import (BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, F_COS_SQRT, F_EXP_NEG,
+                                        F_INVSQRT, F_PHI1_NEG, ORTHO_RGS, Krylov, apply_batched, build,
+                                        krylov_expm)
 
     build.build()
+    basis = {"df64": BASIS_DF64, "f64": BASIS_F64, "f32": BASIS_F32, "bf16": BASIS_BF16}[args.basis]
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     warmup = max(args.warmup, 3)
@@ -300,7 +302,7 @@ def secondary_main(args):
     if wl == "convdiff3d_128_rgs":
         A, b = make_inputs()
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=WORKLOAD["t"], m=WORKLOAD["m"], k=WORKLOAD["m"],
-                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=BASIS_DF64, ortho=ORTHO_RGS)
+                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=basis, ortho=ORTHO_RGS)
         bd = torch.from_numpy(b).cuda()
         cycles = 10
 
@@ -310,13 +312,13 @@ def secondary_main(args):
 
         metric = "seconds to 1e-8 rel err per f(A)b at n=2.1M, randomized Gram-Schmidt with the full window"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": 40, "k": 40, "s": 160, "zeta": 8, "t": 1e-2,
-                  "cycles": cycles, "basis": "df64", "ortho": "rgs"}
+                  "cycles": cycles, "basis": args.basis, "ortho": "rgs"}
         units = 1
     elif wl == "convdiff3d_128_phi1":
         # phi_1(-tA) b (the phi function of Sec. 5) on the headline operator
         A, b = make_inputs()
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_PHI1_NEG, t=WORKLOAD["t"], m=WORKLOAD["m"], k=WORKLOAD["k"],
-                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=BASIS_DF64)
+                    s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=basis)
         bd = torch.from_numpy(b).cuda()
         cycles = PHI1_CYCLES
 
@@ -326,7 +328,7 @@ def secondary_main(args):
 
         metric = "seconds to 1e-8 rel err per phi_1(-tA)b at n=2.1M"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": 40, "k": 2, "s": 160, "zeta": 8, "t": 1e-2,
-                  "cycles": cycles, "basis": "df64", "f": "phi1"}
+                  "cycles": cycles, "basis": args.basis, "f": "phi1"}
         units = 1
     elif wl == "poisson2d_1448_cos":
         # cos(t sqrt(A)) b (the membrane example of Sec. 5) on a 2D 5-point
@@ -334,7 +336,7 @@ def secondary_main(args):
         A = W.poisson2d(1448)
         b = W.rhs_uniform(A.n, SEED)
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_COS_SQRT, t=0.05, m=40, k=2, s=160, seed=SEED, zeta=8,
-                    basis=BASIS_DF64)
+                    basis=basis)
         bd = torch.from_numpy(b).cuda()
         cycles = COS_CYCLES
 
@@ -344,7 +346,7 @@ def secondary_main(args):
 
         metric = "seconds to 1e-8 rel err per cos(t sqrt(A))b at n=2.1M (2D Laplacian)"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": 40, "k": 2, "s": 160, "zeta": 8, "t": 0.05,
-                  "cycles": cycles, "basis": "df64", "f": "cos_sqrt"}
+                  "cycles": cycles, "basis": args.basis, "f": "cos_sqrt"}
         units = 1
     elif wl == "rmat20_heat":
         # the graph example of Sec. 5: heat kernel exp(-tL) x_0 on the out-degree
@@ -354,7 +356,7 @@ def secondary_main(args):
         A = W.rmat_laplacian(20, 16, SEED)
         b = W.rhs_probability(A.n, SEED)
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=0.1, m=40, k=40, s=320, seed=SEED, zeta=8,
-                    basis=BASIS_DF64, ortho=ORTHO_RGS)
+                    basis=basis, ortho=ORTHO_RGS)
         bd = torch.from_numpy(b).cuda()
         cycles = 4  # 2e-12 from an 8-cycle solve (3 cycles: 4e-8); tests/test_gpu_graph.py checks it
 
@@ -364,14 +366,14 @@ def secondary_main(args):
 
         metric = "seconds to 1e-8 rel err per heat kernel exp(-tL)x_0 on a 1M-node R-MAT graph (32M nonzeros)"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "max_row": int(np.diff(A.row_ptr).max()), "m": 40,
-                  "k": 40, "s": 320, "zeta": 8, "t": 0.1, "cycles": cycles, "basis": "df64", "ortho": "rgs"}
+                  "k": 40, "s": 320, "zeta": 8, "t": 0.1, "cycles": cycles, "basis": args.basis, "ortho": "rgs"}
         units = 1
     elif wl == "fem_kuhn_160":
         cfg = W.CONFIGS["fem_kuhn_160"]
         A = cfg["matrix"]()
         b = cfg["rhs"](A.n)
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_INVSQRT, t=1.0, m=cfg["m"], k=cfg["k"], s=cfg["s"], seed=W.SEED,
-                    zeta=cfg["zeta"], basis=BASIS_DF64)
+                    zeta=cfg["zeta"], basis=basis)
         bd = torch.from_numpy(b).cuda()
         cycles = 20
 
@@ -381,7 +383,7 @@ def secondary_main(args):
 
         metric = "seconds per 20 restart cycles of A^{-1/2} b at n=4.0M (P1 FEM, k=4)"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": cfg["m"], "k": cfg["k"], "s": cfg["s"],
-                  "zeta": cfg["zeta"], "cycles": cycles, "basis": "df64", "f": "invsqrt"}
+                  "zeta": cfg["zeta"], "cycles": cycles, "basis": args.basis, "f": "invsqrt"}
         units = 1
     elif wl == "batched16":
         insts = W.batched_instances(16, W.SEED)
@@ -389,7 +391,7 @@ def secondary_main(args):
         for i, inst in enumerate(insts):
             Ai = W.batched_matrix(inst)
             hs.append(Krylov(Ai.row_ptr, Ai.col_idx, Ai.val, f=F_EXP_NEG, t=inst["t"], m=30, k=2, s=120, seed=W.SEED,
-                             zeta=8, basis=BASIS_DF64))
+                             zeta=8, basis=basis))
             B.append(torch.from_numpy(W.rhs_normal(inst["n"] * 64, 100 + i).reshape(inst["n"], 64)).cuda())
         cycles = 2
         ts = [inst["t"] for inst in insts]
@@ -400,13 +402,13 @@ def secondary_main(args):
 
         metric = "seconds per batched call: 16 matrices x 64 right-hand sides, 2 restart cycles each"
         config = {"workload": wl, "instances": 16, "rhs": 64, "n_total": int(sum(i["n"] for i in insts)),
-                  "m": 30, "k": 2, "s": 120, "zeta": 8, "cycles": cycles, "basis": "df64"}
+                  "m": 30, "k": 2, "s": 120, "zeta": 8, "cycles": cycles, "basis": args.basis}
         units = 1
     else:  # convdiff3d_96_adjoint
         cfg = W.CONFIGS["convdiff3d_96_adjoint"]
         A = cfg["matrix"]()
         kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=cfg["t"], m=cfg["m"], k=cfg["k"], s=cfg["s"],
-                    seed=W.SEED, zeta=cfg["zeta"], basis=BASIS_DF64)
+                    seed=W.SEED, zeta=cfg["zeta"], basis=basis)
         b0 = torch.from_numpy(cfg["rhs"](A.n)).cuda()
         y = torch.from_numpy(W.rhs_normal(A.n, W.SEED + 1)).cuda()
 
@@ -419,7 +421,7 @@ def secondary_main(args):
 
         metric = "seconds per loss gradient (grad_b and grad_t of ||exp(-tA)b - y||^2) at n=885K"
         config = {"workload": wl, "n": A.n, "nnz": A.nnz, "m": cfg["m"], "k": 2, "s": 160, "zeta": 8,
-                  "t": cfg["t"], "tol": 1e-10, "basis": "df64"}
+                  "t": cfg["t"], "tol": 1e-10, "basis": args.basis}
         units = 1
     with ClockSampler(0, enabled=not args.profile) as clk:
         ms = _timed(fn, args.steps, warmup, stream)
@@ -434,7 +436,7 @@ def secondary_main(args):
     line = {
         "metric": metric, "value": value, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "df64", "data": "synthetic", "config": config,
+        "dtype": args.basis, "data": "synthetic", "config": config,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "kernel": "Arnoldi-step phase (step kernels of every cycle)",
