@@ -46,7 +46,7 @@ typedef enum {
   KRYLOV_ENOMEM = -2,         /* device allocation failed                       */
   KRYLOV_ECUDA = -3,          /* CUDA runtime / launch error                    */
   KRYLOV_ENONFINITE = -4,     /* NaN/Inf in b or in the projected problem       */
-  KRYLOV_ETIMEOUT = -5,       /* reserved: a bounded device wait gave up        */
+  KRYLOV_ETIMEOUT = -5,       /* a bounded device wait gave up (result invalid) */
   KRYLOV_EUNSUPPORTED = -6    /* option combination not implemented             */
 } krylov_status;
 
