@@ -268,6 +268,19 @@ krylov_status krylov_sketch_columns(int64_t n, int s, int zeta, uint64_t seed, i
 krylov_status krylov_last_cycle(const krylov_handle* h, double* T, int64_t T_cap, double* X,
                                 int64_t X_cap, double* z, int64_t z_cap, int* m_eff);
 
+/* Self-test of failure detection without a fault.  The staged kernels wait
+ * for their bulk copies with a bounded mbarrier wait (1 s per wait); when a
+ * wait gives up the kernel sets a timeout flag, drains its own copies (again
+ * with a bound) and returns, and the call reports KRYLOV_ETIMEOUT.  This probe runs that wait in
+ * one CTA on the current device, on a barrier phase that completes and on one
+ * that never does (transaction bytes announced, no copy issued), with the
+ * bound limit_ns (1 .. 10^10 ns, else EINVAL):
+ *   timed_out : host, 2 ints: 1 where the wait gave up (expected: 0, 1);
+ *   wait_ns   : host, 2 doubles: the waits' durations in ns (the second one
+ *               at least limit_ns).
+ * The device stays usable afterwards. */
+krylov_status krylov_probe_bounded_wait(uint64_t limit_ns, int* timed_out, double* wait_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,7 @@ EXPORTED = [
     "krylov_last_cycle",
     "krylov_spmv_dot_noalloc",
     "krylov_apply_batched",
+    "krylov_probe_bounded_wait",
 ]
 
 
@@ -129,6 +130,8 @@ def load() -> C.CDLL:
     lib.krylov_spmv_dot_noalloc.restype = C.c_int
     lib.krylov_apply_batched.argtypes = [P, C.c_int, C.c_int, P, P, P, C.c_double, C.c_int, C.POINTER(Stats)]
     lib.krylov_apply_batched.restype = C.c_int
+    lib.krylov_probe_bounded_wait.argtypes = [C.c_uint64, P, P]
+    lib.krylov_probe_bounded_wait.restype = C.c_int
     _lib = lib
     return lib
 

@@ -1705,4 +1705,21 @@ krylov_status krylov_last_cycle(const krylov_handle* h, double* T, int64_t T_cap
   return KRYLOV_OK;
 }
 
+krylov_status krylov_probe_bounded_wait(uint64_t limit_ns, int* timed_out, double* wait_ns) {
+  if (limit_ns < 1 || limit_ns > 10000000000ull || !timed_out || !wait_ns) return KRYLOV_EINVAL;
+  unsigned long long* d_out = nullptr;
+  CK(cudaMalloc(&d_out, 4 * sizeof(unsigned long long)));
+  unsigned long long h_out[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemset(d_out, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = probe_bounded_wait((unsigned long long)limit_ns, d_out, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h_out, d_out, sizeof(h_out), cudaMemcpyDeviceToHost);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int c = 0; c < 2; ++c) {
+    timed_out[c] = (int)h_out[c];
+    wait_ns[c] = (double)h_out[2 + c];
+  }
+  return KRYLOV_OK;
+}
+
 }  // extern "C"

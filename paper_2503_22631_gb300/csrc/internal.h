@@ -175,6 +175,10 @@ void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTabl
 int sketch_bin_copies(int basis, int s);
 int sketch_word_bits(int rows_per_cta, int copies);
 
+// one CTA runs the bounded mbarrier wait on a completing and a never-completing
+// phase; d_out (4 values): gave-up flags, then durations in ns
+cudaError_t probe_bounded_wait(unsigned long long limit_ns, unsigned long long* d_out, cudaStream_t st);
+
 // ---- handle creation ------------------------------------------------------
 cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* d_flag, int* h_flag,
                          cudaStream_t st);

@@ -152,7 +152,38 @@ __global__ void row_abs_sum_kernel(int n, const int* rp, const double* val, unsi
   }
 }
 
+// Self-test of the bounded mbarrier wait that the staged kernels use.  Case 0
+// waits on a phase that completes (one plain arrival), case 1 on a phase that
+// never completes (16 transaction bytes announced, no copy issued: nothing
+// will ever arrive).  out[c] = 1 if the wait of case c gave up, out[2 + c] =
+// its duration in nanoseconds.  No copy is in flight at any time, so the CTA
+// may leave with the phase of case 1 still open.
+__global__ void wait_probe_kernel(unsigned long long limit_ns, unsigned long long* out) {
+  __shared__ __align__(8) uint64_t bar[2];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive(&bar[0]);
+    mbar_arrive_expect_tx(&bar[1], 16);
+    for (int c = 0; c < 2; ++c) {
+      const uint64_t t0 = global_ns();
+      const bool done = mbar_wait_bounded(&bar[c], 0u, limit_ns);
+      out[c] = done ? 0ull : 1ull;
+      out[2 + c] = global_ns() - t0;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t probe_bounded_wait(unsigned long long limit_ns, unsigned long long* d_out, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(limit_ns, d_out);
+  return cudaGetLastError();
+}
 
 // Raise (never lower) a kernel's dynamic shared-memory limit.  The limit is
 // per function and context, so threads that launch the same kernel with

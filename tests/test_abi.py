@@ -194,3 +194,9 @@ def test_calls_on_a_null_handle_are_rejected(lib):
                  (8, 64, 33, 0, 0, 1), (8, 8, 1, 0, -1, 1), (8, 8, 1, 0, 4, 5), (8, 8, 1, 0, 0, -1)]:
         assert lib.krylov_sketch_columns(*args, r, s_) == -1, args
     assert lib.krylov_sketch_columns(8, 8, 1, 0, 0, 0, r, s_) == 0  # nothing to generate
+    # bounded-wait probe: bound out of range or missing outputs
+    to = (C.c_int * 2)()
+    ns = (C.c_double * 2)()
+    pto, pns = C.cast(to, C.c_void_p), C.cast(ns, C.c_void_p)
+    for args in [(0, pto, pns), (10**10 + 1, pto, pns), (1000, None, pns), (1000, pto, None)]:
+        assert lib.krylov_probe_bounded_wait(*args) == -1, args
