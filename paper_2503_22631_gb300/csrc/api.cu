@@ -15,6 +15,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/krylov.h"
 #include "internal.h"
 #include "kernels.cuh"
@@ -254,6 +256,49 @@ krylov_status cuda_status(cudaError_t e) {
     cudaError_t e_ = (call);                              \
     if (e_ != cudaSuccess) return cuda_status(e_);        \
   } while (0)
+
+// Two timing events, destroyed on every path out of the scope that made them
+// (the calls below return early on errors).
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    return e;
+  }
+};
+
+// An NVTX range (visible to profilers that attach; a no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Consecutive NVTX ranges inside one scope: next() closes the open one and
+// opens the next; the last one closes with the scope.
+struct NvtxPhase {
+  bool open = false;
+  NvtxPhase() = default;
+  NvtxPhase(const NvtxPhase&) = delete;
+  NvtxPhase& operator=(const NvtxPhase&) = delete;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhase() {
+    if (open) nvtxRangePop();
+  }
+};
 
 template <typename T>
 cudaError_t dalloc(krylov_handle* h, T** p, size_t count) {
@@ -677,9 +722,9 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
   cudaStream_t st = h->st;
   CK(cudaMemsetAsync(h->W, 0, sizeof(float2) * 2 * (size_t)h->ldw, st));
   CK(cudaMemsetAsync(h->cd.flags, 0, 4 * sizeof(int), st));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  EventPair evp;
+  CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   auto time_variant = [&](bool seg) -> float {
     StepLaunch L = step_args(h, op, transpose, use32, 1e-12, 1);
     L.grid_spmv = seg ? grid_seg : grid_gather;
@@ -702,8 +747,6 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
     t_seg = std::min(t_seg, time_variant(true));
     t_gather = std::min(t_gather, time_variant(false));
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   CK(cudaGetLastError());
   if (!(t_seg < 0.97f * t_gather)) {
     sp.seg = nullptr;
@@ -728,9 +771,10 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   const int n = h->n, M = h->m;
   cudaStream_t st = h->st;
   krylov_stats stats{};
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  NvtxRange call_range(transpose ? "krylov_apply_adjoint" : "krylov_apply");
+  EventPair evp;
+  CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   CK(cudaEventRecord(e0, st));
 
   int levels_needed = 1;
@@ -763,6 +807,9 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   double maxX = 0.0, maxG = 0.0;
   krylov_status result = KRYLOV_NOT_CONVERGED;
   for (int c = 1; c <= max_cycles; ++c) {
+    NvtxRange cycle_range("restart cycle");
+    NvtxPhase phase;
+    phase.next("arnoldi steps");
     launch_cycle_reset(h->cd, M, st);
     CK(cudaEventRecord(h->ev[0], st));
     const bool rgs = (h->opt.ortho == KRYLOV_ORTHO_RGS);
@@ -825,6 +872,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
         stats.step_bytes += me * model_bytes_step(h, use32);
       }
     }
+    phase.next("small problem");
     if (rgs) {
       launch_rgs_small(h->sd, h->cd, M, me, has_next, c, h->f.t, st);
       stats.launches += 1;
@@ -869,6 +917,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     } else {
       return KRYLOV_EUNSUPPORTED;
     }
+    phase.next("update");
     launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid_update, h->cd, M, st);
     stats.launches += 1;
     CK(cudaGetLastError());
@@ -905,8 +954,6 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   stats.ms_total = ms;
   const double bv = basis_bytes(basis);
   stats.bytes_moved = stats.steps * model_bytes_step(h, use32) +
@@ -1113,9 +1160,10 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
   L.rows_p = (n + L.grid_p - 1) / L.grid_p;
   L.fx_wb = sketch_word_bits(L.rows_per_cta, 1);
   L.thr = 1e-12;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  NvtxRange call_range("krylov_apply_batched block");
+  EventPair evp;
+  CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   CK(cudaEventRecord(e0, s_));
   // x = 0 in the block's columns; flags, misc cleared
   launch_zero_columns(X, n, ldb, nb, s_);
@@ -1236,8 +1284,6 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   // block-wide figures are reported once, on the block's first right-hand side
   for (int r = 0; r < nb; ++r) {
     st[r].ms_total = ms;
@@ -1601,9 +1647,10 @@ krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* 
     CK(dalloc(h, &h->stage_b, (size_t)h->n));
     CK(dalloc(h, &h->stage_x, (size_t)h->n));
   }
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  NvtxRange call_range("krylov_apply_host");
+  EventPair evp;
+  CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   CK(cudaEventRecord(e0, h->st));
   krylov_status r = KRYLOV_ECUDA;
   if (cudaMemcpyAsync(h->stage_b, b_host, sizeof(double) * (size_t)h->n, cudaMemcpyHostToDevice, h->st) ==
@@ -1618,8 +1665,6 @@ krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* 
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   if (st) st->ms_total = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return r;
 }
 
