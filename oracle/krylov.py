@@ -33,6 +33,14 @@ Readings where the paper is silent (each one is listed in the design notes):
   columns; the decomposition is then exact and the method stops.
 * RGS cycles c >= 2 normalize the start vector by alpha' = ||S w_{m+1}||
   (= 1 up to rounding) and discard alpha', as Algorithm 2 does.
+* Reduced-precision storage of the basis (TRUNC only, ``store``): every basis
+  vector is rounded to the storage precision when it is stored (the start
+  vector w_1 and each new w_{j+1} = p / r_{j+1,j}); every later use -- the next
+  product, the window dots and updates, the sketch, the restart vector and
+  x += W z -- reads the stored value, and all arithmetic stays FP64.  The
+  Arnoldi-like relation of Sec. 2.2 (Eq. 5) then holds for the stored vectors
+  up to the storage rounding of each new column, which is the perturbation a
+  float32 or bfloat16 basis makes to the method.
 """
 from __future__ import annotations
 
@@ -48,6 +56,26 @@ RGS = "rgs"
 TRUNC = "trunc"
 
 BREAKDOWN_REL = 1e-14
+
+F64, F32, BF16 = "f64", "f32", "bf16"
+
+
+def round_storage(v, store):
+    """v rounded to the storage format `store` and returned as float64:
+    F64 (or None) leaves v as is; F32 rounds to IEEE binary32; BF16 rounds to
+    bfloat16 (binary32's sign, exponent and top 7 fraction bits) to nearest
+    with ties to even, from the binary32 value."""
+    if store is None or store == F64:
+        return np.asarray(v, dtype=np.float64)
+    f = np.asarray(v, dtype=np.float64).astype(np.float32)
+    if store == F32:
+        return f.astype(np.float64)
+    if store != BF16:
+        raise ValueError(f"unknown storage format {store!r}")
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)  # ties go to the even upper half
+    r = ((u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
 
 
 def csr_matvec(A, x):
@@ -131,12 +159,13 @@ def _arnoldi_randomized(A, S, w_start, m, k):
     return alpha, W, R, Us, m, False
 
 
-def _arnoldi_truncated(A, w1, m, k):
-    """Incomplete Arnoldi: classical Gram-Schmidt against the last k vectors."""
+def _arnoldi_truncated(A, w1, m, k, store=None):
+    """Incomplete Arnoldi: classical Gram-Schmidt against the last k vectors.
+    Stored vectors are rounded to `store` (see round_storage)."""
     n = w1.size
     W = np.zeros((n, m + 1))
     R = np.zeros((m + 1, m))
-    W[:, 0] = w1
+    W[:, 0] = round_storage(w1, store)
     for j in range(m):
         p = csr_matvec(A, W[:, j])
         pn = np.linalg.norm(p)
@@ -148,7 +177,7 @@ def _arnoldi_truncated(A, w1, m, k):
         R[j + 1, j] = np.linalg.norm(p)
         if R[j + 1, j] <= BREAKDOWN_REL * pn:
             return W[:, : j + 1], R[: j + 1, : j + 1], j + 1, True
-        W[:, j + 1] = p / R[j + 1, j]
+        W[:, j + 1] = round_storage(p / R[j + 1, j], store)
     return W, R, m, False
 
 
@@ -165,7 +194,7 @@ def _append_block(H, X, gamma):
 
 
 def restarted(A, b, fkind, t, m, k, s, zeta, seed, mode=TRUNC, tol=0.0, max_cycles=1,
-              sketch=None, keep=False, abs_tol=False):
+              sketch=None, keep=False, abs_tol=False, store=None):
     """Approximate f(A) b by the restarted method of the chosen mode.
 
     A       workloads.Csr; b: (n,) float64.
@@ -174,7 +203,10 @@ def restarted(A, b, fkind, t, m, k, s, zeta, seed, mode=TRUNC, tol=0.0, max_cycl
     s, zeta sketch rows and nonzeros per sketch column; seed keys the sketch.
     tol     stop once ||y|| <= tol * ||x|| (or <= tol if abs_tol).
     keep    keep per-cycle matrices (R, T, X, W, U, z) in the result's info.
+    store   TRUNC only: storage format of the basis (F64 = None, F32, BF16).
     """
+    if store not in (None, F64) and mode != TRUNC:
+        raise ValueError("reduced-precision storage is modelled for the TRUNC mode only")
     b = np.asarray(b, dtype=np.float64)
     n = b.size
     if mode != CLASSICAL and sketch is None:
@@ -228,7 +260,7 @@ def restarted(A, b, fkind, t, m, k, s, zeta, seed, mode=TRUNC, tol=0.0, max_cycl
                 w1 = b / eta
             else:
                 w1 = start
-            W, Rbar, me, brk = _arnoldi_truncated(A, w1, m, k)
+            W, Rbar, me, brk = _arnoldi_truncated(A, w1, m, k, store)
             ncols = me if brk else me + 1
             U = S.apply(W[:, :ncols])
             Q, T = dense.qr_positive(U)

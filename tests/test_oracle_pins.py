@@ -619,3 +619,83 @@ def test_rmat_laplacian_directed():
     ones = np.ones(L.n)
     r = K.restarted(L, ones, D.EXP_NEG, 0.1, 20, 20, 60, 8, 3, mode=K.RGS, tol=0.0, max_cycles=2)
     assert rel(r.x, ones) < 1e-13
+
+
+# ---- reduced-precision storage of the basis (the precision form) ----------
+def test_round_storage_bf16_matches_torch_conversion():
+    """bfloat16 rounding (nearest, ties to even) against torch's float32 ->
+    bfloat16 conversion, on random values and on exact halfway cases."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-30, 30, 4000),
+                        [0.0, -0.0, 1.0, -2.5, 3.0e38]])
+    f = v.astype(np.float32)
+    # halfway cases: the dropped 16 bits are exactly 0x8000, upper half odd and even
+    u = f.view(np.uint32)
+    halves = ((u & np.uint32(0xFFFF0000)) | np.uint32(0x8000)).view(np.float32)
+    f = np.concatenate([f, halves])
+    want = torch.from_numpy(f).to(torch.bfloat16).to(torch.float64).numpy()
+    got = K.round_storage(f.astype(np.float64), K.BF16)
+    assert np.array_equal(got, want)
+
+
+def test_round_storage_f32_and_f64():
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(1000) * 1e3
+    assert np.array_equal(K.round_storage(v, K.F64), v)
+    assert np.array_equal(K.round_storage(v, None), v)
+    r = K.round_storage(v, K.F32)
+    assert np.array_equal(r, v.astype(np.float32).astype(np.float64))
+    assert np.all(np.abs(r - v) <= 2.0**-24 * np.abs(v))
+    with pytest.raises(ValueError):
+        K.round_storage(v, "f16")
+
+
+@pytest.mark.parametrize("store,u", [(K.F32, 2.0**-24), (K.BF16, 2.0**-8)])
+def test_stored_basis_is_representable_and_relation_holds_to_storage_rounding(store, u):
+    """With a reduced-precision basis every stored column is exactly
+    representable in the storage format, and the Arnoldi-like relation
+    A W_m = W_{m+1} R_m (Eq. 5) holds for the stored vectors up to the storage
+    rounding of each new column: column j's residual is at most
+    u r_{j+1,j} ||w_{j+1}|| (u the unit roundoff of the format), while with
+    FP64 storage it is at the FP64 rounding level."""
+    A = W.convdiff(14, 2, (30.0, 10.0))
+    b = W.rhs_normal(A.n, 8)
+    m, k = 12, 2
+    r = K.restarted(A, b, D.EXP_NEG, 1e-3, m, k, 40, 8, 9, mode=K.TRUNC, max_cycles=2, keep=True, store=store)
+    r64 = K.restarted(A, b, D.EXP_NEG, 1e-3, m, k, 40, 8, 9, mode=K.TRUNC, max_cycles=2, keep=True)
+    for ci, c64 in zip(r.info, r64.info):
+        Wst, R = ci.W, ci.R
+        assert np.array_equal(Wst, K.round_storage(Wst, store))
+        AW = np.column_stack([K.csr_matvec(A, Wst[:, j]) for j in range(m)])
+        res = np.linalg.norm(AW - Wst @ R, axis=0)
+        bound = u * np.abs(np.diag(R, -1)) * np.linalg.norm(Wst[:, 1:], axis=0)
+        assert np.all(res <= 1.01 * bound + 1e-12 * np.linalg.norm(AW, axis=0))
+        # the storage rounding is what the relation misses: not FP64-level
+        assert res.max() > 1e3 * 2.0**-53 * np.abs(np.diag(R, -1)).max()
+        AW64 = np.column_stack([K.csr_matvec(A, c64.W[:, j]) for j in range(m)])
+        res64 = np.linalg.norm(AW64 - c64.W @ c64.R, axis=0)
+        assert np.all(res64 <= 1e-13 * np.linalg.norm(AW64, axis=0))
+
+
+def test_store_rounds_the_start_vector():
+    """A = c I: every vector is an eigenvector, so the cycle breaks down after
+    one column and x = eta exp(-t c) w_1 exactly, with w_1 the STORED start
+    vector round(b / eta); with FP64 storage that is exp(-t c) b.  The
+    reduced-precision result differs from the FP64 one by exactly the storage
+    rounding of b / eta."""
+    n, c, t = 64, 3.7, 0.3
+    A = W.Csr(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, c))
+    b = W.rhs_normal(n, 6)
+    eta = np.linalg.norm(b)
+    r64 = K.restarted(A, b, D.EXP_NEG, t, 4, 2, 20, 8, 3, mode=K.TRUNC, max_cycles=1)
+    assert r64.breakdown
+    np.testing.assert_allclose(r64.x, np.exp(-t * c) * b, rtol=1e-14)
+    for store in (K.F32, K.BF16):
+        r = K.restarted(A, b, D.EXP_NEG, t, 4, 2, 20, 8, 3, mode=K.TRUNC, max_cycles=1, store=store)
+        assert r.breakdown
+        w1 = K.round_storage(b / eta, store)
+        np.testing.assert_allclose(r.x, eta * np.exp(-t * c) * w1, rtol=1e-14)
+        assert not np.allclose(r.x, r64.x, rtol=1e-3 * (2.0**-24 if store == K.F32 else 2.0**-8), atol=0)
+    with pytest.raises(ValueError):
+        K.restarted(A, b, D.EXP_NEG, t, 4, 2, 20, 8, 3, mode=K.RGS, max_cycles=1, store=K.F32)
