@@ -200,8 +200,10 @@ krylov_status krylov_spmv(krylov_handle* h, const double* x, double* y, int tran
 
 /* y <- A x and, if dot_with is not NULL, *dot_out <- <dot_with, y>, without
  * allocating anything.  The paper has no counterpart: this is for callers that
- * cannot allocate device memory when they need the product (during CUDA graph
- * capture, inside a custom allocator, in latency-critical loops).  Unlike
+ * cannot allocate device memory when they need the product -- numerical code
+ * called back from inside a custom device allocator or memory pool (a nested
+ * allocation would re-enter it) and real-time loops in which cudaMalloc may
+ * block or synchronize the device.  Unlike
  * krylov_spmv it needs no handle: row_ptr (n+1), col_idx, val (nnz, float64),
  * x, y (n) and dot_with, dot_out (n and 1 element) are caller-owned DEVICE
  * pointers (dot_with and dot_out both NULL or both set); stream is a
@@ -209,8 +211,10 @@ krylov_status krylov_spmv(krylov_handle* h, const double* x, double* y, int tran
  * that stream; it does not validate the CSR structure (krylov_create does).
  * Scratch: a fixed 16 KiB device array inside the library, shared by all
  * calls on a device and kept until the process exits; the first call on a
- * device looks its address up (make it before any stream capture), and calls
- * that overlap on the GPU race on it.  Limits: 1 <= n <= 2^31 - 2,
+ * device looks its address up (make it before any stream capture: a first
+ * call on a capturing stream returns KRYLOV_EINVAL), and calls that overlap
+ * on the GPU race on it (serialize them).  The grid is capped at 2048 CTAs,
+ * rows per CTA grow with n.  Limits: 1 <= n <= 2^31 - 2,
  * 0 <= nnz <= 2^31 - 1, else KRYLOV_EINVAL. */
 krylov_status krylov_spmv_dot_noalloc(int64_t n, int64_t nnz, const int32_t* row_ptr,
                                       const int32_t* col_idx, const double* val, const double* x,

@@ -1,10 +1,10 @@
 // noalloc.cu -- y = A x and <d, y> for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the moment they need this product:
-// code running while a CUDA graph is being captured on the stream, allocators
-// that forbid nested allocation (a custom memory pool calling back into
-// numerical code), or real-time loops where an allocation may block on the
-// driver.  This entry point therefore allocates nothing: the caller passes the
+// numerical code called back from inside a custom device memory pool or
+// allocator (a nested allocation would re-enter the allocator that is running),
+// and real-time loops in which cudaMalloc may block on the driver or
+// synchronize the device.  This entry point therefore allocates nothing: the caller passes the
 // matrix, the input and the outputs as device pointers, and the only scratch
 // memory (per-CTA partial sums of the dot product and the arrival counter of
 // the final reduction) is the file-scope device array below, which exists on
@@ -12,7 +12,8 @@
 //
 // Set-up: the first call on a device (with that device current) resolves the
 // array's device address with cudaGetSymbolAddress; make that first call
-// before any stream capture.  All calls share the array and it keeps the
+// before any stream capture (a first call on a capturing stream is refused
+// with KRYLOV_EINVAL).  All calls share the array and it keeps the
 // contents of the last call: the counter is cleared at the start of every
 // call, and two calls whose work overlaps on the GPU (different streams,
 // different host threads) race on it -- serialize them.
@@ -42,10 +43,13 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) spmv_dot_noalloc_kernel(
     NoallocScratch* scr, int rows_per_cta) {
   __shared__ double red[32];
   __shared__ int s_last;
-  const int r0 = blockIdx.x * rows_per_cta;
-  const int r1 = (int)min((long long)n, (long long)r0 + rows_per_cta);
+  // 64-bit row indices: r0 + rows_per_cta and i + blockDim.x may pass INT_MAX
+  // for n near the limit; CTAs past the last row (the grid is capped, so
+  // rows_per_cta is rounded up) have an empty range and add 0 to the dot.
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = min((long long)n, r0 + rows_per_cta);
   double acc = 0.0;
-  for (int i = r0 + (int)threadIdx.x; i < r1; i += blockDim.x) {
+  for (long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     double yi = 0.0;
     for (int e = rp[i]; e < rp[i + 1]; ++e) yi = fma(val[e], x[ci[e]], yi);
     y[i] = yi;
@@ -85,6 +89,11 @@ extern "C" krylov_status krylov_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
+      // the symbol lookup may load the module, which is not allowed while the
+      // stream is being captured: refuse instead of invalidating the capture
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs) != cudaSuccess) return KRYLOV_ECUDA;
+      if (cs != cudaStreamCaptureStatusNone) return KRYLOV_EINVAL;
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, krylov_noalloc_scratch) != cudaSuccess || p == nullptr) return KRYLOV_ECUDA;
       g_scratch_ptr[dev] = static_cast<NoallocScratch*>(p);
