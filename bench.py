@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--basis", default="df64", choices=["df64", "f64", "f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64-basis solve timed beside the headline")
     ap.add_argument("--cycles", type=int, default=None, help="override the cycle count (profiling)")
     ap.add_argument("--workload", default="convdiff3d_128",
                     choices=["convdiff3d_128", "convdiff3d_128_rgs", "convdiff3d_128_phi1", "poisson2d_1448_cos",
@@ -98,14 +99,28 @@ def make_inputs():
 
 
 # ------------------------------------------------------------------ oracle --
-ORACLE_SAMPLE_STEPS = 8
+def host_cpu():
+    """Host core count and CPU model (for the baseline's description)."""
+    model = ""
+    try:
+        for line in Path("/proc/cpuinfo").read_text().splitlines():
+            k = line.split(":", 1)[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return os.cpu_count() or 1, model
 
 
-def _oracle_sample_child(out_path: str, steps: int):
-    """Child process: time `steps` Arnoldi steps of one oracle cycle plus its
-    whitening and dense f on the full workload (single thread)."""
-    import numpy as np
-
+def _oracle_sample_child(out_path: str, cycles: int):
+    """Child process: time `cycles` whole restart cycles of the oracle (m = 40
+    Arnoldi steps, the sketch, the whitening QR, the dense exp of the block
+    matrix and the update each) on the full headline workload."""
     import workloads as W
     from oracle import dense as D
     from oracle import krylov as K
@@ -114,38 +129,55 @@ def _oracle_sample_child(out_path: str, steps: int):
     A, b = make_inputs()
     S = SparseSign(A.n, WORKLOAD["s"], WORKLOAD["zeta"], W.SEED)  # generated once per run
     t0 = time.perf_counter()
-    K.restarted(A, b, D.EXP_NEG, WORKLOAD["t"], steps, WORKLOAD["k"], WORKLOAD["s"], WORKLOAD["zeta"], W.SEED,
-                mode=K.TRUNC, tol=0.0, max_cycles=1, sketch=S)
+    K.restarted(A, b, D.EXP_NEG, WORKLOAD["t"], WORKLOAD["m"], WORKLOAD["k"], WORKLOAD["s"], WORKLOAD["zeta"],
+                W.SEED, mode=K.TRUNC, tol=0.0, max_cycles=cycles, sketch=S)
     dt = time.perf_counter() - t0
-    Path(out_path).write_text(json.dumps({"seconds": dt, "steps": steps}))
+    Path(out_path).write_text(json.dumps({"seconds": dt, "cycles": cycles}))
 
 
-def oracle_seconds_per_solve(cycles: int, steps: int = ORACLE_SAMPLE_STEPS):
-    """Run the oracle sample in a fresh single-threaded process; extrapolate
-    linearly in Arnoldi steps to `cycles` x m steps."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def oracle_seconds_per_solve(cycles: int, threads: int = 1, sample_cycles: int = 1):
+    """Run `sample_cycles` whole oracle cycles in a fresh process with `threads`
+    BLAS threads (the oracle's only multithreaded parts are its dense BLAS
+    calls; its sparse product is one numpy pass); scale linearly in cycles."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     with tempfile.TemporaryDirectory() as td:
         out = Path(td) / "o.json"
         code = (f"import sys; sys.path.insert(0, {str(ROOT)!r}); import bench; "
-                f"bench._oracle_sample_child({str(out)!r}, {steps})")
+                f"bench._oracle_sample_child({str(out)!r}, {sample_cycles})")
         subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=str(ROOT))
         r = json.loads(out.read_text())
-    per_step = r["seconds"] / r["steps"]
-    total_steps = cycles * WORKLOAD["m"]
-    return per_step * total_steps, r
+    return r["seconds"] / r["cycles"] * cycles, r
+
+
+def cpu_baseline_line(cycles: int):
+    """The oracle timed on the host: one whole restart cycle at full size on one
+    thread and on all host cores, scaled to `cycles` cycles."""
+    ncpu, model = host_cpu()
+    v1, r1 = oracle_seconds_per_solve(cycles, 1)
+    vn, rn = oracle_seconds_per_solve(cycles, ncpu)
+    best, cores = (vn, ncpu) if vn < v1 else (v1, 1)
+    return {"value": best, "unit": "s", "cores": cores, "kind": "oracle",
+            "host": {"nproc": ncpu, "cpu": model},
+            "single_thread": {"value": v1, "cores": 1, "cycle_seconds": r1["seconds"]},
+            "all_cores": {"value": vn, "cores": ncpu, "cycle_seconds": rn["seconds"]},
+            "sample": (f"one whole oracle restart cycle (40 Arnoldi steps, sketch, whitening QR, dense exp, "
+                       f"update) on the full workload, {r1['seconds']:.1f} s on 1 thread and "
+                       f"{rn['seconds']:.1f} s with {ncpu} BLAS threads, scaled linearly to {cycles} cycles; "
+                       f"value = the faster of the two")}
 
 
 def reference_main(args, rank):
     if rank != 0:
         return
     cycles = CYCLES_TO_1E8["df64"]
+    ncpu, model = host_cpu()
     vals = []
     sample = None
     for _ in range(args.warmup):
-        oracle_seconds_per_solve(cycles, 2)
+        oracle_seconds_per_solve(cycles, ncpu)
     for _ in range(args.steps):
-        v, sample = oracle_seconds_per_solve(cycles)
+        v, sample = oracle_seconds_per_solve(cycles, ncpu)
         vals.append(v)
     value = statistics.median(vals)
     line = {
@@ -164,10 +196,11 @@ def reference_main(args, rank):
         "data": "synthetic",
         "config": {"workload": WORKLOAD["workload"], "n": 128**3, "m": 40, "k": 2, "s": 160, "zeta": 8,
                    "t": 1e-2, "cycles": cycles},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"{ORACLE_SAMPLE_STEPS} Arnoldi steps of one oracle cycle (plus its "
-                                   f"whitening and dense exp) at full size per bench step, scaled linearly "
-                                   f"to {cycles} cycles x m=40 steps; median of {args.steps}"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": ncpu, "kind": "oracle",
+                         "host": {"nproc": ncpu, "cpu": model},
+                         "sample": f"one whole oracle restart cycle at full size per bench step ({ncpu} BLAS "
+                                   f"threads; last {sample['seconds']:.1f} s), scaled linearly to {cycles} "
+                                   f"cycles; median of {args.steps}"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -448,6 +481,38 @@ def secondary_main(args):
     print(json.dumps(line), flush=True)
 
 
+def plain_fp64_solve(A, bd, cycles, warmup, steps, stream, peak, barrier):
+    """Time the same solve with the float64 basis (float64 streaming arithmetic)
+    on the same stream and GPU; returns its sub-object of the JSON line."""
+    import torch
+
+    from paper_2503_22631_gb300 import BASIS_F64, F_EXP_NEG, Krylov
+
+    kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=WORKLOAD["t"], m=WORKLOAD["m"], k=WORKLOAD["k"],
+                s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], basis=BASIS_F64, stream=stream)
+    x = torch.empty_like(bd)
+    for _ in range(warmup):
+        kr.apply(bd, tol=0.0, max_cycles=cycles, out=x)
+    barrier()
+    stats = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        kr.apply(bd, tol=0.0, max_cycles=cycles, out=x)
+        stats.append(dict(kr.stats))
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    steps_ms = sum(s["ms_steps"] for s in stats)
+    achieved = sum(s["step_bytes"] for s in stats) / (steps_ms / 1e3) / 1e9
+    del kr
+    return {"basis": "f64", "value": ms / 1e3 / steps, "unit": "s", "ms_total": ms, "cycles": cycles,
+            "ms_steps_per_solve": steps_ms / steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "Arnoldi step: step_kernel<double> (fused SpMV + truncated orthogonalization + "
+                                   "sketch, float64 arithmetic)"}}
+
+
 # ------------------------------------------------------------------- main ---
 def main():
     args = parse()
@@ -539,16 +604,22 @@ def main():
             e2e_s = (time.perf_counter() - t0) / (args.steps * world)
             e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * A.n, "d2h_bytes_per_step": 8 * A.n}
 
+        # the plain float64 form on the same GPU and workload (same cycles, same
+        # timing protocol): the mixed-precision comparison point
+        fp64 = None
+        if not args.no_fp64 and not args.profile and args.basis != "f64":
+            fp64 = plain_fp64_solve(A, bd, cycles, warmup, args.steps, stream, peak, barrier)
+            if world > 1:
+                fp64["value"] = seconds_per_solve(max_over_ranks(fp64["ms_total"], world,
+                                                                 torch.device("cuda", local)), args.steps, world)
+
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, r = oracle_seconds_per_solve(cycles)
-        cpu = {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"{r['steps']} Arnoldi steps of one oracle cycle (plus its whitening and dense exp) "
-                         f"at full size in {r['seconds']:.1f} s, scaled linearly to {cycles} cycles x m=40 steps"}
+        cpu = cpu_baseline_line(cycles)
     line = {
         "metric": METRIC,
         "value": sec_per_solve,
@@ -577,6 +648,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
+        "fp64": fp64,
         "solve": {"cycles": stats[-1]["cycles"], "step_launches_per_solve": step_launches // args.steps,
                   "ms_steps_per_solve": steps_ms / args.steps, "last_update_rel": stats[-1]["last_update_norm"] /
                   max(stats[-1]["x_norm"], 1e-300)},

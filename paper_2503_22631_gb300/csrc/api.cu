@@ -565,9 +565,11 @@ krylov_status build_transpose(krylov_handle* h) {
 double model_bytes_step(const krylov_handle* h, int use32) {
   const double bv = basis_bytes(h->opt.basis_dtype);
   const double ba = use32 ? 4.0 : 8.0;
-  // column entries as stored for the product: 2-byte offsets for a banded operator
-  const double bi = (h->dcol != nullptr) ? 2.0 : 4.0;
-  return (double)h->nnz * (ba + bi) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
+  // the lower bound of the roofline model: A read once with 4-byte column
+  // indices (also when the product kernel streams 2-byte offsets instead),
+  // the current vector and the k-1 other window vectors read once, the new
+  // vector written once
+  return (double)h->nnz * (ba + 4.0) + 4.0 * (h->n + 1) + (h->k + 1) * (double)h->n * bv;
 }
 
 // Randomized Gram-Schmidt step j: read A and w_j, write p; the sketch reads p

@@ -186,6 +186,85 @@ __device__ __forceinline__ SketchSpec spec_of(const StepLaunch& L) {
   return t;
 }
 
+// ---- reducers of the step kernels ------------------------------------------
+// The reducers run in the last CTA of a kernel while the rest of the GPU
+// waits for it, and every float64 instruction of a lone warp holds the FP64
+// pipe of its SM sub-partition for many cycles: so all loads come before any
+// store (the stores may alias them, which would serialize round trips to L2),
+// the window slots are handled by parallel lanes, and no quotient or square
+// root is formed that another one already gives.
+
+// Reducer of a materialized column j (lane 0): record ||w_j||^2 and flag a
+// happy breakdown when ||w_j|| / rho_j, the norm of the orthogonalized
+// product, is below thr ||A w_{j-1}||.  1 / rho_j = R[j, j-1] was stored by
+// the reducer of the product p_{j-1}; the test is taken on squares.  Returns
+// whether the cycle has ended in breakdown.
+__device__ __forceinline__ bool reduce_mat(const StepLaunch& L, const CycleDev& cd, double sig2, int mat) {
+  const int j = L.j;
+  const int ldr = L.m + 1;  // R is (m+1) x m, column-major
+  const double rsub = mat ? __ldcg(cd.R + (size_t)(j - 1) * ldr + j) : 0.0;
+  const double pprev = mat ? __ldcg(cd.pi + j - 1) : 0.0;
+  int brk = __ldcg(cd.flags + 1);
+  cd.sig2[j] = sig2;
+  if (!isfinite(sig2)) cd.flags[2] |= ERR_NONFINITE;
+  if (mat) {
+    const double rn2 = sig2 * (rsub * rsub);
+    if (!(rn2 > (L.thr * L.thr) * pprev) && brk == 0) {
+      cd.flags[1] = 1;
+      cd.flags[0] = j;
+      brk = 1;
+    }
+  }
+  return brk != 0;
+}
+
+// Reducer of a product p_j = A w_j (one warp; lane q takes window slot
+// dlo + q): projection coefficients h_q = <w_q, p_j> / ||w_q||^2, R[q, j] =
+// h_q, the scale rho_{j+1} = 1 / sqrt(||p_j||^2 - sum_q h_q^2 ||w_q||^2) of
+// the next column (the window is orthogonal) with R[j+1, j] = 1 / rho_{j+1},
+// and the bound rho_{j+1} (||p_j|| + sum_q |h_q| ||w_q||) on |w_{j+1}[i]|
+// (triangle inequality) for the next materialization's fixed-point sketch.
+// brk: the cycle has already ended in breakdown (no further coefficients).
+// own_s2: ||w_j||^2 when this kernel formed w_j itself (its reducer has only
+// just stored it), negative otherwise (read from memory).
+__device__ __forceinline__ void reduce_spmv(const StepLaunch& L, const CycleDev& cd, const double* tot, bool brk,
+                                            double own_s2 = -1.0) {
+  const int lane = threadIdx.x & 31;
+  const int j = L.j;
+  const int ldr = L.m + 1;
+  const int dlo = max(0, j - L.k + 1);
+  const int slot = dlo + lane;
+  const bool inwin = !L.rgs && lane < MAX_WINDOW && slot <= j;
+  const double s2 = !inwin ? 0.0 : ((slot == j && own_s2 >= 0.0) ? own_s2 : __ldcg(cd.sig2 + slot));
+  const double pi = tot[1];
+  const double dq = inwin ? tot[2 + lane] : 0.0;
+  if (brk) return;
+  if (lane == 0) {
+    cd.pi[j] = pi;
+    if (!isfinite(pi)) cd.flags[2] |= ERR_NONFINITE;
+  }
+  if (L.rgs) return;  // the sketch-space orthogonalization takes it from here
+  const double h = (inwin && s2 > 0.0) ? dq / s2 : 0.0;
+  double e2 = h * h * s2;
+  double bq = inwin ? fabs(h) * sqrt(s2) : 0.0;
+  static_assert(MAX_WINDOW == 4, "window sums over groups of four lanes");
+  e2 += __shfl_xor_sync(FULL, e2, 1);
+  e2 += __shfl_xor_sync(FULL, e2, 2);
+  bq += __shfl_xor_sync(FULL, bq, 1);
+  bq += __shfl_xor_sync(FULL, bq, 2);
+  double* c = cd.coef + (size_t)j * (MAX_WINDOW + 1);
+  if (inwin) cd.R[(size_t)j * ldr + slot] = h;
+  if (lane < MAX_WINDOW) c[lane] = h;
+  if (lane == 0) {
+    const double est = fmax(pi - e2, 1e-20 * pi);
+    const double r = (pi > 0.0) ? sqrt(est) : 1.0;  // 1 / rho_{j+1}
+    const double rho = 1.0 / r;
+    c[MAX_WINDOW] = rho;
+    cd.R[(size_t)j * ldr + j + 1] = r;
+    cd.scal[6] = (sqrt(pi) + bq) * rho;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Float-float basis ("df64"): (hi, lo) float pairs, arithmetic on the FP32
 // pipes.

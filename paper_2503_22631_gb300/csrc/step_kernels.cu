@@ -60,84 +60,6 @@ template <> struct Types<double> {
 
 constexpr int STAGE = 512;          // staged nonzeros per warp in the CSR stream
 
-// The reducers run in the last CTA of a kernel while the rest of the GPU
-// waits for it, and every float64 instruction of a lone warp holds the FP64
-// pipe of its SM sub-partition for many cycles: so all loads come before any
-// store (the stores may alias them, which would serialize round trips to L2),
-// the window slots are handled by parallel lanes, and no quotient or square
-// root is formed that another one already gives.
-
-// Reducer of a materialized column j (lane 0): record ||w_j||^2 and flag a
-// happy breakdown when ||w_j|| / rho_j, the norm of the orthogonalized
-// product, is below thr ||A w_{j-1}||.  1 / rho_j = R[j, j-1] was stored by
-// the reducer of the product p_{j-1}; the test is taken on squares.  Returns
-// whether the cycle has ended in breakdown.
-__device__ __forceinline__ bool reduce_mat(const StepLaunch& L, const CycleDev& cd, double sig2, int mat) {
-  const int j = L.j;
-  const int ldr = L.m + 1;  // R is (m+1) x m, column-major
-  const double rsub = mat ? __ldcg(cd.R + (size_t)(j - 1) * ldr + j) : 0.0;
-  const double pprev = mat ? __ldcg(cd.pi + j - 1) : 0.0;
-  int brk = __ldcg(cd.flags + 1);
-  cd.sig2[j] = sig2;
-  if (!isfinite(sig2)) cd.flags[2] |= ERR_NONFINITE;
-  if (mat) {
-    const double rn2 = sig2 * (rsub * rsub);
-    if (!(rn2 > (L.thr * L.thr) * pprev) && brk == 0) {
-      cd.flags[1] = 1;
-      cd.flags[0] = j;
-      brk = 1;
-    }
-  }
-  return brk != 0;
-}
-
-// Reducer of a product p_j = A w_j (one warp; lane q takes window slot
-// dlo + q): projection coefficients h_q = <w_q, p_j> / ||w_q||^2, R[q, j] =
-// h_q, the scale rho_{j+1} = 1 / sqrt(||p_j||^2 - sum_q h_q^2 ||w_q||^2) of
-// the next column (the window is orthogonal) with R[j+1, j] = 1 / rho_{j+1},
-// and the bound rho_{j+1} (||p_j|| + sum_q |h_q| ||w_q||) on |w_{j+1}[i]|
-// (triangle inequality) for the next materialization's fixed-point sketch.
-// brk: the cycle has already ended in breakdown (no further coefficients).
-// own_s2: ||w_j||^2 when this kernel formed w_j itself (its reducer has only
-// just stored it), negative otherwise (read from memory).
-__device__ __forceinline__ void reduce_spmv(const StepLaunch& L, const CycleDev& cd, const double* tot, bool brk,
-                                            double own_s2 = -1.0) {
-  const int lane = threadIdx.x & 31;
-  const int j = L.j;
-  const int ldr = L.m + 1;
-  const int dlo = max(0, j - L.k + 1);
-  const int slot = dlo + lane;
-  const bool inwin = !L.rgs && lane < MAX_WINDOW && slot <= j;
-  const double s2 = !inwin ? 0.0 : ((slot == j && own_s2 >= 0.0) ? own_s2 : __ldcg(cd.sig2 + slot));
-  const double pi = tot[1];
-  const double dq = inwin ? tot[2 + lane] : 0.0;
-  if (brk) return;
-  if (lane == 0) {
-    cd.pi[j] = pi;
-    if (!isfinite(pi)) cd.flags[2] |= ERR_NONFINITE;
-  }
-  if (L.rgs) return;  // the sketch-space orthogonalization takes it from here
-  const double h = (inwin && s2 > 0.0) ? dq / s2 : 0.0;
-  double e2 = h * h * s2;
-  double bq = inwin ? fabs(h) * sqrt(s2) : 0.0;
-  static_assert(MAX_WINDOW == 4, "window sums over groups of four lanes");
-  e2 += __shfl_xor_sync(FULL, e2, 1);
-  e2 += __shfl_xor_sync(FULL, e2, 2);
-  bq += __shfl_xor_sync(FULL, bq, 1);
-  bq += __shfl_xor_sync(FULL, bq, 2);
-  double* c = cd.coef + (size_t)j * (MAX_WINDOW + 1);
-  if (inwin) cd.R[(size_t)j * ldr + slot] = h;
-  if (lane < MAX_WINDOW) c[lane] = h;
-  if (lane == 0) {
-    const double est = fmax(pi - e2, 1e-20 * pi);
-    const double r = (pi > 0.0) ? sqrt(est) : 1.0;  // 1 / rho_{j+1}
-    const double rho = 1.0 / r;
-    c[MAX_WINDOW] = rho;
-    cd.R[(size_t)j * ldr + j + 1] = r;
-    cd.scal[6] = (sqrt(pi) + bq) * rho;
-  }
-}
-
 // Products of the CSR stream are formed in batches of U nonzeros per lane:
 // all column indices and values of a batch are loaded first, then all the
 // gathers, so each lane keeps many independent loads in flight.
@@ -490,14 +412,38 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
 // to 16 rows (the row arrays are padded to the slot stride).
 constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
 constexpr int MT_ROWS = STEP_THREADS;
-constexpr int MT_STAGES = 3;
+#ifndef KRYLOV_MT_STAGES
+#define KRYLOV_MT_STAGES 3
+#endif
+constexpr int MT_STAGES = KRYLOV_MT_STAGES;
 __host__ __device__ constexpr size_t mt_stage_bytes(int kw) {
   return (size_t)MT_ROWS * 8 * (2 + kw) + MT_ROWS;
 }
 
-template <bool MAT, int KW>
+// Bins of this kernel keep the three words of a (bin, copy) next to each other,
+// [s][C][3] ints, so the three atomic adds of a sketch entry share one address
+// computation (immediate offsets); lane l works in copy l mod C, and with 32
+// copies the words a warp adds at one time sit in 32 different banks (word
+// stride 3 is odd).  C (copies) and Z (zeta, 0 = runtime value <= 8) are
+// compile-time so that the entry loop carries no parameter loads.
+template <int C>
+__device__ __forceinline__ double fx_value_il(const int* bins, int b, const FxScale& f, int WB) {
+  long long t[3];
+#pragma unroll
+  for (int w = 0; w < 3; ++w) {
+    long long u = 0;
+#pragma unroll 8
+    for (int c = 0; c < C; ++c) u += bins[(b * C + ((c + b) & (C - 1))) * 3 + w];
+    t[w] = u;
+  }
+  const long long low = t[1] * (1ll << WB) + t[2];
+  return fma((double)t[0], pow2d(f.E - WB), (double)low * pow2d(f.E - 3 * WB));
+}
+
+template <bool MAT, int KW, int C, int Z>
 __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
   constexpr int NW = 3;
+  static_assert(C == 16 || C == 32, "lane copies of the bins");
   constexpr size_t SB = mt_stage_bytes(KW);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[MT_STAGES];
@@ -506,8 +452,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   __shared__ FxScale s_fx;
   __shared__ ff s_h[MAX_WINDOW + 1];
   const int lane = threadIdx.x & 31;
-  const int C = L.sk_copies;
-  int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
+  int* bins = reinterpret_cast<int*>(smem);  // [s][C][NW]
   unsigned char* stages = smem + align16(bins_bytes(3, L.s, C));
   const int j = L.j;
   const int lo = MAT ? max(0, j - L.k) : j;
@@ -590,8 +535,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   }
   __syncthreads();
   const FxScale fxs = s_fx;
-  const int cp = lane & (C - 1);
-  const int sC = L.s * C;
+  int* const mybins = bins + (lane & (C - 1)) * NW;
+  const int zeta = (Z > 0) ? Z : L.zeta;
   ff h[KW];
 #pragma unroll
   for (int q = 0; q < KW; ++q) h[q] = s_h[q];
@@ -623,10 +568,18 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
       const uint2 rr = st_r(st)[k];
       const uint32_t ng = st_n(st)[k];
       const FxWords<NW> xw = fx_split<NW>(wj.hi, wj.lo, fxs);
+      const int q0 = xw.q[0], q1 = xw.q[1], q2 = xw.q[2];
+      const int n0 = -q0, n1 = -q1, n2 = -q2;
 #pragma unroll
       for (int e = 0; e < 8; ++e)
-        if (e < L.zeta)
-          fx_emit<NW>(bins, sC, (int)(((e < 4 ? rr.x : rr.y) >> (8 * (e & 3))) & 0xFFu), cp, xw, (ng >> e) & 1u, C);
+        if (Z == 8 || e < zeta) {
+          const int row = (int)__byte_perm(e < 4 ? rr.x : rr.y, 0u, 0x4440u | (uint32_t)(e & 3));
+          int* b = mybins + row * (C * NW);
+          const bool neg = (ng >> e) & 1u;
+          atomicAdd(b, neg ? n0 : q0);
+          atomicAdd(b + 1, neg ? n1 : q1);
+          atomicAdd(b + 2, neg ? n2 : q2);
+        }
     }
     __syncthreads();  // every thread is done with stage st
     if (threadIdx.x == 0 && t + MT_STAGES < ntiles && !timed_out) {
@@ -646,7 +599,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   if (threadIdx.x == 0) part[0] = v;
   __syncthreads();
   double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
-  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value<NW>(bins, L.s, C, b, fxs, L.fx_wb);
+  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value_il<C>(bins, b, fxs, L.fx_wb);
   if (!last_block_flag(cd.counter, &s_last)) return;
   if (threadIdx.x < 32) {
     const double tsum = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
@@ -813,6 +766,13 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
 constexpr int TMA_ROWS = STEP_THREADS;     // rows per staged tile
 constexpr int TMA_RP = TMA_ROWS + 4;       // staged row_ptr entries (16-byte multiple)
 constexpr int TMA_ROW_FAST = 8;            // rows up to this length issue all gathers together
+#ifndef KRYLOV_SPMV_STAGES
+#define KRYLOV_SPMV_STAGES 2
+#endif
+constexpr int TMA_STAGES = KRYLOV_SPMV_STAGES;  // CSR tiles in flight per CTA of the staged product
+// a stage holds at most 260 row_ptr entries and 4104 (int, float2) nonzeros
+// (50.3 KB): four of them still fit the 227 KB of shared memory of a CTA
+static_assert(TMA_STAGES >= 2 && TMA_STAGES <= 4, "staged CSR tiles in flight");
 
 // Stage of the staged product kernel: row_ptr slice, columns (4-byte indices,
 // or 2-byte offsets col - row when DI), values.  cap is a multiple of 8.
@@ -835,7 +795,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   using CT = typename std::conditional<DI, int16_t, int>::type;  // staged column entry
   constexpr int EA = DI ? 8 : 4;  // staged nonzero ranges start on 16-byte boundaries
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[TMA_STAGES];
   __shared__ float rhi[32], rlo[32];
   __shared__ int s_last;
   __shared__ double tot[NQ];
@@ -859,14 +819,13 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   const int r1 = min(L.n, r0 + L.rows_spmv);
   const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int q = 0; q < TMA_STAGES; ++q) mbar_init(&bars[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
   // thread 0: stage tile t given its nonzero range [e0, e1)
   auto issue = [&](int t, int e0, int e1) {
-    const int st = t & 1;
+    const int st = t % TMA_STAGES;
     const int ts = r0 + t * TMA_ROWS;
     const int ea = e0 & ~(EA - 1), eb = (e1 + EA - 1) & ~(EA - 1);
     const uint32_t brp = TMA_RP * 4u, bcol = (uint32_t)(eb - ea) * (uint32_t)sizeof(CT),
@@ -879,32 +838,31 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
     }
   };
   auto tile_end = [&](int t) { return min(r0 + (t + 1) * TMA_ROWS, r1); };
-  if (threadIdx.x == 0) {
-    if (ntiles > 0) issue(0, __ldg(L.row_ptr + r0), __ldg(L.row_ptr + tile_end(0)));
-    if (ntiles > 1) issue(1, __ldg(L.row_ptr + r0 + TMA_ROWS), __ldg(L.row_ptr + tile_end(1)));
-  }
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(ntiles, TMA_STAGES); ++t)
+      issue(t, __ldg(L.row_ptr + r0 + t * TMA_ROWS), __ldg(L.row_ptr + tile_end(t)));
   // the CSR stream does not depend on earlier kernels: its first tiles are on
   // their way before waiting for the kernel that produced w_j
   pdl_wait();
   if (cd.flags[1] != 0) {  // breakdown in this cycle: no further products
     if (threadIdx.x == 0)
-      for (int t = 0; t < min(ntiles, 2); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+      for (int t = 0; t < min(ntiles, TMA_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
     return;
   }
   ffacc acc_pi;
   ffacc acc_dot[KW];
   bool timed_out = false;
-  int last_issued = min(ntiles, 2) - 1;  // thread 0: last tile whose copies were issued
+  int last_issued = min(ntiles, TMA_STAGES) - 1;  // thread 0: last tile whose copies were issued
   for (int t = 0; t < ntiles; ++t) {
-    const int st = t & 1;
-    const uint32_t par = (uint32_t)(t >> 1) & 1u;
+    const int st = t % TMA_STAGES;
+    const uint32_t par = (uint32_t)(t / TMA_STAGES) & 1u;
     const int ts = r0 + t * TMA_ROWS;
     const int i = ts + (int)threadIdx.x;
     const bool valid = i < tile_end(t);
     int nb0 = 0, nb1 = 0;
-    if (threadIdx.x == 0 && t + 2 < ntiles) {  // boundaries of tile t+2, loaded early
-      nb0 = __ldg(L.row_ptr + ts + 2 * TMA_ROWS);
-      nb1 = __ldg(L.row_ptr + tile_end(t + 2));
+    if (threadIdx.x == 0 && t + TMA_STAGES < ntiles) {  // boundaries of the next tile to issue, loaded early
+      nb0 = __ldg(L.row_ptr + ts + TMA_STAGES * TMA_ROWS);
+      nb1 = __ldg(L.row_ptr + tile_end(t + TMA_STAGES));
     }
     ff wq[KW];
     if (valid) {
@@ -942,18 +900,18 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
         if (q < nd) acc_dot[q].add_prod(wq[q], p);
     }
     __syncthreads();  // every thread is done with stage st
-    if (threadIdx.x == 0 && t + 2 < ntiles && !timed_out) {
+    if (threadIdx.x == 0 && t + TMA_STAGES < ntiles && !timed_out) {
       fence_proxy_async();
-      issue(t + 2, nb0, nb1);
-      last_issued = t + 2;
+      issue(t + TMA_STAGES, nb0, nb1);
+      last_issued = t + TMA_STAGES;
     }
   }
   pdl_trigger();
   if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
   if (threadIdx.x == 0 && timed_out) {
     // let copies still in flight land before the CTA exits (bounded again)
-    for (int t = max(0, last_issued - 1); t <= last_issued; ++t)
-      (void)mbar_wait_bounded(&bars[t & 1], (uint32_t)(t >> 1) & 1u, TMA_WAIT_NS);
+    for (int t = max(0, last_issued - TMA_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % TMA_STAGES], (uint32_t)(t / TMA_STAGES) & 1u, TMA_WAIT_NS);
   }
   double* part = L.part + (size_t)blockIdx.x * NQ;
   double v = block_sum_ff(acc_pi.result(), rhi, rlo);
@@ -1043,7 +1001,12 @@ void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
     case SK_TAB8: {  // packed table: row streams staged by bulk copies
       const int kw = (L.k <= 2) ? 2 : MAX_WINDOW;
       const size_t smem = mt_smem(L.s, L.sk_copies, kw);
-      auto k = (L.k <= 2) ? ff_mat_tma_kernel<MAT, 2> : ff_mat_tma_kernel<MAT, MAX_WINDOW>;
+      auto pick = [&](auto kw2, auto kw4) { return (L.k <= 2) ? kw2 : kw4; };
+      auto k = (L.sk_copies == 32)
+                   ? ((L.zeta == 8) ? pick(ff_mat_tma_kernel<MAT, 2, 32, 8>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 32, 8>)
+                                    : pick(ff_mat_tma_kernel<MAT, 2, 32, 0>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 32, 0>))
+                   : ((L.zeta == 8) ? pick(ff_mat_tma_kernel<MAT, 2, 16, 8>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 16, 8>)
+                                    : pick(ff_mat_tma_kernel<MAT, 2, 16, 0>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 16, 0>));
       raise_smem_limit((const void*)k, smem);
       launch_pdl(k, L.grid, smem, st, L, cd);
       break;
@@ -1328,14 +1291,14 @@ void launch_ff_spmv_main(const StepLaunch& L, const CycleDev& cd, cudaStream_t s
   }
   if (L.tma_cap > 0 && L.dcol != nullptr) {
     auto k = ff_spmv_tma_kernel<AT, KW, true>;
-    const size_t smem = 2 * tma_stage_bytes<AT, true>(L.tma_cap);
+    const size_t smem = TMA_STAGES * tma_stage_bytes<AT, true>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
   }
   if (L.tma_cap > 0) {
     auto k = ff_spmv_tma_kernel<AT, KW, false>;
-    const size_t smem = 2 * tma_stage_bytes<AT>(L.tma_cap);
+    const size_t smem = TMA_STAGES * tma_stage_bytes<AT>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
@@ -1407,14 +1370,15 @@ int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap) {
     return vals_f32 ? occ(ff_spmv_seg_kernel<float, 2>, 2 * seg_stage_bytes<float>(lcap, seg_cap))
                     : occ(ff_spmv_seg_kernel<float2, 2>, 2 * seg_stage_bytes<float2>(lcap, seg_cap));
   if (tma_cap > 0)
-    return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2, false>, 2 * tma_stage_bytes<float>(tma_cap))
-                    : occ(ff_spmv_tma_kernel<float2, 2, false>, 2 * tma_stage_bytes<float2>(tma_cap));
+    return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2, false>, TMA_STAGES * tma_stage_bytes<float>(tma_cap))
+                    : occ(ff_spmv_tma_kernel<float2, 2, false>, TMA_STAGES * tma_stage_bytes<float2>(tma_cap));
   return vals_f32 ? occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM) : occ(ff_spmv_kernel<float2, 2>, FF_STAGE_SMEM);
 }
 
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
   if (basis == 3)
-    return (sk_mode == SK_TAB8) ? occ(ff_mat_tma_kernel<true, 2>, mt_smem(s, copies, 2))
+    return (sk_mode == SK_TAB8) ? ((copies == 32) ? occ(ff_mat_tma_kernel<true, 2, 32, 8>, mt_smem(s, copies, 2))
+                                                  : occ(ff_mat_tma_kernel<true, 2, 16, 8>, mt_smem(s, copies, 2)))
                                 : occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
   const size_t smem = fused_smem(basis, s, copies);
   if (basis == 0)
