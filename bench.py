@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64-basis solve timed beside the headline")
+    ap.add_argument("--parallelism", default="replicas", choices=["replicas", "partition"],
+                    help="N > 1: independent replicas of the headline solve (default), or one solve of the "
+                         "headline problem row-partitioned over the N ranks (float64 basis)")
     ap.add_argument("--cycles", type=int, default=None, help="override the cycle count (profiling)")
     ap.add_argument("--workload", default="convdiff3d_128",
                     choices=["convdiff3d_128", "convdiff3d_128_rgs", "convdiff3d_128_phi1", "poisson2d_1448_cos",
@@ -513,6 +516,54 @@ def plain_fp64_solve(A, bd, cycles, warmup, steps, stream, peak, barrier):
                                    "sketch, float64 arithmetic)"}}
 
 
+def partition_main(args, rank, world, local):
+    """One headline solve row-partitioned over the ranks (NCCL collectives,
+    float64 basis): every timed step is one whole f(A) b of the full problem."""
+    import torch
+
+    from paper_2503_22631_gb300 import F_EXP_NEG, build
+    from paper_2503_22631_gb300.dist import PartitionedKrylov, TorchComm, plan_partition
+
+    build.build()
+    cycles = args.cycles or CYCLES_TO_1E8["f64"]
+    warmup = max(args.warmup, 3)
+    A, b = make_inputs()
+    plan = plan_partition(A.row_ptr, A.col_idx, A.val, world, rank)
+    stream = torch.cuda.current_stream()
+    kr = PartitionedKrylov(plan, TorchComm(plan), f=F_EXP_NEG, t=WORKLOAD["t"], m=WORKLOAD["m"], k=WORKLOAD["k"],
+                           s=WORKLOAD["s"], seed=SEED, zeta=WORKLOAD["zeta"], stream=stream)
+    bl = torch.from_numpy(b[plan.lo:plan.hi].copy()).cuda()
+    x = torch.empty_like(bl)
+    for _ in range(warmup):
+        kr.apply(bl, tol=0.0, max_cycles=cycles, out=x)
+    torch.cuda.synchronize()
+    torch.distributed.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            kr.apply(bl, tol=0.0, max_cycles=cycles, out=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.distributed.barrier()
+    ms_max = max_over_ranks(e0.elapsed_time(e1), world, torch.device("cuda", local))
+    if rank != 0:
+        return
+    value = ms_max / 1e3 / args.steps  # one whole problem per step for the job
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], "n": A.n, "nnz": A.nnz, "m": WORKLOAD["m"], "k": WORKLOAD["k"],
+                   "s": WORKLOAD["s"], "zeta": WORKLOAD["zeta"], "t": WORKLOAD["t"], "cycles": cycles,
+                   "basis": "f64", "parallelism": f"row partition over {world} ranks (halo exchange + all-reduce "
+                                                  f"per step)", "l2": "working set > L2 (no flush)"},
+        "roofline": None, "cpu_baseline": None, "e2e": None,
+        "gpu_launches": int(kr.stats["launches"]) * args.steps, "clocks": clk.summary()}), flush=True)
+
+
 # ------------------------------------------------------------------- main ---
 def main():
     args = parse()
@@ -533,6 +584,10 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if args.parallelism == "partition":
+            partition_main(args, rank, world, local)
+            dist.destroy_process_group()
+            return
     from paper_2503_22631_gb300 import BASIS_BF16, BASIS_DF64, BASIS_F32, BASIS_F64, F_EXP_NEG, Krylov, build
 
     build.build()

@@ -167,6 +167,54 @@ void krylov_options_default(krylov_options* opt);
 krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, int s,
                             uint64_t seed, const krylov_options* opt, krylov_handle** out);
 
+/* Row-partitioned solve (one process per GPU).  A rank owns a contiguous
+ * block of rows of A and the same rows of b and x.  Per Arnoldi step the
+ * ranks exchange the halo of the current basis vector (the entries of other
+ * ranks' rows that their rows reference) and sum k + 2 scalars (||A w_j||^2
+ * and the window dots of Algorithm 1's loop body, then ||w_{j+1}||^2); the
+ * sketch columns are keyed by global row, so the sketch of a basis vector is
+ * the sum over ranks of their rows' sketches (Sec. 2.1, Eq. 3 applied
+ * columnwise), summed exactly once per cycle.  The small projected problem is
+ * solved redundantly on every rank from identical inputs; the solution update
+ * x += W z stays local.  The library calls back into the caller for every
+ * exchange (see krylov_comm); the callbacks must be collective: every rank
+ * calls them in the same order with the same counts. */
+typedef struct {
+  void* ctx;  /* passed back unchanged */
+  /* in-place sum over all ranks of count float64 values at the DEVICE pointer
+   * buf; work already issued on `stream` must complete first, and the sum must
+   * be complete (visible on `stream`) when the callback returns.  0 = success. */
+  int (*allreduce_sum_f64)(void* ctx, double* buf, int64_t count, void* stream);
+  /* same for int64 values (exact integer sums) */
+  int (*allreduce_sum_i64)(void* ctx, int64_t* buf, int64_t count, void* stream);
+  /* in-place maximum over all ranks of count float64 values (device) */
+  int (*allreduce_max_f64)(void* ctx, double* buf, int64_t count, void* stream);
+  /* halo exchange: send (device, n_send values, in the order of the send_idx
+   * given at create) goes to the neighbours, recv (device, n_halo values, in
+   * the order of the halo columns n .. n + n_halo - 1) is filled from them */
+  int (*halo_exchange_f64)(void* ctx, const double* send, double* recv, void* stream);
+} krylov_comm;
+
+/* Create this rank's handle of a row-partitioned solve.
+ *   A_local : the rank's rows (A->n = n_local rows) with columns renumbered:
+ *             [0, n_local) are the rank's own rows, [n_local, n_local + n_halo)
+ *             the halo columns in the order the exchange delivers them
+ *             (borrowed, copied; EINVAL on a column outside that range);
+ *   row0    : global index of local row 0 (keys the sketch columns);
+ *   n_global: rows of the whole matrix;
+ *   send_idx: host, n_send local row indices whose entries the neighbours
+ *             need, in the order the exchange sends them;
+ *   comm    : collective callbacks (copied; ctx must outlive the handle);
+ *   f, m, k, s, seed, opt : as for krylov_create, with the float64 basis and
+ *             TRUNC orthogonalization (EUNSUPPORTED otherwise).
+ * krylov_apply on such a handle takes the rank's rows of b and x and is
+ * collective.  krylov_apply_adjoint, krylov_apply_batched, krylov_spmv and
+ * krylov_apply_host return EUNSUPPORTED on it. */
+krylov_status krylov_create_partition(const krylov_csr* A_local, int64_t n_halo, int64_t row0, int64_t n_global,
+                                      const int32_t* send_idx, int64_t n_send, const krylov_comm* comm,
+                                      krylov_func f, int m, int k, int s, uint64_t seed,
+                                      const krylov_options* opt, krylov_handle** out);
+
 /* x <- approximation of f(A) b by Algorithm 2 (with the whitened restart of
  * App. A).  b: device, n float64, read only; x: device, n float64, overwritten.
  * tol: stopping tolerance (relative unless opt.abs_tol); tol = 0 runs exactly

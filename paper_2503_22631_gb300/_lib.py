@@ -55,6 +55,7 @@ EXPORTED = [
     "krylov_spmv_dot_noalloc",
     "krylov_apply_batched",
     "krylov_probe_bounded_wait",
+    "krylov_create_partition",
 ]
 
 
@@ -83,6 +84,17 @@ class Stats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# collective callbacks of a row-partitioned solve (krylov_comm)
+ALLREDUCE_F64 = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p)
+ALLREDUCE_I64 = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p)
+HALO_F64 = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Comm(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("allreduce_sum_f64", ALLREDUCE_F64), ("allreduce_sum_i64", ALLREDUCE_I64),
+                ("allreduce_max_f64", ALLREDUCE_F64), ("halo_exchange_f64", HALO_F64)]
 
 
 class KrylovError(RuntimeError):
@@ -132,6 +144,10 @@ def load() -> C.CDLL:
     lib.krylov_apply_batched.restype = C.c_int
     lib.krylov_probe_bounded_wait.argtypes = [C.c_uint64, P, P]
     lib.krylov_probe_bounded_wait.restype = C.c_int
+    lib.krylov_create_partition.argtypes = [C.POINTER(Csr), C.c_int64, C.c_int64, C.c_int64, P, C.c_int64,
+                                            C.POINTER(Comm), Func, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                            C.POINTER(Options), C.POINTER(P)]
+    lib.krylov_create_partition.restype = C.c_int
     _lib = lib
     return lib
 

@@ -233,6 +233,20 @@ struct krylov_handle {
   int sk_mode = SK_TAB8;
   int sk_copies = 32;
 
+  // row-partitioned solve (krylov_create_partition); part_mode == 0 otherwise
+  int part_mode = 0;
+  int staged32 = 0;  // float32 / bfloat16 basis: staged two-kernel step (forward operator)
+  int n_halo = 0, n_send = 0;
+  int64_t row0 = 0, n_global = 0;
+  krylov_comm comm{};
+  int* send_idx = nullptr;         // device, n_send local rows to send
+  double* sendbuf = nullptr;       // device, n_send
+  double* recvbuf = nullptr;       // device, n_halo
+  double* red = nullptr;           // device, NQ + 1 all-reduced step sums
+  long long* part_acc = nullptr;   // device, [m+1][3][s] exact sketch word sums
+  int* part_E = nullptr;           // device, [m+1] fixed-point exponents
+  int part_grid = 0, part_rows = 0, part_wb = 0;
+
   // host mirrors
   int* h_flags = nullptr;     // pinned: flags[4]
   double* h_scal = nullptr;   // pinned: 16 doubles
@@ -431,7 +445,7 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose);
 // its copies.  Null otherwise.
 krylov_status install_delta16(krylov_handle* h, const int* rp_dev, const int* ci_dev, int16_t** out) {
   *out = nullptr;
-  if (h->opt.basis_dtype != 3 || h->nnz == 0) return KRYLOV_OK;
+  if ((h->opt.basis_dtype != 3 && !h->staged32) || h->nnz == 0) return KRYLOV_OK;
   CK(csr_bandwidth(h->n, rp_dev, ci_dev, h->d_flag, h->h_flags, h->st));
   if (h->h_flags[0] > 32767) return KRYLOV_OK;
   int16_t* d = nullptr;
@@ -613,8 +627,10 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   // whole 256-row tiles per CTA (tiles then start at multiples of 256)
   L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
   L.m = M;
-  L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : 0;
-  L.dcol = (basis == 3) ? (transpose ? h->dcolt : h->dcol) : nullptr;
+  // float32 / bfloat16: the staged kernels run on the forward operator only
+  const int st32 = h->staged32 && !transpose;
+  L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : (st32 ? h->tma_cap : 0);
+  L.dcol = (basis == 3) ? (transpose ? h->dcolt : h->dcol) : (st32 ? h->dcol : nullptr);
   if (basis == 3) {
     const SegPlan& sp = transpose ? h->seg_t : h->seg_a;
     L.seg = sp.seg;
@@ -757,6 +773,74 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
   return KRYLOV_OK;
 }
 
+// ---- row-partitioned solve ---------------------------------------------------
+constexpr int PART_NQ = 2 + MAX_WINDOW;  // step sums of the product: [1] ||p||^2, [2..] window dots
+
+krylov_status comm_status(int rc) { return rc == 0 ? KRYLOV_OK : KRYLOV_ECUDA; }
+
+// The m + 1 columns of a cycle on this rank's rows: for column j, the
+// materialization (and its rows' share of ||w_j||^2 and of S w_j), the sum of
+// ||w_j||^2 over ranks and its reducer; then, for j < m, the halo exchange of
+// w_j, the product p_j = A w_j on the rank's rows with its shares of ||p_j||^2
+// and of the window dots, their sum over ranks and the coefficient reducer.
+// Every rank runs the same sequence of collective calls; a breakdown is seen
+// by all ranks alike (the reducers act on the all-reduced sums), and the
+// kernels of the columns after it return at once.
+krylov_status part_cycle_steps(krylov_handle* h, double thr, cudaStream_t st) {
+  const int M = h->m;
+  const int64_t nacc = (int64_t)(M + 1) * 3 * h->s;
+  CK(cudaMemsetAsync(h->part_acc, 0, sizeof(long long) * (size_t)nacc, st));
+  StepLaunch L{};
+  L.n = h->n;
+  L.k = h->k;
+  L.m = M;
+  L.s = h->s;
+  L.zeta = h->opt.zeta;
+  L.seed = h->seed;
+  L.thr = thr;
+  L.sk_tab = h->sk_tab;
+  L.sk_mode = h->sk_mode;
+  L.sk_copies = 1;
+  L.fx_wb = h->part_wb;
+  L.rows_per_cta = h->part_rows;
+  L.grid = h->part_grid;
+  PartLaunch P{};
+  P.n = h->n;
+  P.rp = h->rp;
+  P.ci = h->ci;
+  P.val = h->val;
+  P.W = static_cast<double*>(h->W);
+  P.ldw = h->ldw;
+  P.p = static_cast<double*>(h->p[0]);
+  P.part = h->part;
+  P.red = h->red;
+  P.acc = h->part_acc;
+  P.E = h->part_E;
+  P.grid = h->part_grid;
+  P.rows_per_cta = h->part_rows;
+  krylov_status cs = KRYLOV_OK;
+  for (int j = 0; j <= M; ++j) {
+    L.j = j;
+    launch_part_mat(P, L, h->cd, j > 0 ? 1 : 0, st);
+    CK(cudaGetLastError());
+    if ((cs = comm_status(h->comm.allreduce_sum_f64(h->comm.ctx, h->red + PART_NQ, 1, st))) != KRYLOV_OK) return cs;
+    launch_part_reduce_mat(L, h->cd, h->red, j > 0 ? 1 : 0, st);
+    if (j == M) break;
+    double* Wj = P.W + (int64_t)j * P.ldw;
+    launch_part_pack(Wj, h->send_idx, h->n_send, h->sendbuf, st);
+    CK(cudaGetLastError());
+    if ((cs = comm_status(h->comm.halo_exchange_f64(h->comm.ctx, h->sendbuf, h->recvbuf, st))) != KRYLOV_OK)
+      return cs;
+    launch_part_unpack(h->recvbuf, h->n_halo, Wj + h->n, st);
+    launch_part_product(P, L, h->cd, st);
+    CK(cudaGetLastError());
+    if ((cs = comm_status(h->comm.allreduce_sum_f64(h->comm.ctx, h->red, PART_NQ, st))) != KRYLOV_OK) return cs;
+    launch_part_reduce_product(L, h->cd, h->red, st);
+  }
+  CK(cudaGetLastError());
+  return KRYLOV_OK;
+}
+
 krylov_status apply_core(krylov_handle* h, int transpose, const double* b, double* x, double tol,
                          int max_cycles, krylov_stats* stout) {
   if (!h || !b || !x || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
@@ -790,6 +874,13 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   CK(cudaMemsetAsync(h->sd.misc, 0, 8 * sizeof(double), st));
   launch_norm_b(b, n, h->part, h->grid, h->cd, st);
   stats.launches += 1;
+  if (h->part_mode) {  // ||b||^2 over all ranks
+    CK(cudaGetLastError());
+    cs = comm_status(h->comm.allreduce_sum_f64(h->comm.ctx, h->cd.scal + 4, 1, st));
+    if (cs != KRYLOV_OK) return cs;
+    launch_part_norm_finish(h->cd, st);
+    stats.launches += 1;
+  }
   CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -818,9 +909,15 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     if (rgs) {
       stats.launches += rgs_cycle_steps(h, op, transpose, use32, thr, c, st);
     }
+    if (h->part_mode) {
+      cs = part_cycle_steps(h, thr, st);
+      if (cs != KRYLOV_OK) return cs;
+      stats.launches += 5 * M + 2;
+      stats.step_launches += 2 * M + 1;
+    }
     // the first run is eager (it also raises the kernels' shared-memory
     // limits); later cycles replay a graph of the same launches
-    const bool use_graph = !rgs && h->opt.use_graph && h->step_runs[transpose] > 0;
+    const bool use_graph = !rgs && !h->part_mode && h->opt.use_graph && h->step_runs[transpose] > 0;
     if (use_graph && !h->step_graph[transpose]) {
       // captured on a private stream (the caller's may be the legacy default
       // stream, which cannot be captured); the graph is launched on st
@@ -839,7 +936,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
         (void)cudaGetLastError();
       }
     }
-    if (rgs) {
+    if (rgs || h->part_mode) {
       // launched above
     } else if (use_graph && h->step_graph[transpose]) {
       CK(cudaGraphLaunch(h->step_graph[transpose], st));
@@ -848,9 +945,10 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       h->step_runs[transpose] += 1;
     }
     CK(cudaEventRecord(h->ev[1], st));
-    if (!rgs) {
-      stats.launches += (basis == 3 ? 2 * M + 1 : M + 1) + 1;
-      stats.step_launches += (basis == 3 ? 2 * M + 1 : M + 1);
+    if (!rgs && !h->part_mode) {
+      const bool two = (basis == 3) || (h->staged32 && !transpose);
+      stats.launches += (two ? 2 * M + 1 : M + 1) + 1;
+      stats.step_launches += (two ? 2 * M + 1 : M + 1);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -879,7 +977,14 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       launch_rgs_small(h->sd, h->cd, M, me, has_next, c, h->f.t, st);
       stats.launches += 1;
     } else {
-      launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
+      if (h->part_mode) {  // S W_{m+1}: the exact word sums of all ranks
+        cs = comm_status(h->comm.allreduce_sum_i64(h->comm.ctx, reinterpret_cast<int64_t*>(h->part_acc),
+                                                   (int64_t)nc * 3 * h->s, st));
+        if (cs != KRYLOV_OK) return cs;
+        launch_part_sketch_u(h->part_acc, h->part_E, nc, h->s, h->opt.zeta, h->part_wb, h->sd.U, st);
+      } else {
+        launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
+      }
       launch_whiten(h->sd, h->cd, h->s, M, nc, me, has_next, c, h->k, h->f.t, st);
       stats.launches += 2;
     }
@@ -923,6 +1028,11 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid_update, h->cd, M, st);
     stats.launches += 1;
     CK(cudaGetLastError());
+    if (h->part_mode) {  // ||y||^2, ||x||^2 and ||v_next||^2 over all ranks
+      cs = comm_status(h->comm.allreduce_sum_f64(h->comm.ctx, h->cd.scal + 2, 2, st));
+      if (cs == KRYLOV_OK) cs = comm_status(h->comm.allreduce_sum_f64(h->comm.ctx, h->cd.scal + 5, 1, st));
+      if (cs != KRYLOV_OK) return cs;
+    }
     CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_scal + 8, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1411,8 +1521,16 @@ void krylov_destroy(krylov_handle* h) {
   delete h;
 }
 
-krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, int s, uint64_t seed,
-                            const krylov_options* opt_in, krylov_handle** out) {
+// what krylov_create_partition adds to krylov_create (null for a whole matrix)
+struct PartSpec {
+  int64_t n_halo, row0, n_global;
+  const int32_t* send_idx;
+  int64_t n_send;
+  const krylov_comm* comm;
+};
+
+static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int k, int s, uint64_t seed,
+                                 const krylov_options* opt_in, const PartSpec* ps, krylov_handle** out) {
   if (!A || !out) return KRYLOV_EINVAL;
   *out = nullptr;
   krylov_options opt;
@@ -1433,11 +1551,27 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
       f.kind != KRYLOV_F_PHI1_NEG && f.kind != KRYLOV_F_COS_SQRT)
     return KRYLOV_EINVAL;
   if (!std::isfinite(f.t)) return KRYLOV_EINVAL;
+  if (ps) {
+    const krylov_comm* cm = ps->comm;
+    if (!cm || !cm->allreduce_sum_f64 || !cm->allreduce_sum_i64 || !cm->allreduce_max_f64 ||
+        !cm->halo_exchange_f64)
+      return KRYLOV_EINVAL;
+    if (ps->n_halo < 0 || ps->n_send < 0 || ps->row0 < 0 || ps->n_global < A->n || ps->row0 + A->n > ps->n_global)
+      return KRYLOV_EINVAL;
+    if (ps->n_global > 0xFFFFFFFFLL || A->n + ps->n_halo > 0x7FF00000LL || ps->n_send > 0x7FF00000LL)
+      return KRYLOV_EINVAL;
+    if (ps->n_send > 0 && !ps->send_idx) return KRYLOV_EINVAL;
+    for (int64_t e = 0; e < ps->n_send; ++e)
+      if (ps->send_idx[e] < 0 || ps->send_idx[e] >= A->n) return KRYLOV_EINVAL;
+    if (opt.basis_dtype != KRYLOV_BASIS_F64 || opt.ortho != KRYLOV_ORTHO_TRUNC || opt.sketch_regenerate)
+      return KRYLOV_EUNSUPPORTED;
+  }
+  const int64_t ncols = A->n + (ps ? ps->n_halo : 0);  // columns of the stored rows
 
   krylov_handle* h = new (std::nothrow) krylov_handle();
   if (!h) return KRYLOV_ENOMEM;
   h->n = (int)A->n;
-  h->ldw = (A->n + 63) / 64 * 64;  // basis slot stride (also the padded length of row arrays)
+  h->ldw = (ncols + 63) / 64 * 64;  // basis slot stride (also the padded length of row arrays)
   h->nnz = A->nnz;
   h->m = m;
   h->k = k;
@@ -1478,7 +1612,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   CKF(cudaMemsetAsync(h->ci + nnz, 0, CSR_PAD * sizeof(int), h->st));
   CKF(cudaMemsetAsync(h->rp + n + 1, 0, RP_PAD * sizeof(int), h->st));
   CKF(cudaMemsetAsync(h->val + nnz, 0, CSR_PAD * sizeof(double), h->st));
-  CKF(validate_csr(n, nnz, h->rp, h->ci, h->d_flag, h->h_flags, h->st));
+  CKF(validate_csr(n, nnz, h->rp, h->ci, h->d_flag, h->h_flags, h->st, (int)ncols));
   if (h->h_flags[0] != 0) return fail(KRYLOV_EINVAL);
   // float32 copy of the values: exact-narrowing test, and the operand of the
   // float32/bfloat16 basis modes
@@ -1514,7 +1648,7 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
       CKF(dalloc(h, &h->sk_tab.neg32, (size_t)n));
     }
     CKF(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->st));
-    launch_sketch_table(n, s, opt.zeta, seed, h->sk_tab, h->d_flag, h->st);
+    launch_sketch_table(n, s, opt.zeta, seed, h->sk_tab, h->d_flag, h->st, ps ? ps->row0 : 0);
     CKF(cudaGetLastError());
     CKF(cudaMemcpyAsync(h->h_flags, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CKF(cudaStreamSynchronize(h->st));
@@ -1523,8 +1657,13 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   // workspaces: one persistent wave of the step kernel(s)
   const int vals32 = (opt.basis_dtype == 1 || opt.basis_dtype == 2) ||
                      (h->vals_exact_f32 && opt.narrow_values_if_exact);
-  h->grid = std::max(1, std::min(h->num_sms * step_ctas_per_sm(opt.basis_dtype, h->sk_mode, s, h->sk_copies, vals32),
-                                 (n + STEP_THREADS - 1) / STEP_THREADS));
+  // float32 / bfloat16 bases: the staged pair of step kernels when the packed
+  // sketch table and the staged CSR tiles apply, else the fused kernel
+  h->staged32 = (opt.basis_dtype == 1 || opt.basis_dtype == 2) && h->sk_mode == SK_TAB8 && h->tma_cap > 0 &&
+                opt.ortho == KRYLOV_ORTHO_TRUNC && !ps;
+  const int cps = h->staged32 ? s32_ctas_per_sm(opt.basis_dtype, s, h->sk_copies)
+                              : step_ctas_per_sm(opt.basis_dtype, h->sk_mode, s, h->sk_copies, vals32);
+  h->grid = std::max(1, std::min(h->num_sms * cps, (n + STEP_THREADS - 1) / STEP_THREADS));
   const int bb = basis_bytes(opt.basis_dtype);
   CKF(cudaMalloc(&h->W, (size_t)(m + 1) * h->ldw * bb));
   h->allocs.push_back(h->W);
@@ -1550,6 +1689,12 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
     const int tcap = h->long_a.n_long ? h->long_a.tma_cap : h->tma_cap;
     h->grid_spmv = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(vals32, tcap, sp.seg ? sp.seg_cap : 0,
                                                                       sp.lcap),
+                                        (n + STEP_THREADS - 1) / STEP_THREADS));
+  }
+  if (h->staged32) {
+    const krylov_status ps2 = install_delta16(h, h->rp, h->ci, &h->dcol);
+    if (ps2 != KRYLOV_OK) return fail(ps2);
+    h->grid_spmv = std::max(1, std::min(h->num_sms * s32_spmv_ctas_per_sm(h->tma_cap, h->dcol != nullptr ? 1 : 0),
                                         (n + STEP_THREADS - 1) / STEP_THREADS));
   }
   h->grid_spmv_t = h->grid_spmv;
@@ -1579,6 +1724,15 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   if (f.kind == KRYLOV_F_INVSQRT) {
     double alpha = 0.0;
     CKF(norm_inf(n, h->rp, h->val, h->d_flag, h->h_flags, &alpha, h->st));
+    if (ps) {  // ||A||_inf over all ranks' rows
+      double* d = nullptr;
+      CKF(dalloc(h, &d, 1));
+      CKF(cudaMemcpyAsync(d, &alpha, sizeof(double), cudaMemcpyHostToDevice, h->st));
+      CKF(cudaStreamSynchronize(h->st));
+      if (ps->comm->allreduce_max_f64(ps->comm->ctx, d, 1, h->st) != 0) return fail(KRYLOV_ECUDA);
+      CKF(cudaMemcpyAsync(&alpha, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CKF(cudaStreamSynchronize(h->st));
+    }
     if (!std::isfinite(alpha)) return fail(KRYLOV_EINVAL);
     if (alpha == 0.0) alpha = 1.0;
     const double u_lo = 0.5 * std::log(alpha * 1e-18) - 38.0;
@@ -1591,6 +1745,27 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
       CKF(dalloc(h, &h->sd.qwork, (size_t)h->q_nodes * m * m));
   }
   CKF(dalloc(h, &h->d_dot, 1));
+  if (ps) {
+    h->part_mode = 1;
+    h->n_halo = (int)ps->n_halo;
+    h->n_send = (int)ps->n_send;
+    h->row0 = ps->row0;
+    h->n_global = ps->n_global;
+    h->comm = *ps->comm;
+    CKF(dalloc(h, &h->send_idx, (size_t)h->n_send));
+    if (h->n_send > 0)
+      CKF(cudaMemcpyAsync(h->send_idx, ps->send_idx, sizeof(int) * (size_t)h->n_send, cudaMemcpyHostToDevice,
+                          h->st));
+    CKF(dalloc(h, &h->sendbuf, (size_t)h->n_send));
+    CKF(dalloc(h, &h->recvbuf, (size_t)h->n_halo));
+    CKF(dalloc(h, &h->red, (size_t)PART_NQ + 1));
+    CKF(dalloc(h, &h->part_acc, (size_t)(m + 1) * 3 * s));
+    CKF(dalloc(h, &h->part_E, (size_t)m + 1));
+    CKF(cudaMemsetAsync(h->W, 0, (size_t)(m + 1) * h->ldw * sizeof(double), h->st));
+    h->part_grid = std::max(1, std::min(h->part_cap, std::min(h->num_sms * 4, (n + STEP_THREADS - 1) / STEP_THREADS)));
+    h->part_rows = (n + h->part_grid - 1) / h->part_grid;
+    h->part_wb = sketch_word_bits(h->part_rows, 1);
+  }
   CKF(cudaStreamSynchronize(h->st));
   {
     const krylov_status cs = choose_product_kernel(h, 0);
@@ -1601,6 +1776,20 @@ krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, in
   return KRYLOV_OK;
 }
 
+krylov_status krylov_create(const krylov_csr* A, krylov_func f, int m, int k, int s, uint64_t seed,
+                            const krylov_options* opt_in, krylov_handle** out) {
+  return create_impl(A, f, m, k, s, seed, opt_in, nullptr, out);
+}
+
+krylov_status krylov_create_partition(const krylov_csr* A_local, int64_t n_halo, int64_t row0, int64_t n_global,
+                                      const int32_t* send_idx, int64_t n_send, const krylov_comm* comm,
+                                      krylov_func f, int m, int k, int s, uint64_t seed,
+                                      const krylov_options* opt, krylov_handle** out) {
+  if (!comm) return KRYLOV_EINVAL;
+  const PartSpec ps{n_halo, row0, n_global, send_idx, n_send, comm};
+  return create_impl(A_local, f, m, k, s, seed, opt, &ps, out);
+}
+
 krylov_status krylov_apply(krylov_handle* h, const double* b, double* x, double tol, int max_cycles,
                            krylov_stats* st) {
   return apply_impl(h, 0, b, x, tol, max_cycles, st);
@@ -1608,6 +1797,7 @@ krylov_status krylov_apply(krylov_handle* h, const double* b, double* x, double 
 
 krylov_status krylov_apply_adjoint(krylov_handle* h, const double* b, double* x, double tol, int max_cycles,
                                    krylov_stats* st) {
+  if (h && h->part_mode) return KRYLOV_EUNSUPPORTED;
   return apply_impl(h, 1, b, x, tol, max_cycles, st);
 }
 
@@ -1617,6 +1807,7 @@ krylov_status krylov_apply_batched(krylov_handle* const* hs, int n_inst, int n_r
   if (!hs || !B || !X || n_inst < 1 || n_rhs < 1 || max_cycles < 1 || !(tol >= 0.0)) return KRYLOV_EINVAL;
   for (int i = 0; i < n_inst; ++i) {
     if (!hs[i] || !B[i] || !X[i]) return KRYLOV_EINVAL;
+    if (hs[i]->part_mode) return KRYLOV_EUNSUPPORTED;
     if (t_per_inst && !std::isfinite(t_per_inst[i])) return KRYLOV_EINVAL;
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return KRYLOV_EINVAL;  // a handle is not thread-safe
@@ -1645,6 +1836,7 @@ krylov_status krylov_apply_batched(krylov_handle* const* hs, int n_inst, int n_r
 krylov_status krylov_apply_host(krylov_handle* h, const double* b_host, double* x_host, double tol,
                                 int max_cycles, krylov_stats* st) {
   if (!h || !b_host || !x_host) return KRYLOV_EINVAL;
+  if (h->part_mode) return KRYLOV_EUNSUPPORTED;
   if (!h->stage_b) {
     CK(dalloc(h, &h->stage_b, (size_t)h->n));
     CK(dalloc(h, &h->stage_x, (size_t)h->n));
@@ -1679,6 +1871,7 @@ krylov_status krylov_set_param(krylov_handle* h, double t) {
 krylov_status krylov_spmv(krylov_handle* h, const double* x, double* y, int transpose, const double* dot_with,
                           double* dot_out) {
   if (!h || !x || !y) return KRYLOV_EINVAL;
+  if (h->part_mode) return KRYLOV_EUNSUPPORTED;
   if (transpose) {
     krylov_status s = build_transpose(h);
     if (s != KRYLOV_OK) return s;

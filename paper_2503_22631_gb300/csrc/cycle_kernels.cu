@@ -349,21 +349,21 @@ __global__ void sketch_columns_kernel(int64_t col0, int64_t count, SketchSpec sp
 // The table of S: packed (s <= 255, zeta <= 8): 8 row bytes per column in a
 // uint2 (0xFF in unused bytes) and a sign byte; generic: zeta uint16 rows and
 // a 32-bit sign mask per column.
-__global__ void sketch_table_kernel(int n, SketchSpec sp, SketchTable tab, int* err) {
+__global__ void sketch_table_kernel(int n, SketchSpec sp, SketchTable tab, int* err, int64_t col0) {
   const int stride = gridDim.x * blockDim.x;
   const uint32_t inv_s = sketch_inv_s(sp.s);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     int got;
     if (tab.packed) {
       uint32_t p0, p1, ng;
-      got = sketch_column_packed((uint32_t)i, sp, inv_s, &p0, &p1, &ng);
+      got = sketch_column_packed((uint32_t)(col0 + i), sp, inv_s, &p0, &p1, &ng);
       tab.rows8[i] = make_uint2(p0, p1);
       tab.neg8[i] = (uint8_t)ng;
     } else {
       int e = 0;
       uint32_t ng = 0u;
       uint16_t* rr = tab.rows16 + (size_t)i * sp.zeta;
-      got = sketch_column<MAX_ZETA>((uint32_t)i, sp, [&](int row, bool neg) {
+      got = sketch_column<MAX_ZETA>((uint32_t)(col0 + i), sp, [&](int row, bool neg) {
         rr[e] = (uint16_t)row;
         ng |= (neg ? 1u : 0u) << e;
         ++e;
@@ -450,10 +450,11 @@ void launch_sketch_columns(int64_t col0, int64_t count, int s, int zeta, uint64_
   if (grid > 0) sketch_columns_kernel<<<grid, 256, 0, st>>>(col0, count, sp, rows, signs, err);
 }
 
-void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTable& tab, int* err, cudaStream_t st) {
+void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTable& tab, int* err, cudaStream_t st,
+                         int64_t col0) {
   const SketchSpec sp = make_sketch_spec(s, zeta, seed);
   const int grid = std::max(1, std::min(8192, (n + 255) / 256));
-  sketch_table_kernel<<<grid, 256, 0, st>>>(n, sp, tab, err);
+  sketch_table_kernel<<<grid, 256, 0, st>>>(n, sp, tab, err, col0);
 }
 
 // Column r of a row-major n x ncols block <-> a contiguous vector.

@@ -147,6 +147,12 @@ struct RgsArgs {
 int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap);
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
+// float32 / bfloat16 bases with staged row streams (step32_kernels.cu): the
+// materialize+sketch kernel and the product kernel of step L.j
+size_t s32_mat_smem(int s, int copies, int kw, int vt_bytes);
+int s32_ctas_per_sm(int basis, int s, int copies);
+int s32_spmv_ctas_per_sm(int tma_cap, int di);
+void launch_step32(int basis, const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
 // float-float product kernel alone (p_j = A w_j, window dots unless L.rgs)
 void launch_ff_product(const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
 // randomized Gram-Schmidt cycle (rgs_kernels.cu)
@@ -170,8 +176,9 @@ void launch_dot_f64(const double* a, const double* b, int n, double* part, int g
                     unsigned* counter, cudaStream_t st);
 void launch_sketch_columns(int64_t col0, int64_t count, int s, int zeta, uint64_t seed, int* rows,
                            signed char* signs, int* err, cudaStream_t st);
+// table entry i holds column col0 + i of S (a rank's rows in a partitioned solve)
 void launch_sketch_table(int n, int s, int zeta, uint64_t seed, const SketchTable& tab, int* err,
-                         cudaStream_t st);
+                         cudaStream_t st, int64_t col0 = 0);
 int sketch_bin_copies(int basis, int s);
 int sketch_word_bits(int rows_per_cta, int copies);
 
@@ -180,8 +187,9 @@ int sketch_word_bits(int rows_per_cta, int copies);
 cudaError_t probe_bounded_wait(unsigned long long limit_ns, unsigned long long* d_out, cudaStream_t st);
 
 // ---- handle creation ------------------------------------------------------
+// column indices must lie in [0, ncols) (ncols <= 0: [0, n))
 cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* d_flag, int* h_flag,
-                         cudaStream_t st);
+                         cudaStream_t st, int ncols = 0);
 cudaError_t narrow_values(int64_t nnz, const double* v, float* v32, int* d_flag, int* h_flag,
                           cudaStream_t st);
 cudaError_t raise_smem_limit(const void* kern, size_t bytes);
@@ -270,6 +278,34 @@ void launch_bk_step(const BlockLaunch& B, int mat, int spmv, cudaStream_t st);
 void launch_bk_sketch_fin(const BlockLaunch& B, const SmallDev& sd, int ncols, cudaStream_t st);
 void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int has_next, double* x, int64_t ldx,
                       const int* active, cudaStream_t st);
+
+// ---- row-partitioned solve (part_kernels.cu) --------------------------------
+// One rank's block of n rows; its CSR columns index [0, n + halo): the local
+// rows, then the halo entries of the current basis vector.
+struct PartLaunch {
+  int n;
+  const int* rp;
+  const int* ci;
+  const double* val;
+  double* W;            // basis slots (float64), stride ldw >= n + halo
+  int64_t ldw;
+  double* p;            // product of the current step (n)
+  double* part;         // per-CTA partials (grid x NQ)
+  double* red;          // all-reduced sums: [0, NQ) product, [NQ] ||w_j||^2
+  long long* acc;       // [m+1][3][s] exact sketch word sums (zeroed per cycle)
+  int* E;               // [m+1] fixed-point exponent of each column's words
+  int grid, rows_per_cta;
+};
+size_t part_mat_smem(int s);
+void launch_part_pack(const double* w, const int* idx, int count, double* out, cudaStream_t st);
+void launch_part_unpack(const double* in, int count, double* w_halo, cudaStream_t st);
+void launch_part_norm_finish(const CycleDev& cd, cudaStream_t st);
+void launch_part_mat(const PartLaunch& P, const StepLaunch& L, const CycleDev& cd, int mat, cudaStream_t st);
+void launch_part_product(const PartLaunch& P, const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
+void launch_part_reduce_mat(const StepLaunch& L, const CycleDev& cd, const double* red, int mat, cudaStream_t st);
+void launch_part_reduce_product(const StepLaunch& L, const CycleDev& cd, const double* red, cudaStream_t st);
+void launch_part_sketch_u(const long long* acc, const int* E, int ncols, int s, int zeta, int wb, double* U,
+                          cudaStream_t st);
 
 void launch_whiten(const SmallDev& sd, const CycleDev& cd, int s, int m, int ncols, int m_eff,
                    int has_next, int cycle, int kw, double t, cudaStream_t st);

@@ -15,7 +15,7 @@
 namespace krylov {
 namespace {
 
-__global__ void validate_kernel(int n, int64_t nnz, const int* rp, const int* ci, int* bad) {
+__global__ void validate_kernel(int n, int64_t nnz, const int* rp, const int* ci, int ncols, int* bad) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = tid; i < n; i += stride) {
@@ -25,7 +25,7 @@ __global__ void validate_kernel(int n, int64_t nnz, const int* rp, const int* ci
   if (tid == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz)) atomicOr(bad, 2);
   for (int64_t e = tid; e < nnz; e += stride) {
     const int c = ci[e];
-    if (c < 0 || c >= n) atomicOr(bad, 4);
+    if (c < 0 || c >= ncols) atomicOr(bad, 4);
   }
 }
 
@@ -214,9 +214,10 @@ int grid_for(int64_t work) {
 }  // namespace
 
 cudaError_t validate_csr(int n, int64_t nnz, const int* rp, const int* ci, int* d_flag, int* h_flag,
-                         cudaStream_t st) {
+                         cudaStream_t st, int ncols) {
   cudaMemsetAsync(d_flag, 0, sizeof(int), st);
-  validate_kernel<<<grid_for(std::max<int64_t>(n, nnz)), 256, 0, st>>>(n, nnz, rp, ci, d_flag);
+  validate_kernel<<<grid_for(std::max<int64_t>(n, nnz)), 256, 0, st>>>(n, nnz, rp, ci, ncols > 0 ? ncols : n,
+                                                                        d_flag);
   cudaMemcpyAsync(h_flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   return cudaStreamSynchronize(st);
 }
