@@ -146,6 +146,10 @@ typedef struct {
   double ms_steps;         /* device time of the step-kernel phases (CUDA events) */
   double step_bytes;       /* algorithmic HBM bytes of those phases */
   int status;              /* krylov_status of the call (per right-hand side in the batched form) */
+  int fquad_cycles;        /* exp(-t z): cycles whose block of f(H) came from the contour quadrature
+                              alone (the cycle count beyond which scaling and squaring stops) */
+  double ms_small;         /* device time of the small-problem phases (sketch sums, whitening, f of
+                              the projected matrix, z) */
 } krylov_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -80,7 +80,7 @@ class Stats(C.Structure):
                 ("last_update_norm", C.c_double), ("x_norm", C.c_double), ("kappa_T_max", C.c_double),
                 ("ms_total", C.c_double), ("bytes_moved", C.c_double), ("launches", C.c_int),
                 ("step_launches", C.c_int), ("ms_steps", C.c_double), ("step_bytes", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("fquad_cycles", C.c_int), ("ms_small", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

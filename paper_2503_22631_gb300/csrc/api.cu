@@ -37,6 +37,9 @@ constexpr size_t CSR_PAD = 8;
 // 256-row tile are copied as 260 entries.
 constexpr size_t RP_PAD = 272;
 constexpr int TMA_MAX_CAP = 4096;  // largest staged tile span (nonzeros)
+constexpr int EXP_SQ_CYCLES = 16;              // exp: cycles also evaluated by scaling and squaring
+constexpr double QUAD_TOL_CONTOURS = 1e-12;    // exp quadrature: largest difference of the two contours
+constexpr double QUAD_TOL_SQUARING = 1e-11;    // ... and to scaling and squaring (relative to the first column)
 // z^{-1/2}: trapezoidal nodes in u (s = e^u) with step INVSQRT_H on
 // [0.5 ln(alpha * 1e-18) - 38, 0.5 ln(alpha * 1e4) + 38], alpha = ||A||_inf >= |lambda|:
 // the two tails are below e^-38 relative for spectra inside [1e-18 alpha, 1e4 alpha], and
@@ -215,7 +218,8 @@ struct krylov_handle {
   double* part = nullptr;
   CycleDev cd{};
   SmallDev sd{};
-  int cap_rows = 0;     // block rows of the projected-function storage
+  int cap_rows = 0;     // block rows of the projected-problem storage (X blocks, couplings)
+  int cap_grows = 0;    // block rows of the exponential's scale levels in sd.G
   int cap_levels = 0;   // scale levels allocated in sd.G
   int64_t gphi_stride = 0;  // phi_1 vectors: doubles per scale level in sd.gphi
   int64_t level_stride = 0;
@@ -223,7 +227,7 @@ struct krylov_handle {
   double* d_dot = nullptr;
   double* stage_b = nullptr;  // device staging of krylov_apply_host
   double* stage_x = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // step phase, small problem
   // the m + 1 step launches of a cycle for A (0) and A^T (1), captured once
   // (their arguments do not change between cycles or calls) and replayed
   cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
@@ -249,7 +253,7 @@ struct krylov_handle {
 
   // host mirrors
   int* h_flags = nullptr;     // pinned: flags[4]
-  double* h_scal = nullptr;   // pinned: 16 doubles
+  double* h_scal = nullptr;   // pinned: 32 doubles ([0, 8) cycle scalars, [8, 16) misc, [16, 20) quadrature checks)
   int last_me = 0, last_nc = 0, last_cycle = 0;
   std::vector<void*> allocs;
 };
@@ -334,31 +338,37 @@ void dfree(krylov_handle* h, void* p) {
 }
 
 // Projected-function storage for `rows` block rows and `levels` scale levels.
-krylov_status ensure_small_capacity(krylov_handle* h, int rows, int levels) {
+// Storage of the projected problem: X blocks and couplings for `rows` cycles,
+// and the scale levels of the exponential's block rows (sd.G) for `grows`
+// rows (grows < 0: as many as rows).  Reallocating G discards its rows; the
+// caller recomputes them from the X blocks.
+krylov_status ensure_small_capacity(krylov_handle* h, int rows, int levels, int grows = -1) {
   const size_t MM = (size_t)h->m * h->m;
+  if (grows < 0) grows = rows;
   if (rows > h->cap_rows) {
     int nr = std::max(rows, std::max(8, 2 * h->cap_rows));
     dfree(h, h->sd.Xblk);
     dfree(h, h->sd.gam);
     dfree(h, h->sd.S0);
-    dfree(h, h->sd.G);
-    h->sd.G = nullptr;
     CK(dalloc(h, &h->sd.Xblk, (size_t)nr * MM));
     CK(dalloc(h, &h->sd.gam, (size_t)nr));
     CK(dalloc(h, &h->sd.S0, std::max<size_t>(2 * (size_t)nr * MM, (size_t)h->m * h->m)));
     h->cap_rows = nr;
-    h->cap_levels = 0;
   }
-  if (levels > h->cap_levels || h->sd.G == nullptr) {
-    int nl = std::max(levels, h->cap_levels + 4);
+  grows = std::min(grows, h->cap_rows);
+  if (grows > h->cap_grows || levels > h->cap_levels || h->sd.G == nullptr) {
+    const int ng = std::max(grows, h->cap_grows);
+    const int nl = (levels > h->cap_levels) ? std::max(levels, h->cap_levels + 4) : h->cap_levels;
     dfree(h, h->sd.G);
-    h->level_stride = (int64_t)h->cap_rows * (h->cap_rows + 1) / 2 * (int64_t)MM;
+    h->sd.G = nullptr;
+    h->level_stride = (int64_t)ng * (ng + 1) / 2 * (int64_t)MM;
     CK(dalloc(h, &h->sd.G, (size_t)nl * h->level_stride));
     if (h->f.kind == KRYLOV_F_PHI1_NEG) {  // the augmented column: one m-vector per block row and level
       dfree(h, h->sd.gphi);
-      h->gphi_stride = (int64_t)h->cap_rows * h->m;
+      h->gphi_stride = (int64_t)ng * h->m;
       CK(dalloc(h, &h->sd.gphi, (size_t)nl * h->gphi_stride));
     }
+    h->cap_grows = ng;
     h->cap_levels = nl;
   }
   return KRYLOV_OK;
@@ -866,7 +876,12 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   int levels_needed = 1;
   if (h->f.kind == KRYLOV_F_EXP_NEG || h->f.kind == KRYLOV_F_PHI1_NEG || h->f.kind == KRYLOV_F_COS_SQRT)
     levels_needed = std::max(1, h->cap_levels);
-  krylov_status cs = ensure_small_capacity(h, max_cycles, levels_needed);
+  // exp(-t z), t > 0: the contour quadrature runs from the first cycle; the
+  // scaling-and-squaring block rows are formed in the first EXP_SQ_CYCLES
+  // cycles (they validate the quadrature) and afterwards only if a check fails
+  bool quad = (h->f.kind == KRYLOV_F_EXP_NEG && h->f.t > 0.0 && h->sd.qstat != nullptr);
+  krylov_status cs =
+      ensure_small_capacity(h, max_cycles, levels_needed, quad ? std::min(max_cycles, EXP_SQ_CYCLES) : max_cycles);
   if (cs != KRYLOV_OK) return cs;
 
   CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st));
@@ -973,6 +988,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       }
     }
     phase.next("small problem");
+    CK(cudaEventRecord(h->ev[2], st));
     if (rgs) {
       launch_rgs_small(h->sd, h->cd, M, me, has_next, c, h->f.t, st);
       stats.launches += 1;
@@ -999,18 +1015,49 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       // ||t X||_1 + |t gamma| bounds ||t H||_1; cos(t sqrt(H)) scales t^2 H
       const int need = (h->f.kind == KRYLOV_F_COS_SQRT) ? cos_levels_for(std::fabs(h->f.t) * (maxX + maxG))
                                                          : scale_levels_for(maxX + maxG);
-      if (need > s_lv) {
-        s_lv = need;
-        cs = ensure_small_capacity(h, max_cycles, s_lv + 1);
-        if (cs != KRYLOV_OK) return cs;
-        for (int ap = 0; ap < a; ++ap) stats.launches += exp_row(h, ap, s_lv);
-      }
-      stats.launches += exp_row(h, a, s_lv);
       const size_t MM = (size_t)M * M;
       // exp: first column of block (a, 0); phi_1: block row a of the extra column
-      const double* fsrc = (h->f.kind == KRYLOV_F_PHI1_NEG)
-                               ? h->sd.gphi + (size_t)s_lv * h->gphi_stride + (size_t)a * M
-                               : h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
+      auto square_row = [&]() -> const double* {
+        return (h->f.kind == KRYLOV_F_PHI1_NEG)
+                   ? h->sd.gphi + (size_t)s_lv * h->gphi_stride + (size_t)a * M
+                   : h->sd.G + (size_t)s_lv * h->level_stride + (size_t)a * (a + 1) / 2 * MM;
+      };
+      // scaling and squaring of block row a (all earlier rows at a new scale)
+      auto squaring = [&](bool all_rows) -> krylov_status {
+        if (need > s_lv || all_rows) {
+          s_lv = std::max(s_lv, need);
+          const krylov_status c2 = ensure_small_capacity(h, max_cycles, s_lv + 1,
+                                                         quad ? std::min(max_cycles, EXP_SQ_CYCLES) : max_cycles);
+          if (c2 != KRYLOV_OK) return c2;
+          for (int ap = 0; ap < a; ++ap) stats.launches += exp_row(h, ap, s_lv);
+        }
+        stats.launches += exp_row(h, a, s_lv);
+        return KRYLOV_OK;
+      };
+      const bool sq = !quad || c <= EXP_SQ_CYCLES;
+      const double* fsq = nullptr;
+      if (sq) {
+        if ((cs = squaring(false)) != KRYLOV_OK) return cs;
+        fsq = square_row();
+      }
+      const double* fsrc = fsq;
+      if (quad) {
+        if (c == 1) launch_exp_quad_sigma(h->sd, me, h->f.t, fsq, st);
+        launch_exp_quad(h->sd, h->cd, M, me, a, h->f.t, fsq, st);
+        stats.launches += (c == 1) ? 3 : 2;
+        if (!sq) {  // the contours must agree before the result is used
+          CK(cudaMemcpyAsync(h->h_scal + 16, h->sd.qstat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if (h->h_scal[19] <= QUAD_TOL_CONTOURS) {
+            fsrc = h->sd.fcol;
+            stats.fquad_cycles += 1;
+          } else {  // squaring from here on, all block rows formed now
+            quad = false;
+            if ((cs = squaring(true)) != KRYLOV_OK) return cs;
+            fsrc = square_row();
+          }
+        }
+      }
       launch_z(h->sd, M, me, fsrc, st);
       stats.launches += 1;
     } else if (h->f.kind == KRYLOV_F_INVSQRT) {
@@ -1024,6 +1071,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     } else {
       return KRYLOV_EUNSUPPORTED;
     }
+    CK(cudaEventRecord(h->ev[3], st));
     phase.next("update");
     launch_update(basis, h->W, h->ldw, n, me, has_next, h->sd.zg, x, h->part, h->grid_update, h->cd, M, st);
     stats.launches += 1;
@@ -1036,7 +1084,22 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     CK(cudaMemcpyAsync(h->h_scal, h->cd.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_scal + 8, h->sd.misc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_flags, h->cd.flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (quad) CK(cudaMemcpyAsync(h->h_scal + 16, h->sd.qstat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    // a cycle with both evaluations: the quadrature must match the squaring and
+    // its two contours each other, else the squaring continues alone
+    if (quad && c <= EXP_SQ_CYCLES &&
+        !(h->h_scal[18] <= QUAD_TOL_SQUARING && h->h_scal[19] <= QUAD_TOL_CONTOURS)) {
+      quad = false;
+      cs = ensure_small_capacity(h, max_cycles, s_lv + 1, max_cycles);  // rows beyond EXP_SQ_CYCLES
+      if (cs != KRYLOV_OK) return cs;
+      for (int ap = 0; ap <= c - 1; ++ap) stats.launches += exp_row(h, ap, s_lv);
+    }
+    {
+      float ms_q = 0.f;
+      CK(cudaEventElapsedTime(&ms_q, h->ev[2], h->ev[3]));
+      stats.ms_small += ms_q;
+    }
     if (h->h_flags[2] & ERR_TIMEOUT) return KRYLOV_ETIMEOUT;  // a bounded wait of the small problem
     if (h->h_flags[2] & ERR_NONFINITE) return KRYLOV_ENONFINITE;
     stats.kappa_T_max = std::max(stats.kappa_T_max, h->h_scal[8 + 4]);
@@ -1590,7 +1653,7 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
   if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(KRYLOV_ECUDA);
   if (cudaMallocHost(&h->h_flags, 16 * sizeof(int)) != cudaSuccess) return fail(KRYLOV_ENOMEM);
-  if (cudaMallocHost(&h->h_scal, 16 * sizeof(double)) != cudaSuccess) return fail(KRYLOV_ENOMEM);
+  if (cudaMallocHost(&h->h_scal, 32 * sizeof(double)) != cudaSuccess) return fail(KRYLOV_ENOMEM);
 
   const int n = h->n;
   const int64_t nnz = h->nnz;
@@ -1628,8 +1691,8 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
     CKF(split_values(nnz, h->val, h->valff, h->st));
   }
 
-  if (cudaEventCreate(&h->ev[0]) != cudaSuccess || cudaEventCreate(&h->ev[1]) != cudaSuccess)
-    return fail(KRYLOV_ECUDA);
+  for (auto& e : h->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(KRYLOV_ECUDA);
   // the sparse sign embedding S: a device table (default) or regenerated in
   // every step kernel
   const bool packed = (s <= 255 && opt.zeta <= 8);
@@ -1743,6 +1806,14 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
     CKF(dalloc(h, &h->sd.qpart, (size_t)h->q_nodes * m));
     if (invsqrt_smem(m) == (size_t)256 * sizeof(double))
       CKF(dalloc(h, &h->sd.qwork, (size_t)h->q_nodes * m * m));
+  }
+  if (f.kind == KRYLOV_F_EXP_NEG) {  // contour-quadrature state of exp(-t z)
+    const int nodes = exp_quad_nodes();
+    CKF(dalloc(h, &h->sd.qstat, 4));
+    CKF(dalloc(h, &h->sd.qcarry, (size_t)2 * nodes));
+    CKF(dalloc(h, &h->sd.qpart, (size_t)nodes * m));
+    if (exp_quad_smem(m) == (size_t)256 * 2 * sizeof(double))
+      CKF(dalloc(h, &h->sd.qwork, (size_t)nodes * m * m * 2));
   }
   CKF(dalloc(h, &h->d_dot, 1));
   if (ps) {

@@ -227,11 +227,24 @@ struct SmallDev {
   double* qwork;   // z^{-1/2}: nodes x m x m LU work when it does not fit in shared memory
   double* gphi;    // phi_1: per scale level and block row, the m-vector of the augmented
                    // exponential's extra column (levels x cycles x m)
+  double* qstat;   // exp by contour quadrature: [0] sigma, [1] largest |entry| of the first
+                   // column so far, [2] difference to scaling and squaring, [3] difference
+                   // between the two contours (both relative to [1])
 };
 
 // z^{-1/2} quadrature nodes keep their m x m LU work in shared memory up to this size.
 constexpr size_t INVSQRT_SMEM_MAX = 100 * 1024;
 size_t invsqrt_smem(int m);
+// exp(-t z) by contour quadrature (small_kernels.cu): complex m x m LU work per
+// point in shared memory up to this size, else in sd.qwork (points x m x m complex)
+constexpr size_t EXP_QUAD_SMEM_MAX = 200 * 1024;
+size_t exp_quad_smem(int m);
+int exp_quad_nodes();
+void launch_exp_quad_sigma(const SmallDev& sd, int m_eff, double t, const double* fsq, cudaStream_t st);
+// block row a of the first column of exp(-t H) into sd.fcol (fsq: the
+// scaling-and-squaring block to compare with, or null)
+void launch_exp_quad(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double t, const double* fsq,
+                     cudaStream_t st);
 
 __host__ __device__ inline SmallDev offset_sd(SmallDev sd, const BatchStride& b, int r) {
   sd.U += b.U * r;

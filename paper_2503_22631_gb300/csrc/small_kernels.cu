@@ -810,6 +810,212 @@ __global__ void invsqrt_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, int 
   }
 }
 
+// f(z) = exp(-t z) with a cost per cycle that does not grow with the cycle
+// count: the exponential as a resolvent integral,
+//   e^w = (1 / 2 pi i) int_Gamma e^zeta (zeta - w)^{-1} d zeta,
+// Gamma winding once around the spectrum of w = -t (H - sigma I), discretized by
+// the midpoint rule on two contours published for e^w with w on (-inf, 0]
+// (Trefethen, Weideman and Schmelzer, BIT 46, 2006):
+//   parabolic   zeta(th) = N (0.1309 - 0.1194 th^2 + 0.2500 i th),
+//   hyperbolic  zeta(th) = 2.246 N (1 - sin(1.1721 - 0.3443 i th)),
+// N = EQ_N points th_k = -pi + (k - 1/2) h, h = 2 pi / N.  For a real matrix and
+// vector the points come in conjugate pairs, so the K = N / 2 points with
+// th > 0 give e^w v = (h / pi) sum_k Im(e^{zeta_k} zeta'(th_k) (zeta_k - w)^{-1} v).
+// (zeta_k I + t (H - sigma I))^{-1} e_1 is found block by block on the block
+// lower-bidiagonal H exactly as for 1/z: block a solves
+// ((zeta_k - t sigma) I + t X_a) y = rhs, rhs = e_1 (a = 0) or
+// -t gamma_{a-1} carry_k e_1 with carry_k the last entry of point k's solution
+// in block a - 1, so a cycle costs 2 K complex m x m LU factorizations and the
+// state kept across cycles is one complex number per point.  The shift sigma
+// (fixed in the first cycle) brings the largest e^w near 1, so the quadrature's
+// absolute error is relative to the result.  The two contours enclose
+// different regions; their results agree only when both enclose the spectrum,
+// which the host checks every cycle before using the result.
+constexpr int EQ_N = 32;
+constexpr int EQ_K = EQ_N / 2;  // points per contour used (th > 0)
+
+struct cplx {
+  double re, im;
+};
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+// point k of contour c: zeta and zeta'(th)
+__device__ __forceinline__ void eq_point(int c, int k, cplx* z, cplx* dz) {
+  const double h = 2.0 * 3.14159265358979323846 / EQ_N;
+  const double th = (k + 0.5) * h;
+  if (c == 0) {
+    *z = {EQ_N * (0.1309 - 0.1194 * th * th), EQ_N * 0.25 * th};
+    *dz = {EQ_N * (-2.0 * 0.1194 * th), EQ_N * 0.25};
+  } else {
+    // sin(u - i v) = sin u cosh v - i cos u sinh v, cos(u - i v) = cos u cosh v + i sin u sinh v
+    const double u = 1.1721, v = 0.3443 * th, A = 2.246 * EQ_N;
+    const double su = sin(u), cu = cos(u), chv = cosh(v), shv = sinh(v);
+    *z = {A * (1.0 - su * chv), A * (cu * shv)};
+    // d/dth [A (1 - sin(u - i 0.3443 th))] = A * 0.3443 i * cos(u - i v)
+    const cplx cs{cu * chv, su * shv};
+    *dz = cmul({0.0, A * 0.3443}, cs);
+  }
+}
+
+constexpr int EQ_THREADS = 128;
+__global__ void __launch_bounds__(EQ_THREADS) exp_quad_nodes_kernel(SmallDev sd, int M, int me, int a, double t,
+                                                                   int glob) {
+  extern __shared__ double qs[];
+  __shared__ int piv;
+  const int node = blockIdx.x;  // contour node / EQ_K, point node % EQ_K
+  const int tid = threadIdx.x;
+  cplx z, dz;
+  eq_point(node / EQ_K, node % EQ_K, &z, &dz);
+  const double sigma = sd.qstat[0];
+  const cplx shift{z.re - t * sigma, z.im};
+  cplx* y = reinterpret_cast<cplx*>(qs);
+  cplx* work = glob ? reinterpret_cast<cplx*>(sd.qwork) + (size_t)node * M * M : y + 256;
+  const double* X = sd.Xblk + (size_t)a * M * M;
+  cplx rhs0{1.0, 0.0};
+  if (a > 0) {
+    const double g = -t * sd.gam[a - 1];
+    rhs0 = {g * sd.qcarry[2 * node], g * sd.qcarry[2 * node + 1]};
+  }
+  for (int e = tid; e < me * me; e += blockDim.x) {
+    const int r = e % me, c = e / me;
+    work[e] = {t * X[(size_t)c * M + r] + (r == c ? shift.re : 0.0), r == c ? shift.im : 0.0};
+  }
+  for (int r = tid; r < me; r += blockDim.x) y[r] = (r == 0) ? rhs0 : cplx{0.0, 0.0};
+  __syncthreads();
+  for (int c = 0; c < me; ++c) {  // LU with partial pivoting (|re| + |im|; ties: first row)
+    if (tid < 32) {
+      double best = -1.0;
+      int p = c;
+      for (int r = c + tid; r < me; r += 32) {
+        const cplx v = work[(size_t)c * me + r];
+        const double m1 = fabs(v.re) + fabs(v.im);
+        if (m1 > best) {
+          best = m1;
+          p = r;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) {
+          best = ob;
+          p = op;
+        }
+      }
+      if (tid == 0) piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != c) {
+      for (int l = tid; l < me; l += blockDim.x) {
+        const cplx tmp = work[(size_t)l * me + c];
+        work[(size_t)l * me + c] = work[(size_t)l * me + p];
+        work[(size_t)l * me + p] = tmp;
+      }
+      if (tid == 0) {
+        const cplx ty = y[c];
+        y[c] = y[p];
+        y[p] = ty;
+      }
+    }
+    __syncthreads();
+    const cplx d = work[(size_t)c * me + c];
+    for (int r = c + 1 + tid; r < me; r += blockDim.x) {
+      const cplx f = cdiv(work[(size_t)c * me + r], d);
+      for (int l = c + 1; l < me; ++l) {
+        const cplx u = cmul(f, work[(size_t)l * me + c]);
+        work[(size_t)l * me + r].re -= u.re;
+        work[(size_t)l * me + r].im -= u.im;
+      }
+      const cplx u = cmul(f, y[c]);
+      y[r].re -= u.re;
+      y[r].im -= u.im;
+    }
+    __syncthreads();
+  }
+  for (int c = me - 1; c >= 0; --c) {  // back substitution
+    if (tid == 0) y[c] = cdiv(y[c], work[(size_t)c * me + c]);
+    __syncthreads();
+    const cplx yc = y[c];
+    for (int r = tid; r < c; r += blockDim.x) {
+      const cplx u = cmul(work[(size_t)c * me + r], yc);
+      y[r].re -= u.re;
+      y[r].im -= u.im;
+    }
+    __syncthreads();
+  }
+  // weight (h / pi) e^zeta zeta'
+  const double h = 2.0 * 3.14159265358979323846 / EQ_N;
+  const double ez = exp(z.re) * (h / 3.14159265358979323846);
+  const cplx w = cmul({ez * cos(z.im), ez * sin(z.im)}, dz);
+  for (int r = tid; r < me; r += blockDim.x) sd.qpart[(size_t)node * M + r] = cmul(w, y[r]).im;
+  if (tid == 0) {
+    sd.qcarry[2 * node] = y[me - 1].re;
+    sd.qcarry[2 * node + 1] = y[me - 1].im;
+  }
+}
+
+// fcol = e^{-t sigma} (sum over the parabolic contour's points, in point
+// order); qstat[3] = max |difference to the hyperbolic contour's sum| and
+// qstat[2] = max |difference to fsq| (when given: the block row of the
+// scaling-and-squaring evaluation), both relative to the largest |entry| of
+// the first column met so far (qstat[1]).
+__global__ void exp_quad_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, double t, const double* fsq) {
+  __shared__ double s_d[3][256];
+  const double E = exp(-t * sd.qstat[0]);
+  double dq = 0.0, dsq = 0.0, mx = 0.0;
+  for (int r = threadIdx.x; r < me; r += blockDim.x) {
+    double f1 = 0.0, f2 = 0.0;
+    for (int k = 0; k < EQ_K; ++k) {
+      f1 += sd.qpart[(size_t)k * M + r];
+      f2 += sd.qpart[(size_t)(EQ_K + k) * M + r];
+    }
+    f1 *= E;
+    f2 *= E;
+    sd.fcol[r] = f1;
+    if (!isfinite(f1)) atomicOr(&cd.flags[2], ERR_NONFINITE);
+    dq = fmax(dq, fabs(f1 - f2));
+    mx = fmax(mx, fabs(f1));
+    if (fsq) {
+      dsq = fmax(dsq, fabs(f1 - fsq[r]));
+      mx = fmax(mx, fabs(fsq[r]));
+    }
+  }
+  s_d[0][threadIdx.x] = dq;
+  s_d[1][threadIdx.x] = dsq;
+  s_d[2][threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)blockDim.x; ++i) {
+      dq = fmax(dq, s_d[0][i]);
+      dsq = fmax(dsq, s_d[1][i]);
+      mx = fmax(mx, s_d[2][i]);
+    }
+    const double scale = fmax(sd.qstat[1], mx);
+    sd.qstat[1] = scale;
+    sd.qstat[2] = (scale > 0.0) ? dsq / scale : INFINITY;
+    sd.qstat[3] = (scale > 0.0 && isfinite(dq)) ? dq / scale : INFINITY;
+  }
+}
+
+// sigma from the first cycle's block of the scaling-and-squaring evaluation:
+// ||f_1|| ~ e^{-t lambda_min} for the smallest real eigenvalue lambda_min the
+// first column meets; sigma = (-ln ||f_1|| - 5) / t keeps w = -t (lambda - sigma)
+// at most ~5 above its value at lambda_min (inside both contours).
+__global__ void exp_quad_sigma_kernel(SmallDev sd, int me, double t, const double* fsq) {
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int r = 0; r < me; ++r) nrm = fma(fsq[r], fsq[r], nrm);
+    nrm = sqrt(nrm);
+    sd.qstat[0] = (nrm > 0.0 && isfinite(nrm)) ? (-log(nrm) - 5.0) / t : 0.0;
+    sd.qstat[1] = 0.0;
+  }
+}
+
 __global__ void z_kernel(SmallDev sd, int M, int me, const double* fsrc, const BatchStride bs, int64_t fstride) {
   sd = offset_sd(sd, bs, blockIdx.x);  // problem blockIdx.x of a batch
   fsrc += fstride * blockIdx.x;
@@ -985,6 +1191,26 @@ void launch_invsqrt_block(const SmallDev& sd, const CycleDev& cd, int m, int m_e
   raise_smem_limit((const void*)invsqrt_nodes_kernel, smem);
   invsqrt_nodes_kernel<<<nodes, QN_THREADS, smem, st>>>(sd, m, m_eff, a, u0, hq, glob);
   invsqrt_sum_kernel<<<1, 256, 0, st>>>(sd, cd, m, m_eff, nodes);
+}
+
+size_t exp_quad_smem(int m) {
+  const size_t b = (size_t)(256 + (size_t)m * m) * 2 * sizeof(double);
+  return b <= EXP_QUAD_SMEM_MAX ? b : (size_t)256 * 2 * sizeof(double);
+}
+
+int exp_quad_nodes() { return 2 * EQ_K; }
+
+void launch_exp_quad_sigma(const SmallDev& sd, int m_eff, double t, const double* fsq, cudaStream_t st) {
+  exp_quad_sigma_kernel<<<1, 32, 0, st>>>(sd, m_eff, t, fsq);
+}
+
+void launch_exp_quad(const SmallDev& sd, const CycleDev& cd, int m, int m_eff, int a, double t, const double* fsq,
+                     cudaStream_t st) {
+  const size_t smem = exp_quad_smem(m);
+  const int glob = (smem == (size_t)256 * 2 * sizeof(double)) ? 1 : 0;
+  raise_smem_limit((const void*)exp_quad_nodes_kernel, smem);
+  exp_quad_nodes_kernel<<<2 * EQ_K, EQ_THREADS, smem, st>>>(sd, m, m_eff, a, t, glob);
+  exp_quad_sum_kernel<<<1, 256, 0, st>>>(sd, cd, m, m_eff, t, fsq);
 }
 
 void launch_z(const SmallDev& sd, int m, int m_eff, const double* fcol_src, cudaStream_t st) {

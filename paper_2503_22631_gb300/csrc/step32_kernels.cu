@@ -1,0 +1,440 @@
+// step32_kernels.cu -- the Arnoldi-step kernels of the float32 and bfloat16
+// bases with their row streams staged in shared memory by bulk asynchronous
+// copies (the layout of the float-float pair in step_kernels.cu, with float32
+// arithmetic):
+//
+//   s32_mat_tma_kernel    w_j = rho_j (p_{j-1} - sum_q h_q w_q) rounded to the
+//                         storage type and stored in slot j; its sketch
+//                         S w_j (exact fixed-point words of the STORED value)
+//                         and ||w_j||^2
+//   s32_spmv_tma_kernel   p_j = A w_j (float32 products summed in storage
+//                         order, CSR tiles staged), ||p_j||^2 and the window
+//                         dots <w_q, p_j>
+//
+// Per-thread sums are float32; CTA and cross-CTA sums are float64 in a fixed
+// order, and the last CTA applies the same reducers as the other bases.
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "step_common.cuh"
+
+namespace krylov {
+namespace {
+
+constexpr int R32 = STEP_THREADS;         // rows per staged tile
+constexpr int MT32_STAGES = 3;            // tiles in flight in the materialize kernel
+constexpr int SP32_STAGES = 2;            // CSR tiles in flight in the product kernel
+constexpr int RP32 = R32 + 4;             // staged row_ptr entries (16-byte multiple)
+constexpr int FAST32 = 8;                 // rows up to this length issue all gathers together
+constexpr uint64_t WAIT32_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
+
+template <typename VT> __device__ __forceinline__ float to_f(VT v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Stage of the materialize kernel: the previous product (float, or the stored
+// start vector when there is nothing to materialize), KW window columns, the
+// packed sketch table (8 row bytes and a sign byte per column).
+template <typename VT>
+__host__ __device__ constexpr size_t mt32_stage_bytes(int kw) {
+  return (size_t)R32 * (4 + kw * sizeof(VT) + 8 + 1);
+}
+
+template <typename VT, bool MAT, int KW, int C, int Z>
+__global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
+  constexpr int NW = 2;  // fixed-point words per contribution (float32 significands)
+  static_assert(C == 16 || C == 32, "lane copies of the bins");
+  constexpr size_t SB = mt32_stage_bytes<VT>(KW);
+  constexpr size_t OFF_W = (size_t)R32 * 4;
+  constexpr size_t OFF_R = OFF_W + (size_t)R32 * KW * sizeof(VT);
+  constexpr size_t OFF_N = OFF_R + (size_t)R32 * 8;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[MT32_STAGES];
+  __shared__ double red[32];
+  __shared__ int s_last;
+  __shared__ FxScale s_fx;
+  __shared__ float s_h[MAX_WINDOW + 1];
+  const int lane = threadIdx.x & 31;
+  int* bins = reinterpret_cast<int*>(smem);  // [s][C][NW]
+  unsigned char* stages = smem + align16((size_t)NW * L.s * C * sizeof(int));
+  const int j = L.j;
+  const int lo = MAT ? max(0, j - L.k) : j;
+  const int nl = j - lo;
+  const int r0 = blockIdx.x * L.rows_per_cta;
+  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + R32 - 1) / R32 : 0;
+  const VT* W = static_cast<const VT*>(L.W);
+  VT* Wj = static_cast<VT*>(L.W) + (int64_t)j * L.ldw;
+  const VT* Wq[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * L.ldw;
+  // the first part of a tile's copies (window, table) does not depend on the
+  // kernel just before and is issued before the dependent-launch wait; the
+  // product's copy arrives with the last byte count
+  auto rows_of = [&](int t) { return (uint32_t)((min(R32, r1 - (r0 + t * R32)) + 15) & ~15); };
+  auto issue_static = [&](int t) {
+    const int st = t % MT32_STAGES;
+    const int ts = r0 + t * R32;
+    const uint32_t rc = rows_of(t);
+    unsigned char* base = stages + st * SB;
+    mbar_expect_tx(&bars[st], rc * (uint32_t)sizeof(VT) * (MAT ? (uint32_t)nl : 0u) + rc * 9u);
+    if (MAT) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nl)
+          bulk_g2s(base + OFF_W + (size_t)q * R32 * sizeof(VT), Wq[q] + ts, rc * (uint32_t)sizeof(VT), &bars[st]);
+    }
+    bulk_g2s(base + OFF_R, L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
+    bulk_g2s(base + OFF_N, L.sk_tab.neg8 + ts, rc, &bars[st]);
+  };
+  auto issue_p = [&](int t) {
+    const int st = t % MT32_STAGES;
+    const uint32_t rc = rows_of(t);
+    const int ts = r0 + t * R32;
+    if (MAT) {
+      mbar_arrive_expect_tx(&bars[st], rc * 4u);
+      bulk_g2s(stages + st * SB, static_cast<const float*>(L.p_prev) + ts, rc * 4u, &bars[st]);
+    } else {
+      mbar_arrive_expect_tx(&bars[st], rc * (uint32_t)sizeof(VT));
+      bulk_g2s(stages + st * SB, Wj + ts, rc * (uint32_t)sizeof(VT), &bars[st]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < MT32_STAGES; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  {
+    const int nb = NW * L.s * C;
+    int4* b4 = reinterpret_cast<int4*>(bins);
+    for (int e = threadIdx.x; e < nb / 4; e += blockDim.x) b4[e] = make_int4(0, 0, 0, 0);
+    for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
+  }
+  const int npre = min(ntiles, MT32_STAGES);
+  if (threadIdx.x == 0)
+    for (int t = 0; t < npre; ++t) issue_static(t);
+  pdl_wait();
+  if (cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
+    if (threadIdx.x == 0)
+      for (int t = 0; t < npre; ++t) {
+        mbar_arrive(&bars[t]);
+        (void)mbar_wait_bounded(&bars[t], 0u, WAIT32_NS);
+      }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < npre; ++t) issue_p(t);
+    s_fx = fx_scale(L, cd, MAT ? 1 : 0);
+    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? (float)c[q] : 0.f;
+    s_h[MAX_WINDOW] = MAT ? (float)c[MAX_WINDOW] : 1.f;
+  }
+  __syncthreads();
+  const FxScale fxs = s_fx;
+  int* const mybins = bins + (lane & (C - 1)) * NW;
+  const int zeta = (Z > 0) ? Z : L.zeta;
+  float h[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) h[q] = s_h[q];
+  const float rho = s_h[MAX_WINDOW];
+  float acc_sig = 0.f;
+  bool timed_out = false;
+  int last_issued = npre - 1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % MT32_STAGES;
+    const uint32_t par = (uint32_t)(t / MT32_STAGES) & 1u;
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, WAIT32_NS)) timed_out = true;
+    const unsigned char* base = stages + st * SB;
+    const int k = (int)threadIdx.x;
+    const int i = r0 + t * R32 + k;
+    if (i < r1 && !timed_out) {
+      float wj;
+      if (MAT) {
+        float a = reinterpret_cast<const float*>(base)[k];
+#pragma unroll
+        for (int q = 0; q < KW; ++q)
+          if (q < nl) a = __fmaf_rn(-h[q], to_f(reinterpret_cast<const VT*>(base + OFF_W + (size_t)q * R32 * sizeof(VT))[k]), a);
+        const float v = a * rho;
+        Store<VT>::put(Wj + i, v);
+        wj = stored<VT, float>(v);  // the sketch and the norm see the stored value
+      } else {
+        wj = to_f(reinterpret_cast<const VT*>(base)[k]);
+      }
+      acc_sig = __fmaf_rn(wj, wj, acc_sig);
+      const uint2 rr = reinterpret_cast<const uint2*>(base + OFF_R)[k];
+      const uint32_t ng = (base + OFF_N)[k];
+      const FxWords<NW> xw = fx_split<NW>(wj, 0.f, fxs);
+      const int q0 = xw.q[0], q1 = xw.q[1];
+      const int n0 = -q0, n1 = -q1;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (Z == 8 || e < zeta) {
+          const int row = (int)__byte_perm(e < 4 ? rr.x : rr.y, 0u, 0x4440u | (uint32_t)(e & 3));
+          int* b = mybins + row * (C * NW);
+          const bool neg = (ng >> e) & 1u;
+          atomicAdd(b, neg ? n0 : q0);
+          atomicAdd(b + 1, neg ? n1 : q1);
+        }
+    }
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && t + MT32_STAGES < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue_static(t + MT32_STAGES);
+      issue_p(t + MT32_STAGES);
+      last_issued = t + MT32_STAGES;
+    }
+  }
+  pdl_trigger();
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    for (int t = max(0, last_issued - MT32_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % MT32_STAGES], (uint32_t)(t / MT32_STAGES) & 1u, WAIT32_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  const double v = block_sum((double)acc_sig, red);
+  if (threadIdx.x == 0) part[0] = v;
+  __syncthreads();
+  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
+  for (int b = threadIdx.x; b < L.s; b += blockDim.x) {
+    long long t0 = 0, t1 = 0;
+#pragma unroll 8
+    for (int c = 0; c < C; ++c) {
+      const int* w = bins + (b * C + ((c + b) & (C - 1))) * NW;
+      t0 += w[0];
+      t1 += w[1];
+    }
+    out[b] = (double)(t0 * (1ll << L.fx_wb) + t1) * pow2d(fxs.E - 2 * L.fx_wb);
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  if (threadIdx.x < 32) {
+    const double tsum = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
+    if (threadIdx.x == 0) {
+      (void)reduce_mat(L, cd, tsum, MAT ? 1 : 0);
+      *cd.counter = 0u;
+    }
+  }
+}
+
+// Stage of the product kernel: row_ptr slice, column entries (4-byte indices,
+// or 2-byte offsets col - row when DI), float values.  cap: a multiple of 8.
+template <bool DI>
+__host__ __device__ constexpr size_t sp32_stage_bytes(int cap) {
+  return (size_t)RP32 * 4 + (size_t)cap * (DI ? 2 : 4) + (size_t)cap * 4;
+}
+
+template <typename VT, int KW, bool DI>
+__global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_tma_kernel(const StepLaunch L, const CycleDev cd) {
+  using CT = typename std::conditional<DI, int16_t, int>::type;
+  constexpr int EA = DI ? 8 : 4;  // staged nonzero ranges start on 16-byte boundaries
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[SP32_STAGES];
+  __shared__ double red[32];
+  __shared__ int s_last;
+  __shared__ double tot[NQ];
+  const int j = L.j;
+  const int cap = L.tma_cap;
+  const size_t sb = sp32_stage_bytes<DI>(cap);
+  auto rp_st = [&](int st) { return reinterpret_cast<int*>(smem + (size_t)st * sb); };
+  auto col_st = [&](int st) { return reinterpret_cast<CT*>(rp_st(st) + RP32); };
+  auto val_st = [&](int st) { return reinterpret_cast<float*>(col_st(st) + cap); };
+  const CT* colsrc = DI ? reinterpret_cast<const CT*>(L.dcol) : reinterpret_cast<const CT*>(L.col);
+  const VT* W = static_cast<const VT*>(L.W);
+  const VT* Wj = W + (int64_t)j * L.ldw;
+  const float* val = static_cast<const float*>(L.val);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = j - dlo + 1;
+  const VT* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
+  const int r0 = blockIdx.x * L.rows_spmv;
+  const int r1 = min(L.n, r0 + L.rows_spmv);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + R32 - 1) / R32 : 0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < SP32_STAGES; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t, int e0, int e1) {  // thread 0: stage tile t given its nonzero range
+    const int st = t % SP32_STAGES;
+    const int ts = r0 + t * R32;
+    const int ea = e0 & ~(EA - 1), eb = (e1 + EA - 1) & ~(EA - 1);
+    const uint32_t brp = RP32 * 4u, bcol = (uint32_t)(eb - ea) * (uint32_t)sizeof(CT),
+                   bval = (uint32_t)(eb - ea) * 4u;
+    mbar_arrive_expect_tx(&bars[st], brp + bcol + bval);
+    bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
+    if (eb > ea) {
+      bulk_g2s(col_st(st), colsrc + ea, bcol, &bars[st]);
+      bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
+    }
+  };
+  auto tile_end = [&](int t) { return min(r0 + (t + 1) * R32, r1); };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(ntiles, SP32_STAGES); ++t)
+      issue(t, __ldg(L.row_ptr + r0 + t * R32), __ldg(L.row_ptr + tile_end(t)));
+  pdl_wait();  // w_j comes from the kernel just before
+  if (cd.flags[1] != 0) {  // breakdown in this cycle: no further products
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(ntiles, SP32_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, WAIT32_NS);
+    return;
+  }
+  float acc_pi = 0.f, acc_dot[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) acc_dot[q] = 0.f;
+  bool timed_out = false;
+  int last_issued = min(ntiles, SP32_STAGES) - 1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % SP32_STAGES;
+    const uint32_t par = (uint32_t)(t / SP32_STAGES) & 1u;
+    const int ts = r0 + t * R32;
+    const int i = ts + (int)threadIdx.x;
+    const bool valid = i < tile_end(t);
+    int nb0 = 0, nb1 = 0;
+    if (threadIdx.x == 0 && t + SP32_STAGES < ntiles) {
+      nb0 = __ldg(L.row_ptr + ts + SP32_STAGES * R32);
+      nb1 = __ldg(L.row_ptr + tile_end(t + SP32_STAGES));
+    }
+    float wq[KW];
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) wq[q] = to_f(Wd[q][i]);
+    }
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, WAIT32_NS)) timed_out = true;
+    if (valid && !timed_out) {
+      const int* rps = rp_st(st);
+      const CT* cs = col_st(st);
+      const float* vs = val_st(st);
+      const int ea = rps[0] & ~(EA - 1);
+      const int rb = rps[threadIdx.x] - ea, re = rps[threadIdx.x + 1] - ea;
+      const int cbase = DI ? i : 0;
+      float acc = 0.f;
+      if (re - rb <= FAST32) {
+        float wv[FAST32];
+#pragma unroll
+        for (int q = 0; q < FAST32; ++q)
+          if (rb + q < re) wv[q] = to_f(Wj[cbase + (int)cs[rb + q]]);
+#pragma unroll
+        for (int q = 0; q < FAST32; ++q)
+          if (rb + q < re) acc = __fmaf_rn(vs[rb + q], wv[q], acc);
+      } else {
+#pragma unroll 4
+        for (int e = rb; e < re; ++e) acc = __fmaf_rn(vs[e], to_f(Wj[cbase + (int)cs[e]]), acc);
+      }
+      static_cast<float*>(L.p_out)[i] = acc;
+      acc_pi = __fmaf_rn(acc, acc, acc_pi);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) acc_dot[q] = __fmaf_rn(wq[q], acc, acc_dot[q]);
+    }
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && t + SP32_STAGES < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue(t + SP32_STAGES, nb0, nb1);
+      last_issued = t + SP32_STAGES;
+    }
+  }
+  pdl_trigger();
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    for (int t = max(0, last_issued - SP32_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % SP32_STAGES], (uint32_t)(t / SP32_STAGES) & 1u, WAIT32_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  double v = block_sum((double)acc_pi, red);
+  if (threadIdx.x == 0) part[1] = v;
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;  // uniform over the block
+    __syncthreads();
+    v = block_sum((double)acc_dot[q], red);
+    if (threadIdx.x == 0) part[2 + q] = v;
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
+    if ((threadIdx.x & 31) == 0) tot[q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
+    if (threadIdx.x == 0) *cd.counter = 0u;
+  }
+}
+
+template <typename K> int occ32(K kern, size_t smem) {
+  raise_smem_limit((const void*)kern, smem);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, STEP_THREADS, smem);
+  return b < 1 ? 1 : b;
+}
+
+template <typename VT, bool MAT, int KW>
+void launch_mat32(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  const size_t smem = s32_mat_smem(L.s, L.sk_copies, KW, sizeof(VT));
+  auto k = (L.sk_copies == 32)
+               ? ((L.zeta == 8) ? s32_mat_tma_kernel<VT, MAT, KW, 32, 8> : s32_mat_tma_kernel<VT, MAT, KW, 32, 0>)
+               : ((L.zeta == 8) ? s32_mat_tma_kernel<VT, MAT, KW, 16, 8> : s32_mat_tma_kernel<VT, MAT, KW, 16, 0>);
+  raise_smem_limit((const void*)k, smem);
+  launch_pdl(k, L.grid, smem, st, L, cd);
+}
+
+template <typename VT, int KW>
+void launch_spmv32(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (L.dcol != nullptr) {
+    auto k = s32_spmv_tma_kernel<VT, KW, true>;
+    const size_t smem = SP32_STAGES * sp32_stage_bytes<true>(L.tma_cap);
+    raise_smem_limit((const void*)k, smem);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+  } else {
+    auto k = s32_spmv_tma_kernel<VT, KW, false>;
+    const size_t smem = SP32_STAGES * sp32_stage_bytes<false>(L.tma_cap);
+    raise_smem_limit((const void*)k, smem);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+  }
+}
+
+template <typename VT>
+void launch_step32_t(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  const bool w2 = L.k <= 2;
+  if (L.mat) {
+    if (w2) launch_mat32<VT, true, 2>(L, cd, st);
+    else launch_mat32<VT, true, MAX_WINDOW>(L, cd, st);
+  } else {
+    if (w2) launch_mat32<VT, false, 2>(L, cd, st);
+    else launch_mat32<VT, false, MAX_WINDOW>(L, cd, st);
+  }
+  if (L.spmv) {
+    if (w2) launch_spmv32<VT, 2>(L, cd, st);
+    else launch_spmv32<VT, MAX_WINDOW>(L, cd, st);
+  }
+}
+
+}  // namespace
+
+size_t s32_mat_smem(int s, int copies, int kw, int vt_bytes) {
+  const size_t stage = (size_t)R32 * (4 + (size_t)kw * vt_bytes + 9);
+  return align16((size_t)2 * s * copies * sizeof(int)) + MT32_STAGES * stage;
+}
+
+int s32_ctas_per_sm(int basis, int s, int copies) {
+  const size_t smem = s32_mat_smem(s, copies, 2, basis == 1 ? 4 : 2);
+  if (basis == 1)
+    return copies == 32 ? occ32(s32_mat_tma_kernel<float, true, 2, 32, 8>, smem)
+                        : occ32(s32_mat_tma_kernel<float, true, 2, 16, 8>, smem);
+  return copies == 32 ? occ32(s32_mat_tma_kernel<__nv_bfloat16, true, 2, 32, 8>, smem)
+                      : occ32(s32_mat_tma_kernel<__nv_bfloat16, true, 2, 16, 8>, smem);
+}
+
+int s32_spmv_ctas_per_sm(int tma_cap, int di) {
+  return di ? occ32(s32_spmv_tma_kernel<float, 2, true>, SP32_STAGES * sp32_stage_bytes<true>(tma_cap))
+            : occ32(s32_spmv_tma_kernel<float, 2, false>, SP32_STAGES * sp32_stage_bytes<false>(tma_cap));
+}
+
+void launch_step32(int basis, const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (basis == 1) launch_step32_t<float>(L, cd, st);
+  else launch_step32_t<__nv_bfloat16>(L, cd, st);
+}
+
+}  // namespace krylov

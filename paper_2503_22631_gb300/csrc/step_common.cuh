@@ -353,5 +353,22 @@ __device__ __forceinline__ double block_sum_ff(ff v, float* sh_hi, float* sh_lo)
   return r;
 }
 
+// Launch with programmatic stream serialization (the kernel calls pdl_wait()
+// before touching anything an earlier kernel produced).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), int grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(STEP_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 }  // namespace
 }  // namespace krylov
