@@ -773,10 +773,6 @@ constexpr int TMA_STAGES = KRYLOV_SPMV_STAGES;  // CSR tiles in flight per CTA o
 // a stage holds at most 260 row_ptr entries and 4104 (int, float2) nonzeros
 // (50.3 KB): four of them still fit the 227 KB of shared memory of a CTA
 static_assert(TMA_STAGES >= 2 && TMA_STAGES <= 4, "staged CSR tiles in flight");
-#ifndef KRYLOV_SPMV_RPT
-#define KRYLOV_SPMV_RPT 1
-#endif
-constexpr int SPMV_RPT = KRYLOV_SPMV_RPT;  // rows per thread and iteration of the staged product (1 or 2)
 
 // Stage of the staged product kernel: row_ptr slice, columns (4-byte indices,
 // or 2-byte offsets col - row when DI), values.  cap is a multiple of 8.
@@ -931,191 +927,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
     const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
     if ((threadIdx.x & 31) == 0) tot[q] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
-}
-
-// The staged product with two rows per thread: each iteration takes two
-// consecutive 256-row tiles (four tiles in flight per CTA), issues the
-// gathers of both rows before any arithmetic and forms both, so a warp keeps
-// twice the independent loads in flight for the same loop overhead.  The
-// sums of every row, and the order of the dot and norm sums per thread
-// (tile by tile), are those of ff_spmv_tma_kernel.
-constexpr int T2_STAGES = 4;
-template <typename AT, int KW, bool DI>
-__global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma2_kernel(const StepLaunch L, const CycleDev cd) {
-  using CT = typename std::conditional<DI, int16_t, int>::type;
-  constexpr int EA = DI ? 8 : 4;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[T2_STAGES];
-  __shared__ float rhi[32], rlo[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
-  const int j = L.j;
-  const int cap = L.tma_cap;
-  const size_t sb = tma_stage_bytes<AT, DI>(cap);
-  auto rp_st = [&](int st) { return reinterpret_cast<int*>(smem + (size_t)st * sb); };
-  auto col_st = [&](int st) { return reinterpret_cast<CT*>(rp_st(st) + TMA_RP); };
-  auto val_st = [&](int st) { return reinterpret_cast<AT*>(col_st(st) + cap); };
-  const CT* colsrc = DI ? reinterpret_cast<const CT*>(L.dcol) : reinterpret_cast<const CT*>(L.col);
-  const float2* W = static_cast<const float2*>(L.W);
-  const float2* Wj = W + (int64_t)j * L.ldw;
-  const AT* val = static_cast<const AT*>(L.val);
-  const int dlo = max(0, j - L.k + 1);
-  const int nd = L.rgs ? 0 : j - dlo + 1;
-  const float2* Wd[KW];
-#pragma unroll
-  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
-  const int r0 = blockIdx.x * L.rows_spmv;
-  const int r1 = min(L.n, r0 + L.rows_spmv);
-  const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < T2_STAGES; ++q) mbar_init(&bars[q], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  auto issue = [&](int t, int e0, int e1) {
-    const int st = t % T2_STAGES;
-    const int ts = r0 + t * TMA_ROWS;
-    const int ea = e0 & ~(EA - 1), eb = (e1 + EA - 1) & ~(EA - 1);
-    const uint32_t brp = TMA_RP * 4u, bcol = (uint32_t)(eb - ea) * (uint32_t)sizeof(CT),
-                   bval = (uint32_t)(eb - ea) * sizeof(AT);
-    mbar_arrive_expect_tx(&bars[st], brp + bcol + bval);
-    bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
-    if (eb > ea) {
-      bulk_g2s(col_st(st), colsrc + ea, bcol, &bars[st]);
-      bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
-    }
-  };
-  auto tile_end = [&](int t) { return min(r0 + (t + 1) * TMA_ROWS, r1); };
-  if (threadIdx.x == 0)
-    for (int t = 0; t < min(ntiles, T2_STAGES); ++t)
-      issue(t, __ldg(L.row_ptr + r0 + t * TMA_ROWS), __ldg(L.row_ptr + tile_end(t)));
-  pdl_wait();
-  if (cd.flags[1] != 0) {
-    if (threadIdx.x == 0)
-      for (int t = 0; t < min(ntiles, T2_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
-    return;
-  }
-  ffacc acc_pi;
-  ffacc acc_dot[KW];
-  bool timed_out = false;
-  int last_issued = min(ntiles, T2_STAGES) - 1;
-  for (int t = 0; t < ntiles; t += 2) {
-    const bool two = t + 1 < ntiles;
-    int nb[3] = {0, 0, 0};
-    if (threadIdx.x == 0 && t + T2_STAGES < ntiles) {  // boundaries of the next two tiles to issue
-      nb[0] = __ldg(L.row_ptr + r0 + (t + T2_STAGES) * TMA_ROWS);
-      nb[1] = __ldg(L.row_ptr + tile_end(t + T2_STAGES));
-      if (t + T2_STAGES + 1 < ntiles) nb[2] = __ldg(L.row_ptr + tile_end(t + T2_STAGES + 1));
-    }
-    int i[2];
-    bool valid[2];
-    ff wq[2][KW];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      i[r] = r0 + (t + r) * TMA_ROWS + (int)threadIdx.x;
-      valid[r] = (r == 0 || two) && i[r] < tile_end(t + r);
-      if (valid[r]) {
-#pragma unroll
-        for (int q = 0; q < KW; ++q)
-          if (q < nd) wq[r][q] = ld_ff(Wd[q] + i[r]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-      if (r == 0 || two) {
-        const int tt = t + r;
-        if (!timed_out && !mbar_wait_bounded(&bars[tt % T2_STAGES], (uint32_t)(tt / T2_STAGES) & 1u, TMA_WAIT_NS))
-          timed_out = true;
-      }
-    int rb[2], re[2], cb[2];
-    const int* rps[2];
-    const CT* cs[2];
-    const AT* vs[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int st = (t + r) % T2_STAGES;
-      rps[r] = rp_st(st);
-      cs[r] = col_st(st);
-      vs[r] = val_st(st);
-      const bool go = valid[r] && !timed_out;
-      const int ea = go ? (rps[r][0] & ~(EA - 1)) : 0;
-      rb[r] = go ? rps[r][threadIdx.x] - ea : 0;
-      re[r] = go ? rps[r][threadIdx.x + 1] - ea : 0;
-      cb[r] = DI ? i[r] : 0;
-    }
-    const bool fast = (re[0] - rb[0] <= TMA_ROW_FAST) && (re[1] - rb[1] <= TMA_ROW_FAST);
-    ff p[2];
-    if (fast) {  // every gather of both rows in flight at once
-      float2 wv[2][TMA_ROW_FAST];
-#pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int q = 0; q < TMA_ROW_FAST; ++q)
-          if (rb[r] + q < re[r]) wv[r][q] = __ldg(Wj + (cb[r] + (int)cs[r][rb[r] + q]));
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        ffacc acc;
-#pragma unroll
-        for (int q = 0; q < TMA_ROW_FAST; ++q)
-          if (rb[r] + q < re[r]) acc_val(acc, vs[r][rb[r] + q], ff{wv[r][q].x, wv[r][q].y});
-        p[r] = acc.result();
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        ffacc acc;
-        for (int e = rb[r]; e < re[r]; ++e) acc_val(acc, vs[r][e], ld_ff(Wj + (cb[r] + (int)cs[r][e])));
-        p[r] = acc.result();
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-      if (valid[r] && !timed_out) {
-        st_ff(static_cast<float2*>(L.p_out) + i[r], p[r]);
-        acc_pi.add_prod(p[r], p[r]);
-#pragma unroll
-        for (int q = 0; q < KW; ++q)
-          if (q < nd) acc_dot[q].add_prod(wq[r][q], p[r]);
-      }
-    __syncthreads();  // every thread is done with both stages
-    if (threadIdx.x == 0 && !timed_out) {
-      if (t + T2_STAGES < ntiles) {
-        fence_proxy_async();
-        issue(t + T2_STAGES, nb[0], nb[1]);
-        last_issued = t + T2_STAGES;
-        if (t + T2_STAGES + 1 < ntiles) {
-          issue(t + T2_STAGES + 1, nb[1], nb[2]);
-          last_issued = t + T2_STAGES + 1;
-        }
-      }
-    }
-  }
-  pdl_trigger();
-  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
-  if (threadIdx.x == 0 && timed_out) {
-    for (int t = max(0, last_issued - T2_STAGES + 1); t <= last_issued; ++t)
-      (void)mbar_wait_bounded(&bars[t % T2_STAGES], (uint32_t)(t / T2_STAGES) & 1u, TMA_WAIT_NS);
-  }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;
-    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (L.n_long > 0) return;
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double tt = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = tt;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -1462,15 +1273,15 @@ void launch_ff_spmv_main(const StepLaunch& L, const CycleDev& cd, cudaStream_t s
     return;
   }
   if (L.tma_cap > 0 && L.dcol != nullptr) {
-    auto k = SPMV_RPT == 2 ? ff_spmv_tma2_kernel<AT, KW, true> : ff_spmv_tma_kernel<AT, KW, true>;
-    const size_t smem = (SPMV_RPT == 2 ? T2_STAGES : TMA_STAGES) * tma_stage_bytes<AT, true>(L.tma_cap);
+    auto k = ff_spmv_tma_kernel<AT, KW, true>;
+    const size_t smem = TMA_STAGES * tma_stage_bytes<AT, true>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
   }
   if (L.tma_cap > 0) {
-    auto k = SPMV_RPT == 2 ? ff_spmv_tma2_kernel<AT, KW, false> : ff_spmv_tma_kernel<AT, KW, false>;
-    const size_t smem = (SPMV_RPT == 2 ? T2_STAGES : TMA_STAGES) * tma_stage_bytes<AT>(L.tma_cap);
+    auto k = ff_spmv_tma_kernel<AT, KW, false>;
+    const size_t smem = TMA_STAGES * tma_stage_bytes<AT>(L.tma_cap);
     raise_smem_limit((const void*)k, smem);
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
@@ -1541,9 +1352,6 @@ int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap) {
   if (seg_cap > 0)
     return vals_f32 ? occ(ff_spmv_seg_kernel<float, 2>, 2 * seg_stage_bytes<float>(lcap, seg_cap))
                     : occ(ff_spmv_seg_kernel<float2, 2>, 2 * seg_stage_bytes<float2>(lcap, seg_cap));
-  if (tma_cap > 0 && SPMV_RPT == 2)
-    return vals_f32 ? occ(ff_spmv_tma2_kernel<float, 2, false>, T2_STAGES * tma_stage_bytes<float>(tma_cap))
-                    : occ(ff_spmv_tma2_kernel<float2, 2, false>, T2_STAGES * tma_stage_bytes<float2>(tma_cap));
   if (tma_cap > 0)
     return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2, false>, TMA_STAGES * tma_stage_bytes<float>(tma_cap))
                     : occ(ff_spmv_tma_kernel<float2, 2, false>, TMA_STAGES * tma_stage_bytes<float2>(tma_cap));
