@@ -128,8 +128,9 @@ typedef struct {
                       pieces whenever the operator has a segment plan; 2 always gathers
                       (a fixed kernel choice, e.g. for profiling); other values: EINVAL */
   int block_rhs;   /* batched form: 1 (default) advances up to 64 right-hand sides of a matrix
-                      together through the block kernels (float-float basis, TRUNC, exp, packed
-                      sketch table, m <= 64, max_cycles <= 16); 0 solves them one by one */
+                      together through the block kernels (float-float or float32 basis, TRUNC,
+                      exp, packed sketch table, m <= 64, max_cycles <= 16); 0 solves them one by
+                      one */
 } krylov_options;
 
 typedef struct {

@@ -40,6 +40,7 @@ constexpr int TMA_MAX_CAP = 4096;  // largest staged tile span (nonzeros)
 constexpr int EXP_SQ_CYCLES = 16;              // exp: cycles also evaluated by scaling and squaring
 constexpr double QUAD_TOL_CONTOURS = 1e-12;    // exp quadrature: largest difference of the two contours
 constexpr double QUAD_TOL_SQUARING = 1e-11;    // ... and to scaling and squaring (relative to the first column)
+constexpr int QUAD_RETRIES = 2;                // lower shifts tried after a failed check
 // z^{-1/2}: trapezoidal nodes in u (s = e^u) with step INVSQRT_H on
 // [0.5 ln(alpha * 1e-18) - 38, 0.5 ln(alpha * 1e4) + 38], alpha = ||A||_inf >= |lambda|:
 // the two tails are below e^-38 relative for spectra inside [1e-18 alpha, 1e4 alpha], and
@@ -253,7 +254,7 @@ struct krylov_handle {
 
   // host mirrors
   int* h_flags = nullptr;     // pinned: flags[4]
-  double* h_scal = nullptr;   // pinned: 32 doubles ([0, 8) cycle scalars, [8, 16) misc, [16, 20) quadrature checks)
+  double* h_scal = nullptr;   // pinned: 32 doubles ([0, 8) cycle scalars, [8, 16) misc, [16, 22) quadrature)
   int last_me = 0, last_nc = 0, last_cycle = 0;
   std::vector<void*> allocs;
 };
@@ -879,7 +880,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
   // exp(-t z), t > 0: the contour quadrature runs from the first cycle; the
   // scaling-and-squaring block rows are formed in the first EXP_SQ_CYCLES
   // cycles (they validate the quadrature) and afterwards only if a check fails
-  bool quad = (h->f.kind == KRYLOV_F_EXP_NEG && h->f.t > 0.0 && h->sd.qstat != nullptr);
+  bool quad = (h->f.kind == KRYLOV_F_EXP_NEG && h->f.t > 0.0 && h->sd.qstat != nullptr && max_cycles > EXP_SQ_CYCLES);
   krylov_status cs =
       ensure_small_capacity(h, max_cycles, levels_needed, quad ? std::min(max_cycles, EXP_SQ_CYCLES) : max_cycles);
   if (cs != KRYLOV_OK) return cs;
@@ -1090,10 +1091,31 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     // its two contours each other, else the squaring continues alone
     if (quad && c <= EXP_SQ_CYCLES &&
         !(h->h_scal[18] <= QUAD_TOL_SQUARING && h->h_scal[19] <= QUAD_TOL_CONTOURS)) {
-      quad = false;
-      cs = ensure_small_capacity(h, max_cycles, s_lv + 1, max_cycles);  // rows beyond EXP_SQ_CYCLES
-      if (cs != KRYLOV_OK) return cs;
-      for (int ap = 0; ap <= c - 1; ++ap) stats.launches += exp_row(h, ap, s_lv);
+      // a Ritz value outside the contours: up to two retries with the shift
+      // lowered by 3 / t (the quadrature of every block so far recomputed and
+      // checked against the squaring block by block), else squaring alone
+      bool fixed = false;
+      const size_t MMq = (size_t)M * M;
+      for (int attempt = 0; attempt < QUAD_RETRIES && !fixed; ++attempt) {
+        h->h_scal[20] = h->h_scal[16] - 3.0 / h->f.t;  // sigma
+        h->h_scal[21] = 0.0;                           // largest entry so far
+        CK(cudaMemcpyAsync(h->sd.qstat, h->h_scal + 20, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+        fixed = true;
+        for (int ap = 0; ap <= c - 1 && fixed; ++ap) {
+          const double* fsq_ap = h->sd.G + (size_t)s_lv * h->level_stride + (size_t)ap * (ap + 1) / 2 * MMq;
+          launch_exp_quad(h->sd, h->cd, M, ap == c - 1 ? me : M, ap, h->f.t, fsq_ap, st);
+          stats.launches += 2;
+          CK(cudaMemcpyAsync(h->h_scal + 16, h->sd.qstat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          fixed = (h->h_scal[18] <= QUAD_TOL_SQUARING && h->h_scal[19] <= QUAD_TOL_CONTOURS);
+        }
+      }
+      if (!fixed) {
+        quad = false;
+        cs = ensure_small_capacity(h, max_cycles, s_lv + 1, max_cycles);  // rows beyond EXP_SQ_CYCLES
+        if (cs != KRYLOV_OK) return cs;
+        for (int ap = 0; ap <= c - 1; ++ap) stats.launches += exp_row(h, ap, s_lv);
+      }
     }
     {
       float ms_q = 0.f;
@@ -1157,8 +1179,8 @@ constexpr int NQ_HOST = 2 + MAX_WINDOW;  // per-CTA scalar slots of the product 
 struct BlockWs {
   int nb_cap = 0, rows_cap = 0, levels_cap = 0;
   int64_t level_stride = 0;
-  float2* W = nullptr;
-  float2* P[2] = {nullptr, nullptr};
+  void* W = nullptr;                 // float2 pairs, or floats for the float32 basis
+  void* P[2] = {nullptr, nullptr};
   double* part = nullptr;
   long long* acc = nullptr;
   int* E = nullptr;
@@ -1197,7 +1219,8 @@ void free_block_ws(BlockWs& b) {
 
 // Can the block kernels run this configuration?
 bool block_eligible(const krylov_handle* h, int n_rhs, int max_cycles) {
-  return h->opt.block_rhs && n_rhs > 1 && h->opt.basis_dtype == KRYLOV_BASIS_DF64 &&
+  return h->opt.block_rhs && n_rhs > 1 &&
+         (h->opt.basis_dtype == KRYLOV_BASIS_DF64 || h->opt.basis_dtype == KRYLOV_BASIS_F32) &&
          h->opt.ortho == KRYLOV_ORTHO_TRUNC && h->f.kind == KRYLOV_F_EXP_NEG && h->sk_mode == SK_TAB8 &&
          max_cycles <= BK_MAX_CYCLES && h->m <= 64 && bk_mat_smem(h->s, BK_NB) <= 200 * 1024;
 }
@@ -1210,9 +1233,17 @@ krylov_status ensure_block_ws(krylov_handle* h, int levels) {
     const size_t n = (size_t)h->n;
     b.nb_cap = BK_NB;
     b.rows_cap = BK_MAX_CYCLES;
-    CK(balloc(b, &b.W, (size_t)(M + 1) * n * BK_NB));
-    CK(balloc(b, &b.P[0], n * BK_NB));
-    CK(balloc(b, &b.P[1], n * BK_NB));
+    // float-float pairs take two floats per entry, the float32 basis one
+    const size_t fl = (h->opt.basis_dtype == KRYLOV_BASIS_F32) ? 1 : 2;
+    float* w = nullptr;
+    float* p0 = nullptr;
+    float* p1 = nullptr;
+    CK(balloc(b, &w, (size_t)(M + 1) * n * BK_NB * fl));
+    CK(balloc(b, &p0, n * BK_NB * fl));
+    CK(balloc(b, &p1, n * BK_NB * fl));
+    b.W = w;
+    b.P[0] = p0;
+    b.P[1] = p1;
     CK(balloc(b, &b.part, (size_t)h->num_sms * 8 * NQ_HOST * BK_NB));
     CK(balloc(b, &b.acc, (size_t)(M + 1) * 3 * s * BK_NB));
     CK(balloc(b, &b.E, (size_t)(M + 1) * BK_NB));
@@ -1301,8 +1332,10 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
   const size_t MM = (size_t)M * M;
   krylov_status cs = ensure_block_ws(h, std::max(1, b.levels_cap));
   if (cs != KRYLOV_OK) return cs;
-  const int use32 = (h->opt.narrow_values_if_exact && h->vals_exact_f32) ? 1 : 0;
+  const int b32 = (h->opt.basis_dtype == KRYLOV_BASIS_F32) ? 1 : 0;
+  const int use32 = (b32 || (h->opt.narrow_values_if_exact && h->vals_exact_f32)) ? 1 : 0;
   BlockLaunch L{};
+  L.basis32 = b32;
   L.n = n;
   L.nb = nb;
   L.m = M;
@@ -1334,7 +1367,7 @@ krylov_status block_solve(krylov_handle* h, const double* B, double* X, int64_t 
   L.grid_p = std::max(1, std::min(std::min(part_ctas, h->num_sms * per_sm_p), (n + 7) / 8));
   L.rows_p = (n + L.grid_p - 1) / L.grid_p;
   L.fx_wb = sketch_word_bits(L.rows_per_cta, 1);
-  L.thr = 1e-12;
+  L.thr = b32 ? 1e-6 : 1e-12;  // the breakdown thresholds of the single-vector path
   NvtxRange call_range("krylov_apply_batched block");
   EventPair evp;
   CK(evp.create());

@@ -1,6 +1,11 @@
 // block_kernels.cu -- the block form of the truncated cycle: nb independent
 // right-hand sides of one matrix advanced together (float-float basis).
 //
+// The basis and the products are stored as float-float pairs or, for the
+// float32 basis, as floats (basis32); the arithmetic is float-float in both,
+// and every value used after a store (norms, sketches, dots, the next kernel)
+// is the stored one.
+//
 // Every vector of the cycle is stored row-major n x nb (the nb values of a row
 // contiguous), so one pass over A serves all right-hand sides: a warp takes a
 // row, its lanes take right-hand sides lane and lane + 32, the column index
@@ -30,6 +35,18 @@ constexpr int BK_WARPS = STEP_THREADS / 32;
 __device__ __forceinline__ ff ldf(const float2* p) {
   const float2 v = *p;
   return ff{v.x, v.y};
+}
+__device__ __forceinline__ ff ldv(const float2* p) { return ldf(p); }
+__device__ __forceinline__ ff ldv(const float* p) { return ff{*p, 0.f}; }
+// store v in the storage type; returns the stored value
+__device__ __forceinline__ ff stv(float2* p, ff v) {
+  *p = make_float2(v.hi, v.lo);
+  return v;
+}
+__device__ __forceinline__ ff stv(float* p, ff v) {
+  const float f = __fadd_rn(v.hi, v.lo);
+  *p = f;
+  return ff{f, 0.f};
 }
 
 // ---- norms of the right-hand sides and the start vectors ------------------
@@ -69,18 +86,19 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_norm_kernel(const BlockLaunch
   if (threadIdx.x == 0) *B.counter = 0u;
 }
 
+template <typename VT>
 __global__ void bk_start_kernel(const BlockLaunch B, const double* b, int64_t ldb) {
   const int64_t total = (int64_t)B.n * B.nb;
+  VT* W = static_cast<VT*>(B.W);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / B.nb), r = (int)(e % B.nb);
     const double inv = offset_cd(B.cd, B.bs, r).scal[1];
-    const ff v = ff_from_double(b[(int64_t)i * ldb + r] * inv);
-    B.W[e] = make_float2(v.hi, v.lo);
+    (void)stv(W + e, ff_from_double(b[(int64_t)i * ldb + r] * inv));
   }
 }
 
 // ---- materialize + sketch of column j for every right-hand side ------------
-template <bool MAT, int KW>
+template <typename VT, bool MAT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS) bk_mat_kernel(const BlockLaunch B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float s_tofix[BK_MAXNB];
@@ -108,10 +126,12 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_mat_kernel(const BlockLaunch 
   }
   __syncthreads();
   const float word = ldexpf(1.0f, B.fx_wb);
-  const float2* Wq[KW];
+  VT* const W = static_cast<VT*>(B.W);
+  const VT* Wq[KW];
 #pragma unroll
-  for (int q = 0; q < KW; ++q) Wq[q] = B.W + (int64_t)(lo + (q < nl ? q : 0)) * B.slot;
-  float2* Wj = B.W + (int64_t)j * B.slot;
+  for (int q = 0; q < KW; ++q) Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * B.slot;
+  VT* Wj = W + (int64_t)j * B.slot;
+  const VT* Pp = static_cast<const VT*>(B.p_prev);
   ffacc sig[2];
   const int r0 = blockIdx.x * B.rows_per_cta, r1 = min(B.n, r0 + B.rows_per_cta);
   for (int i = r0 + wid; i < r1; i += BK_WARPS) {
@@ -124,14 +144,13 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_mat_kernel(const BlockLaunch 
       const int64_t e = (int64_t)i * nb + r;
       ff w;
       if (MAT) {
-        ff acc = ldf(B.p_prev + e);
+        ff acc = ldv(Pp + e);
 #pragma unroll
         for (int q = 0; q < KW; ++q)
-          if (q < nl) acc = ff_add(acc, ff_mul(s_h[q][r], ldf(Wq[q] + e)));
-        w = ff_mul(acc, s_rho[r]);
-        Wj[e] = make_float2(w.hi, w.lo);
+          if (q < nl) acc = ff_add(acc, ff_mul(s_h[q][r], ldv(Wq[q] + e)));
+        w = stv(Wj + e, ff_mul(acc, s_rho[r]));
       } else {
-        w = ldf(Wj + e);
+        w = ldv(Wj + e);
       }
       sig[h].add_prod(w, w);
       FxScale f;
@@ -192,7 +211,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_mat_kernel(const BlockLaunch 
 }
 
 // ---- product + window dots for every right-hand side -----------------------
-template <typename AT, int KW>
+template <typename VT, typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS) bk_spmv_kernel(const BlockLaunch B) {
   __shared__ double red[BK_WARPS][BK_MAXNB];
   __shared__ double tot[NQ][BK_MAXNB];
@@ -201,10 +220,12 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_spmv_kernel(const BlockLaunch
   const int nb = B.nb, j = B.j;
   const int dlo = max(0, j - B.k + 1);
   const int nd = j - dlo + 1;
-  const float2* Wj = B.W + (int64_t)j * B.slot;
-  const float2* Wd[KW];
+  const VT* const W = static_cast<const VT*>(B.W);
+  const VT* Wj = W + (int64_t)j * B.slot;
+  const VT* Wd[KW];
 #pragma unroll
-  for (int q = 0; q < KW; ++q) Wd[q] = B.W + (int64_t)(dlo + (q < nd ? q : 0)) * B.slot;
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * B.slot;
+  VT* Po = static_cast<VT*>(B.p_out);
   const AT* val = static_cast<const AT*>(B.val);
   ffacc pi[2], dots[KW][2];
   const int r0 = blockIdx.x * B.rows_p, r1 = min(B.n, r0 + B.rows_p);
@@ -222,13 +243,13 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_spmv_kernel(const BlockLaunch
           cc[u] = __ldg(B.ci + e0 + u);
           av[u] = __ldg(val + e0 + u);
         }
-      float2 wv[4][2];
+      ff wv[4][2];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (e0 + u < ee) {
-          const float2* wc = Wj + (int64_t)cc[u] * nb;
-          if (lane < nb) wv[u][0] = wc[lane];
-          if (lane + 32 < nb) wv[u][1] = wc[lane + 32];
+          const VT* wc = Wj + (int64_t)cc[u] * nb;
+          if (lane < nb) wv[u][0] = ldv(wc + lane);
+          if (lane + 32 < nb) wv[u][1] = ldv(wc + lane + 32);
         }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -236,7 +257,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_spmv_kernel(const BlockLaunch
 #pragma unroll
           for (int h = 0; h < 2; ++h)
             if (lane + 32 * h < nb) {
-              const float2 pe = prod_pe(av[u], ff{wv[u][h].x, wv[u][h].y});
+              const float2 pe = prod_pe(av[u], wv[u][h]);
               acc[h].add_pe(pe.x, pe.y);
             }
         }
@@ -246,12 +267,11 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_spmv_kernel(const BlockLaunch
       const int r = lane + 32 * h;
       if (r >= nb) continue;
       const int64_t e = (int64_t)i * nb + r;
-      const ff p = acc[h].result();
-      B.p_out[e] = make_float2(p.hi, p.lo);
+      const ff p = stv(Po + e, acc[h].result());
       pi[h].add_prod(p, p);
 #pragma unroll
       for (int q = 0; q < KW; ++q)
-        if (q < nd) dots[q][h].add_prod(ldf(Wd[q] + e), p);
+        if (q < nd) dots[q][h].add_prod(ldv(Wd[q] + e), p);
     }
   }
   // per-CTA partials [NQ][nb] (slot 1: ||p||^2, 2 + q: <w_q, p>)
@@ -341,6 +361,7 @@ __global__ void bk_sketch_fin_kernel(const BlockLaunch B, SmallDev sd, int ncols
 // x_r += W z_r (right-hand sides still active), next start vector
 // v_r = (w_{m+1} - W g_r) / tau_r into slot 0, and per right-hand side
 // ||y||^2, ||x||^2, ||v||^2.
+template <typename VT>
 __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaunch B, SmallDev sd, int m_eff,
                                                                   int has_next, double* x, int64_t ldx,
                                                                   const int* active) {
@@ -374,6 +395,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
   }
   for (int r = threadIdx.x; r < nb; r += blockDim.x) s_tinv[r] = ff_from_double(offset_sd(sd, B.bs, r).zg[2 * M]);
   __syncthreads();
+  VT* const W = static_cast<VT*>(B.W);
   double ay[2] = {0.0, 0.0}, ax[2] = {0.0, 0.0}, av[2] = {0.0, 0.0};
   const int r0 = blockIdx.x * B.rows_p, r1 = min(B.n, r0 + B.rows_p);
   for (int i = r0 + wid; i < r1; i += BK_WARPS) {
@@ -384,7 +406,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
       const int64_t e = (int64_t)i * nb + r;
       ffacc y, v;
       if (has_next) {
-        const ff wm = ldf(B.W + (int64_t)m_eff * B.slot + e);
+        const ff wm = ldv(W + (int64_t)m_eff * B.slot + e);
         v.S = wm.hi;
         v.E = wm.lo;
       }
@@ -392,7 +414,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
         ff wv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (q0 + u < m_eff) wv[u] = ldf(B.W + (int64_t)(q0 + u) * B.slot + e);
+          if (q0 + u < m_eff) wv[u] = ldv(W + (int64_t)(q0 + u) * B.slot + e);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
           if (q0 + u < m_eff) {
@@ -406,8 +428,7 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
       const double xn = active[r] ? *xp + yd : *xp;
       *xp = xn;
       if (has_next) {
-        const ff vn = ff_mul(v.result(), s_tinv[r]);
-        B.W[e] = make_float2(vn.hi, vn.lo);
+        const ff vn = stv(W + e, ff_mul(v.result(), s_tinv[r]));
         av[h] = fma((double)vn.hi, (double)vn.hi, av[h]);
       }
       ay[h] = fma(yd, yd, ay[h]);
@@ -441,41 +462,66 @@ __global__ void __launch_bounds__(STEP_THREADS) bk_update_kernel(const BlockLaun
 size_t bk_mat_smem(int s, int nb) { return (size_t)NWB * s * nb * sizeof(int); }
 
 int bk_ctas_per_sm(int kernel, size_t smem) {
-  const void* k = (kernel == 0) ? (const void*)bk_mat_kernel<true, 2>
-                  : (kernel == 1) ? (const void*)bk_spmv_kernel<float2, 2> : (const void*)bk_update_kernel;
+  const void* k = (kernel == 0) ? (const void*)bk_mat_kernel<float2, true, 2>
+                  : (kernel == 1) ? (const void*)bk_spmv_kernel<float2, float2, 2>
+                                  : (const void*)bk_update_kernel<float2>;
   raise_smem_limit(k, smem);
   int b = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, STEP_THREADS, smem);
   return std::max(1, b);
 }
 
-void launch_bk_norm_start(const BlockLaunch& B, const double* b, int64_t ldb, cudaStream_t st) {
+namespace {
+
+template <typename VT>
+void bk_norm_start_t(const BlockLaunch& B, const double* b, int64_t ldb, cudaStream_t st) {
   bk_norm_kernel<<<B.grid, STEP_THREADS, 0, st>>>(B, b, ldb);
   const int64_t total = (int64_t)B.n * B.nb;
   const int g = (int)std::min<int64_t>(4096, (total + 255) / 256);
-  bk_start_kernel<<<g, 256, 0, st>>>(B, b, ldb);
+  bk_start_kernel<VT><<<g, 256, 0, st>>>(B, b, ldb);
 }
 
-void launch_bk_step(const BlockLaunch& B, int mat, int spmv, cudaStream_t st) {
+template <typename VT>
+void bk_step_t(const BlockLaunch& B, int mat, int spmv, cudaStream_t st) {
   const size_t smem = bk_mat_smem(B.s, B.nb);
   if (mat) {
-    auto k = (B.k <= 2) ? bk_mat_kernel<true, 2> : bk_mat_kernel<true, MAX_WINDOW>;
+    auto k = (B.k <= 2) ? bk_mat_kernel<VT, true, 2> : bk_mat_kernel<VT, true, MAX_WINDOW>;
     raise_smem_limit((const void*)k, smem);
     k<<<B.grid, STEP_THREADS, smem, st>>>(B);
   } else {
-    auto k = (B.k <= 2) ? bk_mat_kernel<false, 2> : bk_mat_kernel<false, MAX_WINDOW>;
+    auto k = (B.k <= 2) ? bk_mat_kernel<VT, false, 2> : bk_mat_kernel<VT, false, MAX_WINDOW>;
     raise_smem_limit((const void*)k, smem);
     k<<<B.grid, STEP_THREADS, smem, st>>>(B);
   }
   if (spmv) {
     if (B.val_f32) {
-      if (B.k <= 2) bk_spmv_kernel<float, 2><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
-      else bk_spmv_kernel<float, MAX_WINDOW><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
+      if (B.k <= 2) bk_spmv_kernel<VT, float, 2><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
+      else bk_spmv_kernel<VT, float, MAX_WINDOW><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
     } else {
-      if (B.k <= 2) bk_spmv_kernel<float2, 2><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
-      else bk_spmv_kernel<float2, MAX_WINDOW><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
+      if (B.k <= 2) bk_spmv_kernel<VT, float2, 2><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
+      else bk_spmv_kernel<VT, float2, MAX_WINDOW><<<B.grid_p, STEP_THREADS, 0, st>>>(B);
     }
   }
+}
+
+template <typename VT>
+void bk_update_t(const BlockLaunch& B, const SmallDev& sd, int m_eff, int has_next, double* x, int64_t ldx,
+                 const int* active, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)m_eff * B.nb * sizeof(ff);
+  raise_smem_limit((const void*)bk_update_kernel<VT>, smem);
+  bk_update_kernel<VT><<<B.grid_p, STEP_THREADS, smem, st>>>(B, sd, m_eff, has_next, x, ldx, active);
+}
+
+}  // namespace
+
+void launch_bk_norm_start(const BlockLaunch& B, const double* b, int64_t ldb, cudaStream_t st) {
+  if (B.basis32) bk_norm_start_t<float>(B, b, ldb, st);
+  else bk_norm_start_t<float2>(B, b, ldb, st);
+}
+
+void launch_bk_step(const BlockLaunch& B, int mat, int spmv, cudaStream_t st) {
+  if (B.basis32) bk_step_t<float>(B, mat, spmv, st);
+  else bk_step_t<float2>(B, mat, spmv, st);
 }
 
 void launch_bk_sketch_fin(const BlockLaunch& B, const SmallDev& sd, int ncols, cudaStream_t st) {
@@ -485,9 +531,8 @@ void launch_bk_sketch_fin(const BlockLaunch& B, const SmallDev& sd, int ncols, c
 
 void launch_bk_update(const BlockLaunch& B, const SmallDev& sd, int m_eff, int has_next, double* x, int64_t ldx,
                       const int* active, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)m_eff * B.nb * sizeof(ff);
-  raise_smem_limit((const void*)bk_update_kernel, smem);
-  bk_update_kernel<<<B.grid_p, STEP_THREADS, smem, st>>>(B, sd, m_eff, has_next, x, ldx, active);
+  if (B.basis32) bk_update_t<float>(B, sd, m_eff, has_next, x, ldx, active, st);
+  else bk_update_t<float2>(B, sd, m_eff, has_next, x, ldx, active, st);
 }
 
 }  // namespace krylov

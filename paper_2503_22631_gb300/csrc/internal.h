@@ -110,10 +110,11 @@ struct BlockLaunch {
   const int* ci;
   const void* val;
   int val_f32;
-  float2* W;            // (m+1) slots of n x nb
+  void* W;              // (m+1) slots of n x nb: float2 (float-float) or float (basis32)
   int64_t slot;         // n * nb
-  const float2* p_prev;
-  float2* p_out;
+  const void* p_prev;   // products, same element type as W
+  void* p_out;
+  int basis32;          // 1: float32 storage of the basis and products (float-float arithmetic)
   double* part;         // per-CTA partials [grid][NQ][64]
   CycleDev cd;          // right-hand side 0's cycle state; others at offsets bs
   BatchStride bs;

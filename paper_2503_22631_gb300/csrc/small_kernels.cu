@@ -924,16 +924,20 @@ __global__ void __launch_bounds__(EQ_THREADS) exp_quad_nodes_kernel(SmallDev sd,
     }
     __syncthreads();
     const cplx d = work[(size_t)c * me + c];
-    for (int r = c + 1 + tid; r < me; r += blockDim.x) {
+    for (int r = c + 1 + tid; r < me; r += blockDim.x) {  // multipliers in place of column c
       const cplx f = cdiv(work[(size_t)c * me + r], d);
-      for (int l = c + 1; l < me; ++l) {
-        const cplx u = cmul(f, work[(size_t)l * me + c]);
-        work[(size_t)l * me + r].re -= u.re;
-        work[(size_t)l * me + r].im -= u.im;
-      }
+      work[(size_t)c * me + r] = f;
       const cplx u = cmul(f, y[c]);
       y[r].re -= u.re;
       y[r].im -= u.im;
+    }
+    __syncthreads();
+    const int w = me - c - 1;  // trailing (w x w) update, every thread on it
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int r = c + 1 + e % w, l = c + 1 + e / w;
+      const cplx u = cmul(work[(size_t)c * me + r], work[(size_t)l * me + c]);
+      work[(size_t)l * me + r].re -= u.re;
+      work[(size_t)l * me + r].im -= u.im;
     }
     __syncthreads();
   }
@@ -1004,14 +1008,16 @@ __global__ void exp_quad_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, dou
 
 // sigma from the first cycle's block of the scaling-and-squaring evaluation:
 // ||f_1|| ~ e^{-t lambda_min} for the smallest real eigenvalue lambda_min the
-// first column meets; sigma = (-ln ||f_1|| - 5) / t keeps w = -t (lambda - sigma)
-// at most ~5 above its value at lambda_min (inside both contours).
+// first column meets; sigma = (-ln ||f_1|| - 2) / t puts the largest w near
+// -2 plus ln(1 / (the weight of that eigenvector in e_1)): inside both
+// contours (their rightmost points are 4.19 and 5.66) for weights down to
+// e^-5, and the result within e^2 of the largest contour term.
 __global__ void exp_quad_sigma_kernel(SmallDev sd, int me, double t, const double* fsq) {
   if (threadIdx.x == 0) {
     double nrm = 0.0;
     for (int r = 0; r < me; ++r) nrm = fma(fsq[r], fsq[r], nrm);
     nrm = sqrt(nrm);
-    sd.qstat[0] = (nrm > 0.0 && isfinite(nrm)) ? (-log(nrm) - 5.0) / t : 0.0;
+    sd.qstat[0] = (nrm > 0.0 && isfinite(nrm)) ? (-log(nrm) - 2.0) / t : 0.0;
     sd.qstat[1] = 0.0;
   }
 }

@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const Step
         if (q < nl)
           bulk_g2s(base + OFF_W + (size_t)q * R32 * sizeof(VT), Wq[q] + ts, rc * (uint32_t)sizeof(VT), &bars[st]);
     }
-    bulk_g2s(base + OFF_R, L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
-    bulk_g2s(base + OFF_N, L.sk_tab.neg8 + ts, rc, &bars[st]);
+    bulk_g2s_stream(base + OFF_R, L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
+    bulk_g2s_stream(base + OFF_N, L.sk_tab.neg8 + ts, rc, &bars[st]);
   };
   auto issue_p = [&](int t) {
     const int st = t % MT32_STAGES;
@@ -263,10 +263,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_tma_kernel(const Ste
     const uint32_t brp = RP32 * 4u, bcol = (uint32_t)(eb - ea) * (uint32_t)sizeof(CT),
                    bval = (uint32_t)(eb - ea) * 4u;
     mbar_arrive_expect_tx(&bars[st], brp + bcol + bval);
-    bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
+    bulk_g2s_stream(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
     if (eb > ea) {
-      bulk_g2s(col_st(st), colsrc + ea, bcol, &bars[st]);
-      bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
+      bulk_g2s_stream(col_st(st), colsrc + ea, bcol, &bars[st]);
+      bulk_g2s_stream(val_st(st), val + ea, bval, &bars[st]);
     }
   };
   auto tile_end = [&](int t) { return min(r0 + (t + 1) * R32, r1); };

@@ -489,8 +489,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
       for (int q = 0; q < KW; ++q)
         if (q < nl) bulk_g2s(base + (size_t)MT_ROWS * 8 * (1 + q), Wq[q] + ts, rc * 8u, &bars[st]);
     }
-    bulk_g2s(base + (size_t)MT_ROWS * 8 * (1 + KW), L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
-    bulk_g2s(base + (size_t)MT_ROWS * 8 * (2 + KW), L.sk_tab.neg8 + ts, rc, &bars[st]);
+    bulk_g2s_stream(base + (size_t)MT_ROWS * 8 * (1 + KW), L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
+    bulk_g2s_stream(base + (size_t)MT_ROWS * 8 * (2 + KW), L.sk_tab.neg8 + ts, rc, &bars[st]);
   };
   auto issue_p = [&](int t) {  // thread 0: arrives with the product's bytes
     const int st = t % MT_STAGES;
@@ -831,10 +831,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
     const uint32_t brp = TMA_RP * 4u, bcol = (uint32_t)(eb - ea) * (uint32_t)sizeof(CT),
                    bval = (uint32_t)(eb - ea) * sizeof(AT);
     mbar_arrive_expect_tx(&bars[st], brp + bcol + bval);
-    bulk_g2s(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
+    bulk_g2s_stream(rp_st(st), L.row_ptr + ts, brp, &bars[st]);
     if (eb > ea) {
-      bulk_g2s(col_st(st), colsrc + ea, bcol, &bars[st]);
-      bulk_g2s(val_st(st), val + ea, bval, &bars[st]);
+      bulk_g2s_stream(col_st(st), colsrc + ea, bcol, &bars[st]);
+      bulk_g2s_stream(val_st(st), val + ea, bval, &bars[st]);
     }
   };
   auto tile_end = [&](int t) { return min(r0 + (t + 1) * TMA_ROWS, r1); };

@@ -46,23 +46,23 @@ def _oracle_many(jobs):
         return pool.map(_oracle_one, jobs)
 
 
-def _handles(insts, basis):
+def _handles(insts, basis, block_rhs=True):
     from paper_2503_22631_gb300 import F_EXP_NEG, Krylov
 
     hs = []
     for inst in insts:
         A = W.batched_matrix(inst)
         hs.append(Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=1.0, m=M, k=KW, s=S, seed=W.SEED, zeta=ZETA,
-                         basis=basis))
+                         basis=basis, block_rhs=block_rhs))
     return hs
 
 
-def _run(insts, n_rhs, basis, tol, cycles, raise_on_error=True):
+def _run(insts, n_rhs, basis, tol, cycles, raise_on_error=True, block_rhs=True):
     import torch
 
     from paper_2503_22631_gb300 import apply_batched
 
-    hs = _handles(insts, basis)
+    hs = _handles(insts, basis, block_rhs)
     B = [torch.from_numpy(_rhs_block(inst["n"], n_rhs, 100 + i)).cuda() for i, inst in enumerate(insts)]
     X, st = apply_batched(hs, B, t=[inst["t"] for inst in insts], tol=tol, max_cycles=cycles,
                           raise_on_error=raise_on_error)
@@ -73,8 +73,10 @@ def _run(insts, n_rhs, basis, tol, cycles, raise_on_error=True):
 SMALL = [dict(i, n_rhs=8) for i in W.batched_instances(4, 77, n_lo=1e3, n_hi=2e4)]
 
 
-@pytest.mark.parametrize("basis,tol", [(0, 1e-10), (1, 1e-5)])
+@pytest.mark.parametrize("basis,tol", [(0, 1e-10), (1, 1e-5), (3, 1e-10)])
 def test_small_batch_matches_oracle(lib, cuda, basis, tol):
+    """float64 runs one by one; float32 and float-float through the block
+    kernels (8 right-hand sides of a matrix advanced together)."""
     hs, B, X, st = _run(SMALL, 8, basis, 0.0, 2)
     jobs = [(i, inst, col, 100 + i, 2) for i, inst in enumerate(SMALL) for col in (0, 3, 5, 7)]
     refs = _oracle_many(jobs)
@@ -84,15 +86,28 @@ def test_small_batch_matches_oracle(lib, cuda, basis, tol):
 
 
 def test_batched_equals_single_applies(lib, cuda):
-    """Same kernels, same inputs: the batched call gives each right-hand side's
-    single-call result (and the handle's t is back to its value afterwards)."""
-    hs, B, X, st = _run(SMALL, 8, 1, 1e-6, 10)
+    """Same kernels, same inputs: with the block kernels switched off the
+    batched call gives each right-hand side's single-call result (and the
+    handle's t is back to its value afterwards)."""
+    hs, B, X, st = _run(SMALL, 8, 1, 1e-6, 10, block_rhs=False)
     for i, (h, inst) in enumerate(zip(hs, SMALL)):
         h.set_param(inst["t"])
         for col in range(8):
             x = h.apply(B[i][:, col].contiguous(), tol=1e-6, max_cycles=10).cpu().numpy()
             assert _rel(X[i][:, col], x) <= 1e-14
             assert st[i][col]["cycles"] == h.stats["cycles"]
+
+
+def test_float32_block_form_matches_one_by_one(lib, cuda):
+    """The float32 block kernels (float-float arithmetic on float32 storage)
+    against the float32 single-vector kernels: both are float32 methods, so
+    they agree to the float32 tolerance, not bitwise."""
+    _, _, Xb, stb = _run(SMALL, 8, 1, 0.0, 3)
+    _, _, X1, st1 = _run(SMALL, 8, 1, 0.0, 3, block_rhs=False)
+    for i in range(len(SMALL)):
+        for col in range(8):
+            assert _rel(Xb[i][:, col], X1[i][:, col]) <= 2e-5
+            assert stb[i][col]["cycles"] == st1[i][col]["cycles"] == 3
 
 
 def test_batched_rejects_repeated_handles(lib, cuda):
