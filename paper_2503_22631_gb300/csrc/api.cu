@@ -25,7 +25,7 @@ using namespace krylov;
 
 namespace {
 
-constexpr double EXP_THETA = 2.0;  // ||B||_1 bound after scaling
+constexpr double EXP_THETA = 0.5;  // ||B||_1 bound after scaling
 // cos(t sqrt(z)): Taylor degree 14 in A = t^2 H / 4^s with ||A||_1 <= 4: the
 // first omitted term is below 4^15 / 30! = 4e-24
 constexpr int COS_TAYLOR_DEG = 14;
@@ -37,16 +37,21 @@ constexpr size_t CSR_PAD = 8;
 // 256-row tile are copied as 260 entries.
 constexpr size_t RP_PAD = 272;
 constexpr int TMA_MAX_CAP = 4096;  // largest staged tile span (nonzeros)
+#ifndef KRYLOV_SELL
+#define KRYLOV_SELL 1  // build the sliced layout for the float-float product where it applies
+#endif
 constexpr int EXP_SQ_CYCLES = 16;              // exp: cycles also evaluated by scaling and squaring
 constexpr double QUAD_TOL_CONTOURS = 1e-12;    // exp quadrature: largest difference of the two contours
 constexpr double QUAD_TOL_SQUARING = 1e-11;    // ... and to scaling and squaring (relative to the first column)
 constexpr int QUAD_RETRIES = 2;                // lower shifts tried after a failed check
+constexpr int QUAD_START = 10;                 // first cycle with the quadrature (shorter runs never pay for it)
 // z^{-1/2}: trapezoidal nodes in u (s = e^u) with step INVSQRT_H on
 // [0.5 ln(alpha * 1e-18) - 38, 0.5 ln(alpha * 1e4) + 38], alpha = ||A||_inf >= |lambda|:
 // the two tails are below e^-38 relative for spectra inside [1e-18 alpha, 1e4 alpha], and
 // the step gives geometric accuracy exp(-2 pi d / h) with d = (pi - |arg z|) / 2.
 constexpr double INVSQRT_H = 0.2;
-constexpr int EXP_TAYLOR_DEG = 24; // theta^25/25! e^theta < 2^-53
+constexpr int EXP_TAYLOR_DEG = 14; // theta^15/15! e^theta = 3.9e-17 < 2^-53 (each Taylor step is one launch
+                                    // per block row, a squaring level one more: 14 steps + 2 levels beat 24 steps)
 
 struct DevBuf {
   void* p = nullptr;
@@ -200,6 +205,10 @@ struct krylov_handle {
   double q_u0 = 0.0;               // first node
   int tma_cap = 0, tma_cap_t = 0;  // staged span per tile for A and A^T (0: no staging)
   int16_t* dcol = nullptr;         // col - row per nonzero of A (bandwidth < 2^15, staged float-float product)
+  int* sell_off = nullptr;         // sliced layout of A (float-float product; null: not built)
+  int16_t* sell_col = nullptr;
+  void* sell_val = nullptr;
+  int grid_sell = 0;
   int16_t* dcolt = nullptr;        // the same for A^T
   SegPlan seg_a, seg_t;            // segment plans of A and A^T (float-float basis)
   LongRows long_a, long_t;         // long rows of A and A^T (float-float basis, power-law operators)
@@ -254,7 +263,7 @@ struct krylov_handle {
 
   // host mirrors
   int* h_flags = nullptr;     // pinned: flags[4]
-  double* h_scal = nullptr;   // pinned: 32 doubles ([0, 8) cycle scalars, [8, 16) misc, [16, 22) quadrature)
+  double* h_scal = nullptr;   // pinned: 32 doubles ([0, 8) cycle scalars, [8, 16) misc, [16, 24) quadrature)
   int last_me = 0, last_nc = 0, last_cycle = 0;
   std::vector<void*> allocs;
 };
@@ -467,6 +476,61 @@ krylov_status install_delta16(krylov_handle* h, const int* rp_dev, const int* ci
   return KRYLOV_OK;
 }
 
+// Sliced layout of A for the float-float product kernel (ff_spmv_sell_kernel):
+// every 256-row tile padded to its longest row and stored slot-major.  Built
+// when the band allows 2-byte offsets, no tile has a row longer than
+// SELL_MAXL and the padding adds at most a quarter to the stored entries
+// (stencils and meshes; power-law operators keep the CSR kernels).
+krylov_status install_sell(krylov_handle* h, int use32) {
+  if ((h->opt.basis_dtype != 3 && !h->staged32) || h->long_a.n_long > 0 || h->dcol == nullptr || h->nnz == 0)
+    return KRYLOV_OK;
+  const int n = h->n;
+  const int64_t nnz = h->nnz;
+  std::vector<int> rp((size_t)n + 1), ci((size_t)nnz);
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpy(rp.data(), h->rp, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ci.data(), h->ci, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToHost));
+  const int ntiles = (n + STEP_THREADS - 1) / STEP_THREADS;
+  std::vector<int> off((size_t)ntiles + 1, 0);
+  int64_t total = 0;
+  for (int g = 0; g < ntiles; ++g) {
+    int lmax = 0;
+    for (int r = g * STEP_THREADS; r < std::min(n, (g + 1) * STEP_THREADS); ++r) lmax = std::max(lmax, rp[r + 1] - rp[r]);
+    if (lmax > SELL_MAXL) return KRYLOV_OK;
+    total += (int64_t)lmax * STEP_THREADS;
+    if (total > 0x7FFFFFF0LL) return KRYLOV_OK;
+    off[(size_t)g + 1] = (int)total;
+  }
+  if ((double)total > 1.25 * (double)nnz) return KRYLOV_OK;
+  const size_t vb = use32 ? sizeof(float) : sizeof(float2);
+  std::vector<unsigned char> vsrc((size_t)nnz * vb), vdst((size_t)total * vb, 0);
+  CK(cudaMemcpy(vsrc.data(), use32 ? (const void*)h->val32 : (const void*)h->valff, vsrc.size(),
+                cudaMemcpyDeviceToHost));
+  std::vector<int16_t> col((size_t)total, 0);
+  for (int r = 0; r < n; ++r) {
+    const int g = r / STEP_THREADS, k = r % STEP_THREADS;
+    for (int q = 0; q < rp[r + 1] - rp[r]; ++q) {
+      const size_t e = (size_t)off[g] + (size_t)q * STEP_THREADS + k;
+      const int src = rp[r] + q;
+      col[e] = (int16_t)(ci[src] - r);
+      std::memcpy(vdst.data() + e * vb, vsrc.data() + (size_t)src * vb, vb);
+    }
+  }
+  int16_t* dc = nullptr;
+  unsigned char* dv = nullptr;
+  CK(dalloc(h, &h->sell_off, off.size()));
+  CK(dalloc(h, &dc, (size_t)total));
+  CK(dalloc(h, &dv, (size_t)total * vb));
+  CK(cudaMemcpy(h->sell_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dc, col.data(), sizeof(int16_t) * col.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dv, vdst.data(), vdst.size(), cudaMemcpyHostToDevice));
+  h->sell_col = dc;
+  h->sell_val = dv;
+  const int per_sm = h->staged32 ? s32_sell_ctas_per_sm() : sell_ctas_per_sm(use32);
+  h->grid_sell = std::max(1, std::min(h->num_sms * per_sm, std::min(h->part_cap, (n + STEP_THREADS - 1) / STEP_THREADS)));
+  return KRYLOV_OK;
+}
+
 // Long rows of an operator held on the device: if any row has more than
 // LONG_ROW nonzeros (float-float basis), build the operator with those rows
 // emptied (same row count, so every other kernel keeps its layout), the list
@@ -642,6 +706,11 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   const int st32 = h->staged32 && !transpose;
   L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : (st32 ? h->tma_cap : 0);
   L.dcol = (basis == 3) ? (transpose ? h->dcolt : h->dcol) : (st32 ? h->dcol : nullptr);
+  if ((basis == 3 || st32) && !transpose && h->sell_col) {  // the sliced layout of A
+    L.sell_off = h->sell_off;
+    L.sell_col = h->sell_col;
+    L.sell_val = h->sell_val;
+  }
   if (basis == 3) {
     const SegPlan& sp = transpose ? h->seg_t : h->seg_a;
     L.seg = sp.seg;
@@ -741,8 +810,13 @@ krylov_status choose_product_kernel(krylov_handle* h, int transpose) {
   const int n = h->n;
   const int tcap = transpose ? h->tma_cap_t : h->tma_cap;
   const int grid_seg = grid;
-  const int grid_gather = std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(use32, tcap, 0, 0),
-                                               std::min(h->part_cap, (n + STEP_THREADS - 1) / STEP_THREADS)));
+  // the alternative to the staged pieces: the sliced-layout kernel where it
+  // was built, else the CSR gather kernel
+  const int grid_gather =
+      (!transpose && h->sell_col)
+          ? h->grid_sell
+          : std::max(1, std::min(h->num_sms * spmv_ctas_per_sm(use32, tcap, 0, 0),
+                                 std::min(h->part_cap, (n + STEP_THREADS - 1) / STEP_THREADS)));
   if (h->opt.autotune == 2) {  // fixed choice: the gather kernel
     sp.seg = nullptr;
     grid = grid_gather;
@@ -1042,10 +1116,18 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
         fsq = square_row();
       }
       const double* fsrc = fsq;
-      if (quad) {
-        if (c == 1) launch_exp_quad_sigma(h->sd, me, h->f.t, fsq, st);
+      if (quad && c >= QUAD_START) {
+        // fresh check maxima for this cycle (at the start, for every block so far)
+        CK(cudaMemsetAsync(h->sd.qstat + 2, 0, 2 * sizeof(double), st));
+        if (c == QUAD_START) {  // shift from the first block, then blocks 0 .. a - 1
+          const double* f0 = h->sd.G + (size_t)s_lv * h->level_stride;
+          launch_exp_quad_sigma(h->sd, M, h->f.t, f0, st);
+          for (int ap = 0; ap < a; ++ap)
+            launch_exp_quad(h->sd, h->cd, M, M, ap, h->f.t, f0 + (size_t)ap * (ap + 1) / 2 * MM, st);
+          stats.launches += 1 + 2 * a;
+        }
         launch_exp_quad(h->sd, h->cd, M, me, a, h->f.t, fsq, st);
-        stats.launches += (c == 1) ? 3 : 2;
+        stats.launches += 3;
         if (!sq) {  // the contours must agree before the result is used
           CK(cudaMemcpyAsync(h->h_scal + 16, h->sd.qstat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
@@ -1089,7 +1171,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     CK(cudaStreamSynchronize(st));
     // a cycle with both evaluations: the quadrature must match the squaring and
     // its two contours each other, else the squaring continues alone
-    if (quad && c <= EXP_SQ_CYCLES &&
+    if (quad && c >= QUAD_START && c <= EXP_SQ_CYCLES &&
         !(h->h_scal[18] <= QUAD_TOL_SQUARING && h->h_scal[19] <= QUAD_TOL_CONTOURS)) {
       // a Ritz value outside the contours: up to two retries with the shift
       // lowered by 3 / t (the quadrature of every block so far recomputed and
@@ -1098,17 +1180,16 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
       const size_t MMq = (size_t)M * M;
       for (int attempt = 0; attempt < QUAD_RETRIES && !fixed; ++attempt) {
         h->h_scal[20] = h->h_scal[16] - 3.0 / h->f.t;  // sigma
-        h->h_scal[21] = 0.0;                           // largest entry so far
-        CK(cudaMemcpyAsync(h->sd.qstat, h->h_scal + 20, 2 * sizeof(double), cudaMemcpyHostToDevice, st));
-        fixed = true;
-        for (int ap = 0; ap <= c - 1 && fixed; ++ap) {
+        for (int q = 21; q < 24; ++q) h->h_scal[q] = 0.0;  // largest entry and check maxima
+        CK(cudaMemcpyAsync(h->sd.qstat, h->h_scal + 20, 4 * sizeof(double), cudaMemcpyHostToDevice, st));
+        for (int ap = 0; ap <= c - 1; ++ap) {
           const double* fsq_ap = h->sd.G + (size_t)s_lv * h->level_stride + (size_t)ap * (ap + 1) / 2 * MMq;
           launch_exp_quad(h->sd, h->cd, M, ap == c - 1 ? me : M, ap, h->f.t, fsq_ap, st);
           stats.launches += 2;
-          CK(cudaMemcpyAsync(h->h_scal + 16, h->sd.qstat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-          CK(cudaStreamSynchronize(st));
-          fixed = (h->h_scal[18] <= QUAD_TOL_SQUARING && h->h_scal[19] <= QUAD_TOL_CONTOURS);
         }
+        CK(cudaMemcpyAsync(h->h_scal + 16, h->sd.qstat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        fixed = (h->h_scal[18] <= QUAD_TOL_SQUARING && h->h_scal[19] <= QUAD_TOL_CONTOURS);
       }
       if (!fixed) {
         quad = false;
@@ -1796,6 +1877,11 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
   h->grid_spmv_t = h->grid_spmv;
   h->part_cap = std::max(h->grid, std::min(h->num_sms * 32, (n + STEP_THREADS - 1) / STEP_THREADS));
   CKF(dalloc(h, &h->part, (size_t)h->part_cap * 8));
+  if ((opt.basis_dtype == 3 || h->staged32) && KRYLOV_SELL) {
+    const krylov_status ps3 = install_sell(h, vals32);
+    if (ps3 != KRYLOV_OK) return fail(ps3);
+    if (h->sell_col && !h->seg_a.seg) h->grid_spmv = h->grid_sell;
+  }
   // the update pass streams m + 2 vectors: 8 resident CTAs per SM
   h->grid_update = std::max(1, std::min(h->part_cap, std::min(h->num_sms * 8, (n + STEP_THREADS - 1) / STEP_THREADS)));
   CKF(dalloc(h, &h->cd.flags, 4));

@@ -88,7 +88,15 @@ struct StepLaunch {
   const uint16_t* lcol;     // [nnz + 16] tile-local column positions
   int seg_cap;              // max staged entries of w_j per tile (even)
   int lcap;                 // max aligned nonzero span per tile (multiple of 8)
+  // sliced layout of the operator (float-float basis; sell_col null: none):
+  // 256-row tile g holds entries [sell_off[g], sell_off[g + 1]) of sell_col /
+  // sell_val, padded to the tile's longest row, entry q of row r at q * 256 + r
+  const int* sell_off;      // [tiles + 1]
+  const int16_t* sell_col;  // col - row (padding: 0)
+  const void* sell_val;     // float or float2 like val (padding: 0)
 };
+
+constexpr int SELL_MAXL = 16;  // longest row of a tile in the sliced layout
 
 constexpr int SEG_MAX = 16;        // pieces of w_j per tile
 constexpr int SEG_CAP_MAX = 3072;  // staged entries of w_j per tile (24 KB float-float)
@@ -146,6 +154,7 @@ struct RgsArgs {
 
 // basis dtype codes (krylov_basis)
 int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap);
+int sell_ctas_per_sm(int vals_f32);
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
 // float32 / bfloat16 bases with staged row streams (step32_kernels.cu): the
@@ -153,6 +162,7 @@ void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cuda
 size_t s32_mat_smem(int s, int copies, int kw, int vt_bytes);
 int s32_ctas_per_sm(int basis, int s, int copies);
 int s32_spmv_ctas_per_sm(int tma_cap, int di);
+int s32_sell_ctas_per_sm();
 void launch_step32(int basis, const StepLaunch& L, const CycleDev& cd, cudaStream_t st);
 // float-float product kernel alone (p_j = A w_j, window dots unless L.rgs)
 void launch_ff_product(const StepLaunch& L, const CycleDev& cd, cudaStream_t st);

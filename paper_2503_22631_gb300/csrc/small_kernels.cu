@@ -967,7 +967,8 @@ __global__ void __launch_bounds__(EQ_THREADS) exp_quad_nodes_kernel(SmallDev sd,
 // order); qstat[3] = max |difference to the hyperbolic contour's sum| and
 // qstat[2] = max |difference to fsq| (when given: the block row of the
 // scaling-and-squaring evaluation), both relative to the largest |entry| of
-// the first column met so far (qstat[1]).
+// the first column met so far (qstat[1]) and kept as running maxima until the
+// host clears them.
 __global__ void exp_quad_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, double t, const double* fsq) {
   __shared__ double s_d[3][256];
   const double E = exp(-t * sd.qstat[0]);
@@ -1001,8 +1002,9 @@ __global__ void exp_quad_sum_kernel(SmallDev sd, CycleDev cd, int M, int me, dou
     }
     const double scale = fmax(sd.qstat[1], mx);
     sd.qstat[1] = scale;
-    sd.qstat[2] = (scale > 0.0) ? dsq / scale : INFINITY;
-    sd.qstat[3] = (scale > 0.0 && isfinite(dq)) ? dq / scale : INFINITY;
+    // running maxima over the blocks since the host last cleared them
+    sd.qstat[2] = fmax(sd.qstat[2], (scale > 0.0) ? dsq / scale : INFINITY);
+    sd.qstat[3] = fmax(sd.qstat[3], (scale > 0.0 && isfinite(dq)) ? dq / scale : INFINITY);
   }
 }
 

@@ -363,6 +363,152 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_tma_kernel(const Ste
   }
 }
 
+// Product kernel on the sliced layout (see ff_spmv_sell_kernel): tiles padded
+// to their longest row L, stored slot-major; the entry loop is unrolled for
+// the tile's L.
+constexpr size_t SELL32_STAGE = (size_t)SELL_MAXL * R32 * (2 + 4);
+
+template <int NL, typename VT>
+__device__ __forceinline__ float sell32_row(const int16_t* cs, const float* vs, const VT* Wj, int i, int k) {
+  float wv[NL], av[NL];
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    av[q] = vs[q * R32 + k];
+    wv[q] = to_f(Wj[i + (int)cs[q * R32 + k]]);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int q = 0; q < NL; ++q) acc = __fmaf_rn(av[q], wv[q], acc);
+  return acc;
+}
+
+template <typename VT, int KW>
+__global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_sell_kernel(const StepLaunch L, const CycleDev cd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[SP32_STAGES];
+  __shared__ double red[32];
+  __shared__ int s_last;
+  __shared__ double tot[NQ];
+  auto col_st = [&](int st) { return reinterpret_cast<const int16_t*>(smem + (size_t)st * SELL32_STAGE); };
+  auto val_st = [&](int st) {
+    return reinterpret_cast<const float*>(smem + (size_t)st * SELL32_STAGE + (size_t)SELL_MAXL * R32 * 2);
+  };
+  const int j = L.j;
+  const VT* W = static_cast<const VT*>(L.W);
+  const VT* Wj = W + (int64_t)j * L.ldw;
+  const float* sval = static_cast<const float*>(L.sell_val);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = j - dlo + 1;
+  const VT* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
+  const int r0 = blockIdx.x * L.rows_spmv;
+  const int r1 = min(L.n, r0 + L.rows_spmv);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + R32 - 1) / R32 : 0;
+  const int g0 = r0 / R32;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < SP32_STAGES; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int st = t % SP32_STAGES;
+    const int e0 = __ldg(L.sell_off + g0 + t), e1 = __ldg(L.sell_off + g0 + t + 1);
+    const uint32_t bc = (uint32_t)(e1 - e0) * 2u, bv = (uint32_t)(e1 - e0) * 4u;
+    mbar_arrive_expect_tx(&bars[st], bc + bv);
+    if (e1 > e0) {
+      unsigned char* base = smem + (size_t)st * SELL32_STAGE;
+      bulk_g2s_stream(base, L.sell_col + e0, bc, &bars[st]);
+      bulk_g2s_stream(base + (size_t)SELL_MAXL * R32 * 2, sval + e0, bv, &bars[st]);
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(ntiles, SP32_STAGES); ++t) issue(t);
+  pdl_wait();
+  if (cd.flags[1] != 0) {
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(ntiles, SP32_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, WAIT32_NS);
+    return;
+  }
+  float acc_pi = 0.f, acc_dot[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) acc_dot[q] = 0.f;
+  bool timed_out = false;
+  int last_issued = min(ntiles, SP32_STAGES) - 1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % SP32_STAGES;
+    const uint32_t par = (uint32_t)(t / SP32_STAGES) & 1u;
+    const int i = r0 + t * R32 + (int)threadIdx.x;
+    const bool valid = i < r1;
+    const int nl = (__ldg(L.sell_off + g0 + t + 1) - __ldg(L.sell_off + g0 + t)) / R32;
+    float wq[KW];
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) wq[q] = to_f(Wd[q][i]);
+    }
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, WAIT32_NS)) timed_out = true;
+    if (valid && !timed_out) {
+      const int16_t* cs = col_st(st);
+      const float* vs = val_st(st);
+      const int k = (int)threadIdx.x;
+      float p;
+      switch (nl) {  // the same for every thread of the CTA
+        case 1: p = sell32_row<1>(cs, vs, Wj, i, k); break;
+        case 2: p = sell32_row<2>(cs, vs, Wj, i, k); break;
+        case 3: p = sell32_row<3>(cs, vs, Wj, i, k); break;
+        case 4: p = sell32_row<4>(cs, vs, Wj, i, k); break;
+        case 5: p = sell32_row<5>(cs, vs, Wj, i, k); break;
+        case 6: p = sell32_row<6>(cs, vs, Wj, i, k); break;
+        case 7: p = sell32_row<7>(cs, vs, Wj, i, k); break;
+        case 8: p = sell32_row<8>(cs, vs, Wj, i, k); break;
+        default: {
+          float a = 0.f;
+          for (int q = 0; q < nl; ++q) a = __fmaf_rn(vs[q * R32 + k], to_f(Wj[i + (int)cs[q * R32 + k]]), a);
+          p = a;
+        }
+      }
+      static_cast<float*>(L.p_out)[i] = p;
+      acc_pi = __fmaf_rn(p, p, acc_pi);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) acc_dot[q] = __fmaf_rn(wq[q], p, acc_dot[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && t + SP32_STAGES < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue(t + SP32_STAGES);
+      last_issued = t + SP32_STAGES;
+    }
+  }
+  pdl_trigger();
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    for (int t = max(0, last_issued - SP32_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % SP32_STAGES], (uint32_t)(t / SP32_STAGES) & 1u, WAIT32_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  double v = block_sum((double)acc_pi, red);
+  if (threadIdx.x == 0) part[1] = v;
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;
+    __syncthreads();
+    v = block_sum((double)acc_dot[q], red);
+    if (threadIdx.x == 0) part[2 + q] = v;
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double tt = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
+    if ((threadIdx.x & 31) == 0) tot[q] = tt;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
+    if (threadIdx.x == 0) *cd.counter = 0u;
+  }
+}
+
 template <typename K> int occ32(K kern, size_t smem) {
   raise_smem_limit((const void*)kern, smem);
   int b = 0;
@@ -382,6 +528,13 @@ void launch_mat32(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
 
 template <typename VT, int KW>
 void launch_spmv32(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
+  if (L.sell_col != nullptr) {
+    auto k = s32_spmv_sell_kernel<VT, KW>;
+    const size_t smem = SP32_STAGES * SELL32_STAGE;
+    raise_smem_limit((const void*)k, smem);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+    return;
+  }
   if (L.dcol != nullptr) {
     auto k = s32_spmv_tma_kernel<VT, KW, true>;
     const size_t smem = SP32_STAGES * sp32_stage_bytes<true>(L.tma_cap);
@@ -426,6 +579,8 @@ int s32_ctas_per_sm(int basis, int s, int copies) {
   return copies == 32 ? occ32(s32_mat_tma_kernel<__nv_bfloat16, true, 2, 32, 8>, smem)
                       : occ32(s32_mat_tma_kernel<__nv_bfloat16, true, 2, 16, 8>, smem);
 }
+
+int s32_sell_ctas_per_sm() { return occ32(s32_spmv_sell_kernel<float, 2>, SP32_STAGES * SELL32_STAGE); }
 
 int s32_spmv_ctas_per_sm(int tma_cap, int di) {
   return di ? occ32(s32_spmv_tma_kernel<float, 2, true>, SP32_STAGES * sp32_stage_bytes<true>(tma_cap))

@@ -935,6 +935,161 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   }
 }
 
+// Product kernel on the sliced layout: a 256-row tile's entries padded to the
+// tile's longest row L and stored slot-major (entry q of row r at q * 256 + r,
+// column offsets col - row, padding offset 0 and value 0), so a tile is two
+// contiguous bulk copies, entry q of every thread is one conflict-free shared
+// load, and a row needs neither row_ptr nor a per-entry bound test: the
+// entry loop is unrolled for the tile's L (uniform over the CTA).  Padding
+// adds exact zeros after a row's own entries, so every row's sum equals the
+// CSR kernels' (storage order).
+template <typename AT>
+__host__ __device__ constexpr size_t sell_stage_bytes() {
+  return (size_t)SELL_MAXL * TMA_ROWS * (2 + sizeof(AT));
+}
+
+template <int NL, typename AT>
+__device__ __forceinline__ ff sell_row(const int16_t* cs, const AT* vs, const float2* Wj, int i, int k) {
+  float2 wv[NL];
+  AT av[NL];
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    av[q] = vs[q * TMA_ROWS + k];
+    wv[q] = __ldg(Wj + (i + (int)cs[q * TMA_ROWS + k]));
+  }
+  ffacc acc;
+#pragma unroll
+  for (int q = 0; q < NL; ++q) acc_val(acc, av[q], ff{wv[q].x, wv[q].y});
+  return acc.result();
+}
+
+template <typename AT, int KW>
+__global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_sell_kernel(const StepLaunch L, const CycleDev cd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[TMA_STAGES];
+  __shared__ float rhi[32], rlo[32];
+  __shared__ int s_last;
+  __shared__ double tot[NQ];
+  constexpr size_t SB = sell_stage_bytes<AT>();
+  auto col_st = [&](int st) { return reinterpret_cast<const int16_t*>(smem + (size_t)st * SB); };
+  auto val_st = [&](int st) {
+    return reinterpret_cast<const AT*>(smem + (size_t)st * SB + (size_t)SELL_MAXL * TMA_ROWS * 2);
+  };
+  const int j = L.j;
+  const float2* W = static_cast<const float2*>(L.W);
+  const float2* Wj = W + (int64_t)j * L.ldw;
+  const AT* sval = static_cast<const AT*>(L.sell_val);
+  const int dlo = max(0, j - L.k + 1);
+  const int nd = L.rgs ? 0 : j - dlo + 1;
+  const float2* Wd[KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) Wd[q] = W + (int64_t)(dlo + (q < nd ? q : 0)) * L.ldw;
+  const int r0 = blockIdx.x * L.rows_spmv;
+  const int r1 = min(L.n, r0 + L.rows_spmv);
+  const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
+  const int g0 = r0 / TMA_ROWS;  // global tile of the CTA's first tile
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < TMA_STAGES; ++q) mbar_init(&bars[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {  // thread 0
+    const int st = t % TMA_STAGES;
+    const int e0 = __ldg(L.sell_off + g0 + t), e1 = __ldg(L.sell_off + g0 + t + 1);
+    const uint32_t bc = (uint32_t)(e1 - e0) * 2u, bv = (uint32_t)(e1 - e0) * (uint32_t)sizeof(AT);
+    mbar_arrive_expect_tx(&bars[st], bc + bv);
+    if (e1 > e0) {
+      unsigned char* base = smem + (size_t)st * SB;
+      bulk_g2s_stream(base, L.sell_col + e0, bc, &bars[st]);
+      bulk_g2s_stream(base + (size_t)SELL_MAXL * TMA_ROWS * 2, sval + e0, bv, &bars[st]);
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int t = 0; t < min(ntiles, TMA_STAGES); ++t) issue(t);
+  pdl_wait();
+  if (cd.flags[1] != 0) {
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(ntiles, TMA_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+    return;
+  }
+  ffacc acc_pi;
+  ffacc acc_dot[KW];
+  bool timed_out = false;
+  int last_issued = min(ntiles, TMA_STAGES) - 1;
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % TMA_STAGES;
+    const uint32_t par = (uint32_t)(t / TMA_STAGES) & 1u;
+    const int i = r0 + t * TMA_ROWS + (int)threadIdx.x;
+    const bool valid = i < r1;
+    const int nl = (__ldg(L.sell_off + g0 + t + 1) - __ldg(L.sell_off + g0 + t)) / TMA_ROWS;
+    ff wq[KW];
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) wq[q] = ld_ff(Wd[q] + i);
+    }
+    if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
+    if (valid && !timed_out) {
+      const int16_t* cs = col_st(st);
+      const AT* vs = val_st(st);
+      const int k = (int)threadIdx.x;
+      ff p;
+      switch (nl) {  // the same for every thread of the CTA
+        case 1: p = sell_row<1>(cs, vs, Wj, i, k); break;
+        case 2: p = sell_row<2>(cs, vs, Wj, i, k); break;
+        case 3: p = sell_row<3>(cs, vs, Wj, i, k); break;
+        case 4: p = sell_row<4>(cs, vs, Wj, i, k); break;
+        case 5: p = sell_row<5>(cs, vs, Wj, i, k); break;
+        case 6: p = sell_row<6>(cs, vs, Wj, i, k); break;
+        case 7: p = sell_row<7>(cs, vs, Wj, i, k); break;
+        case 8: p = sell_row<8>(cs, vs, Wj, i, k); break;
+        default: {
+          ffacc acc;
+          for (int q = 0; q < nl; ++q)
+            acc_val(acc, vs[q * TMA_ROWS + k], ld_ff(Wj + (i + (int)cs[q * TMA_ROWS + k])));
+          p = acc.result();
+        }
+      }
+      st_ff(static_cast<float2*>(L.p_out) + i, p);
+      acc_pi.add_prod(p, p);
+#pragma unroll
+      for (int q = 0; q < KW; ++q)
+        if (q < nd) acc_dot[q].add_prod(wq[q], p);
+    }
+    __syncthreads();  // every thread is done with stage st
+    if (threadIdx.x == 0 && t + TMA_STAGES < ntiles && !timed_out) {
+      fence_proxy_async();
+      issue(t + TMA_STAGES);
+      last_issued = t + TMA_STAGES;
+    }
+  }
+  pdl_trigger();
+  if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
+  if (threadIdx.x == 0 && timed_out) {
+    for (int t = max(0, last_issued - TMA_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % TMA_STAGES], (uint32_t)(t / TMA_STAGES) & 1u, TMA_WAIT_NS);
+  }
+  double* part = L.part + (size_t)blockIdx.x * NQ;
+  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
+  if (threadIdx.x == 0) part[1] = v;
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    if (q >= nd) break;
+    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
+    if (threadIdx.x == 0) part[2 + q] = v;
+  }
+  if (!last_block_flag(cd.counter, &s_last)) return;
+  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
+    const double tt = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
+    if ((threadIdx.x & 31) == 0) tot[q] = tt;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
+    if (threadIdx.x == 0) *cd.counter = 0u;
+  }
+}
+
 // ---------------------------------------------------------------------------
 
 size_t fused_smem(int basis, int s, int copies) {
@@ -1272,6 +1427,13 @@ void launch_ff_spmv_main(const StepLaunch& L, const CycleDev& cd, cudaStream_t s
     launch_pdl(k, L.grid_spmv, smem, st, L, cd);
     return;
   }
+  if (L.sell_col != nullptr) {
+    auto k = ff_spmv_sell_kernel<AT, KW>;
+    const size_t smem = TMA_STAGES * sell_stage_bytes<AT>();
+    raise_smem_limit((const void*)k, smem);
+    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+    return;
+  }
   if (L.tma_cap > 0 && L.dcol != nullptr) {
     auto k = ff_spmv_tma_kernel<AT, KW, true>;
     const size_t smem = TMA_STAGES * tma_stage_bytes<AT, true>(L.tma_cap);
@@ -1356,6 +1518,11 @@ int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap) {
     return vals_f32 ? occ(ff_spmv_tma_kernel<float, 2, false>, TMA_STAGES * tma_stage_bytes<float>(tma_cap))
                     : occ(ff_spmv_tma_kernel<float2, 2, false>, TMA_STAGES * tma_stage_bytes<float2>(tma_cap));
   return vals_f32 ? occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM) : occ(ff_spmv_kernel<float2, 2>, FF_STAGE_SMEM);
+}
+
+int sell_ctas_per_sm(int vals_f32) {
+  return vals_f32 ? occ(ff_spmv_sell_kernel<float, 2>, TMA_STAGES * sell_stage_bytes<float>())
+                  : occ(ff_spmv_sell_kernel<float2, 2>, TMA_STAGES * sell_stage_bytes<float2>());
 }
 
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
