@@ -51,6 +51,29 @@ def test_benchmark_cycle_count_reaches_1e8(lib, cuda, headline, basis):
     assert _rel(x, ref) <= 1e-8
 
 
+@pytest.mark.parametrize("basis,key", [(3, "df64"), (0, "f64")])
+def test_cycle_count_per_seed_is_the_first_to_reach_1e8(lib, cuda, headline, basis, key):
+    """Every right-hand side the benchmark times: its cycle count is the first
+    at which the relative error against the Kronecker closed form is <= 1e-8
+    (the instrumented run behind the benchmark's table)."""
+    import torch
+
+    from paper_2503_22631_gb300 import F_EXP_NEG, Krylov
+
+    A, _, _ = headline
+    wl = bench.WORKLOAD
+    kr = Krylov(A.row_ptr, A.col_idx, A.val, f=F_EXP_NEG, t=wl["t"], m=wl["m"], k=wl["k"], s=wl["s"],
+                seed=bench.SEED, zeta=wl["zeta"], basis=basis)
+    for seed in bench.HEADLINE_SEEDS:
+        b = bench.make_rhs(A.n, seed)
+        ref = TR.kron_expm_apply(wl["grid"], 3, wl["beta"], wl["t"], b)
+        c = bench.CYCLES_BY_SEED[key][seed]
+        bd = torch.from_numpy(b).cuda()
+        errs = [_rel(kr.apply(bd, tol=0.0, max_cycles=cc).cpu().numpy(), ref) for cc in (c - 1, c)]
+        print(f"seed {seed}: {c - 1} cycles {errs[0]:.2e}, {c} cycles {errs[1]:.2e}")
+        assert errs[1] <= 1e-8 < errs[0], seed
+
+
 def test_relative_stop_rule_reaches_1e8(lib, cuda, headline):
     A, b, ref = headline
     x, kr = _solve(A, b, 3, 30, tol=1e-8)
