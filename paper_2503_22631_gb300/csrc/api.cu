@@ -197,6 +197,11 @@ struct krylov_handle {
   float2* valff = nullptr;  // (hi, lo) value pairs for the float-float basis
   int vals_exact_f32 = 0;
   int part_cap = 0;                // per-CTA partial slots (8 doubles each)
+  double* part_w = nullptr;        // [2][part_cap] ||w_j||^2 partials of the float-float materialize kernels
+  int grid_mat = 0;                // CTAs of the float-float materialize kernel with staged row streams
+  int sell_maxl = 0;               // longest tile row of the sliced layout
+  void* sk_acc = nullptr;          // (m+1) x sk_acc_stride int64: exact sketches of the float-float basis
+  int64_t sk_acc_stride = 0;
   long long* rgs_acc = nullptr;    // randomized Gram-Schmidt: exact sketch sums [3][s]
   BlockWs* bk = nullptr;           // block form workspace (allocated on first use)
   int bk_concurrent = 1;           // instances running concurrently in the current batched call
@@ -493,15 +498,19 @@ krylov_status install_sell(krylov_handle* h, int use32) {
   const int ntiles = (n + STEP_THREADS - 1) / STEP_THREADS;
   std::vector<int> off((size_t)ntiles + 1, 0);
   int64_t total = 0;
+  int maxl = 1;
   for (int g = 0; g < ntiles; ++g) {
     int lmax = 0;
     for (int r = g * STEP_THREADS; r < std::min(n, (g + 1) * STEP_THREADS); ++r) lmax = std::max(lmax, rp[r + 1] - rp[r]);
     if (lmax > SELL_MAXL) return KRYLOV_OK;
+    maxl = std::max(maxl, lmax);
     total += (int64_t)lmax * STEP_THREADS;
     if (total > 0x7FFFFFF0LL) return KRYLOV_OK;
     off[(size_t)g + 1] = (int)total;
   }
   if ((double)total > 1.25 * (double)nnz) return KRYLOV_OK;
+  // the float-float product kernel stages several tiles of the longest row
+  if (!h->staged32 && sell_smem_bytes(use32, maxl) > 220 * 1024) return KRYLOV_OK;
   const size_t vb = use32 ? sizeof(float) : sizeof(float2);
   std::vector<unsigned char> vsrc((size_t)nnz * vb), vdst((size_t)total * vb, 0);
   CK(cudaMemcpy(vsrc.data(), use32 ? (const void*)h->val32 : (const void*)h->valff, vsrc.size(),
@@ -526,7 +535,8 @@ krylov_status install_sell(krylov_handle* h, int use32) {
   CK(cudaMemcpy(dv, vdst.data(), vdst.size(), cudaMemcpyHostToDevice));
   h->sell_col = dc;
   h->sell_val = dv;
-  const int per_sm = h->staged32 ? s32_sell_ctas_per_sm() : sell_ctas_per_sm(use32);
+  h->sell_maxl = maxl;
+  const int per_sm = h->staged32 ? s32_sell_ctas_per_sm() : sell_ctas_per_sm(use32, maxl);
   h->grid_sell = std::max(1, std::min(h->num_sms * per_sm, std::min(h->part_cap, (n + STEP_THREADS - 1) / STEP_THREADS)));
   return KRYLOV_OK;
 }
@@ -692,6 +702,10 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   L.p_out = h->p[j & 1];
   L.sk_part = (char*)h->sk_part + (size_t)j * h->sk_col_stride * sizeof(double);
   L.part = h->part;
+  L.part_w = h->part_w;
+  L.part_w_stride = h->part_cap;
+  L.sk_acc = h->sk_acc;
+  L.sk_acc_stride = h->sk_acc_stride;
   L.thr = thr;
   L.s = h->s;
   L.zeta = h->opt.zeta;
@@ -702,6 +716,12 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   // whole 256-row tiles per CTA (tiles then start at multiples of 256)
   L.rows_per_cta = ((n + h->grid - 1) / h->grid + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
   L.m = M;
+  L.grid_mat = L.grid;
+  L.rows_mat = L.rows_per_cta;
+  if (basis == 3 && h->sk_mode == SK_TAB8 && h->grid_mat > 0) {
+    L.grid_mat = h->grid_mat;
+    L.rows_mat = ((n + h->grid_mat - 1) / h->grid_mat + STEP_THREADS - 1) / STEP_THREADS * STEP_THREADS;
+  }
   // float32 / bfloat16: the staged kernels run on the forward operator only
   const int st32 = h->staged32 && !transpose;
   L.tma_cap = (basis == 3) ? (transpose ? h->tma_cap_t : h->tma_cap) : (st32 ? h->tma_cap : 0);
@@ -710,6 +730,7 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
     L.sell_off = h->sell_off;
     L.sell_col = h->sell_col;
     L.sell_val = h->sell_val;
+    L.sell_maxl = h->sell_maxl;
   }
   if (basis == 3) {
     const SegPlan& sp = transpose ? h->seg_t : h->seg_a;
@@ -741,7 +762,7 @@ StepLaunch step_args(const krylov_handle* h, const Operator& op, int transpose, 
   L.sk_tab = h->sk_tab;
   L.sk_mode = h->sk_mode;
   L.sk_copies = h->sk_copies;
-  L.fx_wb = sketch_word_bits(L.rows_per_cta, h->sk_copies);
+  L.fx_wb = sketch_word_bits(basis == 3 ? L.rows_mat : L.rows_per_cta, h->sk_copies);
   return L;
 }
 
@@ -993,7 +1014,9 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     NvtxRange cycle_range("restart cycle");
     NvtxPhase phase;
     phase.next("arnoldi steps");
-    launch_cycle_reset(h->cd, M, st);
+    // float-float materialize kernels: column 0's exact sketch starts from zero
+    const bool ff_mat = (basis == 3) && !(h->opt.ortho == KRYLOV_ORTHO_RGS) && !h->part_mode;
+    launch_cycle_reset(h->cd, M, st, ff_mat ? h->sk_acc : nullptr, ff_mat ? 3 * h->s : 0);
     CK(cudaEventRecord(h->ev[0], st));
     const bool rgs = (h->opt.ortho == KRYLOV_ORTHO_RGS);
     if (rgs) {
@@ -1073,6 +1096,9 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
                                                    (int64_t)nc * 3 * h->s, st));
         if (cs != KRYLOV_OK) return cs;
         launch_part_sketch_u(h->part_acc, h->part_E, nc, h->s, h->opt.zeta, h->part_wb, h->sd.U, st);
+      } else if (basis == 3) {  // exact sketches of the float-float materialize kernels
+        launch_sketch_finish(h->sk_acc, nc, h->s, h->sk_acc_stride, step_args(h, op, transpose, use32, thr, 0).fx_wb,
+                             h->opt.zeta, h->sd.U, st);
       } else {
         launch_sketch_reduce(h->sk_part, nc, h->grid, h->s, h->opt.zeta, h->sk_col_stride, h->sd.U, st);
       }
@@ -1841,6 +1867,8 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
   const int cps = h->staged32 ? s32_ctas_per_sm(opt.basis_dtype, s, h->sk_copies)
                               : step_ctas_per_sm(opt.basis_dtype, h->sk_mode, s, h->sk_copies, vals32);
   h->grid = std::max(1, std::min(h->num_sms * cps, (n + STEP_THREADS - 1) / STEP_THREADS));
+  if (opt.basis_dtype == 3 && h->sk_mode == SK_TAB8)
+    h->grid_mat = std::max(1, std::min(h->num_sms * mat_ctas_per_sm(s, h->sk_copies), (n + STEP_THREADS - 1) / STEP_THREADS));
   const int bb = basis_bytes(opt.basis_dtype);
   CKF(cudaMalloc(&h->W, (size_t)(m + 1) * h->ldw * bb));
   h->allocs.push_back(h->W);
@@ -1877,6 +1905,7 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
   h->grid_spmv_t = h->grid_spmv;
   h->part_cap = std::max(h->grid, std::min(h->num_sms * 32, (n + STEP_THREADS - 1) / STEP_THREADS));
   CKF(dalloc(h, &h->part, (size_t)h->part_cap * 8));
+  CKF(dalloc(h, &h->part_w, (size_t)h->part_cap * 2));
   if ((opt.basis_dtype == 3 || h->staged32) && KRYLOV_SELL) {
     const krylov_status ps3 = install_sell(h, vals32);
     if (ps3 != KRYLOV_OK) return fail(ps3);
@@ -1891,6 +1920,15 @@ static krylov_status create_impl(const krylov_csr* A, krylov_func f, int m, int 
   CKF(dalloc(h, &h->cd.R, (size_t)(m + 1) * m));
   CKF(dalloc(h, &h->cd.scal, 8));
   CKF(dalloc(h, &h->cd.counter, 4));
+  CKF(dalloc(h, &h->cd.sig2ff, (size_t)m + 1));
+  CKF(dalloc(h, &h->cd.piff, (size_t)m + 1));
+  CKF(dalloc(h, &h->cd.rff, (size_t)m + 1));
+  h->sk_acc_stride = 3 * (int64_t)s + 1;
+  {
+    long long* acc = nullptr;
+    CKF(dalloc(h, &acc, (size_t)(m + 1) * h->sk_acc_stride));
+    h->sk_acc = acc;
+  }
   CKF(cudaMemsetAsync(h->cd.counter, 0, 4 * sizeof(unsigned), h->st));
   CKF(cudaMemsetAsync(h->cd.R, 0, sizeof(double) * (size_t)(m + 1) * m, h->st));
   CKF(dalloc(h, &h->sd.U, (size_t)s * (m + 1)));

@@ -374,11 +374,29 @@ __global__ void sketch_table_kernel(int n, SketchSpec sp, SketchTable tab, int* 
   }
 }
 
-__global__ void cycle_reset_kernel(CycleDev cd, int m) {
+__global__ void cycle_reset_kernel(CycleDev cd, int m, unsigned long long* acc0, int n_acc0) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     cd.flags[0] = m;
     cd.flags[1] = 0;
   }
+  for (int e = threadIdx.x; e < n_acc0; e += blockDim.x) acc0[e] = 0ull;
+}
+
+// U[:, j] from the exact sketch of column j (float-float materialize
+// kernels): int64 word sums T_w over all CTAs and the exponent E of the
+// column's fixed-point scale, U = (T_0 2^(E-WB) + T_1 2^(E-2WB) + T_2
+// 2^(E-3WB)) / sqrt(zeta).  The sums are exact (|T_w| < 2^53 converts
+// exactly), so U does not depend on the order in which CTAs added them.
+__global__ void sketch_finish_kernel(const long long* acc, int ncols, int s, int64_t col_stride, int wb, double scale,
+                                     double* U) {
+  const int j = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncols || r >= s) return;
+  const long long* a = acc + (size_t)j * col_stride;
+  const int E = (int)a[3 * s];
+  const double v = fma((double)a[r], ldexp(1.0, E - wb),
+                       fma((double)a[s + r], ldexp(1.0, E - 2 * wb), (double)a[2 * s + r] * ldexp(1.0, E - 3 * wb)));
+  U[(size_t)j * s + r] = v * scale;
 }
 
 }  // namespace
@@ -394,7 +412,16 @@ SketchSpec make_sketch_spec(int s, int zeta, uint64_t seed) {
   return sp;
 }
 
-void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st) { cycle_reset_kernel<<<1, 32, 0, st>>>(cd, m); }
+void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st, void* acc0, int n_acc0) {
+  cycle_reset_kernel<<<1, 128, 0, st>>>(cd, m, static_cast<unsigned long long*>(acc0), n_acc0);
+}
+
+void launch_sketch_finish(const void* acc, int ncols, int s, int64_t col_stride, int wb, int zeta, double* U,
+                          cudaStream_t st) {
+  dim3 g((s + 127) / 128, ncols);
+  sketch_finish_kernel<<<g, 128, 0, st>>>(static_cast<const long long*>(acc), ncols, s, col_stride, wb,
+                                          1.0 / std::sqrt((double)zeta), U);
+}
 
 void launch_norm_b(const double* b, int n, double* part, int grid, const CycleDev& cd, cudaStream_t st) {
   const int rpc = (n + grid - 1) / grid;

@@ -17,6 +17,10 @@ struct CycleDev {
                    // [5] bound on ||w_1||^2 of the next cycle, [6] bound on
                    // ||w_{j+1}|| for the next materialized column (fixed-point sketch scale)
   unsigned* counter;  // arrival counters of the last-block reducers (zeroed)
+  // float-float pairs of the float-float step kernels (the next kernel reads these)
+  float2* sig2ff;  // (m+1) ||w_j||^2
+  float2* piff;    // (m+1) ||p_j||^2
+  float2* rff;     // (m+1) R[j+1, j]
 };
 
 enum : int { ERR_SKETCH = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
@@ -51,11 +55,17 @@ struct StepLaunch {
   void* p_out;
   void* sk_part;     // sketch partials of column j: [grid][s] (double or float)
   double* part;      // scalar partials [grid][2 + MAX_WINDOW]
+  double* part_w;    // float-float basis: ||w_j||^2 CTA partials, half j & 1 of [2][part_w_stride]
+  int part_w_stride;
+  void* sk_acc;      // float-float basis: exact sketch of column j at j * sk_acc_stride: [3][s] int64 word
+  int64_t sk_acc_stride;  // sums, then E (int64); column j + 1's is zeroed by the kernel of column j
   double thr;        // breakdown threshold (relative)
   int s, zeta;
   uint64_t seed;
   int grid;          // number of CTAs (persistent)
   int rows_per_cta;
+  int grid_mat;      // float-float materialize kernel: CTAs and rows per CTA (one CTA
+  int rows_mat;      // per SM with the staged row streams; else grid, rows_per_cta)
   int m;             // restart length (leading dimension of R is m+1)
   SketchTable sk_tab;
   int sk_mode;       // SK_* : stored table or regeneration in the kernel
@@ -92,6 +102,7 @@ struct StepLaunch {
   // 256-row tile g holds entries [sell_off[g], sell_off[g + 1]) of sell_col /
   // sell_val, padded to the tile's longest row, entry q of row r at q * 256 + r
   const int* sell_off;      // [tiles + 1]
+  int sell_maxl;            // longest row of any tile (sizes the product kernel's stages)
   const int16_t* sell_col;  // col - row (padding: 0)
   const void* sell_val;     // float or float2 like val (padding: 0)
 };
@@ -154,8 +165,10 @@ struct RgsArgs {
 
 // basis dtype codes (krylov_basis)
 int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap);
-int sell_ctas_per_sm(int vals_f32);
+int sell_ctas_per_sm(int vals_f32, int maxl);
+size_t sell_smem_bytes(int vals_f32, int maxl);  // dynamic shared memory of the float-float sliced product
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32);
+int mat_ctas_per_sm(int s, int copies);
 void launch_step(int basis, const StepLaunch& L, const CycleDev& cd, int m, cudaStream_t st);
 // float32 / bfloat16 bases with staged row streams (step32_kernels.cu): the
 // materialize+sketch kernel and the product kernel of step L.j
@@ -214,7 +227,11 @@ cudaError_t csr_delta16(int n, const int* rp, const int* ci, int16_t* dcol, cuda
 cudaError_t split_values(int64_t nnz, const double* v, float2* vff, cudaStream_t st);
 cudaError_t transpose_csr(int n, int64_t nnz, const int* rp, const int* ci, const double* v, int* rpt,
                           int* cit, double* vt, int* work, cudaStream_t st);
-void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st);
+// acc0 / n_acc0: the exact sketch accumulator of column 0 (float-float basis), zeroed here
+void launch_cycle_reset(const CycleDev& cd, int m, cudaStream_t st, void* acc0 = nullptr, int n_acc0 = 0);
+// U from the exact int64 sketches of the float-float materialize kernels
+void launch_sketch_finish(const void* acc, int ncols, int s, int64_t col_stride, int wb, int zeta, double* U,
+                          cudaStream_t st);
 void launch_gather_column(const double* B, int64_t n, int ncols, int r, double* b, cudaStream_t st);
 void launch_zero_columns(double* X, int64_t n, int64_t ld, int ncols, cudaStream_t st);
 void launch_scatter_column(const double* x, int64_t n, int ncols, int r, double* X, cudaStream_t st);

@@ -299,9 +299,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   const int C = L.sk_copies;
   int* bins = reinterpret_cast<int*>(smem);  // [NW][s][C]
   __shared__ float red[64];
-  __shared__ int s_last;
-  __shared__ FxScale s_fx;
-  __shared__ ff s_h[MAX_WINDOW + 1];
+  __shared__ MatCoef s_c;
   const int j = L.j;
   if (cd.flags[0] < j) return;
   const int lo = MAT ? max(0, j - L.k) : j;
@@ -312,14 +310,19 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
     for (int e = threadIdx.x; e < nb / 4; e += blockDim.x) b4[e] = make_int4(0, 0, 0, 0);
     for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
   }
-  if (threadIdx.x == 0) {  // per-CTA prologue (float64 work done once)
-    s_fx = fx_scale(L, cd, MAT ? 1 : 0);
-    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
-    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
-    s_h[MAX_WINDOW] = MAT ? ff_from_double(c[MAX_WINDOW]) : ff{1.f, 0.f};
+  if (MAT) {  // the coefficients, from the partials of the kernels before (every CTA)
+    if (!mat_coefficients<KW>(L, cd, s_c)) return;  // column j - 1 ended the cycle
+  } else if (threadIdx.x == 0) {  // the start vector, stored as it is
+    s_c.fx = fx_scale(L, cd, 0);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_c.h[q] = ff{0.f, 0.f};
+    s_c.rho = ff{1.f, 0.f};
   }
   __syncthreads();
-  const FxScale fxs = s_fx;
+  if (blockIdx.x == gridDim.x - 1 && j < L.m) {  // the next column's exact sketch starts from zero
+    unsigned long long* nx = fx_acc_of(L, j + 1);
+    for (int e = threadIdx.x; e < 3 * L.s; e += blockDim.x) nx[e] = 0ull;
+  }
+  const FxScale fxs = s_c.fx;
   const int cp = lane & (C - 1);
   const int sC = L.s * C;
 
@@ -330,10 +333,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
   const float2* Wq[KW];
 #pragma unroll
   for (int q = 0; q < KW; ++q) {
-    h[q] = s_h[q];
+    h[q] = s_c.h[q];
     Wq[q] = W + (int64_t)(lo + (q < nl ? q : 0)) * L.ldw;
   }
-  const ff rho = s_h[MAX_WINDOW];
+  const ff rho = s_c.rho;
   const SketchSpec sp = spec_of(L);
   const uint32_t inv_s = sketch_inv_s(L.s);
   ffacc acc_sig;
@@ -385,21 +388,17 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
     do_row(a, i);
     if (i2 < r1) do_row(b, i2);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  const double v = block_sum_ff(acc_sig.result(), red, red + 32);
-  if (threadIdx.x == 0) part[0] = v;
+  const ff v = block_sum_ff_pair(acc_sig.result(), red, red + 32);
+  if (threadIdx.x == 0) st_part_ff(part_w_of(L, j) + blockIdx.x, v);
   __syncthreads();
-  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
-  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value<NW>(bins, L.s, C, b, fxs, L.fx_wb);
+  unsigned long long* acc = fx_acc_of(L, j);
+  fx_accumulate([&](int b, int c, int w) { return (long long)bins[(w * L.s + b) * C + c]; }, L.s, C, acc);
   if (bad) atomicOr(&cd.flags[2], ERR_SKETCH);
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x < 32) {
-    const double t = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
-    if (threadIdx.x == 0) {
-      (void)reduce_mat(L, cd, t, MAT ? 1 : 0);
-      *cd.counter = 0u;
-    }
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) reinterpret_cast<long long*>(acc)[3 * L.s] = fxs.E;
+    if (MAT) mat_coefficients_store(L, cd, s_c);
   }
+  if (j == L.m) ff_mat_finish(L, cd, MAT ? 1 : 0);  // else the next materialize kernel sums the partials
 }
 
 // Materialize + sketch with the row streams staged in shared memory (packed
@@ -411,7 +410,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
 // of 256 rows (16-byte aligned) and a partial last tile is copied rounded up
 // to 16 rows (the row arrays are padded to the slot stride).
 constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
-constexpr int MT_ROWS = STEP_THREADS;
+// One CTA of MT_THREADS threads per SM (a row per thread in a tile of
+// MT_ROWS rows): two CTAs per SM drifted apart as the product kernel's did
+// (the second finished ~3.5 us after the first, its SM half idle meanwhile).
+constexpr int MT_THREADS = 512;
+constexpr int MT_ROWS = MT_THREADS;
 #ifndef KRYLOV_MT_STAGES
 #define KRYLOV_MT_STAGES 3
 #endif
@@ -426,39 +429,24 @@ __host__ __device__ constexpr size_t mt_stage_bytes(int kw) {
 // copies the words a warp adds at one time sit in 32 different banks (word
 // stride 3 is odd).  C (copies) and Z (zeta, 0 = runtime value <= 8) are
 // compile-time so that the entry loop carries no parameter loads.
-template <int C>
-__device__ __forceinline__ double fx_value_il(const int* bins, int b, const FxScale& f, int WB) {
-  long long t[3];
-#pragma unroll
-  for (int w = 0; w < 3; ++w) {
-    long long u = 0;
-#pragma unroll 8
-    for (int c = 0; c < C; ++c) u += bins[(b * C + ((c + b) & (C - 1))) * 3 + w];
-    t[w] = u;
-  }
-  const long long low = t[1] * (1ll << WB) + t[2];
-  return fma((double)t[0], pow2d(f.E - WB), (double)low * pow2d(f.E - 3 * WB));
-}
 
 template <bool MAT, int KW, int C, int Z>
-__global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
+__global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
   constexpr int NW = 3;
   static_assert(C == 16 || C == 32, "lane copies of the bins");
   constexpr size_t SB = mt_stage_bytes(KW);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[MT_STAGES];
   __shared__ float red[64];
-  __shared__ int s_last;
-  __shared__ FxScale s_fx;
-  __shared__ ff s_h[MAX_WINDOW + 1];
+  __shared__ MatCoef s_c;
   const int lane = threadIdx.x & 31;
   int* bins = reinterpret_cast<int*>(smem);  // [s][C][NW]
   unsigned char* stages = smem + align16(bins_bytes(3, L.s, C));
   const int j = L.j;
   const int lo = MAT ? max(0, j - L.k) : j;
   const int nl = j - lo;
-  const int r0 = blockIdx.x * L.rows_per_cta;
-  const int r1 = min(L.n, r0 + L.rows_per_cta);
+  const int r0 = blockIdx.x * L.rows_mat;
+  const int r1 = min(L.n, r0 + L.rows_mat);
   const int ntiles = (r1 > r0) ? (r1 - r0 + MT_ROWS - 1) / MT_ROWS : 0;
 
   const float2* W = static_cast<const float2*>(L.W);
@@ -518,7 +506,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
   // everything above is independent of the kernel just before; p_{j-1} and
   // the coefficients are not
   pdl_wait();
-  if (cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
+  if (!MAT && cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
     if (threadIdx.x == 0)  // complete the phases and let the copies land before leaving
       for (int t = 0; t < npre; ++t) {
         mbar_arrive(&bars[t]);
@@ -526,21 +514,35 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
       }
     return;
   }
-  if (threadIdx.x == 0) {
+  // p_{j-1} is read even if the cycle has ended (mat_coefficients tells):
+  // the copies are harmless and start early
+  if (threadIdx.x == 0)
     for (int t = 0; t < npre; ++t) issue_p(t);
-    s_fx = fx_scale(L, cd, MAT ? 1 : 0);  // per-CTA prologue, overlapping the first copies
-    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
-    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? ff_neg(ff_from_double(c[q])) : ff{0.f, 0.f};
-    s_h[MAX_WINDOW] = MAT ? ff_from_double(c[MAX_WINDOW]) : ff{1.f, 0.f};
+  // the coefficients, from the partials of the kernels before (every CTA,
+  // while the first tiles land)
+  if (MAT) {
+    if (!mat_coefficients<KW>(L, cd, s_c)) {  // the cycle ended before column j
+      if (threadIdx.x == 0)  // let the issued copies land before leaving
+        for (int t = 0; t < npre; ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+      return;
+    }
+  } else if (threadIdx.x == 0) {  // the start vector, stored as it is
+    s_c.fx = fx_scale(L, cd, 0);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_c.h[q] = ff{0.f, 0.f};
+    s_c.rho = ff{1.f, 0.f};
   }
   __syncthreads();
-  const FxScale fxs = s_fx;
+  if (blockIdx.x == gridDim.x - 1 && j < L.m) {  // the next column's exact sketch starts from zero
+    unsigned long long* nx = fx_acc_of(L, j + 1);
+    for (int e = threadIdx.x; e < 3 * L.s; e += blockDim.x) nx[e] = 0ull;
+  }
+  const FxScale fxs = s_c.fx;
   int* const mybins = bins + (lane & (C - 1)) * NW;
   const int zeta = (Z > 0) ? Z : L.zeta;
   ff h[KW];
 #pragma unroll
-  for (int q = 0; q < KW; ++q) h[q] = s_h[q];
-  const ff rho = s_h[MAX_WINDOW];
+  for (int q = 0; q < KW; ++q) h[q] = s_c.h[q];
+  const ff rho = s_c.rho;
   ffacc acc_sig;
   bool timed_out = false;
   int last_issued = min(ntiles, MT_STAGES) - 1;
@@ -594,20 +596,16 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_mat_tma_kernel(const StepL
     for (int t = max(0, last_issued - MT_STAGES + 1); t <= last_issued; ++t)
       (void)mbar_wait_bounded(&bars[t % MT_STAGES], (uint32_t)(t / MT_STAGES) & 1u, TMA_WAIT_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  const double v = block_sum_ff(acc_sig.result(), red, red + 32);
-  if (threadIdx.x == 0) part[0] = v;
+  const ff v = block_sum_ff_pair(acc_sig.result(), red, red + 32);
+  if (threadIdx.x == 0) st_part_ff(part_w_of(L, j) + blockIdx.x, v);
   __syncthreads();
-  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
-  for (int b = threadIdx.x; b < L.s; b += blockDim.x) out[b] = fx_value_il<C>(bins, b, fxs, L.fx_wb);
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x < 32) {
-    const double tsum = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
-    if (threadIdx.x == 0) {
-      (void)reduce_mat(L, cd, tsum, MAT ? 1 : 0);
-      *cd.counter = 0u;
-    }
+  unsigned long long* acc = fx_acc_of(L, j);
+  fx_accumulate([&](int b, int c, int w) { return (long long)bins[(b * C + c) * NW + w]; }, L.s, C, acc);
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) reinterpret_cast<long long*>(acc)[3 * L.s] = fxs.E;
+    if (MAT) mat_coefficients_store(L, cd, s_c);
   }
+  if (j == L.m) ff_mat_finish(L, cd, MAT ? 1 : 0);  // else the next materialize kernel sums the partials
 }
 
 // Four consecutive matrix values, read as one aligned 16-byte (float) or two
@@ -638,9 +636,6 @@ template <typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaunch L, const CycleDev cd) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* stage = reinterpret_cast<float2*>(smem);  // [warps][STAGE] (p, e)
-  __shared__ float rhi[32], rlo[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
   const int j = L.j;
   if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -732,26 +727,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_spmv_kernel(const StepLaun
         if (q < nd) acc_dot[q].add_prod(wq[q], p);
     }
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;  // nd is uniform across the block
-    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (L.n_long > 0) return;  // the long-row kernel reduces this step
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  ff_spmv_finish<KW>(L, cd, acc_pi, acc_dot, nd, L.part + (size_t)blockIdx.x * NQ, L.rgs && L.n_long == 0,
+                     L.part, (int)gridDim.x, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -796,9 +773,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
   constexpr int EA = DI ? 8 : 4;  // staged nonzero ranges start on 16-byte boundaries
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[TMA_STAGES];
-  __shared__ float rhi[32], rlo[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
   const int j = L.j;
   const int cap = L.tma_cap;
   const size_t sb = tma_stage_bytes<AT, DI>(cap);
@@ -913,26 +887,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
     for (int t = max(0, last_issued - TMA_STAGES + 1); t <= last_issued; ++t)
       (void)mbar_wait_bounded(&bars[t % TMA_STAGES], (uint32_t)(t / TMA_STAGES) & 1u, TMA_WAIT_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;  // nd is uniform across the block
-    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (L.n_long > 0) return;  // the long-row kernel reduces this step
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  ff_spmv_finish<KW>(L, cd, acc_pi, acc_dot, nd, L.part + (size_t)blockIdx.x * NQ, L.rgs && L.n_long == 0,
+                     L.part, (int)gridDim.x, nullptr, 0);
 }
 
 // Product kernel on the sliced layout: a 256-row tile's entries padded to the
@@ -940,12 +896,27 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_tma_kernel(const Step
 // column offsets col - row, padding offset 0 and value 0), so a tile is two
 // contiguous bulk copies, entry q of every thread is one conflict-free shared
 // load, and a row needs neither row_ptr nor a per-entry bound test: the
-// entry loop is unrolled for the tile's L (uniform over the CTA).  Padding
-// adds exact zeros after a row's own entries, so every row's sum equals the
-// CSR kernels' (storage order).
+// entry loop is unrolled for the tile's L (uniform over a 256-thread group).
+// Padding adds exact zeros after a row's own entries, so every row's sum
+// equals the CSR kernels' (storage order).
+//
+// A stage holds SELL_GROUPS consecutive tiles (two bulk copies, the tiles
+// being contiguous) and group g of the CTA's 256-thread groups forms the
+// rows of tile g; stages are sized by the operator's longest tile row.
+// Resident CTAs of one SM drift apart (the warp scheduler favours the
+// oldest: with four 256-thread CTAs per SM the last finished ~5 us after the
+// first), and groups that meet at every stage finish together but wait for
+// each other at the barrier.  Measured per Arnoldi step on the 128^3
+// convection-diffusion operator: four CTAs of one group 54.9 us, one CTA of
+// four groups 54.3 us, two CTAs of two groups 53.4 us.
+constexpr int SELL_GROUPS = 2;
+constexpr int SELL_THREADS = SELL_GROUPS * TMA_ROWS;
+constexpr int SELL_STAGES = 2;
+
+// bytes of one stage for an operator whose longest tile row is maxl
 template <typename AT>
-__host__ __device__ constexpr size_t sell_stage_bytes() {
-  return (size_t)SELL_MAXL * TMA_ROWS * (2 + sizeof(AT));
+__host__ __device__ constexpr size_t sell_stage_bytes(int maxl) {
+  return align16((size_t)SELL_GROUPS * maxl * TMA_ROWS * 2) + (size_t)SELL_GROUPS * maxl * TMA_ROWS * sizeof(AT);
 }
 
 template <int NL, typename AT>
@@ -964,17 +935,11 @@ __device__ __forceinline__ ff sell_row(const int16_t* cs, const AT* vs, const fl
 }
 
 template <typename AT, int KW>
-__global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_sell_kernel(const StepLaunch L, const CycleDev cd) {
+__global__ void __launch_bounds__(SELL_THREADS, SELL_GROUPS == 1 ? 3 : 4 / SELL_GROUPS) ff_spmv_sell_kernel(const StepLaunch L, const CycleDev cd) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[TMA_STAGES];
-  __shared__ float rhi[32], rlo[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
-  constexpr size_t SB = sell_stage_bytes<AT>();
-  auto col_st = [&](int st) { return reinterpret_cast<const int16_t*>(smem + (size_t)st * SB); };
-  auto val_st = [&](int st) {
-    return reinterpret_cast<const AT*>(smem + (size_t)st * SB + (size_t)SELL_MAXL * TMA_ROWS * 2);
-  };
+  __shared__ __align__(8) uint64_t bars[SELL_STAGES];
+  const size_t SB = sell_stage_bytes<AT>(L.sell_maxl);
+  const size_t VOFF = align16((size_t)SELL_GROUPS * L.sell_maxl * TMA_ROWS * 2);  // value part of a stage
   const int j = L.j;
   const float2* W = static_cast<const float2*>(L.W);
   const float2* Wj = W + (int64_t)j * L.ldw;
@@ -987,41 +952,48 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_sell_kernel(const Ste
   const int r0 = blockIdx.x * L.rows_spmv;
   const int r1 = min(L.n, r0 + L.rows_spmv);
   const int ntiles = (r1 > r0) ? (r1 - r0 + TMA_ROWS - 1) / TMA_ROWS : 0;
+  const int nst = (ntiles + SELL_GROUPS - 1) / SELL_GROUPS;  // stages of SELL_GROUPS tiles
   const int g0 = r0 / TMA_ROWS;  // global tile of the CTA's first tile
+  const int grp = (int)threadIdx.x / TMA_ROWS, k = (int)threadIdx.x % TMA_ROWS;
   if (threadIdx.x == 0) {
-    for (int q = 0; q < TMA_STAGES; ++q) mbar_init(&bars[q], 1);
+    for (int q = 0; q < SELL_STAGES; ++q) mbar_init(&bars[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  auto issue = [&](int t) {  // thread 0
-    const int st = t % TMA_STAGES;
-    const int e0 = __ldg(L.sell_off + g0 + t), e1 = __ldg(L.sell_off + g0 + t + 1);
+  auto issue = [&](int t) {  // thread 0: the tiles of stage t, two copies
+    const int st = t % SELL_STAGES;
+    const int ta = g0 + t * SELL_GROUPS, tb = g0 + min(ntiles, (t + 1) * SELL_GROUPS);
+    const int e0 = __ldg(L.sell_off + ta), e1 = __ldg(L.sell_off + tb);
     const uint32_t bc = (uint32_t)(e1 - e0) * 2u, bv = (uint32_t)(e1 - e0) * (uint32_t)sizeof(AT);
     mbar_arrive_expect_tx(&bars[st], bc + bv);
     if (e1 > e0) {
       unsigned char* base = smem + (size_t)st * SB;
       bulk_g2s_stream(base, L.sell_col + e0, bc, &bars[st]);
-      bulk_g2s_stream(base + (size_t)SELL_MAXL * TMA_ROWS * 2, sval + e0, bv, &bars[st]);
+      bulk_g2s_stream(base + VOFF, sval + e0, bv, &bars[st]);
     }
   };
   if (threadIdx.x == 0)
-    for (int t = 0; t < min(ntiles, TMA_STAGES); ++t) issue(t);
+    for (int t = 0; t < min(nst, SELL_STAGES); ++t) issue(t);
   pdl_wait();
   if (cd.flags[1] != 0) {
     if (threadIdx.x == 0)
-      for (int t = 0; t < min(ntiles, TMA_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
+      for (int t = 0; t < min(nst, SELL_STAGES); ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
     return;
   }
   ffacc acc_pi;
   ffacc acc_dot[KW];
   bool timed_out = false;
-  int last_issued = min(ntiles, TMA_STAGES) - 1;
-  for (int t = 0; t < ntiles; ++t) {
-    const int st = t % TMA_STAGES;
-    const uint32_t par = (uint32_t)(t / TMA_STAGES) & 1u;
-    const int i = r0 + t * TMA_ROWS + (int)threadIdx.x;
-    const bool valid = i < r1;
-    const int nl = (__ldg(L.sell_off + g0 + t + 1) - __ldg(L.sell_off + g0 + t)) / TMA_ROWS;
+  int last_issued = min(nst, SELL_STAGES) - 1;
+  for (int t = 0; t < nst; ++t) {
+    const int st = t % SELL_STAGES;
+    const uint32_t par = (uint32_t)(t / SELL_STAGES) & 1u;
+    const int tl = t * SELL_GROUPS + grp;  // this group's tile (local index)
+    const int i = r0 + tl * TMA_ROWS + k;
+    const bool valid = tl < ntiles && i < r1;
+    // this tile's place in the stage and its row length (uniform over the group)
+    const int ea = __ldg(L.sell_off + g0 + t * SELL_GROUPS);
+    const int eg = valid ? __ldg(L.sell_off + g0 + tl) : ea;
+    const int nl = valid ? (__ldg(L.sell_off + g0 + tl + 1) - eg) / TMA_ROWS : 0;
     ff wq[KW];
     if (valid) {
 #pragma unroll
@@ -1030,11 +1002,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_sell_kernel(const Ste
     }
     if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
     if (valid && !timed_out) {
-      const int16_t* cs = col_st(st);
-      const AT* vs = val_st(st);
-      const int k = (int)threadIdx.x;
+      const int16_t* cs = reinterpret_cast<const int16_t*>(smem + (size_t)st * SB) + (eg - ea);
+      const AT* vs = reinterpret_cast<const AT*>(smem + (size_t)st * SB + VOFF) + (eg - ea);
       ff p;
-      switch (nl) {  // the same for every thread of the CTA
+      switch (nl) {  // the same for every thread of the group
         case 1: p = sell_row<1>(cs, vs, Wj, i, k); break;
         case 2: p = sell_row<2>(cs, vs, Wj, i, k); break;
         case 3: p = sell_row<3>(cs, vs, Wj, i, k); break;
@@ -1056,38 +1027,21 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_sell_kernel(const Ste
       for (int q = 0; q < KW; ++q)
         if (q < nd) acc_dot[q].add_prod(wq[q], p);
     }
-    __syncthreads();  // every thread is done with stage st
-    if (threadIdx.x == 0 && t + TMA_STAGES < ntiles && !timed_out) {
+    __syncthreads();  // every group is done with stage st
+    if (threadIdx.x == 0 && t + SELL_STAGES < nst && !timed_out) {
       fence_proxy_async();
-      issue(t + TMA_STAGES);
-      last_issued = t + TMA_STAGES;
+      issue(t + SELL_STAGES);
+      last_issued = t + SELL_STAGES;
     }
   }
   pdl_trigger();
   if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
   if (threadIdx.x == 0 && timed_out) {
-    for (int t = max(0, last_issued - TMA_STAGES + 1); t <= last_issued; ++t)
-      (void)mbar_wait_bounded(&bars[t % TMA_STAGES], (uint32_t)(t / TMA_STAGES) & 1u, TMA_WAIT_NS);
+    for (int t = max(0, last_issued - SELL_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % SELL_STAGES], (uint32_t)(t / SELL_STAGES) & 1u, TMA_WAIT_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;
-    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double tt = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = tt;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  ff_spmv_finish<KW>(L, cd, acc_pi, acc_dot, nd, L.part + (size_t)blockIdx.x * NQ, L.rgs && L.n_long == 0,
+                     L.part, (int)gridDim.x, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1146,7 +1100,7 @@ void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
                    : ((L.zeta == 8) ? pick(ff_mat_tma_kernel<MAT, 2, 16, 8>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 16, 8>)
                                     : pick(ff_mat_tma_kernel<MAT, 2, 16, 0>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 16, 0>));
       raise_smem_limit((const void*)k, smem);
-      launch_pdl(k, L.grid, smem, st, L, cd);
+      launch_pdl_threads(k, L.grid_mat, MT_THREADS, smem, st, L, cd);
       break;
     }
     case SK_TAB16: launch_ff_mat_t<MAT, SK_TAB16>(L, cd, st); break;
@@ -1176,9 +1130,6 @@ template <typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const StepLaunch L, const CycleDev cd) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ float rhi[32], rlo[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
   const int j = L.j;
   const int lcap = L.lcap;
   const size_t sb = seg_stage_bytes<AT>(lcap, L.seg_cap);
@@ -1297,26 +1248,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const Step
     for (int t = max(0, last_issued - 1); t <= last_issued; ++t)
       (void)mbar_wait_bounded(&bars[t & 1], (uint32_t)(t >> 1) & 1u, TMA_WAIT_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;  // nd is uniform across the block
-    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (L.n_long > 0) return;  // the long-row kernel reduces this step
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double tq = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = tq;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  ff_spmv_finish<KW>(L, cd, acc_pi, acc_dot, nd, L.part + (size_t)blockIdx.x * NQ, L.rgs && L.n_long == 0,
+                     L.part, (int)gridDim.x, nullptr, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1334,8 +1267,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const Step
 template <typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLaunch L, const CycleDev cd) {
   __shared__ float rhi[32], rlo[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
   pdl_wait();  // w_j and the products of the other rows are complete
   if (cd.flags[1] != 0) return;  // breakdown in this cycle: no further products
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -1380,29 +1311,8 @@ __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLa
   }
   pdl_trigger();
   // per-CTA partials: only the threads that finished rows hold nonzero sums
-  double* part = L.part_long + (size_t)blockIdx.x * NQ;
-  double v = block_sum_ff(acc_pi.result(), rhi, rlo);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;  // nd is uniform across the block
-    v = block_sum_ff(acc_dot[q].result(), rhi, rlo);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    double t = 0.0;
-    if (q >= 1 && q < 2 + nd) {
-      t = warp_sum_partials(L.part, L.grid_spmv, NQ, q);
-      t += warp_sum_partials(L.part_long, (int)gridDim.x, NQ, q);
-    }
-    if ((threadIdx.x & 31) == 0) tot[q] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  ff_spmv_finish<KW>(L, cd, acc_pi, acc_dot, nd, L.part_long + (size_t)blockIdx.x * NQ, L.rgs != 0, L.part, L.grid_spmv,
+                     L.part_long, (int)gridDim.x);
 }
 
 constexpr size_t FF_STAGE_SMEM = (size_t)(STEP_THREADS / 32) * STAGE * sizeof(float2);
@@ -1429,9 +1339,9 @@ void launch_ff_spmv_main(const StepLaunch& L, const CycleDev& cd, cudaStream_t s
   }
   if (L.sell_col != nullptr) {
     auto k = ff_spmv_sell_kernel<AT, KW>;
-    const size_t smem = TMA_STAGES * sell_stage_bytes<AT>();
+    const size_t smem = SELL_STAGES * sell_stage_bytes<AT>(L.sell_maxl);
     raise_smem_limit((const void*)k, smem);
-    launch_pdl(k, L.grid_spmv, smem, st, L, cd);
+    launch_pdl_threads(k, L.grid_spmv, SELL_THREADS, smem, st, L, cd);
     return;
   }
   if (L.tma_cap > 0 && L.dcol != nullptr) {
@@ -1478,10 +1388,10 @@ void launch_ff_step(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
 }
 
 template <typename K>
-int occ(K kern, size_t smem) {
+int occ(K kern, size_t smem, int threads = STEP_THREADS) {
   raise_smem_limit((const void*)kern, smem);
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, STEP_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem);
   return b < 1 ? 1 : b;
 }
 
@@ -1520,16 +1430,28 @@ int spmv_ctas_per_sm(int vals_f32, int tma_cap, int seg_cap, int lcap) {
   return vals_f32 ? occ(ff_spmv_kernel<float, 2>, FF_STAGE_SMEM) : occ(ff_spmv_kernel<float2, 2>, FF_STAGE_SMEM);
 }
 
-int sell_ctas_per_sm(int vals_f32) {
-  return vals_f32 ? occ(ff_spmv_sell_kernel<float, 2>, TMA_STAGES * sell_stage_bytes<float>())
-                  : occ(ff_spmv_sell_kernel<float2, 2>, TMA_STAGES * sell_stage_bytes<float2>());
+size_t sell_smem_bytes(int vals_f32, int maxl) {
+  return SELL_STAGES * (vals_f32 ? sell_stage_bytes<float>(maxl) : sell_stage_bytes<float2>(maxl));
 }
 
+int sell_ctas_per_sm(int vals_f32, int maxl) {
+  return vals_f32 ? occ(ff_spmv_sell_kernel<float, 2>, SELL_STAGES * sell_stage_bytes<float>(maxl), SELL_THREADS)
+                  : occ(ff_spmv_sell_kernel<float2, 2>, SELL_STAGES * sell_stage_bytes<float2>(maxl), SELL_THREADS);
+}
+
+// Resident CTAs per SM of the float-float materialize kernel with the row
+// streams staged by bulk copies (MT_THREADS threads per CTA).
+int mat_ctas_per_sm(int s, int copies) {
+  return (copies == 32) ? occ(ff_mat_tma_kernel<true, 2, 32, 8>, mt_smem(s, copies, 2), MT_THREADS)
+                        : occ(ff_mat_tma_kernel<true, 2, 16, 8>, mt_smem(s, copies, 2), MT_THREADS);
+}
+
+// CTAs per SM of the 256-thread step kernels (for the float-float basis: of
+// the materialize kernel without staged row streams; the persistent wave of
+// the other per-row kernels of a cycle is sized from it).
 int step_ctas_per_sm(int basis, int sk_mode, int s, int copies, int vals_f32) {
-  if (basis == 3)
-    return (sk_mode == SK_TAB8) ? ((copies == 32) ? occ(ff_mat_tma_kernel<true, 2, 32, 8>, mt_smem(s, copies, 2))
-                                                  : occ(ff_mat_tma_kernel<true, 2, 16, 8>, mt_smem(s, copies, 2)))
-                                : occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
+  (void)sk_mode;
+  if (basis == 3) return occ(ff_mat_kernel<true, SK_TAB8, 2>, bins_bytes(3, s, copies));
   const size_t smem = fused_smem(basis, s, copies);
   if (basis == 0)
     return vals_f32 ? occ(step_kernel<double, float, true, true, SK_TAB8>, smem)
