@@ -1306,13 +1306,16 @@ constexpr int BK_NB = 64;
 constexpr int BK_MAX_CYCLES = 16;  // block exp rows stored for at most this many cycles
 
 template <typename T>
-cudaError_t balloc(BlockWs& b, T** p, size_t count) {
+cudaError_t balloc(BlockWs& b, T** p, size_t count, cudaStream_t st) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
   if (e != cudaSuccess) return e;
   b.allocs.push_back(q);
   *p = static_cast<T*>(q);
-  return cudaMemset(q, 0, std::max<size_t>(count, 1) * sizeof(T));
+  // zeroed on the stream that uses it: the block kernels run on the
+  // instance's non-blocking stream, which a plain cudaMemset (legacy default
+  // stream) does not order against (the zeroing could land after them)
+  return cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), st);
 }
 
 void free_block_ws(BlockWs& b) {
@@ -1345,17 +1348,17 @@ krylov_status ensure_block_ws(krylov_handle* h, int levels) {
     float* w = nullptr;
     float* p0 = nullptr;
     float* p1 = nullptr;
-    CK(balloc(b, &w, (size_t)(M + 1) * n * BK_NB * fl));
-    CK(balloc(b, &p0, n * BK_NB * fl));
-    CK(balloc(b, &p1, n * BK_NB * fl));
+    CK(balloc(b, &w, (size_t)(M + 1) * n * BK_NB * fl, h->st));
+    CK(balloc(b, &p0, n * BK_NB * fl, h->st));
+    CK(balloc(b, &p1, n * BK_NB * fl, h->st));
     b.W = w;
     b.P[0] = p0;
     b.P[1] = p1;
-    CK(balloc(b, &b.part, (size_t)h->num_sms * 8 * NQ_HOST * BK_NB));
-    CK(balloc(b, &b.acc, (size_t)(M + 1) * 3 * s * BK_NB));
-    CK(balloc(b, &b.E, (size_t)(M + 1) * BK_NB));
-    CK(balloc(b, &b.active, (size_t)BK_NB));
-    CK(balloc(b, &b.counter, 4));
+    CK(balloc(b, &b.part, (size_t)h->num_sms * 8 * NQ_HOST * BK_NB, h->st));
+    CK(balloc(b, &b.acc, (size_t)(M + 1) * 3 * s * BK_NB, h->st));
+    CK(balloc(b, &b.E, (size_t)(M + 1) * BK_NB, h->st));
+    CK(balloc(b, &b.active, (size_t)BK_NB, h->st));
+    CK(balloc(b, &b.counter, 4, h->st));
     BatchStride& bs = b.bs;
     bs.flags = 4;
     bs.sig2 = M + 1;
@@ -1372,22 +1375,22 @@ krylov_status ensure_block_ws(krylov_handle* h, int levels) {
     bs.misc = 8;
     bs.S0 = (int64_t)std::max<size_t>(2 * (size_t)b.rows_cap * MM, MM);
     bs.fcol = M;
-    CK(balloc(b, &b.cd.flags, (size_t)bs.flags * BK_NB));
-    CK(balloc(b, &b.cd.sig2, (size_t)bs.sig2 * BK_NB));
-    CK(balloc(b, &b.cd.pi, (size_t)bs.pi * BK_NB));
-    CK(balloc(b, &b.cd.coef, (size_t)bs.coef * BK_NB));
-    CK(balloc(b, &b.cd.R, (size_t)bs.R * BK_NB));
-    CK(balloc(b, &b.cd.scal, (size_t)bs.scal * BK_NB));
+    CK(balloc(b, &b.cd.flags, (size_t)bs.flags * BK_NB, h->st));
+    CK(balloc(b, &b.cd.sig2, (size_t)bs.sig2 * BK_NB, h->st));
+    CK(balloc(b, &b.cd.pi, (size_t)bs.pi * BK_NB, h->st));
+    CK(balloc(b, &b.cd.coef, (size_t)bs.coef * BK_NB, h->st));
+    CK(balloc(b, &b.cd.R, (size_t)bs.R * BK_NB, h->st));
+    CK(balloc(b, &b.cd.scal, (size_t)bs.scal * BK_NB, h->st));
     b.cd.counter = b.counter;
-    CK(balloc(b, &b.sd.U, (size_t)bs.U * BK_NB));
-    CK(balloc(b, &b.sd.Tw, (size_t)bs.Tw * BK_NB));
-    CK(balloc(b, &b.sd.Tinv, (size_t)bs.Tinv * BK_NB));
-    CK(balloc(b, &b.sd.zg, (size_t)bs.zg * BK_NB));
-    CK(balloc(b, &b.sd.Xblk, (size_t)bs.Xblk * BK_NB));
-    CK(balloc(b, &b.sd.gam, (size_t)bs.gam * BK_NB));
-    CK(balloc(b, &b.sd.misc, (size_t)bs.misc * BK_NB));
-    CK(balloc(b, &b.sd.S0, (size_t)bs.S0 * BK_NB));
-    CK(balloc(b, &b.sd.fcol, (size_t)bs.fcol * BK_NB));
+    CK(balloc(b, &b.sd.U, (size_t)bs.U * BK_NB, h->st));
+    CK(balloc(b, &b.sd.Tw, (size_t)bs.Tw * BK_NB, h->st));
+    CK(balloc(b, &b.sd.Tinv, (size_t)bs.Tinv * BK_NB, h->st));
+    CK(balloc(b, &b.sd.zg, (size_t)bs.zg * BK_NB, h->st));
+    CK(balloc(b, &b.sd.Xblk, (size_t)bs.Xblk * BK_NB, h->st));
+    CK(balloc(b, &b.sd.gam, (size_t)bs.gam * BK_NB, h->st));
+    CK(balloc(b, &b.sd.misc, (size_t)bs.misc * BK_NB, h->st));
+    CK(balloc(b, &b.sd.S0, (size_t)bs.S0 * BK_NB, h->st));
+    CK(balloc(b, &b.sd.fcol, (size_t)bs.fcol * BK_NB, h->st));
     if (cudaMallocHost(&b.h_flags, sizeof(int) * 4 * BK_NB) != cudaSuccess) return KRYLOV_ENOMEM;
     if (cudaMallocHost(&b.h_scal, sizeof(double) * 16 * BK_NB) != cudaSuccess) return KRYLOV_ENOMEM;
     if (cudaMallocHost(&b.h_active, sizeof(int) * BK_NB) != cudaSuccess) return KRYLOV_ENOMEM;
@@ -1401,7 +1404,7 @@ krylov_status ensure_block_ws(krylov_handle* h, int levels) {
     }
     b.level_stride = (int64_t)b.rows_cap * (b.rows_cap + 1) / 2 * (int64_t)MM;
     b.bs.G = (int64_t)nl * b.level_stride;
-    CK(balloc(b, &b.sd.G, (size_t)b.bs.G * BK_NB));
+    CK(balloc(b, &b.sd.G, (size_t)b.bs.G * BK_NB, h->st));
     b.levels_cap = nl;
   }
   return KRYLOV_OK;

@@ -709,12 +709,14 @@ __device__ __forceinline__ void mat_coefficients_store(const StepLaunch& L, cons
 // (over the lane copies, in int64) to the column's accumulator [3][s] with
 // integer atomics, so the total is exact and independent of the order in
 // which CTAs arrive; the projected problem's U is formed from it once per
-// cycle.  word(b, c, w): word w of copy c of bin b in shared memory; thread p
-// sums pair (b, w) = (p / 3, p % 3) starting at copy b (bank spread).
-template <typename Word>
+// cycle.  word(b, c, w): word w < NW of copy c of bin b in shared memory;
+// thread p sums pair (b, w) = (p / NW, p % NW) starting at copy b (bank
+// spread).  With NW = 2 (float32 values) the third word of the accumulator
+// stays zero.
+template <int NW = 3, typename Word>
 __device__ __forceinline__ void fx_accumulate(Word word, int s, int C, unsigned long long* acc) {
-  for (int p = (int)threadIdx.x; p < 3 * s; p += (int)blockDim.x) {
-    const int b = p / 3, w = p - 3 * b;
+  for (int p = (int)threadIdx.x; p < NW * s; p += (int)blockDim.x) {
+    const int b = p / NW, w = p - NW * b;
     long long u = 0;
 #pragma unroll 8
     for (int c = 0; c < C; ++c) u += word(b, (c + b) & (C - 1), w);
