@@ -1014,8 +1014,10 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
     NvtxRange cycle_range("restart cycle");
     NvtxPhase phase;
     phase.next("arnoldi steps");
-    // float-float materialize kernels: column 0's exact sketch starts from zero
-    const bool ff_mat = (basis == 3) && !(h->opt.ortho == KRYLOV_ORTHO_RGS) && !h->part_mode;
+    // float-float and staged float32 / bfloat16 materialize kernels: column
+    // 0's exact sketch starts from zero
+    const bool ff_mat = (basis == 3 || (h->staged32 && !transpose)) && !(h->opt.ortho == KRYLOV_ORTHO_RGS) &&
+                        !h->part_mode;
     launch_cycle_reset(h->cd, M, st, ff_mat ? h->sk_acc : nullptr, ff_mat ? 3 * h->s : 0);
     CK(cudaEventRecord(h->ev[0], st));
     const bool rgs = (h->opt.ortho == KRYLOV_ORTHO_RGS);
@@ -1096,7 +1098,7 @@ krylov_status apply_core(krylov_handle* h, int transpose, const double* b, doubl
                                                    (int64_t)nc * 3 * h->s, st));
         if (cs != KRYLOV_OK) return cs;
         launch_part_sketch_u(h->part_acc, h->part_E, nc, h->s, h->opt.zeta, h->part_wb, h->sd.U, st);
-      } else if (basis == 3) {  // exact sketches of the float-float materialize kernels
+      } else if (basis == 3 || (h->staged32 && !transpose)) {  // exact sketches of the staged materialize kernels
         launch_sketch_finish(h->sk_acc, nc, h->s, h->sk_acc_stride, step_args(h, op, transpose, use32, thr, 0).fx_wb,
                              h->opt.zeta, h->sd.U, st);
       } else {

@@ -11,8 +11,10 @@
 //                         order, CSR tiles staged), ||p_j||^2 and the window
 //                         dots <w_q, p_j>
 //
-// Per-thread sums are float32; CTA and cross-CTA sums are float64 in a fixed
-// order, and the last CTA applies the same reducers as the other bases.
+// Per-thread sums are float32, CTA partials float-float pairs; as in the
+// float-float pair, the materialize kernel's CTAs form the coefficients from
+// the product kernel's partials (mat_coefficients) and the sketch of a column
+// is one exact int64 sum per bin word.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -53,10 +55,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const Step
   constexpr size_t OFF_N = OFF_R + (size_t)R32 * 8;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[MT32_STAGES];
-  __shared__ double red[32];
-  __shared__ int s_last;
-  __shared__ FxScale s_fx;
-  __shared__ float s_h[MAX_WINDOW + 1];
+  __shared__ float red[64];
+  __shared__ MatCoef s_c;
   const int lane = threadIdx.x & 31;
   int* bins = reinterpret_cast<int*>(smem);  // [s][C][NW]
   unsigned char* stages = smem + align16((size_t)NW * L.s * C * sizeof(int));
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const Step
   if (threadIdx.x == 0)
     for (int t = 0; t < npre; ++t) issue_static(t);
   pdl_wait();
-  if (cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
+  if (!MAT && cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
     if (threadIdx.x == 0)
       for (int t = 0; t < npre; ++t) {
         mbar_arrive(&bars[t]);
@@ -124,21 +124,32 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const Step
       }
     return;
   }
-  if (threadIdx.x == 0) {
+  // p_{j-1} is read even if the cycle has ended (mat_coefficients tells)
+  if (threadIdx.x == 0)
     for (int t = 0; t < npre; ++t) issue_p(t);
-    s_fx = fx_scale(L, cd, MAT ? 1 : 0);
-    const double* c = cd.coef + (size_t)(j > 0 ? j - 1 : 0) * (MAX_WINDOW + 1);
-    for (int q = 0; q < MAX_WINDOW; ++q) s_h[q] = (MAT && q < nl) ? (float)c[q] : 0.f;
-    s_h[MAX_WINDOW] = MAT ? (float)c[MAX_WINDOW] : 1.f;
+  if (MAT) {  // the coefficients, from the partials of the kernels before (every CTA)
+    if (!mat_coefficients<KW>(L, cd, s_c)) {  // the cycle ended before column j
+      if (threadIdx.x == 0)  // let the issued copies land before leaving
+        for (int t = 0; t < npre; ++t) (void)mbar_wait_bounded(&bars[t], 0u, WAIT32_NS);
+      return;
+    }
+  } else if (threadIdx.x == 0) {  // the start vector, stored as it is
+    s_c.fx = fx_scale(L, cd, 0);
+    for (int q = 0; q < MAX_WINDOW; ++q) s_c.h[q] = ff{0.f, 0.f};
+    s_c.rho = ff{1.f, 0.f};
   }
   __syncthreads();
-  const FxScale fxs = s_fx;
+  if (blockIdx.x == gridDim.x - 1 && j < L.m) {  // the next column's exact sketch starts from zero
+    unsigned long long* nx = fx_acc_of(L, j + 1);
+    for (int e = threadIdx.x; e < 3 * L.s; e += blockDim.x) nx[e] = 0ull;
+  }
+  const FxScale fxs = s_c.fx;
   int* const mybins = bins + (lane & (C - 1)) * NW;
   const int zeta = (Z > 0) ? Z : L.zeta;
-  float h[KW];
+  float h[KW];  // -h_q in float32
 #pragma unroll
-  for (int q = 0; q < KW; ++q) h[q] = s_h[q];
-  const float rho = s_h[MAX_WINDOW];
+  for (int q = 0; q < KW; ++q) h[q] = s_c.h[q].hi;
+  const float rho = s_c.rho.hi;
   float acc_sig = 0.f;
   bool timed_out = false;
   int last_issued = npre - 1;
@@ -155,7 +166,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const Step
         float a = reinterpret_cast<const float*>(base)[k];
 #pragma unroll
         for (int q = 0; q < KW; ++q)
-          if (q < nl) a = __fmaf_rn(-h[q], to_f(reinterpret_cast<const VT*>(base + OFF_W + (size_t)q * R32 * sizeof(VT))[k]), a);
+          if (q < nl) a = __fmaf_rn(h[q], to_f(reinterpret_cast<const VT*>(base + OFF_W + (size_t)q * R32 * sizeof(VT))[k]), a);
         const float v = a * rho;
         Store<VT>::put(Wj + i, v);
         wj = stored<VT, float>(v);  // the sketch and the norm see the stored value
@@ -192,29 +203,29 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_mat_tma_kernel(const Step
     for (int t = max(0, last_issued - MT32_STAGES + 1); t <= last_issued; ++t)
       (void)mbar_wait_bounded(&bars[t % MT32_STAGES], (uint32_t)(t / MT32_STAGES) & 1u, WAIT32_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  const double v = block_sum((double)acc_sig, red);
-  if (threadIdx.x == 0) part[0] = v;
+  const ff v = block_sum_ff_pair(ff{acc_sig, 0.f}, red, red + 32);
+  if (threadIdx.x == 0) st_part_ff(part_w_of(L, j) + blockIdx.x, v);
   __syncthreads();
-  double* out = static_cast<double*>(L.sk_part) + (size_t)blockIdx.x * L.s;
-  for (int b = threadIdx.x; b < L.s; b += blockDim.x) {
-    long long t0 = 0, t1 = 0;
-#pragma unroll 8
-    for (int c = 0; c < C; ++c) {
-      const int* w = bins + (b * C + ((c + b) & (C - 1))) * NW;
-      t0 += w[0];
-      t1 += w[1];
-    }
-    out[b] = (double)(t0 * (1ll << L.fx_wb) + t1) * pow2d(fxs.E - 2 * L.fx_wb);
+  unsigned long long* acc = fx_acc_of(L, j);
+  fx_accumulate<NW>([&](int b, int c, int w) { return (long long)bins[(b * C + c) * NW + w]; }, L.s, C, acc);
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) reinterpret_cast<long long*>(acc)[3 * L.s] = fxs.E;
+    if (MAT) mat_coefficients_store(L, cd, s_c);
   }
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  if (threadIdx.x < 32) {
-    const double tsum = warp_sum_partials(L.part, (int)gridDim.x, NQ, 0);
-    if (threadIdx.x == 0) {
-      (void)reduce_mat(L, cd, tsum, MAT ? 1 : 0);
-      *cd.counter = 0u;
-    }
-  }
+  if (j == L.m) ff_mat_finish(L, cd, MAT ? 1 : 0);  // else the next materialize kernel sums the partials
+}
+
+// CTA partials of a float32 product kernel: ||p_j||^2 and the window dots as
+// float-float pairs (columns 1, 2, ... of the partials), which the next
+// materialize kernel's CTAs sum.
+template <int KW>
+__device__ __forceinline__ void s32_spmv_partials(float acc_pi, const float (&acc_dot)[KW], int nd, double* part_cta) {
+  __shared__ float2 sh[MAX_WARPS][1 + KW];
+  ff v[1 + KW];
+  v[0] = ff{acc_pi, 0.f};
+#pragma unroll
+  for (int q = 0; q < KW; ++q) v[1 + q] = ff{acc_dot[q], 0.f};
+  block_partials_ff<1 + KW>(v, 1 + nd, part_cta, 1, sh);
 }
 
 // Stage of the product kernel: row_ptr slice, column entries (4-byte indices,
@@ -230,9 +241,6 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_tma_kernel(const Ste
   constexpr int EA = DI ? 8 : 4;  // staged nonzero ranges start on 16-byte boundaries
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[SP32_STAGES];
-  __shared__ double red[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
   const int j = L.j;
   const int cap = L.tma_cap;
   const size_t sb = sp32_stage_bytes<DI>(cap);
@@ -341,26 +349,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_tma_kernel(const Ste
     for (int t = max(0, last_issued - SP32_STAGES + 1); t <= last_issued; ++t)
       (void)mbar_wait_bounded(&bars[t % SP32_STAGES], (uint32_t)(t / SP32_STAGES) & 1u, WAIT32_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum((double)acc_pi, red);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;  // uniform over the block
-    __syncthreads();
-    v = block_sum((double)acc_dot[q], red);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double t = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  s32_spmv_partials<KW>(acc_pi, acc_dot, nd, L.part + (size_t)blockIdx.x * NQ);
 }
 
 // Product kernel on the sliced layout (see ff_spmv_sell_kernel): tiles padded
@@ -386,9 +375,6 @@ template <typename VT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_sell_kernel(const StepLaunch L, const CycleDev cd) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[SP32_STAGES];
-  __shared__ double red[32];
-  __shared__ int s_last;
-  __shared__ double tot[NQ];
   auto col_st = [&](int st) { return reinterpret_cast<const int16_t*>(smem + (size_t)st * SELL32_STAGE); };
   auto val_st = [&](int st) {
     return reinterpret_cast<const float*>(smem + (size_t)st * SELL32_STAGE + (size_t)SELL_MAXL * R32 * 2);
@@ -487,26 +473,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) s32_spmv_sell_kernel(const St
     for (int t = max(0, last_issued - SP32_STAGES + 1); t <= last_issued; ++t)
       (void)mbar_wait_bounded(&bars[t % SP32_STAGES], (uint32_t)(t / SP32_STAGES) & 1u, WAIT32_NS);
   }
-  double* part = L.part + (size_t)blockIdx.x * NQ;
-  double v = block_sum((double)acc_pi, red);
-  if (threadIdx.x == 0) part[1] = v;
-#pragma unroll
-  for (int q = 0; q < KW; ++q) {
-    if (q >= nd) break;
-    __syncthreads();
-    v = block_sum((double)acc_dot[q], red);
-    if (threadIdx.x == 0) part[2 + q] = v;
-  }
-  if (!last_block_flag(cd.counter, &s_last)) return;
-  for (int q = (int)(threadIdx.x >> 5); q < NQ; q += (int)(blockDim.x >> 5)) {
-    const double tt = (q >= 1 && q < 2 + nd) ? warp_sum_partials(L.part, (int)gridDim.x, NQ, q) : 0.0;
-    if ((threadIdx.x & 31) == 0) tot[q] = tt;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    reduce_spmv(L, cd, tot, __ldcg(cd.flags + 1) != 0);
-    if (threadIdx.x == 0) *cd.counter = 0u;
-  }
+  s32_spmv_partials<KW>(acc_pi, acc_dot, nd, L.part + (size_t)blockIdx.x * NQ);
 }
 
 template <typename K> int occ32(K kern, size_t smem) {
