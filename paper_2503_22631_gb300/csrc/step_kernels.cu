@@ -410,11 +410,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
 // of 256 rows (16-byte aligned) and a partial last tile is copied rounded up
 // to 16 rows (the row arrays are padded to the slot stride).
 constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
-// One CTA of MT_THREADS threads per SM (a row per thread in a tile of
+// One CTA of MT_THREADS threads per SM (MT_RPT rows per thread in a tile of
 // MT_ROWS rows): two CTAs per SM drifted apart as the product kernel's did
 // (the second finished ~3.5 us after the first, its SM half idle meanwhile).
 constexpr int MT_THREADS = 512;
-constexpr int MT_ROWS = MT_THREADS;
+constexpr int MT_RPT = 2;  // rows per thread and tile: two independent float-float chains
+constexpr int MT_ROWS = MT_THREADS * MT_RPT;
 #ifndef KRYLOV_MT_STAGES
 #define KRYLOV_MT_STAGES 3
 #endif
@@ -550,34 +551,48 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
     const int st = t % MT_STAGES;
     const uint32_t par = (uint32_t)(t / MT_STAGES) & 1u;
     if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
-    const int k = (int)threadIdx.x;
-    const int i = r0 + t * MT_ROWS + k;
-    if (i < r1 && !timed_out) {
-      const float2 p2 = st_p(st)[k];
-      ff wj{p2.x, p2.y};
-      if (MAT) {
-        ff acc = wj;
+    // rows k and k + MT_THREADS of the tile: both rows' materialization and
+    // fixed-point words first (independent chains), then their sketch entries
+    FxWords<NW> xw[MT_RPT];
+    uint2 rr[MT_RPT];
+    uint32_t ng[MT_RPT];
+    bool ok[MT_RPT];
 #pragma unroll
-        for (int q = 0; q < KW; ++q)
-          if (q < nl) {
-            const float2 w2 = st_w(st, q)[k];
-            acc = ff_add(acc, ff_mul(h[q], ff{w2.x, w2.y}));
-          }
-        wj = ff_mul(acc, rho);
-        st_ff(Wj + i, wj);
+    for (int u = 0; u < MT_RPT; ++u) {
+      const int k = (int)threadIdx.x + u * MT_THREADS;
+      const int i = r0 + t * MT_ROWS + k;
+      ok[u] = i < r1 && !timed_out;
+      if (ok[u]) {
+        const float2 p2 = st_p(st)[k];
+        ff wj{p2.x, p2.y};
+        if (MAT) {
+          ff acc = wj;
+#pragma unroll
+          for (int q = 0; q < KW; ++q)
+            if (q < nl) {
+              const float2 w2 = st_w(st, q)[k];
+              acc = ff_add(acc, ff_mul(h[q], ff{w2.x, w2.y}));
+            }
+          wj = ff_mul(acc, rho);
+          st_ff(Wj + i, wj);
+        }
+        acc_sig.add_prod(wj, wj);
+        rr[u] = st_r(st)[k];
+        ng[u] = st_n(st)[k];
+        xw[u] = fx_split<NW>(wj.hi, wj.lo, fxs);
       }
-      acc_sig.add_prod(wj, wj);
-      const uint2 rr = st_r(st)[k];
-      const uint32_t ng = st_n(st)[k];
-      const FxWords<NW> xw = fx_split<NW>(wj.hi, wj.lo, fxs);
-      const int q0 = xw.q[0], q1 = xw.q[1], q2 = xw.q[2];
+    }
+#pragma unroll
+    for (int u = 0; u < MT_RPT; ++u) {
+      if (!ok[u]) continue;
+      const int q0 = xw[u].q[0], q1 = xw[u].q[1], q2 = xw[u].q[2];
       const int n0 = -q0, n1 = -q1, n2 = -q2;
 #pragma unroll
       for (int e = 0; e < 8; ++e)
         if (Z == 8 || e < zeta) {
-          const int row = (int)__byte_perm(e < 4 ? rr.x : rr.y, 0u, 0x4440u | (uint32_t)(e & 3));
+          const int row = (int)__byte_perm(e < 4 ? rr[u].x : rr[u].y, 0u, 0x4440u | (uint32_t)(e & 3));
           int* b = mybins + row * (C * NW);
-          const bool neg = (ng >> e) & 1u;
+          const bool neg = (ng[u] >> e) & 1u;
           atomicAdd(b, neg ? n0 : q0);
           atomicAdd(b + 1, neg ? n1 : q1);
           atomicAdd(b + 2, neg ? n2 : q2);
