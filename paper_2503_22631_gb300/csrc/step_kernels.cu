@@ -410,12 +410,17 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
 // of 256 rows (16-byte aligned) and a partial last tile is copied rounded up
 // to 16 rows (the row arrays are padded to the slot stride).
 constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
-// One CTA of MT_THREADS threads per SM (MT_RPT rows per thread in a tile of
-// MT_ROWS rows): two CTAs per SM drifted apart as the product kernel's did
-// (the second finished ~3.5 us after the first, its SM half idle meanwhile).
+// One CTA per SM (two CTAs per SM drifted apart as the product kernel's did:
+// the second finished ~3.5 us after the first, its SM half idle meanwhile):
+// MT_THREADS row threads (MT_RPT rows per thread in a tile of MT_ROWS rows)
+// and one producer warp, which refills a stage once every row warp has
+// released it (a per-stage "empty" barrier), so that no CTA-wide barrier per
+// tile holds the row warps together.
 constexpr int MT_THREADS = 512;
 constexpr int MT_RPT = 2;  // rows per thread and tile: two independent float-float chains
 constexpr int MT_ROWS = MT_THREADS * MT_RPT;
+constexpr int MT_BLOCK = MT_THREADS + 32;  // + the producer warp
+constexpr int MT_PRODUCER = MT_THREADS;    // the thread that issues the copies
 #ifndef KRYLOV_MT_STAGES
 #define KRYLOV_MT_STAGES 3
 #endif
@@ -432,14 +437,16 @@ __host__ __device__ constexpr size_t mt_stage_bytes(int kw) {
 // compile-time so that the entry loop carries no parameter loads.
 
 template <bool MAT, int KW, int C, int Z>
-__global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
+__global__ void __launch_bounds__(MT_BLOCK, 1) ff_mat_tma_kernel(const StepLaunch L, const CycleDev cd) {
   constexpr int NW = 3;
   static_assert(C == 16 || C == 32, "lane copies of the bins");
   constexpr size_t SB = mt_stage_bytes(KW);
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[MT_STAGES];
+  __shared__ __align__(8) uint64_t bars[MT_STAGES];   // tile landed (bulk-copy bytes)
+  __shared__ __align__(8) uint64_t empty[MT_STAGES];  // every row warp is done with the stage
   __shared__ float red[64];
   __shared__ MatCoef s_c;
+  const bool producer = threadIdx.x == MT_PRODUCER;
   const int lane = threadIdx.x & 31;
   int* bins = reinterpret_cast<int*>(smem);  // [s][C][NW]
   unsigned char* stages = smem + align16(bins_bytes(3, L.s, C));
@@ -467,7 +474,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
   // kernel's reduction tail; the phase completes only once the second part
   // has arrived as well (its arrive carries the last byte count).
   auto rows_of = [&](int t) { return (uint32_t)((min(MT_ROWS, r1 - (r0 + t * MT_ROWS)) + 15) & ~15); };
-  auto issue_static = [&](int t) {  // thread 0: expects its bytes, does not arrive
+  auto issue_static = [&](int t) {  // the producer: expects its bytes, does not arrive
     const int st = t % MT_STAGES;
     const int ts = r0 + t * MT_ROWS;
     const uint32_t rc = rows_of(t);
@@ -481,7 +488,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
     bulk_g2s_stream(base + (size_t)MT_ROWS * 8 * (1 + KW), L.sk_tab.rows8 + ts, rc * 8u, &bars[st]);
     bulk_g2s_stream(base + (size_t)MT_ROWS * 8 * (2 + KW), L.sk_tab.neg8 + ts, rc, &bars[st]);
   };
-  auto issue_p = [&](int t) {  // thread 0: arrives with the product's bytes
+  auto issue_p = [&](int t) {  // the producer: arrives with the product's bytes
     const int st = t % MT_STAGES;
     const uint32_t rc = rows_of(t);
     mbar_arrive_expect_tx(&bars[st], rc * 8u);
@@ -491,8 +498,11 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
     issue_static(t);
     issue_p(t);
   };
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < MT_STAGES; ++q) mbar_init(&bars[q], 1);
+  if (producer) {
+    for (int q = 0; q < MT_STAGES; ++q) {
+      mbar_init(&bars[q], 1);
+      mbar_init(&empty[q], MT_THREADS / 32);
+    }
     fence_mbar_init();
   }
   {
@@ -502,13 +512,13 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
     for (int e = (nb / 4) * 4 + threadIdx.x; e < nb; e += blockDim.x) bins[e] = 0;
   }
   const int npre = min(ntiles, MT_STAGES);
-  if (threadIdx.x == 0)
+  if (producer)
     for (int t = 0; t < npre; ++t) issue_static(t);
   // everything above is independent of the kernel just before; p_{j-1} and
   // the coefficients are not
   pdl_wait();
   if (!MAT && cd.flags[0] < j) {  // the cycle ended before column j (breakdown)
-    if (threadIdx.x == 0)  // complete the phases and let the copies land before leaving
+    if (producer)  // complete the phases and let the copies land before leaving
       for (int t = 0; t < npre; ++t) {
         mbar_arrive(&bars[t]);
         (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
@@ -517,13 +527,13 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
   }
   // p_{j-1} is read even if the cycle has ended (mat_coefficients tells):
   // the copies are harmless and start early
-  if (threadIdx.x == 0)
+  if (producer)
     for (int t = 0; t < npre; ++t) issue_p(t);
   // the coefficients, from the partials of the kernels before (every CTA,
   // while the first tiles land)
   if (MAT) {
     if (!mat_coefficients<KW>(L, cd, s_c)) {  // the cycle ended before column j
-      if (threadIdx.x == 0)  // let the issued copies land before leaving
+      if (producer)  // let the issued copies land before leaving
         for (int t = 0; t < npre; ++t) (void)mbar_wait_bounded(&bars[t], 0u, TMA_WAIT_NS);
       return;
     }
@@ -546,71 +556,85 @@ __global__ void __launch_bounds__(MT_THREADS, 1) ff_mat_tma_kernel(const StepLau
   const ff rho = s_c.rho;
   ffacc acc_sig;
   bool timed_out = false;
-  int last_issued = min(ntiles, MT_STAGES) - 1;
-  for (int t = 0; t < ntiles; ++t) {
-    const int st = t % MT_STAGES;
-    const uint32_t par = (uint32_t)(t / MT_STAGES) & 1u;
-    if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
-    // rows k and k + MT_THREADS of the tile: both rows' materialization and
-    // fixed-point words first (independent chains), then their sketch entries
-    FxWords<NW> xw[MT_RPT];
-    uint2 rr[MT_RPT];
-    uint32_t ng[MT_RPT];
-    bool ok[MT_RPT];
-#pragma unroll
-    for (int u = 0; u < MT_RPT; ++u) {
-      const int k = (int)threadIdx.x + u * MT_THREADS;
-      const int i = r0 + t * MT_ROWS + k;
-      ok[u] = i < r1 && !timed_out;
-      if (ok[u]) {
-        const float2 p2 = st_p(st)[k];
-        ff wj{p2.x, p2.y};
-        if (MAT) {
-          ff acc = wj;
-#pragma unroll
-          for (int q = 0; q < KW; ++q)
-            if (q < nl) {
-              const float2 w2 = st_w(st, q)[k];
-              acc = ff_add(acc, ff_mul(h[q], ff{w2.x, w2.y}));
-            }
-          wj = ff_mul(acc, rho);
-          st_ff(Wj + i, wj);
-        }
-        acc_sig.add_prod(wj, wj);
-        rr[u] = st_r(st)[k];
-        ng[u] = st_n(st)[k];
-        xw[u] = fx_split<NW>(wj.hi, wj.lo, fxs);
+  if (producer) {
+    // refill stage t % MT_STAGES with tile t once every row warp has released
+    // tile t - MT_STAGES (phase t / MT_STAGES - 1 of its empty barrier) and
+    // that tile's copies have landed (already so, unless a row warp gave up
+    // waiting for them)
+    int last_issued = npre - 1;
+    for (int t = MT_STAGES; t < ntiles; ++t) {
+      const int st = t % MT_STAGES;
+      const uint32_t prev = (uint32_t)(t / MT_STAGES - 1) & 1u;
+      if (!mbar_wait_bounded(&empty[st], prev, TMA_WAIT_NS) || !mbar_wait_bounded(&bars[st], prev, TMA_WAIT_NS)) {
+        timed_out = true;
+        break;
       }
-    }
-#pragma unroll
-    for (int u = 0; u < MT_RPT; ++u) {
-      if (!ok[u]) continue;
-      const int q0 = xw[u].q[0], q1 = xw[u].q[1], q2 = xw[u].q[2];
-      const int n0 = -q0, n1 = -q1, n2 = -q2;
-#pragma unroll
-      for (int e = 0; e < 8; ++e)
-        if (Z == 8 || e < zeta) {
-          const int row = (int)__byte_perm(e < 4 ? rr[u].x : rr[u].y, 0u, 0x4440u | (uint32_t)(e & 3));
-          int* b = mybins + row * (C * NW);
-          const bool neg = (ng[u] >> e) & 1u;
-          atomicAdd(b, neg ? n0 : q0);
-          atomicAdd(b + 1, neg ? n1 : q1);
-          atomicAdd(b + 2, neg ? n2 : q2);
-        }
-    }
-    __syncthreads();  // every thread is done with stage st
-    if (threadIdx.x == 0 && t + MT_STAGES < ntiles && !timed_out) {
       fence_proxy_async();
-      issue(t + MT_STAGES);
-      last_issued = t + MT_STAGES;
+      issue(t);
+      last_issued = t;
+    }
+    // the copies in flight land before the CTA leaves (at once, unless a row
+    // warp gave up waiting for them)
+    for (int t = max(0, last_issued - MT_STAGES + 1); t <= last_issued; ++t)
+      (void)mbar_wait_bounded(&bars[t % MT_STAGES], (uint32_t)(t / MT_STAGES) & 1u, TMA_WAIT_NS);
+  } else if (threadIdx.x < MT_THREADS) {
+    for (int t = 0; t < ntiles; ++t) {
+      const int st = t % MT_STAGES;
+      const uint32_t par = (uint32_t)(t / MT_STAGES) & 1u;
+      if (!timed_out && !mbar_wait_bounded(&bars[st], par, TMA_WAIT_NS)) timed_out = true;
+      // rows k and k + MT_THREADS of the tile: both rows' materialization and
+      // fixed-point words first (independent chains), then their sketch entries
+      FxWords<NW> xw[MT_RPT];
+      uint2 rr[MT_RPT];
+      uint32_t ng[MT_RPT];
+      bool ok[MT_RPT];
+#pragma unroll
+      for (int u = 0; u < MT_RPT; ++u) {
+        const int k = (int)threadIdx.x + u * MT_THREADS;
+        const int i = r0 + t * MT_ROWS + k;
+        ok[u] = i < r1 && !timed_out;
+        if (ok[u]) {
+          const float2 p2 = st_p(st)[k];
+          ff wj{p2.x, p2.y};
+          if (MAT) {
+            ff acc = wj;
+#pragma unroll
+            for (int q = 0; q < KW; ++q)
+              if (q < nl) {
+                const float2 w2 = st_w(st, q)[k];
+                acc = ff_add(acc, ff_mul(h[q], ff{w2.x, w2.y}));
+              }
+            wj = ff_mul(acc, rho);
+            st_ff(Wj + i, wj);
+          }
+          acc_sig.add_prod(wj, wj);
+          rr[u] = st_r(st)[k];
+          ng[u] = st_n(st)[k];
+          xw[u] = fx_split<NW>(wj.hi, wj.lo, fxs);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < MT_RPT; ++u) {
+        if (!ok[u]) continue;
+        const int q0 = xw[u].q[0], q1 = xw[u].q[1], q2 = xw[u].q[2];
+        const int n0 = -q0, n1 = -q1, n2 = -q2;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (Z == 8 || e < zeta) {
+            const int row = (int)__byte_perm(e < 4 ? rr[u].x : rr[u].y, 0u, 0x4440u | (uint32_t)(e & 3));
+            int* b = mybins + row * (C * NW);
+            const bool neg = (ng[u] >> e) & 1u;
+            atomicAdd(b, neg ? n0 : q0);
+            atomicAdd(b + 1, neg ? n1 : q1);
+            atomicAdd(b + 2, neg ? n2 : q2);
+          }
+      }
+      __syncwarp();  // the warp is done with stage st
+      if (lane == 0) mbar_arrive(&empty[st]);
     }
   }
   pdl_trigger();
   if (timed_out) atomicOr(&cd.flags[2], ERR_TIMEOUT);
-  if (threadIdx.x == 0 && timed_out) {
-    for (int t = max(0, last_issued - MT_STAGES + 1); t <= last_issued; ++t)
-      (void)mbar_wait_bounded(&bars[t % MT_STAGES], (uint32_t)(t / MT_STAGES) & 1u, TMA_WAIT_NS);
-  }
   const ff v = block_sum_ff_pair(acc_sig.result(), red, red + 32);
   if (threadIdx.x == 0) st_part_ff(part_w_of(L, j) + blockIdx.x, v);
   __syncthreads();
@@ -1115,7 +1139,7 @@ void launch_ff_mat(const StepLaunch& L, const CycleDev& cd, cudaStream_t st) {
                    : ((L.zeta == 8) ? pick(ff_mat_tma_kernel<MAT, 2, 16, 8>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 16, 8>)
                                     : pick(ff_mat_tma_kernel<MAT, 2, 16, 0>, ff_mat_tma_kernel<MAT, MAX_WINDOW, 16, 0>));
       raise_smem_limit((const void*)k, smem);
-      launch_pdl_threads(k, L.grid_mat, MT_THREADS, smem, st, L, cd);
+      launch_pdl_threads(k, L.grid_mat, MT_BLOCK, smem, st, L, cd);
       break;
     }
     case SK_TAB16: launch_ff_mat_t<MAT, SK_TAB16>(L, cd, st); break;
@@ -1455,10 +1479,10 @@ int sell_ctas_per_sm(int vals_f32, int maxl) {
 }
 
 // Resident CTAs per SM of the float-float materialize kernel with the row
-// streams staged by bulk copies (MT_THREADS threads per CTA).
+// streams staged by bulk copies (MT_BLOCK threads per CTA).
 int mat_ctas_per_sm(int s, int copies) {
-  return (copies == 32) ? occ(ff_mat_tma_kernel<true, 2, 32, 8>, mt_smem(s, copies, 2), MT_THREADS)
-                        : occ(ff_mat_tma_kernel<true, 2, 16, 8>, mt_smem(s, copies, 2), MT_THREADS);
+  return (copies == 32) ? occ(ff_mat_tma_kernel<true, 2, 32, 8>, mt_smem(s, copies, 2), MT_BLOCK)
+                        : occ(ff_mat_tma_kernel<true, 2, 16, 8>, mt_smem(s, copies, 2), MT_BLOCK);
 }
 
 // CTAs per SM of the 256-thread step kernels (for the float-float basis: of
