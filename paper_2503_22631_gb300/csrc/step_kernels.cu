@@ -402,13 +402,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 4) ff_mat_kernel(const StepLaunc
 }
 
 // Materialize + sketch with the row streams staged in shared memory (packed
-// sketch table).  Tiles of 256 rows: thread 0 copies the tile's slices of
-// p_{j-1} (or w_0), the window vectors and the sketch table (8 row bytes and
-// a sign byte per column) with bulk asynchronous copies completing on an
-// mbarrier, MT_STAGES tiles ahead; each thread then handles one row from
-// shared memory exactly as ff_mat_kernel does.  Row slices start at multiples
-// of 256 rows (16-byte aligned) and a partial last tile is copied rounded up
-// to 16 rows (the row arrays are padded to the slot stride).
+// sketch table).  Tiles of MT_ROWS rows: the producer thread copies the
+// tile's slices of p_{j-1} (or w_0), the window vectors and the sketch table
+// (8 row bytes and a sign byte per column) with bulk asynchronous copies
+// completing on an mbarrier, MT_STAGES tiles ahead; each row thread then
+// handles MT_RPT rows from shared memory with the arithmetic of
+// ff_mat_kernel.  Row slices start at multiples of 256 rows (16-byte aligned:
+// a CTA's rows are a multiple of 256) and a partial last tile is copied
+// rounded up to 16 rows (the row arrays are padded to the slot stride).
 constexpr uint64_t TMA_WAIT_NS = 1000000000ull;  // 1 s bound on one staged-tile wait
 // One CTA per SM (two CTAs per SM drifted apart as the product kernel's did:
 // the second finished ~3.5 us after the first, its SM half idle meanwhile):
