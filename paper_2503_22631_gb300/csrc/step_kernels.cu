@@ -31,10 +31,16 @@
 // Arnoldi-like relation A w_{j-1} = sum h_q w_q + w_j / rho_j (Eq. 5) holds
 // for whatever rho_j was used.  The whitening absorbs the column scaling.
 //
-// Reductions are deterministic: per-CTA partials in fixed slots, then the
-// last CTA to arrive (atomic ticket) sums them in a fixed order and writes the
-// next column's coefficients.  Sketch partials stay per CTA and are summed
-// once per cycle by sketch_reduce_kernel.
+// Reductions are deterministic: per-CTA partials in fixed slots, summed in a
+// fixed order.  In the fused kernel the last CTA to arrive (atomic ticket)
+// sums them and writes the next column's coefficients, and the sketch
+// partials stay per CTA until sketch_reduce_kernel sums them once per cycle.
+// The staged float-float pair has no reducer between its kernels: every CTA
+// of the next materialize kernel sums the partials and forms the
+// coefficients itself (only the last column of a cycle, which no
+// materialize kernel follows, and ||p_j||^2 in a randomized Gram-Schmidt
+// cycle keep a last-CTA sum), and the sketch of a column is an exact int64
+// sum over the CTAs (sketch_finish_kernel forms U once per cycle).
 #include <algorithm>
 #include <cmath>
 
@@ -1302,8 +1308,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 3) ff_spmv_seg_kernel(const Step
 // (rows n_big + blockIdx.x * warps + warp, stepping by grid * warps) with a
 // fixed shuffle tree.  p_i overwrites the zero and the thread that holds it
 // adds its shares of ||p||^2 and of the window dots; a fixed block sum makes
-// the CTA's partials, and the last CTA reduces both kernels' partials (the
-// emptied operator's CTAs, then these, each in CTA order).
+// the CTA's partials.  The next materialize kernel's CTAs sum both kernels'
+// partials (the emptied operator's CTAs, then these, each in CTA order); in a
+// randomized Gram-Schmidt cycle the last CTA here sums ||p||^2 the same way.
 template <typename AT, int KW>
 __global__ void __launch_bounds__(STEP_THREADS) ff_spmv_long_kernel(const StepLaunch L, const CycleDev cd) {
   __shared__ float rhi[32], rlo[32];
