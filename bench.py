@@ -52,9 +52,6 @@ WORKLOAD = dict(
     workload="convdiff3d_128_exp",
     grid=128, beta=(50.0, 50.0, 50.0), t=1e-2, m=40, k=2, s=160, zeta=8,
 )
-# Restart cycles that reach <= 1e-8 relative error against the closed-form
-# Kronecker reference on this workload with the float64 basis (verified by
-# tests/test_gpu_headline.py at this exact configuration).
 # the Arnoldi-step pair timed by the roofline, per basis (the product kernel of
 # the float-float and float32/bfloat16 bases is picked at create by timing; on
 # the 7-point stencil it is the sliced-layout one)
@@ -65,6 +62,9 @@ STEP_KERNEL_LABEL = {
     "bf16": "Arnoldi step: s32_mat_tma_kernel + s32_spmv_sell_kernel (bfloat16 basis, staged pair)",
     "f64": "Arnoldi step: step_kernel<double> (fused SpMV + truncated orthogonalization + sketch, float64 arithmetic)",
 }
+# Restart cycles that reach <= 1e-8 relative error against the closed-form
+# Kronecker reference on this workload with the float64 basis (verified by
+# tests/test_gpu_headline.py at this exact configuration).
 CYCLES_TO_1E8 = {"df64": 10, "f64": 10, "f32": None, "bf16": None}
 SEED = 20250331  # workloads.SEED
 # The timed solves cycle over five right-hand sides b ~ U[0, 1) (seeds SEED ..
