@@ -10,6 +10,9 @@
 //   s32_spmv_tma_kernel   p_j = A w_j (float32 products summed in storage
 //                         order, CSR tiles staged), ||p_j||^2 and the window
 //                         dots <w_q, p_j>
+//   s32_spmv_sell_kernel  the same product on the sliced layout (tiles padded
+//                         to their longest row, slot-major), when the
+//                         operator has one
 //
 // Per-thread sums are float32, CTA partials float-float pairs; as in the
 // float-float pair, the materialize kernel's CTAs form the coefficients from
