@@ -44,10 +44,11 @@ def invsqrt_first_column(A):
     return acc
 
 
-def test_invsqrt_node_count_of_the_fem_scale():
-    """508 nodes for ||A||_inf of the order of the FEM stiffness matrix."""
-    u, h = invsqrt_nodes(40.0)
-    assert h == 0.2 and len(u) == 508
+def test_invsqrt_node_count_does_not_depend_on_the_norm():
+    """The interval is 0.5 ln(1e22) + 76 long whatever ||A||_inf: 508 nodes."""
+    for alpha in (1e-3, 1.0, 40.0, 3.7e5):
+        u, h = invsqrt_nodes(alpha)
+        assert h == 0.2 and len(u) == 508
 
 
 def invsqrt_scalar(z, alpha):
