@@ -105,3 +105,38 @@ def test_cos_sqrt_series_bound():
     w, V = np.linalg.eigh(A)
     ref = (V * np.cos(np.sqrt(np.maximum(w, 0.0)))) @ V.T
     assert np.abs(S - ref).max() <= 1e-14
+
+
+def test_phi1_extra_column_from_the_horner_iterate_and_squarings():
+    """phi_1(-tH) e_1 as the extra column of exp([[-tH, e_1], [0, 0]]): after
+    the Taylor-Horner steps on B = -tH / 2^s the column is S2 w (w = e_1 2^-s,
+    S2 the iterate before the last step, which equals sum_i B^i / (i+1)!),
+    and a squaring of [[E, g], [0, 1]] maps g to E g + g."""
+    rng = np.random.default_rng(9)
+    H = block_bidiagonal(rng, 3, 8, 150.0)
+    n = H.shape[0]
+    t = 3e-2
+    B = -t * H
+    s = squarings_for(B)
+    Bs = B / 2.0 ** s
+    S = np.eye(n)
+    S2 = None
+    for k in range(DEG, 0, -1):
+        if k == 1:
+            S2 = S
+        S = np.eye(n) + (Bs @ S) / k
+    series = sum(np.linalg.matrix_power(Bs, i) / math.factorial(i + 1) for i in range(DEG))
+    assert np.abs(S2 - series).max() <= 1e-15 * np.abs(series).max()
+    w = np.zeros(n)
+    w[0] = 2.0 ** -s
+    E, g = S, S2 @ w
+    for _ in range(s):
+        E, g = E @ E, E @ g + g
+    aug = np.zeros((n + 1, n + 1))
+    aug[:n, :n] = B
+    aug[0, n] = 1.0
+    ref = sla.expm(aug)[:n, n]
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+    lam, V = np.linalg.eig(B)  # phi_1 by its definition (e^z - 1) / z on the eigenvalues
+    direct = np.real(V @ (np.expm1(lam) / lam * np.linalg.solve(V, np.eye(n)[:, 0])))
+    assert np.abs(g - direct).max() <= 1e-8 * np.abs(direct).max()
