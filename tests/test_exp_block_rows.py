@@ -140,3 +140,27 @@ def test_phi1_extra_column_from_the_horner_iterate_and_squarings():
     lam, V = np.linalg.eig(B)  # phi_1 by its definition (e^z - 1) / z on the eigenvalues
     direct = np.real(V @ (np.expm1(lam) / lam * np.linalg.solve(V, np.eye(n)[:, 0])))
     assert np.abs(g - direct).max() <= 1e-8 * np.abs(direct).max()
+
+
+def test_cos_sqrt_by_series_and_double_angle_steps():
+    """cos(t sqrt(H)) from the series on B = -t^2 H / 4^s (||B||_1 <= 4) and s
+    steps C <- 2 C^2 - I (cos(2x) = 2 cos(x)^2 - 1), against cos(t sqrt(lambda))
+    on the eigendecomposition of a symmetric positive semidefinite H."""
+    rng = np.random.default_rng(10)
+    n = 16
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = rng.uniform(0.0, 5e4, n)
+    H = (Q * lam) @ Q.T
+    t = 0.05
+    B = -(t * t) * H
+    nrm = np.abs(B).sum(axis=0).max()
+    s = max(0, math.ceil(0.5 * math.log2(nrm / 4.0))) if nrm > 4.0 else 0
+    Bs = B / 4.0 ** s
+    assert np.abs(Bs).sum(axis=0).max() <= 4.0
+    C = np.eye(n)
+    for k in range(DEG, 0, -1):  # Horner for sum_k Bs^k / (2k)!
+        C = np.eye(n) + (Bs @ C) / ((2 * k - 1) * (2 * k))
+    for _ in range(s):
+        C = 2.0 * C @ C - np.eye(n)
+    ref = (Q * np.cos(t * np.sqrt(lam))) @ Q.T
+    assert np.abs(C - ref).max() <= 1e-10
