@@ -79,9 +79,12 @@ template <> struct SkColOf<SK_GEN> { using type = SkColGen; };
 
 // ---- exact fixed-point sketch bins ---------------------------------------
 // A contribution v with |v| <= B is scaled by the power of two 2^(WB - E),
-// E = ceil(log2 B) + 1, so |x| <= 2^(WB-1), and split into NW integer words
-// x = q_0 + 2^-WB q_1 + 2^-2WB q_2 + ... (each |q_w| <= 2^(WB-1)), rounding
-// with the 1.5 * 2^23 addition trick on the FP32 pipes.  Word w of bin b
+// E >= ceil(log2 B) + 1, so |x| < 2^(WB-1), and split into NW integer words
+// x = q_0 + 2^-WB q_1 + 2^-2WB q_2 + ... + remainder, rounding with the
+// 1.5 * 2^23 addition trick on the FP32 pipes: |q_0| <= 2^(WB-1), and a later
+// word holds a rounding remainder (at most 1/2) plus the low part carried
+// along, |q_w| < 1.2 * 2^(WB-1); what the last word leaves out (its rounding
+// remainder and the low part dropped there) is below 0.6 * 2^-(NW-1)WB.  Word w of bin b
 // lives in a lane-private column (address (w s + b) C + copy), so the integer
 // atomic adds of a warp hit distinct banks; integer sums are exact and
 // independent of the order in which threads arrive.  WB is chosen on the host

@@ -1457,7 +1457,8 @@ int sketch_bin_copies(int basis, int s) {
 
 // Bits per fixed-point word so that no bin column can overflow: a column
 // receives at most ceil(rows_per_cta / copies) contributions of magnitude
-// <= 2^(wb-1), and the rounding trick needs wb <= 22.
+// below 1.2 * 2^(wb-1), so per * 2^(wb+1) < 2^31 (wb = 30 - log2 per) leaves
+// room, and the rounding trick needs wb <= 22.
 int sketch_word_bits(int rows_per_cta, int copies) {
   const long long per = (rows_per_cta + copies - 1) / copies + 1;
   int lg = 0;
