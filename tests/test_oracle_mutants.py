@@ -32,3 +32,15 @@ def test_planted_mistake_fails_a_pin(label):
     assert len(mut) == 1
     name, status, why = MS.run_one(mut[0])
     assert status == "killed", why
+
+
+def test_every_mutant_still_applies_to_the_oracle():
+    """Each planted edit's pattern occurs exactly once in the current oracle
+    source, so a later change to the oracle cannot silently retire a mutant
+    from the sweep."""
+    stale = []
+    for path, old, _new, label in MS.MUTANTS:
+        with open(os.path.join(MS.ROOT, path)) as fh:
+            if fh.read().count(old) != 1:
+                stale.append(label)
+    assert not stale, stale
